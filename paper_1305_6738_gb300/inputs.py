@@ -1,0 +1,105 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle runs.
+
+This module holds no arithmetic of the method (no sampling from the power law,
+no fitting, no KS).  It only defines the workload configurations -- which
+(alpha, xmin, n, replicates) cells to run, the batched-instance mix and the
+serving request stream -- and the rounded-lognormal alternative data used to
+check the power of the bootstrap test.  Power-law data sets themselves are
+drawn by the method's own sampler with stream tag 2 (test data).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+# stream tags of the Philox counter's last word
+PURPOSE_CUTOFFS = 0
+PURPOSE_BOOTSTRAP = 1
+PURPOSE_TESTDATA = 2
+
+QUANTILES = (0.90, 0.95, 0.99)
+
+
+@dataclass(frozen=True)
+class Cell:
+    alpha: float
+    xmin: int
+    n: int
+    replicates: int
+    cell_id: int
+
+
+def cutoff_cell_small() -> list[Cell]:
+    """Plain method, FP64: alpha = 2.5, xmin = 1, n = 100, 10,000 replicates."""
+    return [Cell(2.5, 1, 100, 10_000, 0)]
+
+
+SWEEP_ALPHAS = (1.5, 1.75, 2.0, 2.25, 2.5, 2.75, 3.0, 3.25, 3.5)
+SWEEP_NS = (10, 20, 50, 100, 200, 500, 1000, 2000, 5000, 10000)
+
+
+def cutoff_table_sweep(replicates: int = 100_000) -> list[Cell]:
+    """Cutoff-table sweep: 9 exponents x 10 sample sizes, xmin = 1; cell id =
+    10 * (exponent index) + (size index)."""
+    return [Cell(a, 1, n, replicates, 10 * i + j)
+            for i, a in enumerate(SWEEP_ALPHAS) for j, n in enumerate(SWEEP_NS)]
+
+
+def large_n_cell(replicates: int = 10_000) -> list[Cell]:
+    """Large-n heavy tail: alpha = 2.0, n = 1,000,000 per replicate."""
+    return [Cell(2.0, 1, 1_000_000, replicates, 0)]
+
+
+def batched_instances(count: int = 4096, replicates: int = 2000, seed: int = 2) -> list[Cell]:
+    """Uneven batch: n log-uniform in [10, 1e5] (rounded), alpha uniform in
+    [1.6, 3.2], xmin uniform over {1, 2, 5}; cell id = instance index."""
+    rng = np.random.default_rng(seed)
+    n = np.rint(np.exp(rng.uniform(np.log(10.0), np.log(1e5), count))).astype(np.int64)
+    alpha = rng.uniform(1.6, 3.2, count)
+    xmin = rng.choice(np.array([1, 2, 5]), count)
+    return [Cell(float(alpha[i]), int(xmin[i]), int(n[i]), replicates, i) for i in range(count)]
+
+
+@dataclass(frozen=True)
+class Request:
+    request_id: int
+    arrival_s: float
+    n: int
+    alpha: float          # exponent of the power-law data (unused when lognormal)
+    xmin: int
+    lognormal: bool
+
+
+def serving_requests(duration_s: float, rate_per_s: float = 200.0, seed: int = 4,
+                     n_lo: float = 50, n_hi: float = 1e6, lognormal_frac: float = 0.1
+                     ) -> list[Request]:
+    """Open-loop Poisson arrivals of fit requests: n log-uniform in [n_lo, n_hi],
+    alpha uniform in [1.5, 3.5], xmin = 1; a fraction carries rounded-lognormal
+    data instead of power-law data."""
+    rng = np.random.default_rng(seed)
+    out = []
+    t = 0.0
+    i = 0
+    while True:
+        t += rng.exponential(1.0 / rate_per_s)
+        if t > duration_s:
+            break
+        n = int(np.rint(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        out.append(Request(i, t, n, float(rng.uniform(1.5, 3.5)), 1,
+                           bool(rng.random() < lognormal_frac)))
+        i += 1
+    return out
+
+
+def rounded_lognormal(rng: np.random.Generator, n: int, mu: float = 2.0, sigma: float = 1.0,
+                      xmin: int = 1) -> np.ndarray:
+    """int32 data: exp(mu + sigma Z) rounded half to even; values below xmin redrawn."""
+    out = np.empty(n, dtype=np.int64)
+    filled = 0
+    while filled < n:
+        v = np.rint(np.exp(mu + sigma * rng.standard_normal(n - filled)))
+        v = v[(v >= xmin) & (v < 2**31 - 1)]
+        out[filled:filled + v.size] = v.astype(np.int64)
+        filled += v.size
+    return out.astype(np.int32)

@@ -1,0 +1,97 @@
+"""Pins for the oracle's Philox4x32-10 generator and the draw mapping.
+
+The generator is Philox4x32-10 of Salmon, Moraes, Dror & Shaw (SC'11).  It is
+pinned against (a) cuRAND's host-side Philox4_32_10 generator, an independent
+implementation whose output block b is the Philox block with counter
+(b div 65536, 0, b mod 65536, 0) and key = the 64-bit seed's halves, and
+(b) the published known-answer vectors of the Random123 distribution.
+"""
+import ctypes
+import ctypes.util
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+
+def _curand():
+    cands = ["/usr/local/cuda/lib64/libcurand.so", ctypes.util.find_library("curand")]
+    for c in cands:
+        if c and (os.path.exists(c) or not c.startswith("/")):
+            try:
+                return ctypes.CDLL(c)
+            except OSError:
+                pass
+    return None
+
+
+def _curand_host_words(lib, seed, count):
+    gen = ctypes.c_void_p()
+    philox = 161  # CURAND_RNG_PSEUDO_PHILOX4_32_10
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), philox) == 0
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        buf = (ctypes.c_uint * count)()
+        assert lib.curandGenerate(gen, buf, ctypes.c_size_t(count)) == 0
+        return np.array(buf, dtype=np.uint32)
+    finally:
+        lib.curandDestroyGenerator(gen)
+
+
+@pytest.mark.parametrize("seed", [1, 12345, 0x123456789ABCDEF0, 0xFFFFFFFFFFFFFFFF])
+def test_philox_matches_curand_host(seed):
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not available")
+    nblk = 65536 + 64
+    words = _curand_host_words(lib, seed, 4 * nblk)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    rng = np.random.default_rng(7)
+    blocks = list(range(16)) + list(rng.integers(0, nblk, 48)) + [65535, 65536, 65537, nblk - 1]
+    for b in blocks:
+        b = int(b)
+        got = oracle.philox4x32_10([b // 65536, 0, b % 65536, 0], key)
+        assert (got == words[4 * b:4 * b + 4]).all(), (seed, b)
+
+
+# Random123 known-answer vectors for philox4x32, 10 rounds: (counter, key, output).
+KAT = [
+    ([0, 0, 0, 0], [0, 0], [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
+    ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2, [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
+    ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
+     [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
+]
+
+
+@pytest.mark.parametrize("ctr,key,expected", KAT)
+def test_philox_known_answers(ctr, key, expected):
+    assert list(oracle.philox4x32_10(ctr, key)) == expected
+
+
+def test_draw_mapping_contract():
+    # draw i -> block (i>>1, rep, cell, purpose), words (2j, 2j+1), top 53 bits + 1
+    seed, cell, rep, purpose = 0xDEADBEEF12345678, 17, 99, 2
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i in [0, 1, 2, 3, 1001, 2**33 - 1]:
+        w = oracle.philox4x32_10([i >> 1, rep, cell, purpose], key)
+        j = i & 1
+        bits = (int(w[2 * j + 1]) << 32) | int(w[2 * j])
+        assert oracle.draw_m(seed, cell, rep, purpose, i) == (bits >> 11) + 1
+
+
+def test_draw_range_and_uniformity():
+    # m in [1, 2^53]; top 8 bits of (m-1) uniform (chi-square, 255 dof)
+    n = 200_000
+    ms = np.array([oracle.draw_m(1, 0, r, 0, i) for r in range(20) for i in range(n // 20)],
+                  dtype=np.uint64)
+    assert ms.min() >= 1 and ms.max() <= 2**53
+    top = ((ms - np.uint64(1)) >> np.uint64(45)).astype(np.int64)
+    counts = np.bincount(top, minlength=256)
+    exp = n / 256
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    # 255 dof: mean 255, sd ~22.6; 6 sd bound
+    assert chi2 < 255 + 6 * 22.6
+    # low bit of m is unbiased too
+    assert abs((ms & np.uint64(1)).mean() - 0.5) < 6 * 0.5 / np.sqrt(n)
