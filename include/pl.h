@@ -1,0 +1,160 @@
+/*
+ * pl.h -- C ABI of the GB300 (sm_103a) library for Monte Carlo
+ * Kolmogorov-Smirnov cutoffs of the discrete power law with a
+ * maximum-likelihood exponent (Rappos & Robert, "Using GPU Simulation to
+ * Accurately Fit to the Power-Law Distribution", 2013).
+ *
+ * The law (Eq. 1, with a lower end xmin; the paper's case is xmin = 1):
+ *     p(k) = k^-alpha / zeta(alpha, xmin),   k = xmin, xmin+1, ...,  alpha > 1.
+ * The fit (Eq. 2):   zeta'(alpha, xmin) / zeta(alpha, xmin) = -(1/n) sum ln x_i.
+ * The statistic (Eq. 3):   D = sup_x |F(x) - S(x)|, F the law at the fitted
+ * exponent, S the empirical CDF.
+ * Cutoffs (Section 3): quantiles of D over replicates simulated at (alpha, n).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Memory: the caller owns every buffer.  Pointers documented "device" must
+ *   be device (or managed) memory of the context's GPU; "host" pointers are
+ *   ordinary host memory.  The library allocates only its own workspace,
+ *   inside the byte budget given to pl_create, and returns PL_ENOMEM rather
+ *   than exceed it.
+ * - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   Work is stream ordered.  Entry points with a host output synchronise
+ *   that stream before returning; the others return once the work is
+ *   enqueued.  One context must not be used from two streams at once (its
+ *   workspace is shared); create one context per concurrent stream.
+ * - Errors: every entry point returns a pl_status; nothing throws or aborts
+ *   across the ABI.  pl_last_error gives a one-line description of the last
+ *   failure on that context.  Errors found on the device (a bounded wait that
+ *   ran out, bad data values) are latched in the context and reported by the
+ *   next pl_sync or by the next entry point with a host output.
+ * - Randomness: draw i of replicate r is a pure function of
+ *   (seed, cell_id, r, purpose, i) through Philox4x32-10 (counter
+ *   (i/2, r, cell_id, purpose), key = seed); results never depend on launch
+ *   shape, batching or precision form.  purpose: 0 = cutoff simulation,
+ *   1 = parametric bootstrap, 2 = test data.
+ * - Heavy tail: simulated values are uint64 and saturate at 2^62.
+ */
+#ifndef PL_H_
+#define PL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pl_ctx pl_ctx;
+
+typedef enum {
+  PL_OK = 0,
+  PL_EINVAL = 1,   /* an argument is out of its domain */
+  PL_ENOMEM = 2,   /* workspace would exceed the context's byte budget */
+  PL_ENOCONV = 3,  /* a Newton solve hit its iteration cap */
+  PL_ETIMEOUT = 4, /* a bounded device wait ran out */
+  PL_ECUDA = 5,    /* a CUDA runtime call failed */
+  PL_EBUSY = 6     /* reserved */
+} pl_status;
+
+typedef enum {
+  PL_FP64 = 0,      /* every floating-point step in binary64 */
+  PL_FP32_BULK = 1  /* log-sums, CDF prefix sums and D comparisons in binary32
+                       with compensated accumulation; Hurwitz zeta, Newton solve
+                       and normaliser stay binary64 */
+} pl_precision;
+
+/* One cell of a cutoff table: `replicates` samples of size n from the law at
+ * (alpha, xmin); cell_id (< 2^32) keys its random streams. */
+typedef struct {
+  double alpha;
+  uint64_t xmin;
+  int64_t n;
+  int64_t replicates;
+  uint64_t cell_id;
+} pl_cell;
+
+/* Create a context on CUDA device `device`; the library's workspace never
+ * exceeds mem_budget_bytes (0 = 40 GiB).  *out receives the context.
+ * Errors: PL_EINVAL (out NULL, bad device), PL_ECUDA. */
+pl_status pl_create(pl_ctx **out, int device, size_t mem_budget_bytes);
+
+/* Free the context and its workspace (synchronises the device first). */
+void pl_destroy(pl_ctx *ctx);
+
+/* Text of the last error on ctx ("" if none).  Owned by the context. */
+const char *pl_last_error(const pl_ctx *ctx);
+
+/* Synchronise `stream` and report device-side errors latched since the last
+ * report (PL_ETIMEOUT, PL_EINVAL for bad data values, PL_ECUDA). */
+pl_status pl_sync(pl_ctx *ctx, void *stream);
+
+/* Counters accumulated on the device since pl_create: Newton solves that hit
+ * the iteration cap, draws inverted in the FP64 tail beyond the threshold
+ * table, and replicates whose spill list was sorted in global memory.
+ * Synchronises `stream`.  Any output pointer may be NULL. */
+pl_status pl_counters(pl_ctx *ctx, void *stream, uint64_t *newton_capped,
+                      uint64_t *tail_draws, uint64_t *global_sorts);
+
+/* Draws from the law (Eq. 1 with lower end xmin) by inverse CDF: with
+ * v = m 2^-53 in (0, 1], X = min{k >= xmin : P(X > k) < v}.
+ * Writes nrep * n values, row r (replicate rep0 + r) at out_dev[r * n].
+ * out_dev: device, uint64[nrep * n].  Errors: PL_EINVAL (alpha <= 1,
+ * xmin < 1, n < 1, nrep < 1, cell_id >= 2^32, rep0 + nrep > 2^32,
+ * n > 2^33). */
+pl_status pl_sample(pl_ctx *ctx, double alpha, uint64_t xmin, uint64_t seed,
+                    uint64_t cell_id, uint32_t purpose, uint64_t rep0,
+                    int64_t nrep, int64_t n, uint64_t *out_dev, void *stream);
+
+/* Maximum-likelihood exponent of a data set (Eq. 2).  If every value equals
+ * xmin the log-sum is increased by ln((xmin+1)/xmin) (one point counted as
+ * xmin+1), as the paper's code does for xmin = 1.  x_dev: device, int32[n],
+ * every value >= xmin.  alpha_hat_host: host double.  Synchronises `stream`.
+ * Errors: PL_EINVAL (n < 1, xmin < 1, a value < xmin), PL_ENOCONV. */
+pl_status pl_fit_mle(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
+                     uint64_t xmin, double *alpha_hat_host, void *stream);
+
+/* KS distance (Eq. 3) between the empirical CDF of x and the law at
+ * exponent alpha (alpha > 1; pass the fitted exponent to use the paper's
+ * tables).  x_dev: device, int32[n], values >= xmin.  D_host: host double.
+ * Synchronises `stream`.  Errors: PL_EINVAL. */
+pl_status pl_ks_stat(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
+                     uint64_t xmin, double alpha, pl_precision prec,
+                     double *D_host, void *stream);
+
+/* Cutoff table (Section 3, Table 1): for every cell simulate `replicates`
+ * samples of size n at (alpha, xmin) (purpose 0), fit each by maximum
+ * likelihood, compute its D at the fitted exponent, and return the order
+ * statistics D_(i), i = floor(R q_j) (0-based, clamped to R-1), for the nq
+ * quantiles q_j in (0, 1).
+ * cells: host, pl_cell[ncells].  q: host, double[nq].
+ * cutoffs: device or host, double[ncells * nq] (row per cell); a host
+ *   pointer makes the call synchronise `stream`.
+ * D_dev_opt: NULL or device, per-replicate D of every cell concatenated in
+ *   cell order (double for PL_FP64, float for PL_FP32_BULK).
+ * alpha_hat_dev_opt: NULL or device double, per-replicate fitted exponents,
+ *   same layout.
+ * Errors: PL_EINVAL (ncells < 1, nq < 1, q outside (0,1), alpha <= 1,
+ * xmin < 1, n < 1, replicates < 1, cell_id >= 2^32), PL_ENOMEM. */
+pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells,
+                        uint64_t seed, const double *q, int nq,
+                        pl_precision prec, double *cutoffs, void *D_dev_opt,
+                        double *alpha_hat_dev_opt, void *stream);
+
+/* Goodness of fit of a data set (Section 3's use of the tables, with the
+ * bespoke cutoff computed by simulation): fit alpha-hat (Eq. 2), compute D
+ * (Eq. 3), simulate B data sets of the same size at alpha-hat (purpose 1,
+ * cell_id = request_id), refit each, and return p = #{D_b >= D} / B.
+ * x_dev: device int32[n] (values >= xmin).  alpha_hat, D, p: host doubles.
+ * Synchronises `stream`.  Errors: PL_EINVAL, PL_ENOMEM, PL_ENOCONV. */
+pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
+                              uint64_t xmin, int64_t B, uint64_t seed,
+                              uint64_t request_id, pl_precision prec,
+                              double *alpha_hat, double *D, double *p,
+                              void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PL_H_ */

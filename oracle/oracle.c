@@ -187,16 +187,18 @@ double or_survival(double alpha, double Z, uint64_t xmin, uint64_t k) {
  * whose cumulative probability reaches the uniform).  Reading: with v in
  * (0,1], X = min{k >= xmin : Q(k) < v}, which has P(X = k) = p(k) and uses
  * the survival function so that tail values keep full relative accuracy.
- * Plain exponential search then bisection on k; values beyond OR_XCAP
- * saturate at OR_XCAP. */
+ * Plain exponential search then bisection on k.  The result is
+ * min(OR_XCAP, that k): values beyond the cap saturate at OR_XCAP. */
 uint64_t or_invert(double alpha, double Z, uint64_t xmin, uint64_t m) {
   double v = ldexp((double)m, -53);
   uint64_t lo = xmin; /* answer >= lo: Q(lo - 1) >= v */
   uint64_t span = 1, hi;
+  if (lo >= OR_XCAP) return OR_XCAP;
   for (;;) {
     hi = lo + span - 1;
-    if (hi >= OR_XCAP) return OR_XCAP;
+    if (hi >= OR_XCAP) hi = OR_XCAP;
     if (or_survival(alpha, Z, xmin, hi) < v) break;
+    if (hi == OR_XCAP) return OR_XCAP; /* answer beyond the cap */
     lo = hi + 1;
     span *= 2;
   }
