@@ -1,0 +1,293 @@
+#!/usr/bin/env python3
+"""Benchmark of the KS cutoff-table sweep on GB300.
+
+Workload (one step = one pass of the whole path): the 90-cell table sweep,
+exponents {1.5, 1.75, ..., 3.5} x sample sizes {10, 20, 50, 100, 200, 500,
+1000, 2000, 5000, 10000}, xmin = 1, 100,000 replicates per cell: for every
+replicate n Philox draws through the inverse-CDF table, the histogram, the
+binary64 Newton fit, the KS distance, then the 90/95/99% order statistics
+per cell.  9,000,000 replicates and 1.6992e10 draws per step.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1305_6738_gb300 import inputs  # noqa: E402
+
+Q = [0.90, 0.95, 0.99]
+METRIC = "KS replicates/sec and samples/sec per (alpha,n) vs roofline; p50/p99 fit-request latency"
+
+# Algorithmic work per unit (the per-unit figures of the work model):
+# one draw = half a Philox4x32-10 block = 10 rounds x 2 32x32->64-bit multiplies
+# (20 IMAD-class ops) + ~20 XOR/ADD ops  ->  40 INT32 ops per draw.
+INT_OPS_PER_DRAW = 40
+# INT32 lanes per SM per clock assumed for the peak (4 SM sub-partitions x 16
+# lanes for 32-bit integer multiply-add, add and logic ops).
+INT32_LANES_PER_SM = 64
+
+# DRAM traffic of the replicate kernel from one ncu capture, keyed by the hash
+# of the kernel sources it was taken on (reported as null once they change).
+TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ["pl_device.cuh", "pl_kernels.cu"]:
+        with open(os.path.join(ROOT, "paper_1305_6738_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                       "-lms", "200", "-i", gpu_id], stdout=self.tmp,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.strip().split(", ") for r in self.tmp.read().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1].split()[0]))
+                smax.append(float(r[2].split()[0]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_query_id(device: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if device < len(ids):
+            return ids[device]
+    return str(device)
+
+
+# ----------------------------------------------------------------------------- cpu
+def cpu_oracle_rate(sample_reps: int, threads: int) -> dict:
+    """The oracle as it stands, on sample_reps replicates of every cell, timed
+    per cell and extrapolated linearly to the full replicate count."""
+    import oracle
+    oracle.build()
+    sweep = inputs.cutoff_table_sweep()
+    t_full = 0.0
+    wall = 0.0
+    for c in sweep:
+        t0 = time.perf_counter()
+        oracle.cell(c.alpha, c.xmin, c.n, sample_reps, seed=1, cell_id=c.cell_id, threads=threads)
+        dt = time.perf_counter() - t0
+        wall += dt
+        t_full += dt / sample_reps * c.replicates
+    total_R = sum(c.replicates for c in sweep)
+    draws = sum(c.replicates * c.n for c in sweep)
+    return {"value": total_R / t_full, "samples_per_s": draws / t_full, "wall_s": wall,
+            "sample": f"{sample_reps} replicates of each of the 90 cells (draws, fit, KS, seed 1), "
+                      f"timed per cell and extrapolated linearly to 100,000 replicates per cell"}
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32-bulk", "fp64"], default="fp32-bulk")
+    ap.add_argument("--cpu-sample", type=int, default=64, help="replicates per cell for the CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--replicates", type=int, default=100_000,
+                    help="replicates per cell (smaller values for profiler captures only)")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    sweep = inputs.cutoff_table_sweep(args.replicates)
+    total_R = sum(c.replicates for c in sweep)
+    draws = sum(c.replicates * c.n for c in sweep)
+    config = {"workload": "KS cutoff-table sweep: alpha in {1.5,...,3.5} (9) x n in {10,...,10000} (10), "
+                          f"xmin=1, {args.replicates:,} replicates per cell",
+              "cells": len(sweep), "replicates_per_step": total_R, "draws_per_step": draws,
+              "precision_form": args.precision, "seed": 1, "quantiles": Q,
+              "l2": "256 MiB buffer written between timed steps (L2 flush)",
+              "parallelism": f"replicas x{args.gpus}"}
+    threads = os.cpu_count() or 1
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        samp = max(1, args.cpu_sample // 4)
+        for _ in range(args.warmup):
+            cpu_oracle_rate(1, threads)
+        vals = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = cpu_oracle_rate(samp, threads)
+            vals.append(r)
+        wall = time.perf_counter() - t0
+        value = statistics.mean(v["value"] for v in vals)
+        sps = statistics.mean(v["samples_per_s"] for v in vals)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "replicates/s",
+                "samples_per_s": sps, "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000.0 * total_R / value, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox streams, seed 1)",
+                "config": config,
+                "cpu_baseline": {"value": value, "unit": "replicates/s", "cores": threads, "kind": "oracle",
+                                 "sample": vals[0]["sample"]},
+                "e2e": {"value": value, "unit": "replicates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0},
+                "wall_s": wall}
+        print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1305_6738_gb300 import pl
+    ctx = pl.Context(local)
+    prec = pl.PL_FP32_BULK if args.precision == "fp32-bulk" else pl.PL_FP64
+    seed = 1 + rank
+    cells = [pl.Cell(c.alpha, c.xmin, c.n, c.replicates, c.cell_id) for c in sweep]
+    cut = torch.empty(len(cells) * len(Q), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx.pl_set_tracing(True)
+    for _ in range(args.warmup):
+        ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=cut)
+    ctx.pl_sync()
+    launches0 = ctx.pl_trace()["launches"]
+
+    sampler = ClockSampler(gpu_query_id(local))
+    barrier()
+    step_ms, kern_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=cut)
+        e1.record(stream)
+        tr = ctx.pl_trace()  # synchronises; kernel time from events on the call's stream
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(tr["replicate_ms"])
+    barrier()
+    clocks = sampler.stop()
+    launches = ctx.pl_trace()["launches"] - launches0
+    ctx.pl_sync()
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * total_R * args.steps / (total_ms / 1000.0)
+    sps = world * draws * args.steps / (total_ms / 1000.0)
+
+    # end to end through the public call with host buffers: host cell table in,
+    # host cutoffs out (the call copies and synchronises), wall clock
+    e2e_s = []
+    host_cut = np.zeros(len(cells) * len(Q))
+    for _ in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=host_cut)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_value = world * total_R / statistics.mean(e2e_s)
+    h2d = len(cells) * 40 + len(Q) * 8
+    d2h = host_cut.nbytes
+
+    # roofline of the replicate kernel (INT32 issue bound)
+    props = torch.cuda.get_device_properties(local)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    int_peak = props.multi_processor_count * INT32_LANES_PER_SM * sm_max * 1e6 / 1e9  # Gop/s
+    kmean = statistics.mean(kern_ms)
+    achieved = INT_OPS_PER_DRAW * draws / (kmean / 1000.0) / 1e9
+    h = kernel_source_hash()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": int_peak, "unit": "Gop/s (INT32)",
+                "frac": achieved / int_peak, "traffic": TRAFFIC.get(h),
+                "kernel": "replicate_warp_kernel", "kernel_ms": kmean,
+                "peak_basis": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} INT32 lanes x "
+                              f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "replicates/s", "samples_per_s": sps,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == pl.PL_FP32_BULK else "f64",
+            "data": "synthetic (Philox streams, seed 1)", "config": config,
+            "e2e": {"value": e2e_value, "unit": "replicates/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_oracle_rate(args.cpu_sample, threads)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": "replicates/s", "cores": threads,
+                                "kind": "oracle", "sample": cb["sample"],
+                                "samples_per_s": cb["samples_per_s"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -96,6 +96,22 @@ pl_status pl_sync(pl_ctx *ctx, void *stream);
 pl_status pl_counters(pl_ctx *ctx, void *stream, uint64_t *newton_capped,
                       uint64_t *tail_draws, uint64_t *global_sorts);
 
+/* Tracing (no counterpart in the paper, which times whole runs with clock()).
+ * With tracing on, pl_ks_cutoffs and pl_bootstrap_pvalue record CUDA events
+ * on their stream around each phase; pl_trace synchronises `stream` and
+ * returns the durations of the last traced call and the number of kernels
+ * this context has launched since pl_create. */
+typedef struct {
+  uint64_t launches;   /* kernels launched by this context */
+  float law_ms;        /* last traced call: law-table set-up kernels */
+  float replicate_ms;  /* last traced call: the replicate kernel */
+  float select_ms;     /* last traced call: quantile selection / p count */
+  float total_ms;      /* last traced call: first to last phase */
+} pl_trace_info;
+
+pl_status pl_set_tracing(pl_ctx *ctx, int on);
+pl_status pl_trace(pl_ctx *ctx, void *stream, pl_trace_info *out);
+
 /* Draws from the law (Eq. 1 with lower end xmin) by inverse CDF: with
  * v = m 2^-53 in (0, 1], X = min{k >= xmin : P(X > k) < v}.
  * Writes nrep * n values, row r (replicate rep0 + r) at out_dev[r * n].

@@ -1,0 +1,580 @@
+// pl_api.cu -- host runtime behind the C ABI of include/pl.h.
+//
+// A context owns one device workspace inside a byte budget and a block of
+// device counters.  Each call plans its buffers, grows the workspace if the
+// plan needs it (never past the budget), stages its small host tables, sets
+// up the law tables on the device, launches the kernels and, for host
+// outputs, copies back and synchronises.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "pl.h"
+#include "pl_kernels.cuh"
+
+using namespace pl;
+
+struct pl_ctx {
+  int device = 0;
+  size_t budget = 0;
+  std::string err;
+  uint8_t *ws = nullptr;
+  size_t ws_size = 0;
+  Counters *ctr = nullptr;
+  int num_sms = 0;
+  int warp_blocks_per_sm[2] = {0, 0};
+  uint64_t launches = 0;
+  bool tracing = false;
+  bool traced = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+constexpr int64_t kWarpNMax = 16384;  // warp form: n per replicate up to this
+
+pl_status fail(pl_ctx *ctx, pl_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  return s;
+}
+
+#define PL_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(ctx, PL_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Workspace carving: the same sequence of take() calls sizes the plan (base
+// null) and then hands out pointers.
+struct Carver {
+  uint8_t *base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T *take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T *p = reinterpret_cast<T *>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+pl_status ensure_ws(pl_ctx *ctx, size_t bytes) {
+  if (bytes > ctx->budget)
+    return fail(ctx, PL_ENOMEM, "workspace of %zu bytes exceeds the budget of %zu", bytes, ctx->budget);
+  if (bytes <= ctx->ws_size) return PL_OK;
+  size_t want = std::min(ctx->budget, std::max(bytes, ctx->ws_size + ctx->ws_size / 2));
+  PL_CUDA(cudaDeviceSynchronize());
+  if (ctx->ws) PL_CUDA(cudaFree(ctx->ws));
+  ctx->ws = nullptr;
+  ctx->ws_size = 0;
+  PL_CUDA(cudaMalloc(&ctx->ws, want));
+  ctx->ws_size = want;
+  return PL_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Length of the inverse-CDF table: the smallest kL1 * 2^k whose last entry
+// leaves at most 1e-6 of the mass (or ~1000 expected draws) beyond it, at most
+// 2^20.  Sizing only: uses the continuous tail approximation.
+uint32_t table_length(double alpha, uint64_t xmin, double draws) {
+  const double x = (double)xmin;
+  const double Zapprox = std::pow(x, -alpha) + std::pow(x + 0.5, 1.0 - alpha) / (alpha - 1.0);
+  const double target = std::max(1e-6, draws > 0 ? 1000.0 / draws : 0.0);
+  uint32_t L = kL1;
+  while (L < (1u << 20)) {
+    const double Q = std::pow(x + L - 0.5, 1.0 - alpha) / ((alpha - 1.0) * Zapprox);
+    if (Q <= target) break;
+    L <<= 1;
+  }
+  return L;
+}
+
+struct LawPlan {
+  double alpha;
+  uint64_t xmin;
+  uint32_t L2;
+};
+
+// Allocate (or size, with a null carver base) one law's tables.
+Law carve_law(Carver &cv, const LawPlan &lp) {
+  Law l{};
+  l.alpha = lp.alpha;
+  l.xmin = lp.xmin;
+  l.L2 = lp.L2;
+  l.T = cv.take<uint64_t>(lp.L2);
+  l.guide = cv.take<uint32_t>(kGuide);
+  l.lnT = cv.take<double>(kLnTable);
+  l.lnT_hi = cv.take<float>(kLnTable);
+  l.lnT_lo = cv.take<float>(kLnTable);
+  return l;
+}
+
+CellConst cell_const(uint64_t xmin) {
+  CellConst c;
+  c.ln_xmin_half = std::log((double)xmin - 0.5);
+  c.ln_allmin = std::log1p(1.0 / (double)xmin);
+  return c;
+}
+
+uint32_t hist_bins(int64_t n) {
+  int64_t H = 32;
+  while (H < 2 * n && H < kHMax) H <<= 1;
+  return (uint32_t)H;
+}
+
+uint64_t next_pow2(uint64_t v) {
+  uint64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Everything one batch of replicate cells needs on the device.
+struct SimPlan {
+  std::vector<LawPlan> laws;
+  std::vector<Cell> cells;
+  std::vector<CellConst> consts;
+  std::vector<WorkItem> items;
+  int64_t total_R = 0;
+  int64_t n_max = 0;
+};
+
+pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpose, SimPlan &sp) {
+  std::map<std::pair<double, uint64_t>, uint32_t> law_of;
+  std::vector<double> law_draws;
+  sp.cells.resize(ncells);
+  sp.consts.resize(ncells);
+  for (int c = 0; c < ncells; ++c) {
+    const pl_cell &x = in[c];
+    if (!(x.alpha > 1.0) || !std::isfinite(x.alpha) || x.alpha > 64.0)
+      return fail(ctx, PL_EINVAL, "cell %d: alpha must be in (1, 64]", c);
+    if (x.xmin < 1 || x.xmin > (1ull << 40)) return fail(ctx, PL_EINVAL, "cell %d: xmin out of range", c);
+    if (x.n < 1) return fail(ctx, PL_EINVAL, "cell %d: n < 1", c);
+    if (x.n > kWarpNMax)
+      return fail(ctx, PL_EINVAL, "cell %d: n = %lld exceeds %lld", c, (long long)x.n, (long long)kWarpNMax);
+    if (x.replicates < 1 || x.replicates > (1ll << 31)) return fail(ctx, PL_EINVAL, "cell %d: replicates", c);
+    if (x.cell_id >= (1ull << 32)) return fail(ctx, PL_EINVAL, "cell %d: cell_id >= 2^32", c);
+    const auto key = std::make_pair(x.alpha, x.xmin);
+    auto it = law_of.find(key);
+    uint32_t li;
+    if (it == law_of.end()) {
+      li = (uint32_t)sp.laws.size();
+      law_of[key] = li;
+      sp.laws.push_back({x.alpha, x.xmin, 0});
+      law_draws.push_back(0.0);
+    } else {
+      li = it->second;
+    }
+    law_draws[li] += (double)x.n * (double)x.replicates;
+    Cell &cd = sp.cells[c];
+    cd.alpha = x.alpha;
+    cd.xmin = x.xmin;
+    cd.n = x.n;
+    cd.R = x.replicates;
+    cd.cell_id = (uint32_t)x.cell_id;
+    cd.law = li;
+    cd.H = hist_bins(x.n);
+    cd.purpose = purpose;
+    cd.out_off = sp.total_R;
+    sp.total_R += x.replicates;
+    sp.n_max = std::max(sp.n_max, x.n);
+    sp.consts[c] = cell_const(x.xmin);
+  }
+  for (size_t l = 0; l < sp.laws.size(); ++l)
+    sp.laws[l].L2 = table_length(sp.laws[l].alpha, sp.laws[l].xmin, law_draws[l]);
+  // work items: cells grouped by law (the block keeps a law's table staged),
+  // larger n first within a law
+  std::vector<int> order(ncells);
+  for (int c = 0; c < ncells; ++c) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (sp.cells[a].law != sp.cells[b].law) return sp.cells[a].law < sp.cells[b].law;
+    return sp.cells[a].n > sp.cells[b].n;
+  });
+  const int64_t per_item = (int64_t)kWarps * 32;
+  for (int c : order)
+    for (int64_t r0 = 0; r0 < sp.cells[c].R; r0 += per_item) sp.items.push_back({(uint32_t)c, (uint32_t)r0});
+  return PL_OK;
+}
+
+struct SimBuffers {
+  Law *laws_dev;
+  std::vector<Law> laws_host;
+  Cell *cells;
+  CellConst *consts;
+  WorkItem *items;
+  uint8_t *scratch;
+  size_t spill_cap, arena_bytes;
+  int blocks;
+};
+
+// Lay out (or size) the device buffers of a simulation plan.
+void carve_sim(Carver &cv, const SimPlan &sp, int blocks, SimBuffers &b) {
+  b.laws_host.clear();
+  for (const auto &lp : sp.laws) b.laws_host.push_back(carve_law(cv, lp));
+  b.laws_dev = cv.take<Law>(sp.laws.size());
+  b.cells = cv.take<Cell>(sp.cells.size());
+  b.consts = cv.take<CellConst>(sp.consts.size());
+  b.items = cv.take<WorkItem>(sp.items.size());
+  b.spill_cap = next_pow2((uint64_t)std::max<int64_t>(sp.n_max, kSortSmem));
+  b.arena_bytes = (((size_t)kHMax * 4 + 16 * (size_t)sp.n_max + 16) + (size_t)32 * kHMax * 4 + 255) & ~(size_t)255;
+  b.blocks = blocks;
+  b.scratch = cv.take<uint8_t>((size_t)blocks * kWarps * (b.spill_cap * 8 + b.arena_bytes));
+}
+
+pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t st) {
+  PL_CUDA(cudaMemcpyAsync(b.laws_dev, b.laws_host.data(), sizeof(Law) * b.laws_host.size(),
+                          cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(b.cells, sp.cells.data(), sizeof(Cell) * sp.cells.size(), cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(b.consts, sp.consts.data(), sizeof(CellConst) * sp.consts.size(),
+                          cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(b.items, sp.items.data(), sizeof(WorkItem) * sp.items.size(),
+                          cudaMemcpyHostToDevice, st));
+  PL_CUDA(launch_law_setup(b.laws_dev, (int)b.laws_host.size(), st));
+  ctx->launches += 3;
+  return PL_OK;
+}
+
+pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, bool f32, void *D,
+                  double *A, cudaStream_t st) {
+  PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
+  WarpLaunch wl{};
+  wl.cells = b.cells;
+  wl.consts = b.consts;
+  wl.laws = b.laws_dev;
+  wl.items = b.items;
+  wl.nitems = (uint32_t)sp.items.size();
+  wl.seed = seed;
+  wl.D_out = D;
+  wl.A_out = A;
+  wl.scratch = b.scratch;
+  wl.spill_cap = b.spill_cap;
+  wl.arena_bytes = b.arena_bytes;
+  wl.ctr = ctx->ctr;
+  wl.blocks = b.blocks;
+  PL_CUDA(launch_replicates_warp(wl, f32, st));
+  ctx->launches += 1;
+  return PL_OK;
+}
+
+int sim_blocks(pl_ctx *ctx, bool f32, size_t nitems) {
+  const int per_sm = std::max(1, ctx->warp_blocks_per_sm[f32 ? 1 : 0]);
+  return (int)std::max<size_t>(1, std::min<size_t>((size_t)ctx->num_sms * per_sm, nitems));
+}
+
+pl_status mark(pl_ctx *ctx, int i, cudaStream_t st) {
+  if (!ctx->tracing) return PL_OK;
+  PL_CUDA(cudaEventRecord(ctx->ev[i], st));
+  if (i == 3) ctx->traced = true;
+  return PL_OK;
+}
+
+pl_status check_ctx(pl_ctx *ctx) {
+  if (!ctx) return PL_EINVAL;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, PL_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  return PL_OK;
+}
+
+pl_status read_status(pl_ctx *ctx, cudaStream_t st) {
+  PL_CUDA(cudaStreamSynchronize(st));
+  unsigned int status = 0;
+  PL_CUDA(cudaMemcpy(&status, &ctx->ctr->status, sizeof status, cudaMemcpyDeviceToHost));
+  if (status) {
+    PL_CUDA(cudaMemset(&ctx->ctr->status, 0, sizeof status));
+    if (status & kErrTimeout) return fail(ctx, PL_ETIMEOUT, "a bounded device wait ran out");
+    if (status & kErrData) return fail(ctx, PL_EINVAL, "a data value is below xmin (or below 1)");
+    if (status & kErrArena) return fail(ctx, PL_ECUDA, "internal: replicate arena too small");
+  }
+  return PL_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+pl_status pl_create(pl_ctx **out, int device, size_t mem_budget_bytes) {
+  if (!out) return PL_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return PL_EINVAL;
+  pl_ctx *ctx = new pl_ctx();
+  ctx->device = device;
+  ctx->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)40 << 30;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&ctx->ctr, sizeof(Counters)) != cudaSuccess ||
+      cudaMemset(ctx->ctr, 0, sizeof(Counters)) != cudaSuccess) {
+    if (ctx->ctr) cudaFree(ctx->ctr);
+    delete ctx;
+    return PL_ECUDA;
+  }
+  ctx->warp_blocks_per_sm[0] = warp_kernel_blocks_per_sm(false);
+  ctx->warp_blocks_per_sm[1] = warp_kernel_blocks_per_sm(true);
+  cudaGetLastError();
+  *out = ctx;
+  return PL_OK;
+}
+
+void pl_destroy(pl_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto &e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->ctr) cudaFree(ctx->ctr);
+  delete ctx;
+}
+
+const char *pl_last_error(const pl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+pl_status pl_set_tracing(pl_ctx *ctx, int on) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (on && !ctx->ev[0])
+    for (auto &e : ctx->ev) PL_CUDA(cudaEventCreate(&e));
+  ctx->tracing = on != 0;
+  ctx->traced = false;
+  return PL_OK;
+}
+
+pl_status pl_trace(pl_ctx *ctx, void *stream, pl_trace_info *out) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(ctx, PL_EINVAL, "pl_trace: null output");
+  PL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  *out = pl_trace_info{};
+  out->launches = ctx->launches;
+  if (ctx->traced) {
+    PL_CUDA(cudaEventElapsedTime(&out->law_ms, ctx->ev[0], ctx->ev[1]));
+    PL_CUDA(cudaEventElapsedTime(&out->replicate_ms, ctx->ev[1], ctx->ev[2]));
+    PL_CUDA(cudaEventElapsedTime(&out->select_ms, ctx->ev[2], ctx->ev[3]));
+    PL_CUDA(cudaEventElapsedTime(&out->total_ms, ctx->ev[0], ctx->ev[3]));
+  }
+  return PL_OK;
+}
+
+pl_status pl_sync(pl_ctx *ctx, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  return read_status(ctx, (cudaStream_t)stream);
+}
+
+pl_status pl_counters(pl_ctx *ctx, void *stream, uint64_t *newton_capped, uint64_t *tail_draws,
+                      uint64_t *global_sorts) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  PL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  Counters c{};
+  PL_CUDA(cudaMemcpy(&c, ctx->ctr, sizeof c, cudaMemcpyDeviceToHost));
+  if (newton_capped) *newton_capped = c.newton_capped;
+  if (tail_draws) *tail_draws = c.tail_draws;
+  if (global_sorts) *global_sorts = c.global_sorts;
+  return PL_OK;
+}
+
+pl_status pl_sample(pl_ctx *ctx, double alpha, uint64_t xmin, uint64_t seed, uint64_t cell_id,
+                    uint32_t purpose, uint64_t rep0, int64_t nrep, int64_t n, uint64_t *out_dev,
+                    void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!(alpha > 1.0) || alpha > 64.0 || xmin < 1 || xmin > (1ull << 40) || n < 1 || nrep < 1 ||
+      cell_id >= (1ull << 32) || rep0 + (uint64_t)nrep > (1ull << 32) || n > (1ll << 33) || !out_dev)
+    return fail(ctx, PL_EINVAL, "pl_sample: argument out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  LawPlan lp{alpha, xmin, table_length(alpha, xmin, (double)n * (double)nrep)};
+  Carver cv;
+  Law lh = carve_law(cv, lp);
+  Law *ld = cv.take<Law>(1);
+  if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+  cv.base = ctx->ws;
+  cv.off = 0;
+  lh = carve_law(cv, lp);
+  ld = cv.take<Law>(1);
+  PL_CUDA(cudaMemcpyAsync(ld, &lh, sizeof lh, cudaMemcpyHostToDevice, st));
+  PL_CUDA(launch_law_setup(ld, 1, st));
+  ctx->launches += 4;
+  PL_CUDA(launch_sample(ld, seed, (uint32_t)cell_id, purpose, (uint32_t)rep0, nrep, n, out_dev, ctx->ctr,
+                        ctx->num_sms, st));
+  return PL_OK;
+}
+
+// ---------------------------------------------------------------------------
+namespace {
+pl_status run_dataset(pl_ctx *ctx, const int32_t *x, int64_t n, uint64_t xmin, bool fit, double alpha,
+                      pl_precision prec, double out_host[3], cudaStream_t st, Carver *keep = nullptr) {
+  if (!x || n < 1 || xmin < 1 || xmin > (1ull << 31)) return fail(ctx, PL_EINVAL, "data set: bad arguments");
+  if (!fit && (!(alpha > 1.0) || alpha > 64.0)) return fail(ctx, PL_EINVAL, "alpha must be in (1, 64]");
+  LawPlan lp{fit ? 2.0 : alpha, xmin, kL1};
+  const uint64_t cap = next_pow2((uint64_t)n);
+  auto lay = [&](Carver &cv, Law &lh, Law *&ld, uint64_t *&spill, uint64_t *&pairs, double *&out) {
+    lh = carve_law(cv, lp);
+    ld = cv.take<Law>(1);
+    spill = cv.take<uint64_t>(cap);
+    pairs = cv.take<uint64_t>(2 * (size_t)n);
+    out = cv.take<double>(4);
+  };
+  Carver cv;
+  Law lh;
+  Law *ld;
+  uint64_t *spill, *pairs;
+  double *out;
+  lay(cv, lh, ld, spill, pairs, out);
+  if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+  cv.base = ctx->ws;
+  cv.off = 0;
+  lay(cv, lh, ld, spill, pairs, out);
+  PL_CUDA(cudaMemcpyAsync(ld, &lh, sizeof lh, cudaMemcpyHostToDevice, st));
+  PL_CUDA(launch_law_setup(ld, 1, st));
+  ctx->launches += 4;
+  PL_CUDA(launch_dataset(x, n, xmin, fit, alpha, ld, cell_const(xmin), prec == PL_FP32_BULK, spill, pairs, out,
+                         ctx->ctr, st));
+  PL_CUDA(cudaMemcpyAsync(out_host, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (keep) *keep = cv;
+  return read_status(ctx, st);
+}
+}  // namespace
+
+pl_status pl_fit_mle(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint64_t xmin, double *alpha_hat_host,
+                     void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!alpha_hat_host) return fail(ctx, PL_EINVAL, "pl_fit_mle: null output");
+  double o[3];
+  if (pl_status s = run_dataset(ctx, x_dev, n, xmin, true, 0.0, PL_FP64, o, (cudaStream_t)stream)) return s;
+  *alpha_hat_host = o[0];
+  return PL_OK;
+}
+
+pl_status pl_ks_stat(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint64_t xmin, double alpha,
+                     pl_precision prec, double *D_host, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!D_host) return fail(ctx, PL_EINVAL, "pl_ks_stat: null output");
+  double o[3];
+  if (pl_status s = run_dataset(ctx, x_dev, n, xmin, false, alpha, prec, o, (cudaStream_t)stream)) return s;
+  *D_host = o[1];
+  return PL_OK;
+}
+
+pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells, uint64_t seed, const double *q, int nq,
+                        pl_precision prec, double *cutoffs, void *D_dev_opt, double *alpha_hat_dev_opt,
+                        void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!cells || ncells < 1 || !q || nq < 1 || !cutoffs) return fail(ctx, PL_EINVAL, "pl_ks_cutoffs: bad arguments");
+  if (prec != PL_FP64 && prec != PL_FP32_BULK) return fail(ctx, PL_EINVAL, "unknown precision form");
+  for (int j = 0; j < nq; ++j)
+    if (!(q[j] > 0.0 && q[j] < 1.0)) return fail(ctx, PL_EINVAL, "quantile %d outside (0, 1)", j);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f32 = prec == PL_FP32_BULK;
+  SimPlan sp;
+  if (pl_status s = plan_cells(ctx, cells, ncells, 0u, sp)) return s;
+  const bool host_out = !is_device_ptr(cutoffs);
+  const size_t dsz = f32 ? 4 : 8;
+  const int blocks = sim_blocks(ctx, f32, sp.items.size());
+  auto lay = [&](Carver &cv, SimBuffers &b, void *&D, int64_t *&off, int64_t *&Rs, int64_t *&rank, double *&cut) {
+    carve_sim(cv, sp, blocks, b);
+    D = D_dev_opt ? D_dev_opt : (void *)cv.take<uint8_t>((size_t)sp.total_R * dsz);
+    off = cv.take<int64_t>(ncells);
+    Rs = cv.take<int64_t>(ncells);
+    rank = cv.take<int64_t>((size_t)ncells * nq);
+    cut = host_out ? cv.take<double>((size_t)ncells * nq) : cutoffs;
+  };
+  Carver cv;
+  SimBuffers b;
+  void *D;
+  int64_t *off, *Rs, *rank;
+  double *cut;
+  lay(cv, b, D, off, Rs, rank, cut);
+  if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+  cv.base = ctx->ws;
+  cv.off = 0;
+  lay(cv, b, D, off, Rs, rank, cut);
+  if (pl_status s = mark(ctx, 0, st)) return s;
+  if (pl_status s = upload_sim(ctx, sp, b, st)) return s;
+  std::vector<int64_t> h_off(ncells), h_R(ncells), h_rank((size_t)ncells * nq);
+  for (int c = 0; c < ncells; ++c) {
+    h_off[c] = sp.cells[c].out_off;
+    h_R[c] = sp.cells[c].R;
+    for (int j = 0; j < nq; ++j) {
+      int64_t i = (int64_t)std::floor((double)h_R[c] * q[j]);
+      h_rank[(size_t)c * nq + j] = std::min(std::max<int64_t>(i, 0), h_R[c] - 1);
+    }
+  }
+  PL_CUDA(cudaMemcpyAsync(off, h_off.data(), sizeof(int64_t) * ncells, cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(Rs, h_R.data(), sizeof(int64_t) * ncells, cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(rank, h_rank.data(), sizeof(int64_t) * h_rank.size(), cudaMemcpyHostToDevice, st));
+  if (pl_status s = mark(ctx, 1, st)) return s;
+  if (pl_status s = run_sim(ctx, sp, b, seed, f32, D, alpha_hat_dev_opt, st)) return s;
+  if (pl_status s = mark(ctx, 2, st)) return s;
+  PL_CUDA(launch_select(D, f32, off, Rs, rank, ncells, nq, cut, st));
+  ctx->launches += 1;
+  if (pl_status s = mark(ctx, 3, st)) return s;
+  if (host_out) {
+    PL_CUDA(cudaMemcpyAsync(cutoffs, cut, sizeof(double) * ncells * nq, cudaMemcpyDeviceToHost, st));
+    return read_status(ctx, st);
+  }
+  return PL_OK;
+}
+
+pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint64_t xmin, int64_t B,
+                              uint64_t seed, uint64_t request_id, pl_precision prec, double *alpha_hat,
+                              double *D, double *p, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (B < 1 || B > (1ll << 31) || request_id >= (1ull << 32) || !alpha_hat || !D || !p)
+    return fail(ctx, PL_EINVAL, "pl_bootstrap_pvalue: bad arguments");
+  if (prec != PL_FP64 && prec != PL_FP32_BULK) return fail(ctx, PL_EINVAL, "unknown precision form");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f32 = prec == PL_FP32_BULK;
+  double obs[3];
+  if (pl_status s = run_dataset(ctx, x_dev, n, xmin, true, 0.0, prec, obs, st)) return s;
+  pl_cell cell{obs[0], xmin, n, B, request_id};
+  SimPlan sp;
+  if (pl_status s = plan_cells(ctx, &cell, 1, 1u, sp)) return s;
+  const int blocks = sim_blocks(ctx, f32, sp.items.size());
+  auto lay = [&](Carver &cv, SimBuffers &b, void *&Db, double *&dobs, double *&pd) {
+    carve_sim(cv, sp, blocks, b);
+    Db = cv.take<uint8_t>((size_t)B * (f32 ? 4 : 8));
+    dobs = cv.take<double>(1);
+    pd = cv.take<double>(1);
+  };
+  Carver cv;
+  SimBuffers b;
+  void *Db;
+  double *dobs, *pd;
+  lay(cv, b, Db, dobs, pd);
+  if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+  cv.base = ctx->ws;
+  cv.off = 0;
+  lay(cv, b, Db, dobs, pd);
+  PL_CUDA(cudaMemcpyAsync(dobs, &obs[1], sizeof(double), cudaMemcpyHostToDevice, st));
+  if (pl_status s = mark(ctx, 0, st)) return s;
+  if (pl_status s = upload_sim(ctx, sp, b, st)) return s;
+  if (pl_status s = mark(ctx, 1, st)) return s;
+  if (pl_status s = run_sim(ctx, sp, b, seed, f32, Db, nullptr, st)) return s;
+  if (pl_status s = mark(ctx, 2, st)) return s;
+  PL_CUDA(launch_count_ge(Db, f32, B, dobs, pd, st));
+  ctx->launches += 1;
+  if (pl_status s = mark(ctx, 3, st)) return s;
+  double ph = 0.0;
+  PL_CUDA(cudaMemcpyAsync(&ph, pd, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (pl_status s = read_status(ctx, st)) return s;
+  *alpha_hat = obs[0];
+  *D = obs[1];
+  *p = ph;
+  return PL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,407 @@
+// pl_device.cuh -- device building blocks of the sm_103a KS-cutoff kernels.
+//
+// Philox4x32-10 streams, the Hurwitz zeta by Euler-Maclaurin (binary64 with
+// s-derivatives, binary32 for the bulk KS tail), the integer threshold table
+// that inverts the CDF of the law p(k) = k^-alpha / zeta(alpha, xmin)
+// (Eq. 1 with a lower end xmin), the FP64 tail inversion beyond the table,
+// and warp-level scans and sorts.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pl {
+
+// ---------------------------------------------------------------------------
+// Sizes of the on-chip structures.
+constexpr uint64_t kXCap = 1ull << 62;      // simulated values saturate here
+constexpr int kL1 = 2048;                   // thresholds staged in shared memory
+constexpr int kGuideBits = 11;              // guide table: 2^11 buckets of m
+constexpr int kGuide = 1 << kGuideBits;
+constexpr int kHMax = 1024;                 // dense histogram bins per warp
+constexpr int kWarps = 8;                   // warps per block, warp form
+constexpr int kSortSmem = kHMax / 2;        // spills sorted on chip up to this count
+constexpr int kLnTable = 16384;             // ln(xmin + i) tables, i < kLnTable
+constexpr int kNewtonCap = 200;             // Newton iteration cap
+
+// Device status word bits (latched; read by pl_sync).
+constexpr uint32_t kErrTimeout = 1u;        // a bounded mbarrier wait ran out
+constexpr uint32_t kErrData = 2u;           // a data value below xmin
+constexpr uint32_t kErrArena = 4u;          // per-warp arena too small (host bug)
+
+struct Counters {
+  unsigned long long newton_capped;
+  unsigned long long tail_draws;
+  unsigned long long global_sorts;
+  unsigned int status;
+  unsigned int work_next;                   // persistent-kernel work counter
+};
+
+// One distinct (alpha, xmin): its inverse-CDF thresholds and log tables.
+struct Law {
+  double alpha;
+  double Z;               // zeta(alpha, xmin)
+  uint64_t xmin;
+  uint32_t L2;            // table length (>= kL1, multiple of kL1)
+  uint32_t pad;
+  uint64_t *T;            // T[i] = floor(Q(xmin+i) 2^53) + 1, Q(k) = P(X > k)
+  uint32_t *guide;        // guide[j] = min{i : T[i] <= (j+1) 2^(53-g)} (or L2)
+  double *lnT;            // ln(xmin + i), i < kLnTable
+  float *lnT_hi;          // float split of lnT: hi + lo
+  float *lnT_lo;
+};
+
+struct Cell {
+  double alpha;           // exponent of the simulated law
+  uint64_t xmin;
+  int64_t n;
+  int64_t R;
+  uint32_t cell_id;
+  uint32_t law;           // index into the law array
+  uint32_t H;             // dense histogram bins in use (<= kHMax)
+  uint32_t purpose;
+  int64_t out_off;        // offset of replicate 0 in the per-replicate outputs
+};
+
+struct WorkItem {
+  uint32_t cell;
+  uint32_t r0;            // first replicate of this block-sized batch
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// m in [1, 2^53] from the words (lo, hi) of one draw: top 53 bits plus one.
+__device__ __forceinline__ uint64_t draw_bits(uint32_t lo, uint32_t hi) {
+  return ((((uint64_t)hi << 32) | lo) >> 11) + 1ull;
+}
+
+// ---------------------------------------------------------------------------
+// Euler-Maclaurin for the Hurwitz zeta (DLMF 2.10.1, 25.11):
+//   zeta(s,a) = sum_{k<M} (a+k)^-s + N^(1-s)/(s-1) + N^-s/2
+//             + sum_{j=1..8} B_2j/(2j)! s(s+1)..(s+2j-2) N^(-s-2j+1),  N = a+M,
+// with M chosen so that N >= 10 + 1.5 s; the first omitted term is then
+// below 2^-56 of the integral term for every s > 1.
+__device__ __forceinline__ double bern_coef(int j) {
+  // B_2j / (2j)!, j = 1..8
+  switch (j) {
+    case 1: return 1.0 / 12.0;
+    case 2: return -1.0 / 720.0;
+    case 3: return 1.0 / 30240.0;
+    case 4: return -1.0 / 1209600.0;
+    case 5: return 1.0 / 47900160.0;
+    case 6: return -691.0 / 1307674368000.0;
+    case 7: return 1.0 / 74724249600.0;
+    default: return -3617.0 / 10670622842880000.0;
+  }
+}
+
+__device__ __forceinline__ int em_shift(double s, double a) {
+  const double nmin = 10.0 + 1.5 * s;
+  return a < nmin ? (int)ceil(nmin - a) : 0;
+}
+
+// zeta(s, a) and, for ND >= 1/2, its first/second s-derivatives into z[0..ND].
+// PRECISE evaluates powers with pow(); otherwise with exp(-s ln x), the log
+// taken from lnx_table when x - a0 < table_len (table of ln(a0 + i)).
+template <int ND, bool PRECISE>
+__device__ __forceinline__ void hurwitz_em(double s, double a, double *z,
+                                           const double *lnx_table = nullptr,
+                                           double a0 = 0.0, int table_len = 0) {
+  double z0 = 0.0, z1 = 0.0, z2 = 0.0;
+  const int M = em_shift(s, a);
+  for (int k = 0; k < M; ++k) {
+    const double x = a + (double)k;
+    double lx, t;
+    if (PRECISE) {
+      lx = log(x);
+      t = pow(x, -s);
+    } else {
+      const int idx = (int)(x - a0);
+      lx = (lnx_table && idx >= 0 && idx < table_len) ? lnx_table[idx] : log(x);
+      t = exp(-s * lx);
+    }
+    z0 += t;
+    if (ND >= 1) z1 -= lx * t;
+    if (ND >= 2) z2 += lx * lx * t;
+  }
+  const double N = a + (double)M;
+  const double L = log(N);
+  const double Ns = PRECISE ? pow(N, -s) : exp(-s * L);
+  const double u = 1.0 / (s - 1.0);
+  const double N1s = N * Ns;
+  z0 += N1s * u + 0.5 * Ns;
+  if (ND >= 1) z1 += -N1s * (L * u + u * u) - 0.5 * L * Ns;
+  if (ND >= 2) z2 += N1s * (L * L * u + 2.0 * L * u * u + 2.0 * u * u * u) + 0.5 * L * L * Ns;
+  const double inv_n2 = 1.0 / (N * N);
+  double w = Ns / N;                           // N^(-s-1)
+  double P = s, dP = 1.0, d2P = 0.0;           // s(s+1)..(s+2j-2) and derivatives
+#pragma unroll
+  for (int j = 1; j <= 8; ++j) {
+    const double c = bern_coef(j) * w;
+    z0 += c * P;
+    if (ND >= 1) z1 += c * (dP - L * P);
+    if (ND >= 2) z2 += c * (d2P - 2.0 * L * dP + L * L * P);
+#pragma unroll
+    for (int f = 2 * j - 1; f <= 2 * j; ++f) {
+      const double g = s + (double)f;
+      if (ND >= 2) d2P = d2P * g + 2.0 * dP;
+      if (ND >= 1) dP = dP * g + P;
+      P *= g;
+    }
+    w *= inv_n2;
+  }
+  z[0] = z0;
+  if (ND >= 1) z[1] = z1;
+  if (ND >= 2) z[2] = z2;
+}
+
+__device__ __forceinline__ double hurwitz_precise(double s, double a) {
+  double z;
+  hurwitz_em<0, true>(s, a, &z);
+  return z;
+}
+
+// Survival of the law at k: Q(k) = zeta(alpha, k+1) / Z, argument formed as
+// (double)k + 1 (rounded for k > 2^53).
+__device__ __forceinline__ double survival(double alpha, double Z, uint64_t k) {
+  return hurwitz_precise(alpha, (double)k + 1.0) / Z;
+}
+
+// ---------------------------------------------------------------------------
+// Inverse CDF.  X = min(2^62, min{k >= xmin : Q(k) < v}), v = m 2^-53.
+// Table region: T[i] <= m  <=>  Q(xmin+i) < v (T[i] = floor(Q 2^53) + 1 and
+// Q 2^53 is exact), so the search is on 64-bit integers only.  The guide
+// bucket j = (m-1) >> (53-g) bounds the answer to [guide[j], guide[j-1]].
+
+// Beyond the table: FP64 evaluation of Q, started from the continuous
+// approximation zeta(s, k+1) ~ (k + 1/2)^(1-s) / (s-1), then exponential
+// search and bisection (every loop bounded by 64 steps).
+static __device__ __noinline__ uint64_t tail_invert(double alpha, double Z, uint64_t kstart,
+                                             uint64_t m) {
+  const double v = (double)m * 0x1p-53;
+  const double s = alpha;
+  double g = pow((s - 1.0) * Z * v, -1.0 / (s - 1.0)) - 0.5;
+  uint64_t k;
+  if (!(g < (double)kXCap)) k = kXCap;
+  else if (g <= (double)kstart) k = kstart;
+  else k = (uint64_t)ceil(g);
+  uint64_t lo, hi;
+  if (survival(s, Z, k) < v) {
+    hi = k;
+    uint64_t d = 1;
+    for (int it = 0; it < 64; ++it) {
+      if (hi == kstart) break;
+      const uint64_t c = (hi - kstart > d) ? hi - d : kstart;
+      if (survival(s, Z, c) < v) {
+        hi = c;
+        d <<= 1;
+      } else {
+        lo = c + 1;
+        goto bisect;
+      }
+    }
+    return hi;  // hi == kstart (or the loop bound; unreachable for hi < 2^63)
+  } else {
+    if (k >= kXCap) return kXCap;
+    lo = k + 1;
+    uint64_t d = 1;
+    for (int it = 0; it < 64; ++it) {
+      const uint64_t c = (kXCap - lo > d) ? lo + d - 1 : kXCap;
+      if (survival(s, Z, c) < v) {
+        hi = c;
+        goto bisect;
+      }
+      if (c == kXCap) return kXCap;
+      lo = c + 1;
+      d <<= 1;
+    }
+    return kXCap;
+  }
+bisect:
+  for (int it = 0; it < 70 && lo < hi; ++it) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if (survival(s, Z, mid) < v) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Table search: sT / sG are the shared-memory copies of T[0..kL1) and guide.
+__device__ __forceinline__ uint64_t lookup(const uint64_t *sT, const uint32_t *sG,
+                                           const uint64_t *gT, uint32_t L2, uint64_t xmin,
+                                           double alpha, double Z, uint64_t m,
+                                           unsigned long long *tail_counter) {
+  const uint32_t j = (uint32_t)((m - 1ull) >> (53 - kGuideBits));
+  uint32_t lo = sG[j];
+  uint32_t hi = j ? sG[j - 1] : L2;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    const uint64_t t = mid < (uint32_t)kL1 ? sT[mid] : __ldg(gT + mid);
+    if (t <= m) hi = mid;
+    else lo = mid + 1;
+  }
+  if (lo < L2) return xmin + lo;
+  atomicAdd(tail_counter, 1ull);
+  return tail_invert(alpha, Z, xmin + L2, m);
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers.
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ double warp_max(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+__device__ __forceinline__ float warp_maxf(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+__device__ __forceinline__ int64_t warp_sum_i64(int64_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ int64_t warp_max_i64(int64_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = x > y ? x : y;
+  }
+  return x;
+}
+// inclusive scans
+__device__ __forceinline__ double warp_scan(double x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+__device__ __forceinline__ int64_t warp_scan_i64(int64_t x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Error-free sum of two floats (Knuth TwoSum): s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) float pairs: compensated addition.
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float bh, float bl) {
+  float s, e;
+  two_sum(hi, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(lo, bl));
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+// inclusive compensated scan of (hi, lo) pairs
+__device__ __forceinline__ void warp_scan_ff(float &hi, float &lo, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float yh = __shfl_up_sync(0xffffffffu, hi, o);
+    const float yl = __shfl_up_sync(0xffffffffu, lo, o);
+    if (lane >= o) ff_add(hi, lo, yh, yl);
+  }
+}
+__device__ __forceinline__ void warp_sum_ff(float &hi, float &lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float yh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float yl = __shfl_xor_sync(0xffffffffu, lo, o);
+    ff_add(hi, lo, yh, yl);
+  }
+}
+
+// Bitonic sort of P (power of two, <= 32 * 2^k) uint64 keys at `a` by one warp.
+// Works on shared or global memory (generic pointer).
+__device__ __forceinline__ void warp_bitonic_sort(uint64_t *a, uint32_t P, int lane) {
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = lane; i < P; i += 32) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const uint64_t x = a[i], y = a[l];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Bounded mbarrier wait: gives up after ~2^31 clock cycles (about a second)
+// and reports false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity) {
+  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(mbar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
+  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(mbar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(mbar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes)
+               : "memory");
+}
+
+// 1-D bulk copy global -> shared (TMA engine, no tensor map), completion
+// signalled on mbar.  dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *mbar) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(mbar);
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+      "l"(src), "r"(bytes), "r"(b)
+      : "memory");
+}
+
+}  // namespace pl

@@ -1,0 +1,826 @@
+// pl_kernels.cu -- sm_103a kernels of the KS-cutoff simulation.
+//
+// Per replicate (Section 4 of the paper): n draws from the law
+// p(k) = k^-alpha / zeta(alpha, xmin) (Eq. 1), the maximum-likelihood exponent
+// (Eq. 2), and the KS distance at the fitted exponent (Eq. 3); per cell the
+// order statistics of D (the cutoffs of Table 1).
+#include <cfloat>
+#include <cstdio>
+
+#include "pl_kernels.cuh"
+
+namespace pl {
+
+// ===========================================================================
+// Law tables.
+
+__global__ void law_z_kernel(Law *laws, int nlaws) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nlaws) laws[i].Z = hurwitz_precise(laws[i].alpha, (double)laws[i].xmin);
+}
+
+// T[i] = floor(Q(xmin+i) 2^53) + 1 and the log tables of xmin + i.
+__global__ void law_fill_kernel(Law *laws) {
+  const Law law = laws[blockIdx.y];
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < law.L2 || i < (uint32_t)kLnTable;
+       i += stride) {
+    if (i < law.L2) {
+      const double Q = survival(law.alpha, law.Z, law.xmin + i);
+      law.T[i] = (uint64_t)(Q * 0x1p53) + 1ull;
+    }
+    if (i < (uint32_t)kLnTable) {
+      const double l = log((double)(law.xmin + i));
+      const float hi = (float)l;
+      law.lnT[i] = l;
+      law.lnT_hi[i] = hi;
+      law.lnT_lo[i] = (float)(l - (double)hi);
+    }
+  }
+}
+
+// guide[j] = min{i < L2 : T[i] <= (j+1) 2^(53-g)}, or L2.
+__global__ void law_guide_kernel(Law *laws) {
+  const Law law = laws[blockIdx.y];
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= (uint32_t)kGuide) return;
+  const uint64_t bound = (uint64_t)(j + 1) << (53 - kGuideBits);
+  uint32_t lo = 0, hi = law.L2;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (law.T[mid] <= bound) hi = mid;
+    else lo = mid + 1;
+  }
+  law.guide[j] = lo;
+}
+
+cudaError_t launch_law_setup(Law *laws_dev, int nlaws, cudaStream_t st) {
+  if (nlaws <= 0) return cudaSuccess;
+  law_z_kernel<<<(nlaws + 63) / 64, 64, 0, st>>>(laws_dev, nlaws);
+  law_fill_kernel<<<dim3(256, nlaws), 256, 0, st>>>(laws_dev);
+  law_guide_kernel<<<dim3(kGuide / 256, nlaws), 256, 0, st>>>(laws_dev);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Shared-memory staging of a law's level-1 thresholds and guide table by the
+// bulk-copy (TMA) engine.  Every thread waits (bounded); the outcome is made
+// uniform across the block so that no thread leaves a barrier early.
+struct StagedLaw {
+  uint64_t *sT;
+  uint32_t *sG;
+  uint64_t *mbar;
+};
+
+__device__ bool stage_law(const StagedLaw &s, const Law &law, uint32_t &phase, Counters *ctr) {
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(s.mbar, (uint32_t)(kL1 * sizeof(uint64_t) + kGuide * sizeof(uint32_t)));
+    bulk_g2s(s.sT, law.T, (uint32_t)(kL1 * sizeof(uint64_t)), s.mbar);
+    bulk_g2s(s.sG, law.guide, (uint32_t)(kGuide * sizeof(uint32_t)), s.mbar);
+  }
+  const bool ok = mbar_wait_bounded(s.mbar, phase);
+  const int any_fail = __syncthreads_or(!ok);
+  if (any_fail) {
+    if (threadIdx.x == 0) atomicOr(&ctr->status, kErrTimeout);
+    mbar_wait_bounded(s.mbar, phase);  // let copies in flight land before exit
+    return false;
+  }
+  phase ^= 1u;
+  return true;
+}
+
+// ===========================================================================
+// Sampling only (pl_sample): one thread per pair of draws.
+__global__ void __launch_bounds__(256) sample_kernel(const Law *law_p, uint64_t seed,
+                                                     uint32_t cell_id, uint32_t purpose,
+                                                     uint32_t rep0, int64_t nrep, int64_t n,
+                                                     uint64_t *out, Counters *ctr) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  StagedLaw s{(uint64_t *)smem, (uint32_t *)(smem + kL1 * 8), (uint64_t *)(smem + kL1 * 8 + kGuide * 4)};
+  const Law law = *law_p;
+  if (threadIdx.x == 0) mbar_init(s.mbar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  if (!stage_law(s, law, phase, ctr)) return;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  const int64_t npairs = (n + 1) >> 1;
+  const int64_t total = npairs * nrep;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / npairs;
+    const int64_t p = idx - r * npairs;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)p, rep0 + (uint32_t)r, cell_id, purpose), key);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int64_t i = 2 * p + j;
+      if (i < n) {
+        const uint64_t m = draw_bits(j ? w.z : w.x, j ? w.w : w.y);
+        out[r * n + i] = lookup(s.sT, s.sG, law.T, law.L2, law.xmin, law.alpha, law.Z, m,
+                                &ctr->tail_draws);
+      }
+    }
+  }
+}
+
+cudaError_t launch_sample(const Law *law_dev, uint64_t seed, uint32_t cell_id, uint32_t purpose,
+                          uint32_t rep0, int64_t nrep, int64_t n, uint64_t *out, Counters *ctr,
+                          int num_sms, cudaStream_t st) {
+  const size_t smem = kL1 * 8 + kGuide * 4 + 16;
+  const int64_t pairs = ((n + 1) / 2) * nrep;
+  int64_t blocks = (pairs + 255) / 256;
+  const int64_t cap = (int64_t)num_sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  sample_kernel<<<(unsigned)blocks, 256, smem, st>>>(law_dev, seed, cell_id, purpose, rep0, nrep, n,
+                                                     out, ctr);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Newton-Raphson for the MLE (Eq. 2), one lane per replicate, binary64:
+// f(a) = zeta'(a,xmin)/zeta(a,xmin) + mbar is increasing in a (f' is the
+// variance of ln X), safeguarded by bisection on (1 + 2^-40, 64], stopped when
+// a step is within 4 ulp.  Returns the number of iterations (kNewtonCap + 1
+// if the cap was hit); *Z receives zeta(alpha-hat, xmin).
+__device__ int newton_mle(double mbar, uint64_t xmin, double ln_xmin_half, const double *lnT,
+                          double *alpha_hat, double *Z) {
+  double lo = 1.0 + 0x1p-40, hi = 64.0;
+  double a = 1.0 + 1.0 / (mbar - ln_xmin_half);
+  if (!(a > lo && a < hi)) a = 0.5 * (lo + hi);
+  const double x0 = (double)xmin;
+  int it = 1;
+  for (; it <= kNewtonCap; ++it) {
+    double z[3];
+    hurwitz_em<2, false>(a, x0, z, lnT, x0, kLnTable);
+    const double g = z[1] / z[0];
+    const double f = g + mbar;
+    const double fp = z[2] / z[0] - g * g;
+    if (f > 0.0) hi = a;
+    else lo = a;
+    double next = a - f / fp;
+    if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+    const double step = fabs(next - a);
+    a = next;
+    const double tol = 4.0 * ldexp(1.0, ilogb(a) - 52);
+    if (step <= tol || hi - lo <= tol) break;
+  }
+  *alpha_hat = a;
+  double z0;
+  hurwitz_em<0, false>(a, x0, &z0, lnT, x0, kLnTable);
+  *Z = z0;
+  return it;
+}
+
+// ln(a) of a uint64 as a float pair hi + lo: exponent * ln2 (split) + ln(mantissa).
+__device__ __forceinline__ void ln_u64_ff(uint64_t a, float &hi, float &lo) {
+  const int e = 63 - __clzll((long long)a);
+  const uint64_t norm = a << (63 - e);          // leading one at bit 63
+  const uint32_t m25 = (uint32_t)(norm >> 39);  // 1 + 23 fraction bits + 1 rounding bit
+  const float mant = (float)((m25 + 1u) >> 1) * 0x1p-23f;  // mantissa in [1, 2], rounded
+  const float lm = logf(mant);
+  const float ln2_hi = 0.693145751953125f;  // 45425 / 2^16: e * ln2_hi is exact for e < 256
+  const float ln2_lo = 1.4286068203094172e-06f;
+  const float ef = (float)e;
+  hi = ef * ln2_hi;  // exact
+  float s, err;
+  two_sum(hi, lm, s, err);
+  lo = err + ef * ln2_lo;
+  hi = s;
+}
+
+// exp(-(a_hi + a_lo)(l_hi + l_lo)) in binary32, the product's rounding error
+// carried to first order.
+__device__ __forceinline__ float exp_neg_prod(float a_hi, float a_lo, float l_hi, float l_lo) {
+  const float prod = a_hi * l_hi;
+  const float err = fmaf(a_hi, l_hi, -prod);
+  const float tail = err + fmaf(a_hi, l_lo, a_lo * l_hi);
+  return expf(-prod) * (1.0f - tail);
+}
+
+// Per-replicate fitted quantities handed to the KS step.
+struct FitOut {
+  double ahat;
+  double Z;
+  // binary32 form only
+  float a_hi, a_lo, invZ, lnZ, lnc;   // lnc = ln((ahat - 1) Z)
+};
+
+__device__ __forceinline__ FitOut fit_from_logsum(double L, int64_t n, uint64_t xmin,
+                                                  const CellConst &cc, const double *lnT,
+                                                  bool f32, Counters *ctr) {
+  FitOut o;
+  const int it = newton_mle(L / (double)n, xmin, cc.ln_xmin_half, lnT, &o.ahat, &o.Z);
+  if (it > kNewtonCap) atomicAdd(&ctr->newton_capped, 1ull);
+  if (f32) {
+    o.a_hi = (float)o.ahat;
+    o.a_lo = (float)(o.ahat - (double)o.a_hi);
+    o.invZ = (float)(1.0 / o.Z);
+    o.lnZ = (float)log(o.Z);
+    o.lnc = (float)log((o.ahat - 1.0) * o.Z);
+  }
+  return o;
+}
+
+__device__ __forceinline__ FitOut shfl_fit(const FitOut &f, int src) {
+  FitOut o;
+  o.ahat = __shfl_sync(0xffffffffu, f.ahat, src);
+  o.Z = __shfl_sync(0xffffffffu, f.Z, src);
+  o.a_hi = __shfl_sync(0xffffffffu, f.a_hi, src);
+  o.a_lo = __shfl_sync(0xffffffffu, f.a_lo, src);
+  o.invZ = __shfl_sync(0xffffffffu, f.invZ, src);
+  o.lnZ = __shfl_sync(0xffffffffu, f.lnZ, src);
+  o.lnc = __shfl_sync(0xffffffffu, f.lnc, src);
+  return o;
+}
+
+// ===========================================================================
+// KS distance (Eq. 3) of one replicate by one warp.
+//   Dense part: every integer t = xmin + i, i <= tmax; F(t) is the prefix sum
+//   of p(k) = k^-ahat / Z, S(t) = C(t)/n; D >= |F(t) - S(t)| at each t.
+//   Spill part: distinct values v beyond the dense range, ascending, with
+//   counts; on each run of integers where S is constant F increases, so the
+//   maximum is at v (S = C(v)/n) or v - 1 (S = C(v-1)/n):
+//   F(v) = 1 - zeta(ahat, v+1)/Z and F(v-1) = F(v) - p(v).
+// FP64 form: everything binary64.  FP32 form: p and F in binary32 with
+// compensated (two-sum) prefix sums; Q(v) by a 4-term Euler-Maclaurin in
+// binary32 (v - xmin >= 32 keeps it below 1e-8 relative).
+template <bool F32>
+__device__ double ks_warp(const uint32_t *dense, int64_t tmax, const uint64_t *pairs, int64_t nsd,
+                          int64_t n, const FitOut &f, const double *lnT, const float *lnT_hi,
+                          const float *lnT_lo, int lane) {
+  if (!F32) {
+    const double invZ = 1.0 / f.Z;
+    const double inv_n = 1.0 / (double)n;
+    const double a = f.ahat;
+    double carryF = 0.0, best = 0.0;
+    int64_t carryC = 0;
+    for (int64_t i0 = 0; i0 <= tmax; i0 += 32) {
+      const int64_t i = i0 + lane;
+      const bool ok = i <= tmax;
+      const double p = ok ? exp(-a * lnT[i]) * invZ : 0.0;
+      const int64_t c = ok ? (int64_t)dense[i] : 0;
+      const double F = carryF + warp_scan(p, lane);
+      const int64_t C = carryC + warp_scan_i64(c, lane);
+      if (ok) best = fmax(best, fabs(F - (double)C * inv_n));
+      carryF = __shfl_sync(0xffffffffu, F, 31);
+      carryC = __shfl_sync(0xffffffffu, C, 31);
+    }
+    for (int64_t k0 = 0; k0 < nsd; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const bool ok = k < nsd;
+      const uint64_t v = ok ? pairs[2 * k] : 0;
+      const int64_t c = ok ? (int64_t)pairs[2 * k + 1] : 0;
+      const int64_t Ca = carryC + warp_scan_i64(c, lane);
+      if (ok) {
+        const int64_t Cb = Ca - c;
+        double q;
+        hurwitz_em<0, false>(a, (double)v + 1.0, &q);
+        const double Q = q * invZ;
+        const double pv = exp(-a * log((double)v)) * invZ;
+        const double Fv = 1.0 - Q;
+        const double Fb = 1.0 - (Q + pv);
+        best = fmax(best, fmax(fabs(Fv - (double)Ca * inv_n), fabs(Fb - (double)Cb * inv_n)));
+      }
+      carryC = __shfl_sync(0xffffffffu, Ca, 31);
+    }
+    return warp_max(best);
+  } else {
+    const float inv_n = 1.0f / (float)n;
+    float cF_hi = 0.0f, cF_lo = 0.0f, best = 0.0f;
+    int64_t carryC = 0;
+    for (int64_t i0 = 0; i0 <= tmax; i0 += 32) {
+      const int64_t i = i0 + lane;
+      const bool ok = i <= tmax;
+      float ph = ok ? exp_neg_prod(f.a_hi, f.a_lo, lnT_hi[i], lnT_lo[i]) * f.invZ : 0.0f;
+      float pl = 0.0f;
+      warp_scan_ff(ph, pl, lane);
+      ff_add(ph, pl, cF_hi, cF_lo);
+      const int64_t c = ok ? (int64_t)dense[i] : 0;
+      const int64_t C = carryC + warp_scan_i64(c, lane);
+      if (ok) best = fmaxf(best, fabsf(ph - (float)C * inv_n));
+      cF_hi = __shfl_sync(0xffffffffu, ph, 31);
+      cF_lo = __shfl_sync(0xffffffffu, pl, 31);
+      carryC = __shfl_sync(0xffffffffu, C, 31);
+    }
+    const float s = f.a_hi;          // exponent, binary32
+    const float sm1 = (float)(f.ahat - 1.0);
+    for (int64_t k0 = 0; k0 < nsd; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const bool ok = k < nsd;
+      const uint64_t v = ok ? pairs[2 * k] : 0;
+      const int64_t c = ok ? (int64_t)pairs[2 * k + 1] : 0;
+      const int64_t Ca = carryC + warp_scan_i64(c, lane);
+      if (ok && (float)(v + 1ull) < 10.0f + 1.5f * f.a_hi) {
+        // exponent too large for the short binary32 series at this argument
+        const int64_t Cb = Ca - c;
+        double q;
+        hurwitz_em<0, false>(f.ahat, (double)v + 1.0, &q);
+        const float Q = (float)(q / f.Z);
+        const float pv = (float)(exp(-f.ahat * log((double)v)) / f.Z);
+        const float Fv = 1.0f - Q;
+        const float Fb = 1.0f - (Q + pv);
+        best = fmaxf(best, fmaxf(fabsf(Fv - (float)Ca * inv_n), fabsf(Fb - (float)Cb * inv_n)));
+      } else if (ok) {
+        const int64_t Cb = Ca - c;
+        float la_hi, la_lo, lv_hi, lv_lo;
+        ln_u64_ff(v + 1ull, la_hi, la_lo);
+        ln_u64_ff(v, lv_hi, lv_lo);
+        // Q(v) = zeta(s, a)/Z, a = v+1:  a^(1-s)/((s-1)Z) * [1 + (s-1)/(2a)
+        //        + sum_j B2j/(2j)! s(s+1)..(s+2j-2)(s-1) a^-2j]
+        const float af = (float)(v + 1ull);
+        const float ia = 1.0f / af, ia2 = ia * ia;
+        float P = s, br = 1.0f + 0.5f * sm1 * ia, w = ia2;
+        const float cj[4] = {1.0f / 12.0f, -1.0f / 720.0f, 1.0f / 30240.0f, -1.0f / 1209600.0f};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          br += cj[j] * P * sm1 * w;
+          P *= (s + (float)(2 * j + 1)) * (s + (float)(2 * j + 2));
+          w *= ia2;
+        }
+        // ln Q = (1-s) ln a - lnc, with the product's error carried
+        const float prod = sm1 * la_hi;
+        const float perr = fmaf(sm1, la_hi, -prod) + sm1 * la_lo;
+        const float Q = expf(-prod - f.lnc) * (1.0f - perr) * br;
+        const float pv = exp_neg_prod(f.a_hi, f.a_lo, lv_hi, lv_lo) * f.invZ;
+        const float Fv = 1.0f - Q;
+        const float Fb = 1.0f - (Q + pv);
+        best = fmaxf(best, fmaxf(fabsf(Fv - (float)Ca * inv_n), fabsf(Fb - (float)Cb * inv_n)));
+      }
+      carryC = __shfl_sync(0xffffffffu, Ca, 31);
+    }
+    return (double)warp_maxf(best);
+  }
+}
+
+// ===========================================================================
+// Sort the s spill values of one replicate (bitonic, on chip when they fit,
+// else in the warp's global buffer) and run-length encode them into
+// interleaved (value, count) pairs.  Returns the number of distinct values.
+__device__ int64_t spill_compact(uint64_t *spill, uint32_t *onchip, int64_t s, uint64_t *pairs,
+                                 int lane, Counters *ctr) {
+  if (s <= 0) return 0;
+  uint32_t P = 1;
+  while ((int64_t)P < s) P <<= 1;
+  uint64_t *buf;
+  if (s <= kSortSmem) {
+    buf = reinterpret_cast<uint64_t *>(onchip);
+    for (uint32_t i = lane; i < P; i += 32) buf[i] = (int64_t)i < s ? spill[i] : ~0ull;
+  } else {
+    buf = spill;
+    for (uint32_t i = (uint32_t)s + lane; i < P; i += 32) buf[i] = ~0ull;
+    if (lane == 0) atomicAdd(&ctr->global_sorts, 1ull);
+  }
+  __syncwarp();
+  warp_bitonic_sort(buf, P, lane);
+  int64_t base = 0;
+  for (int64_t i0 = 0; i0 < s; i0 += 32) {
+    const int64_t i = i0 + lane;
+    const bool ok = i < s;
+    const uint64_t x = ok ? buf[i] : 0;
+    const bool start = ok && (i == 0 || buf[i - 1] != x);
+    const unsigned bal = __ballot_sync(0xffffffffu, start);
+    const int rank = __popc(bal & ((1u << lane) - 1u));
+    if (start) {
+      pairs[2 * (base + rank)] = x;
+      pairs[2 * (base + rank) + 1] = (uint64_t)i;  // start position; count below
+    }
+    base += __popc(bal);
+  }
+  __syncwarp();
+  for (int64_t k0 = 0; k0 < base; k0 += 32) {
+    const int64_t k = k0 + lane;
+    uint64_t cnt = 0;
+    if (k < base) {
+      const uint64_t st = pairs[2 * k + 1];
+      const uint64_t en = (k + 1 < base) ? pairs[2 * (k + 1) + 1] : (uint64_t)s;
+      cnt = en - st;
+    }
+    __syncwarp();
+    if (k < base) pairs[2 * k + 1] = cnt;
+    __syncwarp();
+  }
+  return base;
+}
+
+// ===========================================================================
+// Warp form: a persistent grid; a block takes a work item (one cell, kWarps*32
+// replicates), stages the law's table in shared memory, and each warp takes
+// 32 replicates:
+//   phase 1 (warp per replicate): draws, histogram, log-sum, compaction of the
+//           histogram and spills into the warp's arena;
+//   phase 2 (lane per replicate): binary64 Newton solve of Eq. 2;
+//   phase 3 (warp per replicate): KS distance.
+// If the arena fills up, phases 2-3 run early for the replicates already in it.
+template <bool F32>
+__global__ void __launch_bounds__(kWarps * 32) replicate_warp_kernel(WarpLaunch a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
+  uint32_t *sG = reinterpret_cast<uint32_t *>(smem + kL1 * 8);
+  uint32_t *sH = reinterpret_cast<uint32_t *>(smem + kL1 * 8 + kGuide * 4);
+  int *s_spill = reinterpret_cast<int *>(smem + kL1 * 8 + kGuide * 4 + kWarps * kHMax * 4);
+  uint32_t *s_item = reinterpret_cast<uint32_t *>(s_spill + kWarps);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kL1 * 8 + kGuide * 4 + kWarps * kHMax * 4 + 64);
+  StagedLaw staged{sT, sG, mbar};
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t *hist = sH + warp * kHMax;
+  const size_t slot = (size_t)blockIdx.x * kWarps + warp;
+  uint64_t *spill = reinterpret_cast<uint64_t *>(a.scratch + slot * (a.spill_cap * 8 + a.arena_bytes));
+  uint8_t *arena = reinterpret_cast<uint8_t *>(spill + a.spill_cap);
+  const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  __syncthreads();
+  uint32_t phase = 0, loaded = 0xffffffffu;
+
+  for (;;) {
+    if (threadIdx.x == 0) *s_item = atomicAdd(&a.ctr->work_next, 1u);
+    __syncthreads();
+    const uint32_t item = *s_item;
+    if (item >= a.nitems) break;
+    const WorkItem wi = a.items[item];
+    const Cell cell = a.cells[wi.cell];
+    const CellConst cc = a.consts[wi.cell];
+    const Law law = a.laws[cell.law];
+    if (cell.law != loaded) {
+      if (!stage_law(staged, law, phase, a.ctr)) return;
+      loaded = cell.law;
+    }
+    const int64_t rbase = (int64_t)wi.r0 + warp * 32;
+    const int nb = (int)min((int64_t)32, cell.R - rbase);
+    if (nb > 0) {
+      const int64_t n = cell.n;
+      const uint64_t xmin = cell.xmin;
+      const int64_t H = cell.H;
+      // per-lane record of replicate `lane`
+      double myL = 0.0;
+      int64_t my_tmax = -1, my_nsd = 0;
+      size_t my_off = 0;
+      size_t arena_off = 0;
+      int done = 0;
+      auto finish = [&](int b0, int b1) {
+        FitOut fo{};
+        if (lane >= b0 && lane < b1) fo = fit_from_logsum(myL, n, xmin, cc, law.lnT, F32, a.ctr);
+        double myD = 0.0;
+        for (int r = b0; r < b1; ++r) {
+          const FitOut fr = shfl_fit(fo, r);
+          const int64_t tm = __shfl_sync(0xffffffffu, my_tmax, r);
+          const int64_t ns = __shfl_sync(0xffffffffu, my_nsd, r);
+          const size_t off = __shfl_sync(0xffffffffu, my_off, r);
+          const size_t dense_bytes = ((size_t)(tm + 1) * 4 + 15) & ~(size_t)15;
+          const double D = ks_warp<F32>(reinterpret_cast<const uint32_t *>(arena + off), tm,
+                                        reinterpret_cast<const uint64_t *>(arena + off + dense_bytes),
+                                        ns, n, fr, law.lnT, law.lnT_hi, law.lnT_lo, lane);
+          if (lane == r) myD = D;
+        }
+        if (lane >= b0 && lane < b1) {
+          const int64_t o = cell.out_off + rbase + lane;
+          if (F32) reinterpret_cast<float *>(a.D_out)[o] = (float)myD;
+          else reinterpret_cast<double *>(a.D_out)[o] = myD;
+          if (a.A_out) a.A_out[o] = fo.ahat;
+        }
+      };
+
+      for (int r = 0; r < nb; ++r) {
+        const uint32_t rep = (uint32_t)(rbase + r);
+        for (int i = lane; i < H; i += 32) hist[i] = 0;
+        if (lane == 0) s_spill[warp] = 0;
+        __syncwarp();
+        uint64_t packed = 0;  // 16-bit counters of bins 0..3 (per lane <= n/32 + 2 draws)
+        int64_t lmax = -1;
+        const int64_t npairs = (n + 1) >> 1;
+        for (int64_t p = lane; p < npairs; p += 32) {
+          const uint4 w = philox4x32_10(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), key);
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            if (2 * p + j < n) {
+              const uint64_t m = draw_bits(j ? w.z : w.x, j ? w.w : w.y);
+              const uint64_t X = lookup(sT, sG, law.T, law.L2, xmin, law.alpha, law.Z, m,
+                                        &a.ctr->tail_draws);
+              const uint64_t b = X - xmin;
+              if (b < 4) packed += 1ull << (16 * b);
+              else if (b < (uint64_t)H) atomicAdd(&hist[b], 1u);
+              else {
+                const int slot_i = atomicAdd(&s_spill[warp], 1);
+                spill[slot_i] = X;
+              }
+              if (b < (uint64_t)H && (int64_t)b > lmax) lmax = (int64_t)b;
+            }
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)((packed >> (16 * q)) & 0xffffu));
+          if (lane == 0 && c) hist[q] += c;
+        }
+        __syncwarp();
+        const int64_t s = s_spill[warp];
+        const int64_t tmax = warp_max_i64(lmax);
+        // log-sum  L = sum ln x_i  (+ ln((xmin+1)/xmin) if every x_i = xmin)
+        double L;
+        if (!F32) {
+          double acc = 0.0;
+          for (int64_t i = lane; i <= tmax; i += 32) acc += (double)hist[i] * law.lnT[i];
+          for (int64_t k = lane; k < s; k += 32) acc += log((double)spill[k]);
+          L = warp_sum(acc);
+        } else {
+          float h = 0.0f, l = 0.0f;
+          for (int64_t i = lane; i <= tmax; i += 32) {
+            const float c = (float)hist[i];
+            const float ph = c * law.lnT_hi[i];
+            const float pe = fmaf(c, law.lnT_hi[i], -ph) + c * law.lnT_lo[i];
+            ff_add(h, l, ph, pe);
+          }
+          for (int64_t k = lane; k < s; k += 32) {
+            float vh, vl;
+            ln_u64_ff(spill[k], vh, vl);
+            ff_add(h, l, vh, vl);
+          }
+          warp_sum_ff(h, l);
+          L = (double)h + (double)l;
+        }
+        if (hist[0] == (uint32_t)n) L += cc.ln_allmin;
+        // arena space for this replicate; run phases 2-3 early if it is full
+        const size_t dense_bytes = ((size_t)(tmax + 1) * 4 + 15) & ~(size_t)15;
+        const size_t need = dense_bytes + (size_t)s * 16;
+        if (arena_off + need > a.arena_bytes) {
+          if (done < r) finish(done, r);
+          done = r;
+          arena_off = 0;
+          if (need > a.arena_bytes) {  // unreachable: the host sizes the arena for one replicate
+            if (lane == 0) atomicOr(&a.ctr->status, kErrArena);
+            break;                     // leave this batch; the block barrier below still meets
+          }
+        }
+        uint32_t *dd = reinterpret_cast<uint32_t *>(arena + arena_off);
+        for (int64_t i = lane; i <= tmax; i += 32) dd[i] = hist[i];
+        __syncwarp();
+        uint64_t *pairs = reinterpret_cast<uint64_t *>(arena + arena_off + dense_bytes);
+        const int64_t nsd = spill_compact(spill, hist, s, pairs, lane, a.ctr);
+        if (lane == r) {
+          myL = L;
+          my_tmax = tmax;
+          my_nsd = nsd;
+          my_off = arena_off;
+        }
+        arena_off += dense_bytes + (size_t)nsd * 16;
+        __syncwarp();
+      }
+      if (done < nb && arena_off > 0) finish(done, nb);
+    }
+    __syncthreads();
+  }
+}
+
+size_t warp_kernel_smem_bytes() {
+  return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kWarps * kHMax * 4 + 64 + 16;
+}
+
+int warp_kernel_blocks_per_sm(bool f32) {
+  int nb = 0;
+  const size_t smem = warp_kernel_smem_bytes();
+  if (f32) {
+    cudaFuncSetAttribute(replicate_warp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, replicate_warp_kernel<true>, kWarps * 32, smem);
+  } else {
+    cudaFuncSetAttribute(replicate_warp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, replicate_warp_kernel<false>, kWarps * 32, smem);
+  }
+  return nb;
+}
+
+cudaError_t launch_replicates_warp(const WarpLaunch &a, bool f32, cudaStream_t st) {
+  const size_t smem = warp_kernel_smem_bytes();
+  if (f32) replicate_warp_kernel<true><<<a.blocks, kWarps * 32, smem, st>>>(a);
+  else replicate_warp_kernel<false><<<a.blocks, kWarps * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// One data set (pl_fit_mle, pl_ks_stat, the observed side of the bootstrap):
+// one block; dense bins [xmin, xmin + kHData) in shared memory, larger values
+// spilled to global memory and sorted there.
+constexpr int kHData = 8192;
+
+template <bool F32>
+__global__ void __launch_bounds__(1024) dataset_kernel(const int32_t *x, int64_t n, uint64_t xmin,
+                                                       bool fit, double alpha_in, const Law *lnlaw,
+                                                       CellConst cc, uint64_t *spill,
+                                                       uint64_t *pairs, double *out, Counters *ctr) {
+  __shared__ uint32_t hist[kHData];
+  __shared__ unsigned long long s_cnt;
+  __shared__ int s_bad;
+  __shared__ long long s_tmax;
+  __shared__ double s_red[32];
+  const Law law = *lnlaw;
+  for (int i = threadIdx.x; i < kHData; i += blockDim.x) hist[i] = 0;
+  if (threadIdx.x == 0) {
+    s_cnt = 0;
+    s_bad = 0;
+    s_tmax = -1;
+  }
+  __syncthreads();
+  long long lmax = -1;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int32_t v = x[i];
+    if (v < 1 || (uint64_t)v < xmin) {
+      s_bad = 1;
+      continue;
+    }
+    const uint64_t b = (uint64_t)v - xmin;
+    if (b < (uint64_t)kHData) {
+      atomicAdd(&hist[b], 1u);
+      if ((long long)b > lmax) lmax = (long long)b;
+    } else {
+      spill[atomicAdd(&s_cnt, 1ull)] = (uint64_t)v;
+    }
+  }
+  atomicMax(&s_tmax, lmax);
+  __syncthreads();
+  if (s_bad) {
+    if (threadIdx.x == 0) {
+      atomicOr(&ctr->status, kErrData);
+      out[0] = out[1] = out[2] = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    return;
+  }
+  const int64_t s = (int64_t)s_cnt;
+  const int64_t tmax = s_tmax;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // log-sum (binary64 here: one data set, no bulk)
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i <= tmax; i += blockDim.x) acc += (double)hist[i] * law.lnT[i];
+  for (int64_t k = threadIdx.x; k < s; k += blockDim.x) acc += log((double)spill[k]);
+  acc = warp_sum(acc);
+  if (lane == 0) s_red[warp] = acc;
+  // sort the spills in global memory (block bitonic), padded to a power of two
+  uint32_t P = 1;
+  while ((int64_t)P < s) P <<= 1;
+  for (uint32_t i = (uint32_t)s + threadIdx.x; s > 0 && i < P; i += blockDim.x) spill[i] = ~0ull;
+  __syncthreads();
+  if (s > 1) {
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+          const uint32_t l = i ^ j;
+          if (l > i) {
+            const uint64_t u = spill[i], w = spill[l];
+            if ((u > w) == ((i & k) == 0)) {
+              spill[i] = w;
+              spill[l] = u;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (warp == 0) {
+    double L = lane < (int)(blockDim.x / 32) ? s_red[lane] : 0.0;
+    L = warp_sum(L);
+    if (hist[0] == (uint64_t)n) L += cc.ln_allmin;
+    // run-length encode the sorted spills (warp 0)
+    int64_t base = 0;
+    for (int64_t i0 = 0; i0 < s; i0 += 32) {
+      const int64_t i = i0 + lane;
+      const bool ok = i < s;
+      const uint64_t v = ok ? spill[i] : 0;
+      const bool start = ok && (i == 0 || spill[i - 1] != v);
+      const unsigned bal = __ballot_sync(0xffffffffu, start);
+      const int rank = __popc(bal & ((1u << lane) - 1u));
+      if (start) {
+        pairs[2 * (base + rank)] = v;
+        pairs[2 * (base + rank) + 1] = (uint64_t)i;
+      }
+      base += __popc(bal);
+    }
+    __syncwarp();
+    for (int64_t k0 = 0; k0 < base; k0 += 32) {
+      const int64_t k = k0 + lane;
+      uint64_t cnt = 0;
+      if (k < base) {
+        const uint64_t st = pairs[2 * k + 1];
+        const uint64_t en = (k + 1 < base) ? pairs[2 * (k + 1) + 1] : (uint64_t)s;
+        cnt = en - st;
+      }
+      __syncwarp();
+      if (k < base) pairs[2 * k + 1] = cnt;
+      __syncwarp();
+    }
+    FitOut fo{};
+    if (fit) {
+      if (lane == 0) fo = fit_from_logsum(L, n, xmin, cc, law.lnT, F32, ctr);
+      fo = shfl_fit(fo, 0);
+    } else {
+      fo.ahat = alpha_in;
+      if (lane == 0) {
+        double z0;
+        hurwitz_em<0, false>(alpha_in, (double)xmin, &z0, law.lnT, (double)xmin, kLnTable);
+        fo.Z = z0;
+        fo.a_hi = (float)alpha_in;
+        fo.a_lo = (float)(alpha_in - (double)fo.a_hi);
+        fo.invZ = (float)(1.0 / z0);
+        fo.lnZ = (float)log(z0);
+        fo.lnc = (float)log((alpha_in - 1.0) * z0);
+      }
+      fo = shfl_fit(fo, 0);
+    }
+    const double D = ks_warp<F32>(hist, tmax, pairs, base, n, fo, law.lnT, law.lnT_hi, law.lnT_lo, lane);
+    if (lane == 0) {
+      out[0] = fo.ahat;
+      out[1] = D;
+      out[2] = fo.Z;
+    }
+  }
+}
+
+cudaError_t launch_dataset(const int32_t *x, int64_t n, uint64_t xmin, bool fit, double alpha,
+                           const Law *lnlaw, CellConst cc, bool f32, uint64_t *spill,
+                           uint64_t *pairs, double *out, Counters *ctr, cudaStream_t st) {
+  if (f32) dataset_kernel<true><<<1, 1024, 0, st>>>(x, n, xmin, fit, alpha, lnlaw, cc, spill, pairs, out, ctr);
+  else dataset_kernel<false><<<1, 1024, 0, st>>>(x, n, xmin, fit, alpha, lnlaw, cc, spill, pairs, out, ctr);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Radix select: exact order statistic of non-negative floating-point keys
+// (their bit patterns order like the values), 8 bits per pass from the top.
+template <typename K>
+__global__ void __launch_bounds__(1024) select_kernel(const K *keys, const int64_t *off,
+                                                      const int64_t *Rs, const int64_t *rank,
+                                                      int nq, double *out) {
+  __shared__ unsigned int h[256];
+  __shared__ K s_prefix;
+  __shared__ long long s_k;
+  const int c = blockIdx.x, j = blockIdx.y;
+  const K *x = keys + off[c];
+  const int64_t R = Rs[c];
+  if (threadIdx.x == 0) {
+    s_prefix = 0;
+    s_k = rank[c * nq + j];
+  }
+  K mask = 0;
+  for (int shift = (int)sizeof(K) * 8 - 8; shift >= 0; shift -= 8) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const K prefix = s_prefix;
+    for (int64_t i = threadIdx.x; i < R; i += blockDim.x) {
+      const K v = x[i];
+      if ((v & mask) == prefix) atomicAdd(&h[(unsigned)((v >> shift) & 0xff)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long k = s_k;
+      int d = 0;
+      for (; d < 255; ++d) {
+        if (k < (long long)h[d]) break;
+        k -= h[d];
+      }
+      s_k = k;
+      s_prefix = prefix | ((K)d << shift);
+    }
+    mask |= (K)0xff << shift;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const K v = s_prefix;
+    double r;
+    if (sizeof(K) == 8) r = __longlong_as_double((long long)v);
+    else r = (double)__uint_as_float((unsigned)v);
+    out[c * nq + j] = r;
+  }
+}
+
+cudaError_t launch_select(const void *keys, bool f32, const int64_t *off, const int64_t *R,
+                          const int64_t *rank, int ncells, int nq, double *out, cudaStream_t st) {
+  const dim3 grid(ncells, nq);
+  if (f32) select_kernel<uint32_t><<<grid, 1024, 0, st>>>((const uint32_t *)keys, off, R, rank, nq, out);
+  else select_kernel<uint64_t><<<grid, 1024, 0, st>>>((const uint64_t *)keys, off, R, rank, nq, out);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+__global__ void count_ge_kernel(const void *D, bool f32, int64_t B, const double *D_obs, double *p) {
+  __shared__ unsigned long long cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const double d0 = *D_obs;
+  unsigned long long local = 0;
+  for (int64_t b = threadIdx.x; b < B; b += blockDim.x) {
+    const double v = f32 ? (double)reinterpret_cast<const float *>(D)[b]
+                         : reinterpret_cast<const double *>(D)[b];
+    local += (f32 ? (float)v >= (float)d0 : v >= d0) ? 1ull : 0ull;
+  }
+  atomicAdd(&cnt, local);
+  __syncthreads();
+  if (threadIdx.x == 0) *p = (double)cnt / (double)B;
+}
+
+cudaError_t launch_count_ge(const void *D, bool f32, int64_t B, const double *D_obs, double *p,
+                            cudaStream_t st) {
+  count_ge_kernel<<<1, 1024, 0, st>>>(D, f32, B, D_obs, p);
+  return cudaGetLastError();
+}
+
+}  // namespace pl

@@ -1,0 +1,201 @@
+"""ctypes binding of the C ABI in include/pl.h (argument marshalling only).
+
+Every compute step runs in the CUDA library ``_build/libpl.so``; this module
+only converts torch tensors / numpy arrays to pointers and status codes to
+exceptions.  Importing it loads the library and raises ``ImportError`` if it
+has not been built -- there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpl.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+PL_OK, PL_EINVAL, PL_ENOMEM, PL_ENOCONV, PL_ETIMEOUT, PL_ECUDA, PL_EBUSY = range(7)
+PL_FP64, PL_FP32_BULK = 0, 1
+_NAMES = {1: "PL_EINVAL", 2: "PL_ENOMEM", 3: "PL_ENOCONV", 4: "PL_ETIMEOUT", 5: "PL_ECUDA",
+          6: "PL_EBUSY"}
+
+EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters", "pl_set_tracing",
+           "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+           "pl_bootstrap_pvalue"]
+
+
+class pl_cell(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("xmin", ctypes.c_uint64), ("n", ctypes.c_int64),
+                ("replicates", ctypes.c_int64), ("cell_id", ctypes.c_uint64)]
+
+
+class pl_trace_info(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("law_ms", ctypes.c_float),
+                ("replicate_ms", ctypes.c_float), ("select_ms", ctypes.c_float),
+                ("total_ms", ctypes.c_float)]
+
+
+_vp = ctypes.c_void_p
+_f64p = ctypes.POINTER(ctypes.c_double)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_lib.pl_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t]
+_lib.pl_create.restype = ctypes.c_int
+_lib.pl_destroy.argtypes = [_vp]
+_lib.pl_destroy.restype = None
+_lib.pl_last_error.argtypes = [_vp]
+_lib.pl_last_error.restype = ctypes.c_char_p
+_lib.pl_sync.argtypes = [_vp, _vp]
+_lib.pl_counters.argtypes = [_vp, _vp, _u64p, _u64p, _u64p]
+_lib.pl_set_tracing.argtypes = [_vp, ctypes.c_int]
+_lib.pl_trace.argtypes = [_vp, _vp, ctypes.POINTER(pl_trace_info)]
+_lib.pl_sample.argtypes = [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                           ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, _vp, _vp]
+_lib.pl_fit_mle.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_uint64, _f64p, _vp]
+_lib.pl_ks_stat.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
+                            _f64p, _vp]
+_lib.pl_ks_cutoffs.argtypes = [_vp, ctypes.POINTER(pl_cell), ctypes.c_int, ctypes.c_uint64, _f64p,
+                               ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+_lib.pl_bootstrap_pvalue.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64,
+                                     ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _f64p, _f64p,
+                                     _f64p, _vp]
+for _f in ["pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+           "pl_bootstrap_pvalue"]:
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+class PLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _ptr(t) -> int:
+    """Device pointer of a torch tensor (or int passthrough)."""
+    if isinstance(t, int):
+        return t
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+@dataclass
+class Cell:
+    alpha: float
+    xmin: int
+    n: int
+    replicates: int
+    cell_id: int
+
+
+class Context:
+    """A library context on one CUDA device, with a workspace byte budget."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        h = _vp()
+        st = _lib.pl_create(ctypes.byref(h), device, mem_budget_bytes)
+        if st != PL_OK:
+            raise PLError(st, "pl_create failed")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != PL_OK:
+            raise PLError(st, _lib.pl_last_error(self._h).decode(errors="replace"))
+
+    # ---- entry points (same names as the C ABI) --------------------------------
+    def pl_sync(self, stream=None):
+        self._check(_lib.pl_sync(self._h, _stream_ptr(stream)))
+
+    def pl_counters(self, stream=None) -> dict:
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(_lib.pl_counters(self._h, _stream_ptr(stream), ctypes.byref(a), ctypes.byref(b),
+                                     ctypes.byref(c)))
+        return {"newton_capped": a.value, "tail_draws": b.value, "global_sorts": c.value}
+
+    def pl_set_tracing(self, on: bool = True):
+        self._check(_lib.pl_set_tracing(self._h, 1 if on else 0))
+
+    def pl_trace(self, stream=None) -> dict:
+        t = pl_trace_info()
+        self._check(_lib.pl_trace(self._h, _stream_ptr(stream), ctypes.byref(t)))
+        return {"launches": t.launches, "law_ms": t.law_ms, "replicate_ms": t.replicate_ms,
+                "select_ms": t.select_ms, "total_ms": t.total_ms}
+
+    def pl_sample(self, alpha: float, xmin: int, seed: int, cell_id: int, purpose: int, rep0: int,
+                  nrep: int, n: int, out, stream=None):
+        """out: torch.uint64 (or int64) device tensor of nrep*n elements."""
+        assert out.numel() >= nrep * n and out.element_size() == 8
+        self._check(_lib.pl_sample(self._h, alpha, xmin, seed, cell_id, purpose, rep0, nrep, n,
+                                   _ptr(out), _stream_ptr(stream)))
+
+    def pl_fit_mle(self, x, xmin: int, stream=None) -> float:
+        """x: torch.int32 device tensor."""
+        a = ctypes.c_double()
+        self._check(_lib.pl_fit_mle(self._h, _ptr(x), x.numel(), xmin, ctypes.byref(a),
+                                    _stream_ptr(stream)))
+        return a.value
+
+    def pl_ks_stat(self, x, xmin: int, alpha: float, prec: int = PL_FP64, stream=None) -> float:
+        d = ctypes.c_double()
+        self._check(_lib.pl_ks_stat(self._h, _ptr(x), x.numel(), xmin, alpha, prec, ctypes.byref(d),
+                                    _stream_ptr(stream)))
+        return d.value
+
+    def pl_ks_cutoffs(self, cells, seed: int, q, prec: int = PL_FP64, cutoffs=None, D=None,
+                      alpha_hat=None, stream=None):
+        """cells: sequence of Cell (or objects with the same fields).  cutoffs: a
+        device tensor (float64, len(cells)*len(q)) or None -> host numpy result.
+        D / alpha_hat: optional device tensors receiving per-replicate values."""
+        arr = (pl_cell * len(cells))(*[pl_cell(c.alpha, c.xmin, c.n, c.replicates, c.cell_id)
+                                       for c in cells])
+        qa = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        host = None
+        if cutoffs is None:
+            host = np.zeros(len(cells) * qa.size)
+            out_ptr = host.ctypes.data
+        elif isinstance(cutoffs, np.ndarray):
+            host = cutoffs
+            out_ptr = cutoffs.ctypes.data
+        else:
+            out_ptr = _ptr(cutoffs)
+        self._check(_lib.pl_ks_cutoffs(self._h, arr, len(cells), seed,
+                                       qa.ctypes.data_as(_f64p), qa.size, prec, out_ptr, _ptr(D),
+                                       _ptr(alpha_hat), _stream_ptr(stream)))
+        if host is not None:
+            return host.reshape(len(cells), qa.size)
+        return cutoffs
+
+    def pl_bootstrap_pvalue(self, x, xmin: int, B: int, seed: int, request_id: int,
+                            prec: int = PL_FP64, stream=None):
+        a, d, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(_lib.pl_bootstrap_pvalue(self._h, _ptr(x), x.numel(), xmin, B, seed, request_id,
+                                             prec, ctypes.byref(a), ctypes.byref(d), ctypes.byref(p),
+                                             _stream_ptr(stream)))
+        return a.value, d.value, p.value
