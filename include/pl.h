@@ -91,10 +91,13 @@ pl_status pl_sync(pl_ctx *ctx, void *stream);
 
 /* Counters accumulated on the device since pl_create: Newton solves that hit
  * the iteration cap, draws inverted in the FP64 tail beyond the threshold
- * table, and replicates whose spill list was sorted in global memory.
- * Synchronises `stream`.  Any output pointer may be NULL. */
+ * table, replicates whose spill list was sorted in global memory, and
+ * replicates fitted by the full Newton iteration instead of the one-step
+ * polish from the interpolated start.  Synchronises `stream`.  Any output
+ * pointer may be NULL. */
 pl_status pl_counters(pl_ctx *ctx, void *stream, uint64_t *newton_capped,
-                      uint64_t *tail_draws, uint64_t *global_sorts);
+                      uint64_t *tail_draws, uint64_t *global_sorts,
+                      uint64_t *fit_fallbacks);
 
 /* Tracing (no counterpart in the paper, which times whole runs with clock()).
  * With tracing on, pl_ks_cutoffs and pl_bootstrap_pvalue record CUDA events

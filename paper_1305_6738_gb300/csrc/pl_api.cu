@@ -132,7 +132,18 @@ CellConst cell_const(uint64_t xmin) {
   CellConst c;
   c.ln_xmin_half = std::log((double)xmin - 0.5);
   c.ln_allmin = std::log1p(1.0 / (double)xmin);
+  c.ln_xmin = std::log((double)xmin);
   return c;
+}
+
+FitTable make_fit_table(Carver &cv, uint64_t xmin) {
+  FitTable f{};
+  f.xmin = xmin;
+  f.nodes = kFitNodes;
+  f.guides = kFitGuides;
+  f.node = cv.take<FitNode>(kFitNodes);
+  f.guide = cv.take<int>(kFitGuides);
+  return f;
 }
 
 uint32_t hist_bins(int64_t n) {
@@ -149,6 +160,7 @@ uint64_t next_pow2(uint64_t v) {
 
 // Everything one batch of replicate cells needs on the device.
 struct SimPlan {
+  std::vector<uint64_t> fit_xmins;
   std::vector<LawPlan> laws;
   std::vector<Cell> cells;
   std::vector<CellConst> consts;
@@ -159,6 +171,7 @@ struct SimPlan {
 
 pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpose, SimPlan &sp) {
   std::map<std::pair<double, uint64_t>, uint32_t> law_of;
+  std::map<uint64_t, uint32_t> fit_of;
   std::vector<double> law_draws;
   sp.cells.resize(ncells);
   sp.consts.resize(ncells);
@@ -194,6 +207,12 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     cd.H = hist_bins(x.n);
     cd.purpose = purpose;
     cd.out_off = sp.total_R;
+    auto fi = fit_of.find(x.xmin);
+    if (fi == fit_of.end()) {
+      fi = fit_of.emplace(x.xmin, (uint32_t)sp.fit_xmins.size()).first;
+      sp.fit_xmins.push_back(x.xmin);
+    }
+    cd.fit = fi->second;
     sp.total_R += x.replicates;
     sp.n_max = std::max(sp.n_max, x.n);
     sp.consts[c] = cell_const(x.xmin);
@@ -215,6 +234,8 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
 }
 
 struct SimBuffers {
+  FitTable *fits_dev;
+  std::vector<FitTable> fits_host;
   Law *laws_dev;
   std::vector<Law> laws_host;
   Cell *cells;
@@ -227,6 +248,9 @@ struct SimBuffers {
 
 // Lay out (or size) the device buffers of a simulation plan.
 void carve_sim(Carver &cv, const SimPlan &sp, int blocks, SimBuffers &b) {
+  b.fits_host.clear();
+  for (uint64_t xm : sp.fit_xmins) b.fits_host.push_back(make_fit_table(cv, xm));
+  b.fits_dev = cv.take<FitTable>(sp.fit_xmins.size());
   b.laws_host.clear();
   for (const auto &lp : sp.laws) b.laws_host.push_back(carve_law(cv, lp));
   b.laws_dev = cv.take<Law>(sp.laws.size());
@@ -247,8 +271,11 @@ pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t
                           cudaMemcpyHostToDevice, st));
   PL_CUDA(cudaMemcpyAsync(b.items, sp.items.data(), sizeof(WorkItem) * sp.items.size(),
                           cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(b.fits_dev, b.fits_host.data(), sizeof(FitTable) * b.fits_host.size(),
+                          cudaMemcpyHostToDevice, st));
   PL_CUDA(launch_law_setup(b.laws_dev, (int)b.laws_host.size(), st));
-  ctx->launches += 3;
+  PL_CUDA(launch_fit_tables(b.fits_dev, (int)b.fits_host.size(), st));
+  ctx->launches += 5;
   return PL_OK;
 }
 
@@ -259,6 +286,7 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
   wl.cells = b.cells;
   wl.consts = b.consts;
   wl.laws = b.laws_dev;
+  wl.fits = b.fits_dev;
   wl.items = b.items;
   wl.nitems = (uint32_t)sp.items.size();
   wl.seed = seed;
@@ -377,7 +405,7 @@ pl_status pl_sync(pl_ctx *ctx, void *stream) {
 }
 
 pl_status pl_counters(pl_ctx *ctx, void *stream, uint64_t *newton_capped, uint64_t *tail_draws,
-                      uint64_t *global_sorts) {
+                      uint64_t *global_sorts, uint64_t *fit_fallbacks) {
   if (pl_status s = check_ctx(ctx)) return s;
   PL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   Counters c{};
@@ -385,6 +413,7 @@ pl_status pl_counters(pl_ctx *ctx, void *stream, uint64_t *newton_capped, uint64
   if (newton_capped) *newton_capped = c.newton_capped;
   if (tail_draws) *tail_draws = c.tail_draws;
   if (global_sorts) *global_sorts = c.global_sorts;
+  if (fit_fallbacks) *fit_fallbacks = c.fit_fallbacks;
   return PL_OK;
 }
 

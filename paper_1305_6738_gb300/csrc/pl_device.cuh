@@ -15,7 +15,13 @@ namespace pl {
 // ---------------------------------------------------------------------------
 // Sizes of the on-chip structures.
 constexpr uint64_t kXCap = 1ull << 62;      // simulated values saturate here
-constexpr int kL1 = 2048;                   // thresholds staged in shared memory
+#ifndef PL_L1_ENTRIES
+#define PL_L1_ENTRIES 2048
+#endif
+#ifndef PL_WARP_MIN_BLOCKS
+#define PL_WARP_MIN_BLOCKS 2
+#endif
+constexpr int kL1 = PL_L1_ENTRIES;          // thresholds staged in shared memory
 constexpr int kGuideBits = 11;              // guide table: 2^11 buckets of m
 constexpr int kGuide = 1 << kGuideBits;
 constexpr int kHMax = 1024;                 // dense histogram bins per warp
@@ -33,6 +39,7 @@ struct Counters {
   unsigned long long newton_capped;
   unsigned long long tail_draws;
   unsigned long long global_sorts;
+  unsigned long long fit_fallbacks;          // replicates fitted by the full Newton iteration
   unsigned int status;
   unsigned int work_next;                   // persistent-kernel work counter
 };
@@ -44,6 +51,8 @@ struct Law {
   uint64_t xmin;
   uint32_t L2;            // table length (>= kL1, multiple of kL1)
   uint32_t pad;
+  float tail_c;           // (alpha - 1) Z, binary32: continuous tail approximation
+  float tail_e;           // -1 / (alpha - 1)
   uint64_t *T;            // T[i] = floor(Q(xmin+i) 2^53) + 1, Q(k) = P(X > k)
   uint32_t *guide;        // guide[j] = min{i : T[i] <= (j+1) 2^(53-g)} (or L2)
   double *lnT;            // ln(xmin + i), i < kLnTable
@@ -61,6 +70,8 @@ struct Cell {
   uint32_t H;             // dense histogram bins in use (<= kHMax)
   uint32_t purpose;
   int64_t out_off;        // offset of replicate 0 in the per-replicate outputs
+  uint32_t fit;           // index into the fit-table array (one per xmin)
+  uint32_t pad;
 };
 
 struct WorkItem {
@@ -181,6 +192,133 @@ __device__ __forceinline__ double survival(double alpha, double Z, uint64_t k) {
   return hurwitz_precise(alpha, (double)k + 1.0) / Z;
 }
 
+
+// ---------------------------------------------------------------------------
+// Single-evaluation form used by the Newton polish: 12 Bernoulli terms and
+// N = max(a, ceil(7 + 0.75 s)) (warp-uniform, passed in), which keeps the first
+// omitted term below 2^-56 of the tail for every s > 1.  For a = 1 and
+// N <= 16 the direct terms k^-s are formed from exp(-s ln p) at the primes
+// p = 2, 3, 5, 7, 11, 13 and products for the composites.
+static __constant__ double c_bern12[12] = {
+    1.0 / 12.0, -1.0 / 720.0, 1.0 / 30240.0, -1.0 / 1209600.0, 1.0 / 47900160.0,
+    -691.0 / 1307674368000.0, 1.0 / 74724249600.0, -3617.0 / 10670622842880000.0,
+    8.586062056277845e-15, -2.174868698558062e-16, 5.5090028283602295e-18,
+    -1.3954464685812522e-19};
+static __constant__ double c_ln_small[17] = {
+    0.0,
+    0.0,
+    0.6931471805599453,
+    1.0986122886681098,
+    1.3862943611198906,
+    1.6094379124341003,
+    1.791759469228055,
+    1.9459101490553132,
+    2.0794415416798357,
+    2.1972245773362196,
+    2.302585092994046,
+    2.3978952727983707,
+    2.4849066497880004,
+    2.5649493574615367,
+    2.6390573296152584,
+    2.70805020110221,
+    2.772588722239781};
+
+__device__ __forceinline__ int polish_shift_n(double s, uint64_t a) {
+  const int n = (int)ceil(7.0 + 0.75 * s);
+  return (uint64_t)n > a ? n : (int)a;
+}
+
+__device__ __forceinline__ void polish_direct_term(double t, double lk, double &z0, double &z1,
+                                                   double &z2) {
+  z0 += t;
+  z1 -= lk * t;
+  z2 += lk * lk * t;
+}
+
+// zeta(s, a), zeta', zeta'' with the warp-uniform shift Nw >= polish_shift_n(s, a).
+__device__ __forceinline__ void hurwitz_polish(double s, uint64_t a, int Nw, const double *lnT,
+                                               double *z) {
+  double z0 = 0.0, z1 = 0.0, z2 = 0.0;
+  if (a == 1 && Nw <= 16) {
+    const double t2 = exp(-s * c_ln_small[2]);
+    const double t3 = exp(-s * c_ln_small[3]);
+    const double t5 = exp(-s * c_ln_small[5]);
+    const double t7 = exp(-s * c_ln_small[7]);
+    z0 = 1.0;  // k = 1
+    polish_direct_term(t2, c_ln_small[2], z0, z1, z2);
+    if (Nw > 3) polish_direct_term(t3, c_ln_small[3], z0, z1, z2);
+    if (Nw > 4) polish_direct_term(t2 * t2, c_ln_small[4], z0, z1, z2);
+    if (Nw > 5) polish_direct_term(t5, c_ln_small[5], z0, z1, z2);
+    if (Nw > 6) polish_direct_term(t2 * t3, c_ln_small[6], z0, z1, z2);
+    if (Nw > 7) polish_direct_term(t7, c_ln_small[7], z0, z1, z2);
+    if (Nw > 8) polish_direct_term(t2 * t2 * t2, c_ln_small[8], z0, z1, z2);
+    if (Nw > 9) polish_direct_term(t3 * t3, c_ln_small[9], z0, z1, z2);
+    if (Nw > 10) polish_direct_term(t2 * t5, c_ln_small[10], z0, z1, z2);
+    if (Nw > 11) polish_direct_term(exp(-s * c_ln_small[11]), c_ln_small[11], z0, z1, z2);
+    if (Nw > 12) polish_direct_term(t2 * t2 * t3, c_ln_small[12], z0, z1, z2);
+    if (Nw > 13) polish_direct_term(exp(-s * c_ln_small[13]), c_ln_small[13], z0, z1, z2);
+    if (Nw > 14) polish_direct_term(t2 * t7, c_ln_small[14], z0, z1, z2);
+    if (Nw > 15) polish_direct_term(t3 * t5, c_ln_small[15], z0, z1, z2);
+  } else {
+    for (uint64_t k = a; k < (uint64_t)Nw; ++k) {
+      const double lk = lnT[k - a];
+      polish_direct_term(exp(-s * lk), lk, z0, z1, z2);
+    }
+  }
+  const double N = (double)Nw;
+  const uint64_t ni = (uint64_t)Nw - a;
+  const double L = (a == 1 && Nw <= 16) ? c_ln_small[Nw] : lnT[ni];
+  const double Ns = exp(-s * L);
+  const double u = 1.0 / (s - 1.0);
+  const double N1s = N * Ns;
+  z0 += N1s * u + 0.5 * Ns;
+  z1 += -N1s * (L * u + u * u) - 0.5 * L * Ns;
+  z2 += N1s * (L * L * u + 2.0 * L * u * u + 2.0 * u * u * u) + 0.5 * L * L * Ns;
+  const double inv_n2 = 1.0 / (N * N);
+  double w = Ns / N;
+  double P = s, dP = 1.0, d2P = 0.0;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    const double c = c_bern12[j] * w;
+    z0 += c * P;
+    z1 += c * (dP - L * P);
+    z2 += c * (d2P - 2.0 * L * dP + L * L * P);
+#pragma unroll
+    for (int f = 2 * j + 1; f <= 2 * j + 2; ++f) {
+      const double g = s + (double)f;
+      d2P = d2P * g + 2.0 * dP;
+      dP = dP * g + P;
+      P *= g;
+    }
+    w *= inv_n2;
+  }
+  z[0] = z0;
+  z[1] = z1;
+  z[2] = z2;
+}
+
+// Inverse of the MLE equation per lower end xmin, for the Newton start.
+// Nodes at a uniform grid of t = ln(alpha - 1) (alpha from 60 down to
+// 1.003), ordered by increasing u = ln(h), h = E[ln(X / xmin)] =
+// -zeta'/zeta - ln xmin; each node holds (u, alpha, d alpha/du = -h/Var(ln X),
+// 1/(u_next - u)) from one Euler-Maclaurin evaluation.  A guide table over a
+// uniform u grid points to the node at or below each bin start.  Lookup:
+// guide, a short forward scan, cubic Hermite interpolation in u.
+struct FitNode {
+  double u, alpha, dadu, inv_du;
+};
+struct FitTable {
+  uint64_t xmin;
+  int nodes;
+  int guides;
+  double ug0, inv_dug;     // guide grid: bin b starts at ug0 + b / inv_dug
+  FitNode *node;
+  int *guide;
+};
+constexpr int kFitNodes = 4096;
+constexpr int kFitGuides = 4096;
+constexpr double kFitAlphaHi = 60.0, kFitAlphaLo = 1.003;
+
 // ---------------------------------------------------------------------------
 // Inverse CDF.  X = min(2^62, min{k >= xmin : Q(k) < v}), v = m 2^-53.
 // Table region: T[i] <= m  <=>  Q(xmin+i) < v (T[i] = floor(Q 2^53) + 1 and
@@ -241,20 +379,65 @@ bisect:
 }
 
 // Table search: sT / sG are the shared-memory copies of T[0..kL1) and guide.
-__device__ __forceinline__ uint64_t lookup(const uint64_t *sT, const uint32_t *sG,
-                                           const uint64_t *gT, uint32_t L2, uint64_t xmin,
-                                           double alpha, double Z, uint64_t m,
-                                           unsigned long long *tail_counter) {
+// Returns xmin + i, or kTailTag | m when the answer lies beyond the table (the
+// caller resolves those with tail_invert).  A wide guide bucket (heavy tail)
+// is first narrowed around the continuous-approximation guess
+// k + 1/2 ~ ((alpha - 1) Z v)^(-1/(alpha-1)) in binary32, then by galloping;
+// the final answer always comes from exact integer comparisons with T.
+constexpr uint64_t kTailTag = 1ull << 63;
+
+__device__ __forceinline__ uint64_t table_at(const uint64_t *sT, const uint64_t *gT, uint32_t i) {
+  return i < (uint32_t)kL1 ? sT[i] : __ldg(gT + i);
+}
+
+__device__ __forceinline__ uint64_t lookup_fast(const uint64_t *sT, const uint32_t *sG,
+                                                const uint64_t *gT, uint32_t L2, uint64_t xmin,
+                                                float tail_c, float tail_e, uint64_t m) {
   const uint32_t j = (uint32_t)((m - 1ull) >> (53 - kGuideBits));
   uint32_t lo = sG[j];
   uint32_t hi = j ? sG[j - 1] : L2;
+  if (hi - lo > 8) {
+    const float v = (float)m * 0x1p-53f;
+    const float kf = exp2f(tail_e * __log2f(tail_c * v)) - 0.5f - (float)xmin;
+    uint32_t g = lo;
+    if (kf >= (float)hi) g = hi - 1;
+    else if (kf > (float)lo) g = (uint32_t)kf;
+    if (table_at(sT, gT, g) <= m) {  // answer in [lo, g]: gallop down
+      hi = g;
+      for (uint32_t d = 1; d < 64u && hi > lo; d <<= 1) {
+        const uint32_t c = hi - lo > d ? hi - d : lo;
+        if (table_at(sT, gT, c) <= m) hi = c;
+        else {
+          lo = c + 1;
+          break;
+        }
+      }
+    } else {  // answer in [g + 1, hi]: gallop up
+      lo = g + 1;
+      for (uint32_t d = 1; d < 64u && lo < hi; d <<= 1) {
+        const uint32_t c = hi - lo > d ? lo + d - 1 : hi - 1;
+        if (table_at(sT, gT, c) <= m) {
+          hi = c;
+          break;
+        }
+        lo = c + 1;
+      }
+    }
+  }
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    const uint64_t t = mid < (uint32_t)kL1 ? sT[mid] : __ldg(gT + mid);
-    if (t <= m) hi = mid;
+    if (table_at(sT, gT, mid) <= m) hi = mid;
     else lo = mid + 1;
   }
-  if (lo < L2) return xmin + lo;
+  return lo < L2 ? xmin + lo : (kTailTag | m);
+}
+
+__device__ __forceinline__ uint64_t lookup(const uint64_t *sT, const uint32_t *sG,
+                                           const uint64_t *gT, uint32_t L2, uint64_t xmin,
+                                           double alpha, double Z, float tail_c, float tail_e,
+                                           uint64_t m, unsigned long long *tail_counter) {
+  const uint64_t x = lookup_fast(sT, sG, gT, L2, xmin, tail_c, tail_e, m);
+  if (!(x & kTailTag)) return x;
   atomicAdd(tail_counter, 1ull);
   return tail_invert(alpha, Z, xmin + L2, m);
 }

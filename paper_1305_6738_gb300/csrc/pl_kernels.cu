@@ -16,7 +16,13 @@ namespace pl {
 
 __global__ void law_z_kernel(Law *laws, int nlaws) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nlaws) laws[i].Z = hurwitz_precise(laws[i].alpha, (double)laws[i].xmin);
+  if (i < nlaws) {
+    const double a = laws[i].alpha;
+    const double Z = hurwitz_precise(a, (double)laws[i].xmin);
+    laws[i].Z = Z;
+    laws[i].tail_c = (float)((a - 1.0) * Z);
+    laws[i].tail_e = (float)(-1.0 / (a - 1.0));
+  }
 }
 
 // T[i] = floor(Q(xmin+i) 2^53) + 1 and the log tables of xmin + i.
@@ -115,8 +121,8 @@ __global__ void __launch_bounds__(256) sample_kernel(const Law *law_p, uint64_t 
       const int64_t i = 2 * p + j;
       if (i < n) {
         const uint64_t m = draw_bits(j ? w.z : w.x, j ? w.w : w.y);
-        out[r * n + i] = lookup(s.sT, s.sG, law.T, law.L2, law.xmin, law.alpha, law.Z, m,
-                                &ctr->tail_draws);
+        out[r * n + i] = lookup(s.sT, s.sG, law.T, law.L2, law.xmin, law.alpha, law.Z, law.tail_c,
+                                law.tail_e, m, &ctr->tail_draws);
       }
     }
   }
@@ -142,6 +148,7 @@ cudaError_t launch_sample(const Law *law_dev, uint64_t seed, uint32_t cell_id, u
 // variance of ln X), safeguarded by bisection on (1 + 2^-40, 64], stopped when
 // a step is within 4 ulp.  Returns the number of iterations (kNewtonCap + 1
 // if the cap was hit); *Z receives zeta(alpha-hat, xmin).
+template <bool PRECISE = false>
 __device__ int newton_mle(double mbar, uint64_t xmin, double ln_xmin_half, const double *lnT,
                           double *alpha_hat, double *Z) {
   double lo = 1.0 + 0x1p-40, hi = 64.0;
@@ -151,7 +158,7 @@ __device__ int newton_mle(double mbar, uint64_t xmin, double ln_xmin_half, const
   int it = 1;
   for (; it <= kNewtonCap; ++it) {
     double z[3];
-    hurwitz_em<2, false>(a, x0, z, lnT, x0, kLnTable);
+    hurwitz_em<2, PRECISE>(a, x0, z, lnT, x0, kLnTable);
     const double g = z[1] / z[0];
     const double f = g + mbar;
     const double fp = z[2] / z[0] - g * g;
@@ -166,9 +173,62 @@ __device__ int newton_mle(double mbar, uint64_t xmin, double ln_xmin_half, const
   }
   *alpha_hat = a;
   double z0;
-  hurwitz_em<0, false>(a, x0, &z0, lnT, x0, kLnTable);
+  hurwitz_em<0, PRECISE>(a, x0, &z0, lnT, x0, kLnTable);
   *Z = z0;
   return it;
+}
+
+// ---------------------------------------------------------------------------
+// Fit tables (one Euler-Maclaurin evaluation per node, pow-based).
+__global__ void fit_nodes_kernel(FitTable *fts) {
+  const FitTable ft = fts[blockIdx.y];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ft.nodes) return;
+  const double t_hi = log(kFitAlphaHi - 1.0), t_lo = log(kFitAlphaLo - 1.0);
+  const double t = t_hi - (t_hi - t_lo) * (double)k / (double)(ft.nodes - 1);
+  const double a = 1.0 + exp(t);
+  const double x0 = (double)ft.xmin;
+  double z[3];
+  hurwitz_em<2, true>(a, x0, z);
+  const double g = z[1] / z[0];
+  const double h = -g - log(x0);
+  const double var = z[2] / z[0] - g * g;
+  FitNode &nd = ft.node[k];
+  nd.u = log(h);
+  nd.alpha = a;
+  nd.dadu = -h / var;
+}
+
+// inv_du of each interval, and the guide: guide[b] = max{k : u_k <= ug0 + b du_g}.
+__global__ void fit_guide_kernel(FitTable *fts) {
+  FitTable &ftr = fts[blockIdx.y];
+  const FitTable ft = ftr;
+  const double u_first = ft.node[0].u, u_last = ft.node[ft.nodes - 1].u;
+  const double dug = (u_last - u_first) / (double)ft.guides;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ftr.ug0 = u_first;
+    ftr.inv_dug = 1.0 / dug;
+  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ft.nodes - 1) ft.node[i].inv_du = 1.0 / (ft.node[i + 1].u - ft.node[i].u);
+  if (i < ft.guides) {
+    const double ub = u_first + dug * (double)i;
+    int lo = 0, hi = ft.nodes - 1;  // last k with u_k <= ub
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ft.node[mid].u <= ub) lo = mid;
+      else hi = mid - 1;
+    }
+    ft.guide[i] = lo;
+  }
+}
+
+cudaError_t launch_fit_tables(FitTable *fts_dev, int nfit, cudaStream_t st) {
+  if (nfit <= 0) return cudaSuccess;
+  fit_nodes_kernel<<<dim3((kFitNodes + 127) / 128, nfit), 128, 0, st>>>(fts_dev);
+  const int n = kFitNodes > kFitGuides ? kFitNodes : kFitGuides;
+  fit_guide_kernel<<<dim3((n + 127) / 128, nfit), 128, 0, st>>>(fts_dev);
+  return cudaGetLastError();
 }
 
 // ln(a) of a uint64 as a float pair hi + lo: exponent * ln2 (split) + ln(mantissa).
@@ -217,6 +277,66 @@ __device__ __forceinline__ FitOut fit_from_logsum(double L, int64_t n, uint64_t 
     o.invZ = (float)(1.0 / o.Z);
     o.lnZ = (float)log(o.Z);
     o.lnc = (float)log((o.ahat - 1.0) * o.Z);
+  }
+  return o;
+}
+
+// Lane-parallel fit (one replicate per lane; every lane of the warp calls it,
+// lanes without a replicate pass a harmless log-sum).  The Newton start comes
+// from the fit table's cubic Hermite interpolation (error ~1e-12), so one
+// Euler-Maclaurin evaluation at the start gives the FP64 root (the step's
+// error is quadratic in the start's), and zeta(alpha-hat) follows from the
+// same evaluation by a second-order Taylor step.  A start outside the table
+// or a step larger than 1e-8 alpha falls back to the full iteration.
+__device__ __forceinline__ FitOut fit_lanes(double L, int64_t n, uint64_t xmin, const CellConst &cc,
+                                            const FitTable &ft, const double *lnT, bool f32,
+                                            Counters *ctr) {
+  const double mbar = L / (double)n;
+  const double h = mbar - cc.ln_xmin;
+  bool ok = false;
+  double a0 = 1.2;
+  if (h > 0.0) {
+    const double u = log(h);
+    const double pos = (u - ft.ug0) * ft.inv_dug;
+    if (pos >= 0.0 && pos < (double)ft.guides) {
+      int k = ft.guide[(int)pos];
+      for (int it = 0; it < 16 && k + 1 < ft.nodes - 1 && ft.node[k + 1].u <= u; ++it) ++k;
+      const FitNode A = ft.node[k], B = ft.node[k + 1];
+      if (u >= A.u && u <= B.u) {
+        const double du = B.u - A.u;
+        const double t = (u - A.u) * A.inv_du, t2 = t * t, t3 = t2 * t;
+        a0 = (2.0 * t3 - 3.0 * t2 + 1.0) * A.alpha + (t3 - 2.0 * t2 + t) * du * A.dadu +
+             (3.0 * t2 - 2.0 * t3) * B.alpha + (t3 - t2) * du * B.dadu;
+        ok = true;
+      }
+    }
+  }
+  const int Nw = __reduce_max_sync(0xffffffffu, (unsigned)polish_shift_n(a0, xmin));
+  double z[3];
+  hurwitz_polish(a0, xmin, Nw, lnT, z);
+  FitOut o;
+  if (ok) {
+    const double inv = 1.0 / z[0];
+    const double g = z[1] * inv;
+    const double step = (g + mbar) / (z[2] * inv - g * g);
+    if (fabs(step) <= 1e-8 * a0) {
+      o.ahat = a0 - step;
+      o.Z = z[0] - step * (z[1] - 0.5 * step * z[2]);
+    } else {
+      ok = false;
+    }
+  }
+  if (!ok) {
+    atomicAdd(&ctr->fit_fallbacks, 1ull);
+    const int it = newton_mle(mbar, xmin, cc.ln_xmin_half, lnT, &o.ahat, &o.Z);
+    if (it > kNewtonCap) atomicAdd(&ctr->newton_capped, 1ull);
+  }
+  if (f32) {
+    o.a_hi = (float)o.ahat;
+    o.a_lo = (float)(o.ahat - (double)o.a_hi);
+    o.invZ = (float)(1.0 / o.Z);
+    o.lnZ = logf((float)o.Z);
+    o.lnc = logf((float)((o.ahat - 1.0) * o.Z));
   }
   return o;
 }
@@ -412,7 +532,7 @@ __device__ int64_t spill_compact(uint64_t *spill, uint32_t *onchip, int64_t s, u
 //   phase 3 (warp per replicate): KS distance.
 // If the arena fills up, phases 2-3 run early for the replicates already in it.
 template <bool F32>
-__global__ void __launch_bounds__(kWarps * 32) replicate_warp_kernel(WarpLaunch a) {
+__global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) replicate_warp_kernel(WarpLaunch a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
   uint32_t *sG = reinterpret_cast<uint32_t *>(smem + kL1 * 8);
@@ -458,9 +578,12 @@ __global__ void __launch_bounds__(kWarps * 32) replicate_warp_kernel(WarpLaunch 
       size_t my_off = 0;
       size_t arena_off = 0;
       int done = 0;
+      const FitTable &ft = a.fits[cell.fit];
       auto finish = [&](int b0, int b1) {
-        FitOut fo{};
-        if (lane >= b0 && lane < b1) fo = fit_from_logsum(myL, n, xmin, cc, law.lnT, F32, a.ctr);
+        const bool mine = lane >= b0 && lane < b1;
+        // lanes without a replicate fit a stand-in log-sum (mean log excess 1/2)
+        const double Lfit = mine ? myL : (double)n * (cc.ln_xmin + 0.5);
+        const FitOut fo = fit_lanes(Lfit, n, xmin, cc, ft, law.lnT, F32, a.ctr);
         double myD = 0.0;
         for (int r = b0; r < b1; ++r) {
           const FitOut fr = shfl_fit(fo, r);
@@ -495,8 +618,8 @@ __global__ void __launch_bounds__(kWarps * 32) replicate_warp_kernel(WarpLaunch 
           for (int j = 0; j < 2; ++j) {
             if (2 * p + j < n) {
               const uint64_t m = draw_bits(j ? w.z : w.x, j ? w.w : w.y);
-              const uint64_t X = lookup(sT, sG, law.T, law.L2, xmin, law.alpha, law.Z, m,
-                                        &a.ctr->tail_draws);
+              // beyond-table draws come back tagged; they always spill and are resolved below
+              const uint64_t X = lookup_fast(sT, sG, law.T, law.L2, xmin, law.tail_c, law.tail_e, m);
               const uint64_t b = X - xmin;
               if (b < 4) packed += 1ull << (16 * b);
               else if (b < (uint64_t)H) atomicAdd(&hist[b], 1u);
@@ -516,6 +639,15 @@ __global__ void __launch_bounds__(kWarps * 32) replicate_warp_kernel(WarpLaunch 
         }
         __syncwarp();
         const int64_t s = s_spill[warp];
+        // resolve the draws that fell beyond the threshold table (binary64 inversion)
+        for (int64_t k = lane; k < s; k += 32) {
+          const uint64_t x = spill[k];
+          if (x & kTailTag) {
+            atomicAdd(&a.ctr->tail_draws, 1ull);
+            spill[k] = tail_invert(law.alpha, law.Z, xmin + law.L2, x & ~kTailTag);
+          }
+        }
+        __syncwarp();
         const int64_t tmax = warp_max_i64(lmax);
         // log-sum  L = sum ln x_i  (+ ln((xmin+1)/xmin) if every x_i = xmin)
         double L;

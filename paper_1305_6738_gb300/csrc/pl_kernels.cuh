@@ -13,7 +13,10 @@ namespace pl {
 struct CellConst {
   double ln_xmin_half;  // ln(xmin - 1/2): start of the Newton iteration
   double ln_allmin;     // ln((xmin + 1) / xmin): the all-equal rule
+  double ln_xmin;       // ln(xmin)
 };
+
+cudaError_t launch_fit_tables(FitTable *fts_dev, int nfit, cudaStream_t st);
 
 cudaError_t launch_law_setup(Law *laws_dev, int nlaws, cudaStream_t st);
 
@@ -25,6 +28,7 @@ struct WarpLaunch {
   const Cell *cells;
   const CellConst *consts;
   const Law *laws;
+  const FitTable *fits;
   const WorkItem *items;
   uint32_t nitems;
   uint64_t seed;

@@ -14,7 +14,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libpl.so")
+LIB_PATH = os.environ.get("PL_LIB_PATH") or os.path.join(_HERE, "_build", "libpl.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
@@ -52,7 +52,7 @@ _lib.pl_destroy.restype = None
 _lib.pl_last_error.argtypes = [_vp]
 _lib.pl_last_error.restype = ctypes.c_char_p
 _lib.pl_sync.argtypes = [_vp, _vp]
-_lib.pl_counters.argtypes = [_vp, _vp, _u64p, _u64p, _u64p]
+_lib.pl_counters.argtypes = [_vp, _vp, _u64p, _u64p, _u64p, _u64p]
 _lib.pl_set_tracing.argtypes = [_vp, ctypes.c_int]
 _lib.pl_trace.argtypes = [_vp, _vp, ctypes.POINTER(pl_trace_info)]
 _lib.pl_sample.argtypes = [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
@@ -134,10 +134,11 @@ class Context:
         self._check(_lib.pl_sync(self._h, _stream_ptr(stream)))
 
     def pl_counters(self, stream=None) -> dict:
-        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        a, b, c, d = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         self._check(_lib.pl_counters(self._h, _stream_ptr(stream), ctypes.byref(a), ctypes.byref(b),
-                                     ctypes.byref(c)))
-        return {"newton_capped": a.value, "tail_draws": b.value, "global_sorts": c.value}
+                                     ctypes.byref(c), ctypes.byref(d)))
+        return {"newton_capped": a.value, "tail_draws": b.value, "global_sorts": c.value,
+                "fit_fallbacks": d.value}
 
     def pl_set_tracing(self, on: bool = True):
         self._check(_lib.pl_set_tracing(self._h, 1 if on else 0))
