@@ -28,7 +28,8 @@ struct pl_ctx {
   size_t ws_size = 0;
   Counters *ctr = nullptr;
   int num_sms = 0;
-  int warp_blocks_per_sm[2] = {0, 0};
+  int finish_blocks_per_sm[2] = {0, 0};
+  int sample_blocks_per_sm = 0;
   uint64_t launches = 0;
   bool tracing = false;
   bool traced = false;
@@ -152,6 +153,18 @@ uint32_t hist_bins(int64_t n) {
   return (uint32_t)H;
 }
 
+// Spill slot of a replicate record: about twice the expected number of draws
+// at or beyond xmin + H plus ten standard deviations (continuous tail
+// approximation); a replicate that overflows it is drawn again by the finisher.
+uint32_t spill_capacity(double alpha, uint64_t xmin, int64_t n, uint32_t H) {
+  const double x = (double)xmin;
+  const double Zapprox = std::pow(x, -alpha) + std::pow(x + 0.5, 1.0 - alpha) / (alpha - 1.0);
+  const double Q = std::pow(x + H - 0.5, 1.0 - alpha) / ((alpha - 1.0) * Zapprox);
+  const double mu = (double)n * std::min(1.0, Q);
+  const double cap = std::ceil(2.0 * mu + 10.0 * std::sqrt(mu) + 32.0);
+  return (uint32_t)std::max<double>(1.0, std::min<double>((double)n, cap));
+}
+
 uint64_t next_pow2(uint64_t v) {
   uint64_t p = 1;
   while (p < v) p <<= 1;
@@ -159,12 +172,19 @@ uint64_t next_pow2(uint64_t v) {
 }
 
 // Everything one batch of replicate cells needs on the device.
+struct Wave {
+  size_t first, count;             // items [first, first + count)
+};
+
 struct SimPlan {
+  uint32_t tail_cap = 0;           // tail-queue entries (largest wave)
   std::vector<uint64_t> fit_xmins;
   std::vector<LawPlan> laws;
   std::vector<Cell> cells;
   std::vector<CellConst> consts;
   std::vector<WorkItem> items;
+  std::vector<Wave> waves;
+  size_t dense_elems = 0, spill_elems = 0, meta_elems = 0;  // largest wave
   int64_t total_R = 0;
   int64_t n_max = 0;
 };
@@ -213,6 +233,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
       sp.fit_xmins.push_back(x.xmin);
     }
     cd.fit = fi->second;
+    cd.scap = spill_capacity(x.alpha, x.xmin, x.n, cd.H);
     sp.total_R += x.replicates;
     sp.n_max = std::max(sp.n_max, x.n);
     sp.consts[c] = cell_const(x.xmin);
@@ -227,9 +248,49 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     if (sp.cells[a].law != sp.cells[b].law) return sp.cells[a].law < sp.cells[b].law;
     return sp.cells[a].n > sp.cells[b].n;
   });
-  const int64_t per_item = (int64_t)kWarps * 32;
-  for (int c : order)
-    for (int64_t r0 = 0; r0 < sp.cells[c].R; r0 += per_item) sp.items.push_back({(uint32_t)c, (uint32_t)r0});
+  // items, and waves whose replicate records fit the wave byte budget
+  const size_t wave_budget = std::min<size_t>(ctx->budget / 4, (size_t)4 << 30);
+  size_t wd = 0, ws = 0, wm = 0, first = 0;
+  double wt = 0.0;  // expected beyond-table draws of the wave
+  auto close_tail = [&]() {
+    const double cap = std::ceil(2.0 * wt + 10.0 * std::sqrt(wt) + 1024.0);
+    sp.tail_cap = std::max<uint32_t>(sp.tail_cap, (uint32_t)std::min(cap, 268435456.0));
+  };
+  for (int c : order) {
+    const Cell &cd = sp.cells[c];
+    const LawPlan &lp = sp.laws[cd.law];
+    const double xq = (double)lp.xmin;
+    const double Zq = std::pow(xq, -lp.alpha) + std::pow(xq + 0.5, 1.0 - lp.alpha) / (lp.alpha - 1.0);
+    const double q_tail = std::min(1.0, std::pow(xq + lp.L2 - 0.5, 1.0 - lp.alpha) / ((lp.alpha - 1.0) * Zq));
+    for (int64_t r0 = 0; r0 < cd.R; r0 += kItemReps) {
+      WorkItem it{};
+      it.cell = (uint32_t)c;
+      it.r0 = (uint32_t)r0;
+      it.nrep = (uint32_t)std::min<int64_t>(kItemReps, cd.R - r0);
+      const size_t d = (size_t)it.nrep * cd.H, sp_ = (size_t)it.nrep * cd.scap, m = it.nrep;
+      const size_t bytes_after = (wd + d) * 2 + (ws + sp_) * 8 + (wm + m) * 8;
+      if (sp.items.size() > first && bytes_after > wave_budget) {
+        sp.waves.push_back({first, sp.items.size() - first});
+        close_tail();
+        first = sp.items.size();
+        wd = ws = wm = 0;
+        wt = 0.0;
+      }
+      wt += (double)it.nrep * (double)cd.n * q_tail;
+      it.dense_off = wd;
+      it.spill_off = ws;
+      it.meta_off = wm;
+      wd += d;
+      ws += sp_;
+      wm += m;
+      sp.dense_elems = std::max(sp.dense_elems, wd);
+      sp.spill_elems = std::max(sp.spill_elems, ws);
+      sp.meta_elems = std::max(sp.meta_elems, wm);
+      sp.items.push_back(it);
+    }
+  }
+  sp.waves.push_back({first, sp.items.size() - first});
+  close_tail();
   return PL_OK;
 }
 
@@ -241,13 +302,17 @@ struct SimBuffers {
   Cell *cells;
   CellConst *consts;
   WorkItem *items;
+  Records rec;
+  uint64_t *tq_pos;
+  uint32_t *tq_law;
+  unsigned int *tq_count;
   uint8_t *scratch;
   size_t spill_cap, arena_bytes;
-  int blocks;
+  int blocks, sample_blocks;
 };
 
 // Lay out (or size) the device buffers of a simulation plan.
-void carve_sim(Carver &cv, const SimPlan &sp, int blocks, SimBuffers &b) {
+void carve_sim(Carver &cv, const SimPlan &sp, int blocks, int sample_blocks, SimBuffers &b) {
   b.fits_host.clear();
   for (uint64_t xm : sp.fit_xmins) b.fits_host.push_back(make_fit_table(cv, xm));
   b.fits_dev = cv.take<FitTable>(sp.fit_xmins.size());
@@ -257,9 +322,16 @@ void carve_sim(Carver &cv, const SimPlan &sp, int blocks, SimBuffers &b) {
   b.cells = cv.take<Cell>(sp.cells.size());
   b.consts = cv.take<CellConst>(sp.consts.size());
   b.items = cv.take<WorkItem>(sp.items.size());
+  b.rec.dense = cv.take<uint16_t>(sp.dense_elems);
+  b.rec.spill = cv.take<uint64_t>(sp.spill_elems);
+  b.rec.meta = cv.take<int2>(sp.meta_elems);
+  b.tq_pos = cv.take<uint64_t>(sp.tail_cap);
+  b.tq_law = cv.take<uint32_t>(sp.tail_cap);
+  b.tq_count = cv.take<unsigned int>(1);
   b.spill_cap = next_pow2((uint64_t)std::max<int64_t>(sp.n_max, kSortSmem));
-  b.arena_bytes = (((size_t)kHMax * 4 + 16 * (size_t)sp.n_max + 16) + (size_t)32 * kHMax * 4 + 255) & ~(size_t)255;
+  b.arena_bytes = ((16 * (size_t)sp.n_max + 16) + (size_t)32 * 2048 + 255) & ~(size_t)255;
   b.blocks = blocks;
+  b.sample_blocks = sample_blocks;
   b.scratch = cv.take<uint8_t>((size_t)blocks * kWarps * (b.spill_cap * 8 + b.arena_bytes));
 }
 
@@ -281,31 +353,54 @@ pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t
 
 pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, bool f32, void *D,
                   double *A, cudaStream_t st) {
-  PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
-  WarpLaunch wl{};
-  wl.cells = b.cells;
-  wl.consts = b.consts;
-  wl.laws = b.laws_dev;
-  wl.fits = b.fits_dev;
-  wl.items = b.items;
-  wl.nitems = (uint32_t)sp.items.size();
-  wl.seed = seed;
-  wl.D_out = D;
-  wl.A_out = A;
-  wl.scratch = b.scratch;
-  wl.spill_cap = b.spill_cap;
-  wl.arena_bytes = b.arena_bytes;
-  wl.ctr = ctx->ctr;
-  wl.blocks = b.blocks;
-  PL_CUDA(launch_replicates_warp(wl, f32, st));
-  ctx->launches += 1;
+  const RoundKeys rk = round_keys(seed);
+  for (const Wave &w : sp.waves) {
+    SampleLaunch sl{};
+    sl.cells = b.cells;
+    sl.laws = b.laws_dev;
+    sl.items = b.items + w.first;
+    sl.nitems = (uint32_t)w.count;
+    sl.rk = rk;
+    sl.rec = b.rec;
+    sl.ctr = ctx->ctr;
+    sl.blocks = (int)std::min<size_t>((size_t)b.sample_blocks, w.count);
+    sl.tq_pos = b.tq_pos;
+    sl.tq_law = b.tq_law;
+    sl.tq_count = b.tq_count;
+    sl.tq_cap = sp.tail_cap;
+    PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
+    PL_CUDA(cudaMemsetAsync(b.tq_count, 0, sizeof(unsigned int), st));
+    PL_CUDA(launch_sample_hist(sl, st));
+    PL_CUDA(launch_tail_queue_raw(b.laws_dev, b.tq_pos, b.tq_law, b.tq_count, sp.tail_cap, b.rec.spill, ctx->ctr,
+                                  ctx->num_sms, st));
+    FinishLaunch fl{};
+    fl.cells = b.cells;
+    fl.consts = b.consts;
+    fl.laws = b.laws_dev;
+    fl.fits = b.fits_dev;
+    fl.items = b.items + w.first;
+    fl.nitems = (uint32_t)w.count;
+    fl.rk = rk;
+    fl.rec = b.rec;
+    fl.D_out = D;
+    fl.A_out = A;
+    fl.scratch = b.scratch;
+    fl.spill_cap = b.spill_cap;
+    fl.arena_bytes = b.arena_bytes;
+    fl.ctr = ctx->ctr;
+    fl.blocks = (int)std::min<size_t>((size_t)b.blocks, w.count);
+    PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
+    PL_CUDA(launch_finish(fl, f32, st));
+    ctx->launches += 3;
+  }
   return PL_OK;
 }
 
-int sim_blocks(pl_ctx *ctx, bool f32, size_t nitems) {
-  const int per_sm = std::max(1, ctx->warp_blocks_per_sm[f32 ? 1 : 0]);
-  return (int)std::max<size_t>(1, std::min<size_t>((size_t)ctx->num_sms * per_sm, nitems));
+int sim_blocks(pl_ctx *ctx, bool f32) {
+  return ctx->num_sms * std::max(1, ctx->finish_blocks_per_sm[f32 ? 1 : 0]);
 }
+
+int sample_blocks(pl_ctx *ctx) { return ctx->num_sms * std::max(1, ctx->sample_blocks_per_sm); }
 
 pl_status mark(pl_ctx *ctx, int i, cudaStream_t st) {
   if (!ctx->tracing) return PL_OK;
@@ -355,8 +450,9 @@ pl_status pl_create(pl_ctx **out, int device, size_t mem_budget_bytes) {
     delete ctx;
     return PL_ECUDA;
   }
-  ctx->warp_blocks_per_sm[0] = warp_kernel_blocks_per_sm(false);
-  ctx->warp_blocks_per_sm[1] = warp_kernel_blocks_per_sm(true);
+  ctx->finish_blocks_per_sm[0] = finish_kernel_blocks_per_sm(false);
+  ctx->finish_blocks_per_sm[1] = finish_kernel_blocks_per_sm(true);
+  ctx->sample_blocks_per_sm = sample_kernel_blocks_per_sm();
   cudaGetLastError();
   *out = ctx;
   return PL_OK;
@@ -512,9 +608,9 @@ pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells, uint64_t 
   if (pl_status s = plan_cells(ctx, cells, ncells, 0u, sp)) return s;
   const bool host_out = !is_device_ptr(cutoffs);
   const size_t dsz = f32 ? 4 : 8;
-  const int blocks = sim_blocks(ctx, f32, sp.items.size());
+  const int blocks = sim_blocks(ctx, f32), sblocks = sample_blocks(ctx);
   auto lay = [&](Carver &cv, SimBuffers &b, void *&D, int64_t *&off, int64_t *&Rs, int64_t *&rank, double *&cut) {
-    carve_sim(cv, sp, blocks, b);
+    carve_sim(cv, sp, blocks, sblocks, b);
     D = D_dev_opt ? D_dev_opt : (void *)cv.take<uint8_t>((size_t)sp.total_R * dsz);
     off = cv.take<int64_t>(ncells);
     Rs = cv.take<int64_t>(ncells);
@@ -572,9 +668,9 @@ pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint
   pl_cell cell{obs[0], xmin, n, B, request_id};
   SimPlan sp;
   if (pl_status s = plan_cells(ctx, &cell, 1, 1u, sp)) return s;
-  const int blocks = sim_blocks(ctx, f32, sp.items.size());
+  const int blocks = sim_blocks(ctx, f32), sblocks = sample_blocks(ctx);
   auto lay = [&](Carver &cv, SimBuffers &b, void *&Db, double *&dobs, double *&pd) {
-    carve_sim(cv, sp, blocks, b);
+    carve_sim(cv, sp, blocks, sblocks, b);
     Db = cv.take<uint8_t>((size_t)B * (f32 ? 4 : 8));
     dobs = cv.take<double>(1);
     pd = cv.take<double>(1);
@@ -605,5 +701,16 @@ pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint
   *p = ph;
   return PL_OK;
 }
+
+#ifdef PL_PHASE_TIMING
+pl_status pl_debug_phase_cycles(pl_ctx *ctx, uint64_t out[8]) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  PL_CUDA(cudaDeviceSynchronize());
+  Counters c{};
+  PL_CUDA(cudaMemcpy(&c, ctx->ctr, sizeof c, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 8; ++i) out[i] = c.phase_cycles[i];
+  return PL_OK;
+}
+#endif
 
 }  // extern "C"

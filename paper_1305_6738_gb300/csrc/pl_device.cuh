@@ -40,8 +40,12 @@ struct Counters {
   unsigned long long tail_draws;
   unsigned long long global_sorts;
   unsigned long long fit_fallbacks;          // replicates fitted by the full Newton iteration
+  unsigned long long resampled;              // replicates whose spill slot overflowed
   unsigned int status;
   unsigned int work_next;                   // persistent-kernel work counter
+#ifdef PL_PHASE_TIMING
+  unsigned long long phase_cycles[8];       // diagnostic build only
+#endif
 };
 
 // One distinct (alpha, xmin): its inverse-CDF thresholds and log tables.
@@ -71,12 +75,20 @@ struct Cell {
   uint32_t purpose;
   int64_t out_off;        // offset of replicate 0 in the per-replicate outputs
   uint32_t fit;           // index into the fit-table array (one per xmin)
-  uint32_t pad;
+  uint32_t scap;          // spill slot capacity of a replicate record
 };
 
+// A block-sized batch of replicates of one cell, with the offsets of its
+// replicate records (dense counts, spill values, meta) in the record buffers.
+constexpr int kItemReps = 256;
 struct WorkItem {
   uint32_t cell;
-  uint32_t r0;            // first replicate of this block-sized batch
+  uint32_t r0;            // first replicate
+  uint32_t nrep;          // replicates in this item (<= kItemReps)
+  uint32_t pad;
+  uint64_t dense_off;     // uint16 index of replicate r0's dense counts
+  uint64_t spill_off;     // uint64 index of replicate r0's spill values
+  uint64_t meta_off;      // index of replicate r0's (tmax, spill count)
 };
 
 // ---------------------------------------------------------------------------
@@ -91,6 +103,36 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
     k.x += 0x9E3779B9u;
     k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// The same generator with the ten round keys precomputed: rk[2r], rk[2r+1]
+// = key + r * (0x9E3779B9, 0xBB67AE85).  The 32x32 -> 64-bit products are
+// taken whole (high and low halves from one multiply).
+struct RoundKeys {
+  uint32_t k[20];
+};
+
+__host__ __device__ inline RoundKeys round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k[2 * r] = k0;
+    rk.k[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const RoundKeys &rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k[2 * r], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ rk.k[2 * r + 1], (uint32_t)p0);
   }
   return c;
 }
@@ -186,10 +228,29 @@ __device__ __forceinline__ double hurwitz_precise(double s, double a) {
   return z;
 }
 
+// zeta(s, a) for large a (a >= 10 + 1.5 s and a >= 1024): Euler-Maclaurin with
+// no direct terms and 4 Bernoulli terms, written around the integral term:
+//   a^(1-s)/(s-1) [1 + (s-1)/(2a) + sum_j B2j/(2j)! s(s+1)..(s+2j-2)(s-1) a^-2j];
+// the first omitted term is below 1e-16 relative for s <= 64.
+__device__ __forceinline__ double hurwitz_large_a(double s, double a) {
+  const double ia2 = 1.0 / (a * a);
+  const double sm1 = s - 1.0;
+  double P = s, w = ia2, br = 1.0 + 0.5 * sm1 / a;
+#pragma unroll
+  for (int j = 1; j <= 4; ++j) {
+    br += bern_coef(j) * P * sm1 * w;
+    P *= (s + (double)(2 * j - 1)) * (s + (double)(2 * j));
+    w *= ia2;
+  }
+  return pow(a, -sm1) / sm1 * br;
+}
+
 // Survival of the law at k: Q(k) = zeta(alpha, k+1) / Z, argument formed as
 // (double)k + 1 (rounded for k > 2^53).
 __device__ __forceinline__ double survival(double alpha, double Z, uint64_t k) {
-  return hurwitz_precise(alpha, (double)k + 1.0) / Z;
+  const double a = (double)k + 1.0;
+  if (a >= 1024.0 && a >= 10.0 + 1.5 * alpha) return hurwitz_large_a(alpha, a) / Z;
+  return hurwitz_precise(alpha, a) / Z;
 }
 
 
@@ -326,8 +387,10 @@ constexpr double kFitAlphaHi = 60.0, kFitAlphaLo = 1.003;
 // bucket j = (m-1) >> (53-g) bounds the answer to [guide[j], guide[j-1]].
 
 // Beyond the table: FP64 evaluation of Q, started from the continuous
-// approximation zeta(s, k+1) ~ (k + 1/2)^(1-s) / (s-1), then exponential
-// search and bisection (every loop bounded by 64 steps).
+// approximation zeta(s, k+1) ~ (k + 1/2)^(1-s) / (s-1), which is within one of
+// the answer beyond a few dozen; the guess is confirmed with
+// Q(k) < v <= Q(k-1) = Q(k) + k^-s / Z.  Otherwise exponential search and
+// bisection (every loop bounded).
 static __device__ __noinline__ uint64_t tail_invert(double alpha, double Z, uint64_t kstart,
                                              uint64_t m) {
   const double v = (double)m * 0x1p-53;
@@ -337,6 +400,10 @@ static __device__ __noinline__ uint64_t tail_invert(double alpha, double Z, uint
   if (!(g < (double)kXCap)) k = kXCap;
   else if (g <= (double)kstart) k = kstart;
   else k = (uint64_t)ceil(g);
+  if (k > kstart && k < kXCap) {
+    const double qk = survival(s, Z, k);
+    if (qk < v && qk + pow((double)k, -s) / Z >= v) return k;
+  }
   uint64_t lo, hi;
   if (survival(s, Z, k) < v) {
     hi = k;
@@ -390,9 +457,10 @@ __device__ __forceinline__ uint64_t table_at(const uint64_t *sT, const uint64_t 
   return i < (uint32_t)kL1 ? sT[i] : __ldg(gT + i);
 }
 
-__device__ __forceinline__ uint64_t lookup_fast(const uint64_t *sT, const uint32_t *sG,
-                                                const uint64_t *gT, uint32_t L2, uint64_t xmin,
-                                                float tail_c, float tail_e, uint64_t m) {
+// Index form: returns i = X - xmin for answers inside the table, L2 beyond it.
+__device__ __forceinline__ uint32_t lookup_index(const uint64_t *sT, const uint32_t *sG,
+                                                 const uint64_t *gT, uint32_t L2, uint64_t xmin,
+                                                 float tail_c, float tail_e, uint64_t m) {
   const uint32_t j = (uint32_t)((m - 1ull) >> (53 - kGuideBits));
   uint32_t lo = sG[j];
   uint32_t hi = j ? sG[j - 1] : L2;
@@ -429,7 +497,14 @@ __device__ __forceinline__ uint64_t lookup_fast(const uint64_t *sT, const uint32
     if (table_at(sT, gT, mid) <= m) hi = mid;
     else lo = mid + 1;
   }
-  return lo < L2 ? xmin + lo : (kTailTag | m);
+  return lo;
+}
+
+__device__ __forceinline__ uint64_t lookup_fast(const uint64_t *sT, const uint32_t *sG,
+                                                const uint64_t *gT, uint32_t L2, uint64_t xmin,
+                                                float tail_c, float tail_e, uint64_t m) {
+  const uint32_t i = lookup_index(sT, sG, gT, L2, xmin, tail_c, tail_e, m);
+  return i < L2 ? xmin + i : (kTailTag | m);
 }
 
 __device__ __forceinline__ uint64_t lookup(const uint64_t *sT, const uint32_t *sG,

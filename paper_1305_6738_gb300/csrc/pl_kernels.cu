@@ -11,6 +11,19 @@
 
 namespace pl {
 
+#ifdef PL_PHASE_TIMING
+#define PL_PHASE(i)                                                                     \
+  do {                                                                                  \
+    const long long t_ = clock64();                                                     \
+    if (lane == 0) atomicAdd(&a.ctr->phase_cycles[i], (unsigned long long)(t_ - pt_)); \
+    pt_ = t_;                                                                           \
+  } while (0)
+#else
+#define PL_PHASE(i) \
+  do {              \
+  } while (0)
+#endif
+
 // ===========================================================================
 // Law tables.
 
@@ -364,8 +377,8 @@ __device__ __forceinline__ FitOut shfl_fit(const FitOut &f, int src) {
 // FP64 form: everything binary64.  FP32 form: p and F in binary32 with
 // compensated (two-sum) prefix sums; Q(v) by a 4-term Euler-Maclaurin in
 // binary32 (v - xmin >= 32 keeps it below 1e-8 relative).
-template <bool F32>
-__device__ double ks_warp(const uint32_t *dense, int64_t tmax, const uint64_t *pairs, int64_t nsd,
+template <bool F32, typename DT>
+__device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, int64_t nsd,
                           int64_t n, const FitOut &f, const double *lnT, const float *lnT_hi,
                           const float *lnT_lo, int lane) {
   if (!F32) {
@@ -406,22 +419,31 @@ __device__ double ks_warp(const uint32_t *dense, int64_t tmax, const uint64_t *p
     return warp_max(best);
   } else {
     const float inv_n = 1.0f / (float)n;
-    float cF_hi = 0.0f, cF_lo = 0.0f, best = 0.0f;
-    int64_t carryC = 0;
-    for (int64_t i0 = 0; i0 <= tmax; i0 += 32) {
-      const int64_t i = i0 + lane;
-      const bool ok = i <= tmax;
-      float ph = ok ? exp_neg_prod(f.a_hi, f.a_lo, lnT_hi[i], lnT_lo[i]) * f.invZ : 0.0f;
-      float pl = 0.0f;
-      warp_scan_ff(ph, pl, lane);
-      ff_add(ph, pl, cF_hi, cF_lo);
-      const int64_t c = ok ? (int64_t)dense[i] : 0;
-      const int64_t C = carryC + warp_scan_i64(c, lane);
-      if (ok) best = fmaxf(best, fabsf(ph - (float)C * inv_n));
-      cF_hi = __shfl_sync(0xffffffffu, ph, 31);
-      cF_lo = __shfl_sync(0xffffffffu, pl, 31);
-      carryC = __shfl_sync(0xffffffffu, C, 31);
+    float best = 0.0f;
+    // dense part, one contiguous chunk of bins per lane: compensated chunk
+    // sums, one warp scan for the chunk offsets, then the running F and C
+    const int64_t nbins = tmax + 1;
+    const int64_t cs = (nbins + 31) >> 5;
+    const int64_t i0 = (int64_t)lane * cs;
+    const int64_t i1 = i0 + cs < nbins ? i0 + cs : nbins;
+    float sh = 0.0f, sl = 0.0f;
+    int64_t sc = 0;
+    for (int64_t i = i0; i < i1; ++i) {
+      ff_add(sh, sl, exp_neg_prod(f.a_hi, f.a_lo, lnT_hi[i], lnT_lo[i]) * f.invZ, 0.0f);
+      sc += (int64_t)dense[i];
     }
+    float eh = sh, el = sl;
+    warp_scan_ff(eh, el, lane);
+    const int64_t incC = warp_scan_i64(sc, lane);
+    float Fh = __shfl_up_sync(0xffffffffu, eh, 1), Fl = __shfl_up_sync(0xffffffffu, el, 1);
+    int64_t C = incC - sc;
+    if (lane == 0) Fh = Fl = 0.0f;
+    for (int64_t i = i0; i < i1; ++i) {
+      ff_add(Fh, Fl, exp_neg_prod(f.a_hi, f.a_lo, lnT_hi[i], lnT_lo[i]) * f.invZ, 0.0f);
+      C += (int64_t)dense[i];
+      best = fmaxf(best, fabsf(Fh - (float)C * inv_n));
+    }
+    int64_t carryC = __shfl_sync(0xffffffffu, incC, 31);
     const float s = f.a_hi;          // exponent, binary32
     const float sm1 = (float)(f.ahat - 1.0);
     for (int64_t k0 = 0; k0 < nsd; k0 += 32) {
@@ -523,16 +545,195 @@ __device__ int64_t spill_compact(uint64_t *spill, uint32_t *onchip, int64_t s, u
 }
 
 // ===========================================================================
-// Warp form: a persistent grid; a block takes a work item (one cell, kWarps*32
-// replicates), stages the law's table in shared memory, and each warp takes
-// 32 replicates:
-//   phase 1 (warp per replicate): draws, histogram, log-sum, compaction of the
-//           histogram and spills into the warp's arena;
-//   phase 2 (lane per replicate): binary64 Newton solve of Eq. 2;
+// The two kernels of a simulation wave.
+//
+// Sampler (many warps, few registers): a block takes a work item (one cell,
+// kItemReps replicates) and stages the law's table in shared memory; each warp
+// draws its replicates (Philox, table search), histograms values below
+// xmin + H in shared memory (two 16-bit bins per word; values xmin..xmin+3 in
+// per-lane register counters) and writes the replicate record: the dense
+// counts, up to scap spilled values (those beyond the table tagged for the
+// finisher), and (tmax, spill count).
+//
+// Finisher: each warp takes 32 replicates of an item:
+//   phase 1 (warp per replicate): resolve tagged tail draws (binary64), the
+//           log-sum, sort and run-length encode the spills into the warp's
+//           arena; a replicate whose spill slot overflowed is drawn again here
+//           with a global spill buffer (same Philox stream, same values);
+//   phase 2 (lane per replicate): binary64 fit (interpolated start + polish);
 //   phase 3 (warp per replicate): KS distance.
-// If the arena fills up, phases 2-3 run early for the replicates already in it.
+constexpr int kAWarps = 16;
+constexpr int kARepsPerWarp = kItemReps / kAWarps;
+constexpr int kBRepsPerWarp = kItemReps / kWarps;
+
+// Draws of one replicate into a histogram.  PACKED: two 16-bit bins per word
+// (hist holds H/2 words); otherwise one 32-bit bin per word.  Spills beyond the
+// capacity are counted but not stored.  Draws beyond the threshold table are
+// stored tagged (kTailTag | m) and, when a queue is given, their positions are
+// queued for the tail kernel.  Returns tmax (the largest bin index below H
+// that was hit, -1 if none) and leaves the spill count in *s_count.
+struct TailQueue {
+  uint64_t *pos;          // element index in the record spill buffer
+  uint32_t *law;          // law of the draw
+  unsigned int *count;
+  uint32_t cap;
+};
+
+template <bool PACKED>
+__device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint32_t *sG, const Law &law,
+                                                  const Cell &cell, uint32_t rep, const RoundKeys &rk,
+                                                  uint32_t *hist, int *s_count, uint64_t *spill,
+                                                  int64_t spill_capacity, int lane,
+                                                  const TailQueue *tq, uint64_t spill_pos0) {
+  const int64_t n = cell.n;
+  const uint64_t xmin = cell.xmin;
+  const uint32_t H = cell.H;
+  const int words = PACKED ? (int)(H / 2) : (int)H;
+  for (int i = lane; i < words; i += 32) hist[i] = 0;
+  if (lane == 0) *s_count = 0;
+  __syncwarp();
+  uint64_t packed = 0;  // 16-bit counters of bins 0..3
+  const int64_t npairs = (n + 1) >> 1;
+  for (int64_t p = lane; p < npairs; p += 32) {
+    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (2 * p + j < n) {
+        const uint64_t m = draw_bits(j ? w.z : w.x, j ? w.w : w.y);
+        const uint32_t b = lookup_index(sT, sG, law.T, law.L2, xmin, law.tail_c, law.tail_e, m);
+        if (b < 4) {
+          packed += 1ull << (16 * b);
+        } else if (b < H) {
+          if (PACKED) atomicAdd(&hist[b >> 1], 1u << ((b & 1u) << 4));
+          else atomicAdd(&hist[b], 1u);
+        } else {
+          const int slot = atomicAdd(s_count, 1);
+          if (slot < spill_capacity) {
+            if (b < law.L2) {
+              spill[slot] = xmin + b;
+            } else {
+              spill[slot] = kTailTag | m;
+              if (tq) {
+                const unsigned q = atomicAdd(tq->count, 1u);
+                if (q < tq->cap) {
+                  tq->pos[q] = spill_pos0 + (uint64_t)slot;
+                  tq->law[q] = cell.law;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  unsigned c[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) c[q] = __reduce_add_sync(0xffffffffu, (unsigned)((packed >> (16 * q)) & 0xffffu));
+  if (lane == 0) {
+    if (PACKED) {
+      hist[0] += c[0] | (c[1] << 16);
+      hist[1] += c[2] | (c[3] << 16);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) hist[q] += c[q];
+    }
+  }
+  __syncwarp();
+  // largest bin hit: highest nonzero word, then its upper half
+  int tw = -1;
+  for (int i = lane; i < words; i += 32)
+    if (hist[i]) tw = i;
+  tw = __reduce_max_sync(0xffffffffu, (unsigned)(tw + 1)) - 1;
+  if (!PACKED || tw < 0) return tw;
+  return 2 * (int64_t)tw + ((hist[tw] >> 16) ? 1 : 0);
+}
+
+__global__ void __launch_bounds__(kAWarps * 32, 4) sample_hist_kernel(SampleLaunch a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
+  uint32_t *sG = reinterpret_cast<uint32_t *>(smem + kL1 * 8);
+  uint32_t *sH = reinterpret_cast<uint32_t *>(smem + kL1 * 8 + kGuide * 4);
+  int *s_spill = reinterpret_cast<int *>(smem + kL1 * 8 + kGuide * 4 + kAWarps * (kHMax / 2) * 4);
+  uint32_t *s_item = reinterpret_cast<uint32_t *>(s_spill + kAWarps);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(s_item + 2);
+  StagedLaw staged{sT, sG, mbar};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t *hist = sH + warp * (kHMax / 2);
+  const TailQueue tq{a.tq_pos, a.tq_law, a.tq_count, a.tq_cap};
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  __syncthreads();
+  uint32_t phase = 0, loaded = 0xffffffffu;
+  for (;;) {
+    if (threadIdx.x == 0) *s_item = atomicAdd(&a.ctr->work_next, 1u);
+    __syncthreads();
+    const uint32_t item = *s_item;
+    if (item >= a.nitems) break;
+    const WorkItem wi = a.items[item];
+    const Cell cell = a.cells[wi.cell];
+    const Law law = a.laws[cell.law];
+    if (cell.law != loaded) {
+      if (!stage_law(staged, law, phase, a.ctr)) return;
+      loaded = cell.law;
+    }
+    for (int jj = 0; jj < kARepsPerWarp; ++jj) {
+      const uint32_t j = warp * kARepsPerWarp + jj;
+      if (j >= wi.nrep) break;
+      const uint64_t pos0 = wi.spill_off + (uint64_t)j * cell.scap;
+      const int64_t tmax = draw_replicate<true>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp],
+                                                a.rec.spill + pos0, cell.scap, lane, &tq, pos0);
+      uint32_t *dense = reinterpret_cast<uint32_t *>(a.rec.dense + wi.dense_off + (uint64_t)j * cell.H);
+      for (int64_t i = lane; i <= (tmax >> 1); i += 32) dense[i] = hist[i];
+      if (lane == 0) a.rec.meta[wi.meta_off + j] = make_int2((int)tmax, s_spill[warp]);
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+// Beyond-table draws queued by the sampler: one thread per draw (full lanes),
+// binary64 inversion written back into the record.
+__global__ void __launch_bounds__(256) tail_queue_kernel(const Law *laws, TailQueue tq, uint64_t *spill,
+                                                         Counters *ctr) {
+  const unsigned cnt = *tq.count;
+  const unsigned nq = cnt < tq.cap ? cnt : tq.cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && nq) atomicAdd(&ctr->tail_draws, (unsigned long long)nq);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
+    const uint64_t pos = tq.pos[i];
+    const uint64_t x = spill[pos];
+    if (x & kTailTag) {
+      const Law &law = laws[tq.law[i]];
+      spill[pos] = tail_invert(law.alpha, law.Z, law.xmin + law.L2, x & ~kTailTag);
+    }
+  }
+}
+
+cudaError_t launch_tail_queue_raw(const Law *laws, uint64_t *pos, uint32_t *law, unsigned int *count,
+                                  uint32_t cap, uint64_t *spill, Counters *ctr, int num_sms, cudaStream_t st) {
+  const TailQueue tq{pos, law, count, cap};
+  tail_queue_kernel<<<num_sms * 4, 256, 0, st>>>(laws, tq, spill, ctr);
+  return cudaGetLastError();
+}
+
+size_t sample_kernel_smem_bytes() {
+  return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kAWarps * (kHMax / 2) * 4 + kAWarps * 4 + 8 + 8 + 16;
+}
+
+int sample_kernel_blocks_per_sm() {
+  int nb = 0;
+  const size_t smem = sample_kernel_smem_bytes();
+  cudaFuncSetAttribute(sample_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_hist_kernel, kAWarps * 32, smem);
+  return nb;
+}
+
+cudaError_t launch_sample_hist(const SampleLaunch &a, cudaStream_t st) {
+  sample_hist_kernel<<<a.blocks, kAWarps * 32, sample_kernel_smem_bytes(), st>>>(a);
+  return cudaGetLastError();
+}
+
 template <bool F32>
-__global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) replicate_warp_kernel(WarpLaunch a) {
+__global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel(FinishLaunch a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
   uint32_t *sG = reinterpret_cast<uint32_t *>(smem + kL1 * 8);
@@ -547,7 +748,6 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) replicate_war
   const size_t slot = (size_t)blockIdx.x * kWarps + warp;
   uint64_t *spill = reinterpret_cast<uint64_t *>(a.scratch + slot * (a.spill_cap * 8 + a.arena_bytes));
   uint8_t *arena = reinterpret_cast<uint8_t *>(spill + a.spill_cap);
-  const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
 
   if (threadIdx.x == 0) mbar_init(mbar, 1);
   __syncthreads();
@@ -566,38 +766,42 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) replicate_war
       if (!stage_law(staged, law, phase, a.ctr)) return;
       loaded = cell.law;
     }
-    const int64_t rbase = (int64_t)wi.r0 + warp * 32;
-    const int nb = (int)min((int64_t)32, cell.R - rbase);
+    const int j0 = warp * kBRepsPerWarp;
+    const int nb = (int)min((int64_t)kBRepsPerWarp, (int64_t)wi.nrep - j0);
     if (nb > 0) {
       const int64_t n = cell.n;
       const uint64_t xmin = cell.xmin;
-      const int64_t H = cell.H;
-      // per-lane record of replicate `lane`
+      // per-lane record of replicate j0 + lane
       double myL = 0.0;
       int64_t my_tmax = -1, my_nsd = 0;
       size_t my_off = 0;
       size_t arena_off = 0;
       int done = 0;
       const FitTable &ft = a.fits[cell.fit];
+#ifdef PL_PHASE_TIMING
+      long long pt_ = clock64();
+#endif
       auto finish = [&](int b0, int b1) {
+        PL_PHASE(6);
         const bool mine = lane >= b0 && lane < b1;
         // lanes without a replicate fit a stand-in log-sum (mean log excess 1/2)
         const double Lfit = mine ? myL : (double)n * (cc.ln_xmin + 0.5);
         const FitOut fo = fit_lanes(Lfit, n, xmin, cc, ft, law.lnT, F32, a.ctr);
+        PL_PHASE(3);
         double myD = 0.0;
         for (int r = b0; r < b1; ++r) {
           const FitOut fr = shfl_fit(fo, r);
           const int64_t tm = __shfl_sync(0xffffffffu, my_tmax, r);
           const int64_t ns = __shfl_sync(0xffffffffu, my_nsd, r);
           const size_t off = __shfl_sync(0xffffffffu, my_off, r);
-          const size_t dense_bytes = ((size_t)(tm + 1) * 4 + 15) & ~(size_t)15;
-          const double D = ks_warp<F32>(reinterpret_cast<const uint32_t *>(arena + off), tm,
-                                        reinterpret_cast<const uint64_t *>(arena + off + dense_bytes),
-                                        ns, n, fr, law.lnT, law.lnT_hi, law.lnT_lo, lane);
+          const uint16_t *dense = a.rec.dense + wi.dense_off + (uint64_t)(j0 + r) * cell.H;
+          const double D = ks_warp<F32, uint16_t>(dense, tm, reinterpret_cast<const uint64_t *>(arena + off), ns,
+                                                  n, fr, law.lnT, law.lnT_hi, law.lnT_lo, lane);
           if (lane == r) myD = D;
         }
-        if (lane >= b0 && lane < b1) {
-          const int64_t o = cell.out_off + rbase + lane;
+        PL_PHASE(4);
+        if (mine) {
+          const int64_t o = cell.out_off + wi.r0 + j0 + lane;
           if (F32) reinterpret_cast<float *>(a.D_out)[o] = (float)myD;
           else reinterpret_cast<double *>(a.D_out)[o] = myD;
           if (a.A_out) a.A_out[o] = fo.ahat;
@@ -605,77 +809,59 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) replicate_war
       };
 
       for (int r = 0; r < nb; ++r) {
-        const uint32_t rep = (uint32_t)(rbase + r);
-        for (int i = lane; i < H; i += 32) hist[i] = 0;
-        if (lane == 0) s_spill[warp] = 0;
-        __syncwarp();
-        uint64_t packed = 0;  // 16-bit counters of bins 0..3 (per lane <= n/32 + 2 draws)
-        int64_t lmax = -1;
-        const int64_t npairs = (n + 1) >> 1;
-        for (int64_t p = lane; p < npairs; p += 32) {
-          const uint4 w = philox4x32_10(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), key);
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            if (2 * p + j < n) {
-              const uint64_t m = draw_bits(j ? w.z : w.x, j ? w.w : w.y);
-              // beyond-table draws come back tagged; they always spill and are resolved below
-              const uint64_t X = lookup_fast(sT, sG, law.T, law.L2, xmin, law.tail_c, law.tail_e, m);
-              const uint64_t b = X - xmin;
-              if (b < 4) packed += 1ull << (16 * b);
-              else if (b < (uint64_t)H) atomicAdd(&hist[b], 1u);
-              else {
-                const int slot_i = atomicAdd(&s_spill[warp], 1);
-                spill[slot_i] = X;
-              }
-              if (b < (uint64_t)H && (int64_t)b > lmax) lmax = (int64_t)b;
-            }
-          }
+        const uint32_t j = (uint32_t)(j0 + r);
+        const int2 meta = a.rec.meta[wi.meta_off + j];
+        int64_t tmax = meta.x;
+        const int64_t s = meta.y;
+        uint16_t *dense = a.rec.dense + wi.dense_off + (uint64_t)j * cell.H;
+        uint64_t *sp = a.rec.spill + wi.spill_off + (uint64_t)j * cell.scap;
+        if (s > (int64_t)cell.scap) {
+          // the record's spill slot overflowed: draw this replicate again with
+          // the warp's global spill buffer (same stream, same values)
+          if (lane == 0) atomicAdd(&a.ctr->resampled, 1ull);
+          tmax = draw_replicate<false>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp], spill,
+                                       (int64_t)a.spill_cap, lane, nullptr, 0);
+          for (int64_t i = lane; i <= tmax; i += 32) dense[i] = (uint16_t)hist[i];
+          __syncwarp();
+          sp = spill;
         }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)((packed >> (16 * q)) & 0xffffu));
-          if (lane == 0 && c) hist[q] += c;
-        }
-        __syncwarp();
-        const int64_t s = s_spill[warp];
+        PL_PHASE(0);
         // resolve the draws that fell beyond the threshold table (binary64 inversion)
         for (int64_t k = lane; k < s; k += 32) {
-          const uint64_t x = spill[k];
+          const uint64_t x = sp[k];
           if (x & kTailTag) {
             atomicAdd(&a.ctr->tail_draws, 1ull);
-            spill[k] = tail_invert(law.alpha, law.Z, xmin + law.L2, x & ~kTailTag);
+            sp[k] = tail_invert(law.alpha, law.Z, xmin + law.L2, x & ~kTailTag);
           }
         }
         __syncwarp();
-        const int64_t tmax = warp_max_i64(lmax);
         // log-sum  L = sum ln x_i  (+ ln((xmin+1)/xmin) if every x_i = xmin)
         double L;
         if (!F32) {
           double acc = 0.0;
-          for (int64_t i = lane; i <= tmax; i += 32) acc += (double)hist[i] * law.lnT[i];
-          for (int64_t k = lane; k < s; k += 32) acc += log((double)spill[k]);
+          for (int64_t i = lane; i <= tmax; i += 32) acc += (double)dense[i] * law.lnT[i];
+          for (int64_t k = lane; k < s; k += 32) acc += log((double)sp[k]);
           L = warp_sum(acc);
         } else {
           float h = 0.0f, l = 0.0f;
           for (int64_t i = lane; i <= tmax; i += 32) {
-            const float c = (float)hist[i];
+            const float c = (float)dense[i];
             const float ph = c * law.lnT_hi[i];
             const float pe = fmaf(c, law.lnT_hi[i], -ph) + c * law.lnT_lo[i];
             ff_add(h, l, ph, pe);
           }
           for (int64_t k = lane; k < s; k += 32) {
             float vh, vl;
-            ln_u64_ff(spill[k], vh, vl);
+            ln_u64_ff(sp[k], vh, vl);
             ff_add(h, l, vh, vl);
           }
           warp_sum_ff(h, l);
           L = (double)h + (double)l;
         }
-        if (hist[0] == (uint32_t)n) L += cc.ln_allmin;
-        // arena space for this replicate; run phases 2-3 early if it is full
-        const size_t dense_bytes = ((size_t)(tmax + 1) * 4 + 15) & ~(size_t)15;
-        const size_t need = dense_bytes + (size_t)s * 16;
+        if (tmax >= 0 && (int64_t)dense[0] == n) L += cc.ln_allmin;
+        PL_PHASE(1);
+        // arena space for this replicate's spill pairs; run phases 2-3 early if full
+        const size_t need = (size_t)s * 16;
         if (arena_off + need > a.arena_bytes) {
           if (done < r) finish(done, r);
           done = r;
@@ -685,47 +871,50 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) replicate_war
             break;                     // leave this batch; the block barrier below still meets
           }
         }
-        uint32_t *dd = reinterpret_cast<uint32_t *>(arena + arena_off);
-        for (int64_t i = lane; i <= tmax; i += 32) dd[i] = hist[i];
-        __syncwarp();
-        uint64_t *pairs = reinterpret_cast<uint64_t *>(arena + arena_off + dense_bytes);
-        const int64_t nsd = spill_compact(spill, hist, s, pairs, lane, a.ctr);
+        if (s > kSortSmem && sp != spill) {  // sorted in the warp's buffer (power-of-two room)
+          for (int64_t k = lane; k < s; k += 32) spill[k] = sp[k];
+          __syncwarp();
+          sp = spill;
+        }
+        uint64_t *pairs = reinterpret_cast<uint64_t *>(arena + arena_off);
+        const int64_t nsd = spill_compact(sp, hist, s, pairs, lane, a.ctr);
         if (lane == r) {
           myL = L;
           my_tmax = tmax;
           my_nsd = nsd;
           my_off = arena_off;
         }
-        arena_off += dense_bytes + (size_t)nsd * 16;
+        arena_off += (size_t)nsd * 16;
         __syncwarp();
+        PL_PHASE(2);
       }
-      if (done < nb && arena_off > 0) finish(done, nb);
+      if (done < nb) finish(done, nb);
     }
     __syncthreads();
   }
 }
 
-size_t warp_kernel_smem_bytes() {
+size_t finish_kernel_smem_bytes() {
   return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kWarps * kHMax * 4 + 64 + 16;
 }
 
-int warp_kernel_blocks_per_sm(bool f32) {
+int finish_kernel_blocks_per_sm(bool f32) {
   int nb = 0;
-  const size_t smem = warp_kernel_smem_bytes();
+  const size_t smem = finish_kernel_smem_bytes();
   if (f32) {
-    cudaFuncSetAttribute(replicate_warp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, replicate_warp_kernel<true>, kWarps * 32, smem);
+    cudaFuncSetAttribute(finish_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, finish_kernel<true>, kWarps * 32, smem);
   } else {
-    cudaFuncSetAttribute(replicate_warp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, replicate_warp_kernel<false>, kWarps * 32, smem);
+    cudaFuncSetAttribute(finish_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, finish_kernel<false>, kWarps * 32, smem);
   }
   return nb;
 }
 
-cudaError_t launch_replicates_warp(const WarpLaunch &a, bool f32, cudaStream_t st) {
-  const size_t smem = warp_kernel_smem_bytes();
-  if (f32) replicate_warp_kernel<true><<<a.blocks, kWarps * 32, smem, st>>>(a);
-  else replicate_warp_kernel<false><<<a.blocks, kWarps * 32, smem, st>>>(a);
+cudaError_t launch_finish(const FinishLaunch &a, bool f32, cudaStream_t st) {
+  const size_t smem = finish_kernel_smem_bytes();
+  if (f32) finish_kernel<true><<<a.blocks, kWarps * 32, smem, st>>>(a);
+  else finish_kernel<false><<<a.blocks, kWarps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -858,7 +1047,7 @@ __global__ void __launch_bounds__(1024) dataset_kernel(const int32_t *x, int64_t
       }
       fo = shfl_fit(fo, 0);
     }
-    const double D = ks_warp<F32>(hist, tmax, pairs, base, n, fo, law.lnT, law.lnT_hi, law.lnT_lo, lane);
+    const double D = ks_warp<F32, uint32_t>(hist, tmax, pairs, base, n, fo, law.lnT, law.lnT_hi, law.lnT_lo, lane);
     if (lane == 0) {
       out[0] = fo.ahat;
       out[1] = D;

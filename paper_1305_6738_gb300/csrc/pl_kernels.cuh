@@ -24,14 +24,46 @@ cudaError_t launch_sample(const Law *law_dev, uint64_t seed, uint32_t cell_id, u
                           uint32_t rep0, int64_t nrep, int64_t n, uint64_t *out, Counters *ctr,
                           int num_sms, cudaStream_t st);
 
-struct WarpLaunch {
+// Records of one wave of work items, written by the sampler and read by the
+// finisher: dense histogram counts (uint16, H per replicate), spill values
+// (uint64, scap per replicate) and (tmax, spill count) per replicate.
+struct Records {
+  uint16_t *dense;
+  uint64_t *spill;
+  int2 *meta;
+};
+
+struct TailQueue;
+struct SampleLaunch {
+  const Cell *cells;
+  const Law *laws;
+  const WorkItem *items;
+  uint32_t nitems;
+  RoundKeys rk;
+  Records rec;
+  Counters *ctr;
+  int blocks;
+  // queue of beyond-table draws (see TailQueue in the kernels)
+  uint64_t *tq_pos;
+  uint32_t *tq_law;
+  unsigned int *tq_count;
+  uint32_t tq_cap;
+};
+int sample_kernel_blocks_per_sm();
+size_t sample_kernel_smem_bytes();
+cudaError_t launch_sample_hist(const SampleLaunch &a, cudaStream_t st);
+cudaError_t launch_tail_queue_raw(const Law *laws, uint64_t *pos, uint32_t *law, unsigned int *count,
+                                  uint32_t cap, uint64_t *spill, Counters *ctr, int num_sms, cudaStream_t st);
+
+struct FinishLaunch {
   const Cell *cells;
   const CellConst *consts;
   const Law *laws;
   const FitTable *fits;
   const WorkItem *items;
   uint32_t nitems;
-  uint64_t seed;
+  RoundKeys rk;
+  Records rec;
   void *D_out;            // double or float per precision
   double *A_out;          // may be null
   uint8_t *scratch;
@@ -40,9 +72,9 @@ struct WarpLaunch {
   Counters *ctr;
   int blocks;             // persistent grid size
 };
-int warp_kernel_blocks_per_sm(bool f32);
-size_t warp_kernel_smem_bytes();
-cudaError_t launch_replicates_warp(const WarpLaunch &a, bool f32, cudaStream_t st);
+int finish_kernel_blocks_per_sm(bool f32);
+size_t finish_kernel_smem_bytes();
+cudaError_t launch_finish(const FinishLaunch &a, bool f32, cudaStream_t st);
 
 // Fit and/or KS of one data set.  out[0] = alpha-hat (or the given alpha),
 // out[1] = D, out[2] = Z.
