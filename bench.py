@@ -32,13 +32,14 @@ from paper_1305_6738_gb300 import inputs  # noqa: E402
 Q = [0.90, 0.95, 0.99]
 METRIC = "KS replicates/sec and samples/sec per (alpha,n) vs roofline; p50/p99 fit-request latency"
 
-# Algorithmic work per unit (the per-unit figures of the work model):
-# one draw = half a Philox4x32-10 block = 10 rounds x 2 32x32->64-bit multiplies
-# (20 IMAD-class ops) + ~20 XOR/ADD ops  ->  40 INT32 ops per draw.
-INT_OPS_PER_DRAW = 40
-# INT32 lanes per SM per clock assumed for the peak (4 SM sub-partitions x 16
-# lanes for 32-bit integer multiply-add, add and logic ops).
-INT32_LANES_PER_SM = 64
+# Roofline of the dominant kernel (the sampler).  Algorithmic work per draw:
+# half a Philox4x32-10 block = 10 rounds x 2 products / 2 draws = 10 full
+# 32x32->64-bit multiplies (plus ~20 XOR/ADD ops on the wider ALU pipe).  The
+# binding unit is the wide-multiply pipe: 32 lanes per SM per clock on GB300
+# (a quarter of the 128 FP32/ALU lanes; measured with an issue-rate probe),
+# so the ceiling is SMs x 32 x clock / 10 draws per second.
+MUL_PER_DRAW = 10
+MUL_LANES_PER_SM = 32
 
 # DRAM traffic of the replicate kernel from one ncu capture, keyed by the hash
 # of the kernel sources it was taken on (reported as null once they change).
@@ -219,7 +220,8 @@ def main():
 
     sampler = ClockSampler(gpu_query_id(local))
     barrier()
-    step_ms, kern_ms = [], []
+    step_ms, kern_ms, fin_ms = [], [], []
+    waves = 0
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -229,7 +231,9 @@ def main():
         e1.record(stream)
         tr = ctx.pl_trace()  # synchronises; kernel time from events on the call's stream
         step_ms.append(e0.elapsed_time(e1))
-        kern_ms.append(tr["replicate_ms"])
+        kern_ms.append(tr["sample_ms"])
+        fin_ms.append(tr["finish_ms"])
+        waves = tr["waves"]
     barrier()
     clocks = sampler.stop()
     launches = ctx.pl_trace()["launches"] - launches0
@@ -255,19 +259,22 @@ def main():
     h2d = len(cells) * 40 + len(Q) * 8
     d2h = host_cut.nbytes
 
-    # roofline of the replicate kernel (INT32 issue bound)
+    # roofline of the sampler kernel (wide-multiply bound), from its CUDA-event
+    # durations on the call's stream, summed over the waves of a step
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
-    int_peak = props.multi_processor_count * INT32_LANES_PER_SM * sm_max * 1e6 / 1e9  # Gop/s
+    mul_peak = props.multi_processor_count * MUL_LANES_PER_SM * sm_max * 1e6 / 1e9  # Gmul/s
     kmean = statistics.mean(kern_ms)
-    achieved = INT_OPS_PER_DRAW * draws / (kmean / 1000.0) / 1e9
+    achieved = MUL_PER_DRAW * draws / (kmean / 1000.0) / 1e9
     h = kernel_source_hash()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": int_peak, "unit": "Gop/s (INT32)",
-                "frac": achieved / int_peak, "traffic": TRAFFIC.get(h),
-                "kernel": "replicate_warp_kernel", "kernel_ms": kmean,
-                "peak_basis": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} INT32 lanes x "
-                              f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)"}
+    roofline = {"bound": "alu", "achieved": achieved, "peak": mul_peak, "unit": "Gmul/s (32x32->64)",
+                "frac": achieved / mul_peak, "traffic": TRAFFIC.get(h),
+                "kernel": "sample_hist_kernel", "kernel_ms_per_step": kmean, "launches_per_step": waves,
+                "finisher_ms_per_step": statistics.mean(fin_ms),
+                "peak_basis": f"{props.multi_processor_count} SMs x {MUL_LANES_PER_SM} multiply lanes x "
+                              f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json); "
+                              f"{MUL_PER_DRAW} multiplies per draw"}
 
     line = {"metric": METRIC, "value": value, "unit": "replicates/s", "samples_per_s": sps,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -89,15 +89,20 @@ const char *pl_last_error(const pl_ctx *ctx);
  * report (PL_ETIMEOUT, PL_EINVAL for bad data values, PL_ECUDA). */
 pl_status pl_sync(pl_ctx *ctx, void *stream);
 
-/* Counters accumulated on the device since pl_create: Newton solves that hit
- * the iteration cap, draws inverted in the FP64 tail beyond the threshold
- * table, replicates whose spill list was sorted in global memory, and
- * replicates fitted by the full Newton iteration instead of the one-step
- * polish from the interpolated start.  Synchronises `stream`.  Any output
- * pointer may be NULL. */
-pl_status pl_counters(pl_ctx *ctx, void *stream, uint64_t *newton_capped,
-                      uint64_t *tail_draws, uint64_t *global_sorts,
-                      uint64_t *fit_fallbacks);
+/* Counters accumulated on the device since pl_create (diagnostics; no
+ * counterpart in the paper). */
+typedef struct {
+  uint64_t newton_capped;  /* Newton solves that hit the iteration cap */
+  uint64_t tail_draws;     /* draws inverted in binary64 beyond the threshold table */
+  uint64_t global_sorts;   /* replicates whose spills were sorted in global memory */
+  uint64_t fit_fallbacks;  /* fits by the full Newton iteration instead of the
+                              one-step polish from the interpolated start */
+  uint64_t resampled;      /* replicates drawn a second time because their
+                              record's spill slot overflowed */
+} pl_counter_info;
+
+/* Synchronises `stream` and copies the counters to *out (host). */
+pl_status pl_counters(pl_ctx *ctx, void *stream, pl_counter_info *out);
 
 /* Tracing (no counterpart in the paper, which times whole runs with clock()).
  * With tracing on, pl_ks_cutoffs and pl_bootstrap_pvalue record CUDA events
@@ -107,9 +112,13 @@ pl_status pl_counters(pl_ctx *ctx, void *stream, uint64_t *newton_capped,
 typedef struct {
   uint64_t launches;   /* kernels launched by this context */
   float law_ms;        /* last traced call: law-table set-up kernels */
-  float replicate_ms;  /* last traced call: the replicate kernel */
+  float replicate_ms;  /* last traced call: all replicate kernels (every wave) */
   float select_ms;     /* last traced call: quantile selection / p count */
   float total_ms;      /* last traced call: first to last phase */
+  float sample_ms;     /* last traced call: sampler launches, summed over waves */
+  float finish_ms;     /* last traced call: finisher launches, summed over waves */
+  uint32_t waves;      /* last traced call: number of waves (sampler launches) */
+  uint64_t draws;      /* last traced call: draws simulated */
 } pl_trace_info;
 
 pl_status pl_set_tracing(pl_ctx *ctx, int on);

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -31,9 +32,17 @@ struct pl_ctx {
   int finish_blocks_per_sm[2] = {0, 0};
   int sample_blocks_per_sm = 0;
   uint64_t launches = 0;
+  // Capacity overrides for tests (environment, read at pl_create; 0 = off):
+  // they only shrink buffers so that the overflow fallbacks run.
+  uint32_t dbg_spill_cap = 0;    // PL_TEST_SPILL_SLOT: record spill slot entries
+  uint32_t dbg_tail_cap = 0;     // PL_TEST_TAIL_QUEUE: tail-queue entries
+  size_t dbg_arena = 0;          // PL_TEST_ARENA_BYTES: finisher arena bytes per warp
   bool tracing = false;
   bool traced = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> wave_ev;   // 4 per wave: sampler start/end, finisher start/end
+  uint32_t traced_waves = 0;
+  uint64_t traced_draws = 0;
 };
 
 namespace {
@@ -234,6 +243,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     }
     cd.fit = fi->second;
     cd.scap = spill_capacity(x.alpha, x.xmin, x.n, cd.H);
+    if (ctx->dbg_spill_cap) cd.scap = std::min(cd.scap, ctx->dbg_spill_cap);
     sp.total_R += x.replicates;
     sp.n_max = std::max(sp.n_max, x.n);
     sp.consts[c] = cell_const(x.xmin);
@@ -291,6 +301,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
   }
   sp.waves.push_back({first, sp.items.size() - first});
   close_tail();
+  if (ctx->dbg_tail_cap) sp.tail_cap = std::min(sp.tail_cap, ctx->dbg_tail_cap);
   return PL_OK;
 }
 
@@ -312,7 +323,7 @@ struct SimBuffers {
 };
 
 // Lay out (or size) the device buffers of a simulation plan.
-void carve_sim(Carver &cv, const SimPlan &sp, int blocks, int sample_blocks, SimBuffers &b) {
+void carve_sim(Carver &cv, const SimPlan &sp, int blocks, int sample_blocks, SimBuffers &b, size_t arena_override) {
   b.fits_host.clear();
   for (uint64_t xm : sp.fit_xmins) b.fits_host.push_back(make_fit_table(cv, xm));
   b.fits_dev = cv.take<FitTable>(sp.fit_xmins.size());
@@ -330,6 +341,7 @@ void carve_sim(Carver &cv, const SimPlan &sp, int blocks, int sample_blocks, Sim
   b.tq_count = cv.take<unsigned int>(1);
   b.spill_cap = next_pow2((uint64_t)std::max<int64_t>(sp.n_max, kSortSmem));
   b.arena_bytes = ((16 * (size_t)sp.n_max + 16) + (size_t)32 * 2048 + 255) & ~(size_t)255;
+  if (arena_override) b.arena_bytes = std::max<size_t>(16 * (size_t)sp.n_max + 16, arena_override);
   b.blocks = blocks;
   b.sample_blocks = sample_blocks;
   b.scratch = cv.take<uint8_t>((size_t)blocks * kWarps * (b.spill_cap * 8 + b.arena_bytes));
@@ -354,7 +366,20 @@ pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t
 pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, bool f32, void *D,
                   double *A, cudaStream_t st) {
   const RoundKeys rk = round_keys(seed);
+  if (ctx->tracing) {
+    while (ctx->wave_ev.size() < 4 * sp.waves.size()) {
+      cudaEvent_t e;
+      PL_CUDA(cudaEventCreate(&e));
+      ctx->wave_ev.push_back(e);
+    }
+    ctx->traced_waves = (uint32_t)sp.waves.size();
+    ctx->traced_draws = 0;
+    for (const Cell &c : sp.cells) ctx->traced_draws += (uint64_t)c.n * (uint64_t)c.R;
+  }
+  size_t wi_ = 0;
   for (const Wave &w : sp.waves) {
+    cudaEvent_t *wev = ctx->tracing ? &ctx->wave_ev[4 * wi_] : nullptr;
+    ++wi_;
     SampleLaunch sl{};
     sl.cells = b.cells;
     sl.laws = b.laws_dev;
@@ -370,7 +395,9 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
     sl.tq_cap = sp.tail_cap;
     PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
     PL_CUDA(cudaMemsetAsync(b.tq_count, 0, sizeof(unsigned int), st));
+    if (wev) PL_CUDA(cudaEventRecord(wev[0], st));
     PL_CUDA(launch_sample_hist(sl, st));
+    if (wev) PL_CUDA(cudaEventRecord(wev[1], st));
     PL_CUDA(launch_tail_queue_raw(b.laws_dev, b.tq_pos, b.tq_law, b.tq_count, sp.tail_cap, b.rec.spill, ctx->ctr,
                                   ctx->num_sms, st));
     FinishLaunch fl{};
@@ -390,7 +417,9 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
     fl.ctr = ctx->ctr;
     fl.blocks = (int)std::min<size_t>((size_t)b.blocks, w.count);
     PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
+    if (wev) PL_CUDA(cudaEventRecord(wev[2], st));
     PL_CUDA(launch_finish(fl, f32, st));
+    if (wev) PL_CUDA(cudaEventRecord(wev[3], st));
     ctx->launches += 3;
   }
   return PL_OK;
@@ -450,6 +479,9 @@ pl_status pl_create(pl_ctx **out, int device, size_t mem_budget_bytes) {
     delete ctx;
     return PL_ECUDA;
   }
+  if (const char *e = getenv("PL_TEST_SPILL_SLOT")) ctx->dbg_spill_cap = (uint32_t)strtoul(e, nullptr, 10);
+  if (const char *e = getenv("PL_TEST_TAIL_QUEUE")) ctx->dbg_tail_cap = (uint32_t)strtoul(e, nullptr, 10);
+  if (const char *e = getenv("PL_TEST_ARENA_BYTES")) ctx->dbg_arena = (size_t)strtoull(e, nullptr, 10);
   ctx->finish_blocks_per_sm[0] = finish_kernel_blocks_per_sm(false);
   ctx->finish_blocks_per_sm[1] = finish_kernel_blocks_per_sm(true);
   ctx->sample_blocks_per_sm = sample_kernel_blocks_per_sm();
@@ -464,6 +496,7 @@ void pl_destroy(pl_ctx *ctx) {
   cudaDeviceSynchronize();
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (auto &e : ctx->wave_ev) cudaEventDestroy(e);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->ctr) cudaFree(ctx->ctr);
   delete ctx;
@@ -491,6 +524,15 @@ pl_status pl_trace(pl_ctx *ctx, void *stream, pl_trace_info *out) {
     PL_CUDA(cudaEventElapsedTime(&out->replicate_ms, ctx->ev[1], ctx->ev[2]));
     PL_CUDA(cudaEventElapsedTime(&out->select_ms, ctx->ev[2], ctx->ev[3]));
     PL_CUDA(cudaEventElapsedTime(&out->total_ms, ctx->ev[0], ctx->ev[3]));
+    for (uint32_t w = 0; w < ctx->traced_waves && 4 * w + 3 < ctx->wave_ev.size(); ++w) {
+      float a = 0.0f, b = 0.0f;
+      PL_CUDA(cudaEventElapsedTime(&a, ctx->wave_ev[4 * w], ctx->wave_ev[4 * w + 1]));
+      PL_CUDA(cudaEventElapsedTime(&b, ctx->wave_ev[4 * w + 2], ctx->wave_ev[4 * w + 3]));
+      out->sample_ms += a;
+      out->finish_ms += b;
+    }
+    out->waves = ctx->traced_waves;
+    out->draws = ctx->traced_draws;
   }
   return PL_OK;
 }
@@ -500,16 +542,17 @@ pl_status pl_sync(pl_ctx *ctx, void *stream) {
   return read_status(ctx, (cudaStream_t)stream);
 }
 
-pl_status pl_counters(pl_ctx *ctx, void *stream, uint64_t *newton_capped, uint64_t *tail_draws,
-                      uint64_t *global_sorts, uint64_t *fit_fallbacks) {
+pl_status pl_counters(pl_ctx *ctx, void *stream, pl_counter_info *out) {
   if (pl_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(ctx, PL_EINVAL, "pl_counters: null output");
   PL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   Counters c{};
   PL_CUDA(cudaMemcpy(&c, ctx->ctr, sizeof c, cudaMemcpyDeviceToHost));
-  if (newton_capped) *newton_capped = c.newton_capped;
-  if (tail_draws) *tail_draws = c.tail_draws;
-  if (global_sorts) *global_sorts = c.global_sorts;
-  if (fit_fallbacks) *fit_fallbacks = c.fit_fallbacks;
+  out->newton_capped = c.newton_capped;
+  out->tail_draws = c.tail_draws;
+  out->global_sorts = c.global_sorts;
+  out->fit_fallbacks = c.fit_fallbacks;
+  out->resampled = c.resampled;
   return PL_OK;
 }
 
@@ -610,7 +653,7 @@ pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells, uint64_t 
   const size_t dsz = f32 ? 4 : 8;
   const int blocks = sim_blocks(ctx, f32), sblocks = sample_blocks(ctx);
   auto lay = [&](Carver &cv, SimBuffers &b, void *&D, int64_t *&off, int64_t *&Rs, int64_t *&rank, double *&cut) {
-    carve_sim(cv, sp, blocks, sblocks, b);
+    carve_sim(cv, sp, blocks, sblocks, b, ctx->dbg_arena);
     D = D_dev_opt ? D_dev_opt : (void *)cv.take<uint8_t>((size_t)sp.total_R * dsz);
     off = cv.take<int64_t>(ncells);
     Rs = cv.take<int64_t>(ncells);
@@ -670,7 +713,7 @@ pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint
   if (pl_status s = plan_cells(ctx, &cell, 1, 1u, sp)) return s;
   const int blocks = sim_blocks(ctx, f32), sblocks = sample_blocks(ctx);
   auto lay = [&](Carver &cv, SimBuffers &b, void *&Db, double *&dobs, double *&pd) {
-    carve_sim(cv, sp, blocks, sblocks, b);
+    carve_sim(cv, sp, blocks, sblocks, b, ctx->dbg_arena);
     Db = cv.take<uint8_t>((size_t)B * (f32 ? 4 : 8));
     dobs = cv.take<double>(1);
     pd = cv.take<double>(1);

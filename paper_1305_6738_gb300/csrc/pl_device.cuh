@@ -55,8 +55,9 @@ struct Law {
   uint64_t xmin;
   uint32_t L2;            // table length (>= kL1, multiple of kL1)
   uint32_t pad;
-  float tail_c;           // (alpha - 1) Z, binary32: continuous tail approximation
+  float tail_c;           // (alpha - 1) Z 2^-32, binary32: continuous tail approximation
   float tail_e;           // -1 / (alpha - 1)
+  float xmin_f;           // xmin + 1/2, binary32
   uint64_t *T;            // T[i] = floor(Q(xmin+i) 2^53) + 1, Q(k) = P(X > k)
   uint32_t *guide;        // guide[j] = min{i : T[i] <= (j+1) 2^(53-g)} (or L2)
   double *lnT;            // ln(xmin + i), i < kLnTable
@@ -459,14 +460,15 @@ __device__ __forceinline__ uint64_t table_at(const uint64_t *sT, const uint64_t 
 
 // Index form: returns i = X - xmin for answers inside the table, L2 beyond it.
 __device__ __forceinline__ uint32_t lookup_index(const uint64_t *sT, const uint32_t *sG,
-                                                 const uint64_t *gT, uint32_t L2, uint64_t xmin,
+                                                 const uint64_t *gT, uint32_t L2, float xmin_f,
                                                  float tail_c, float tail_e, uint64_t m) {
   const uint32_t j = (uint32_t)((m - 1ull) >> (53 - kGuideBits));
   uint32_t lo = sG[j];
   uint32_t hi = j ? sG[j - 1] : L2;
   if (hi - lo > 8) {
-    const float v = (float)m * 0x1p-53f;
-    const float kf = exp2f(tail_e * __log2f(tail_c * v)) - 0.5f - (float)xmin;
+    // v 2^32 from the top 32 of the 53 bits of m (tail_c carries the 2^-32)
+    const float v32 = (float)(uint32_t)(m >> 21);
+    const float kf = exp2f(tail_e * __log2f(tail_c * v32)) - xmin_f;
     uint32_t g = lo;
     if (kf >= (float)hi) g = hi - 1;
     else if (kf > (float)lo) g = (uint32_t)kf;
@@ -502,16 +504,16 @@ __device__ __forceinline__ uint32_t lookup_index(const uint64_t *sT, const uint3
 
 __device__ __forceinline__ uint64_t lookup_fast(const uint64_t *sT, const uint32_t *sG,
                                                 const uint64_t *gT, uint32_t L2, uint64_t xmin,
-                                                float tail_c, float tail_e, uint64_t m) {
-  const uint32_t i = lookup_index(sT, sG, gT, L2, xmin, tail_c, tail_e, m);
+                                                float xmin_f, float tail_c, float tail_e, uint64_t m) {
+  const uint32_t i = lookup_index(sT, sG, gT, L2, xmin_f, tail_c, tail_e, m);
   return i < L2 ? xmin + i : (kTailTag | m);
 }
 
 __device__ __forceinline__ uint64_t lookup(const uint64_t *sT, const uint32_t *sG,
                                            const uint64_t *gT, uint32_t L2, uint64_t xmin,
-                                           double alpha, double Z, float tail_c, float tail_e,
-                                           uint64_t m, unsigned long long *tail_counter) {
-  const uint64_t x = lookup_fast(sT, sG, gT, L2, xmin, tail_c, tail_e, m);
+                                           double alpha, double Z, float xmin_f, float tail_c,
+                                           float tail_e, uint64_t m, unsigned long long *tail_counter) {
+  const uint64_t x = lookup_fast(sT, sG, gT, L2, xmin, xmin_f, tail_c, tail_e, m);
   if (!(x & kTailTag)) return x;
   atomicAdd(tail_counter, 1ull);
   return tail_invert(alpha, Z, xmin + L2, m);

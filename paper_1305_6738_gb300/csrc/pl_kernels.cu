@@ -33,8 +33,9 @@ __global__ void law_z_kernel(Law *laws, int nlaws) {
     const double a = laws[i].alpha;
     const double Z = hurwitz_precise(a, (double)laws[i].xmin);
     laws[i].Z = Z;
-    laws[i].tail_c = (float)((a - 1.0) * Z);
+    laws[i].tail_c = (float)((a - 1.0) * Z * 0x1p-32);
     laws[i].tail_e = (float)(-1.0 / (a - 1.0));
+    laws[i].xmin_f = (float)((double)laws[i].xmin + 0.5);
   }
 }
 
@@ -134,8 +135,8 @@ __global__ void __launch_bounds__(256) sample_kernel(const Law *law_p, uint64_t 
       const int64_t i = 2 * p + j;
       if (i < n) {
         const uint64_t m = draw_bits(j ? w.z : w.x, j ? w.w : w.y);
-        out[r * n + i] = lookup(s.sT, s.sG, law.T, law.L2, law.xmin, law.alpha, law.Z, law.tail_c,
-                                law.tail_e, m, &ctr->tail_draws);
+        out[r * n + i] = lookup(s.sT, s.sG, law.T, law.L2, law.xmin, law.alpha, law.Z, law.xmin_f,
+                                law.tail_c, law.tail_e, m, &ctr->tail_draws);
       }
     }
   }
@@ -600,7 +601,7 @@ __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint
     for (int j = 0; j < 2; ++j) {
       if (2 * p + j < n) {
         const uint64_t m = draw_bits(j ? w.z : w.x, j ? w.w : w.y);
-        const uint32_t b = lookup_index(sT, sG, law.T, law.L2, xmin, law.tail_c, law.tail_e, m);
+        const uint32_t b = lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m);
         if (b < 4) {
           packed += 1ull << (16 * b);
         } else if (b < H) {
@@ -649,7 +650,7 @@ __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint
   return 2 * (int64_t)tw + ((hist[tw] >> 16) ? 1 : 0);
 }
 
-__global__ void __launch_bounds__(kAWarps * 32, 4) sample_hist_kernel(SampleLaunch a) {
+__global__ void __launch_bounds__(kAWarps * 32, 3) sample_hist_kernel(SampleLaunch a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
   uint32_t *sG = reinterpret_cast<uint32_t *>(smem + kL1 * 8);

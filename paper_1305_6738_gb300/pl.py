@@ -36,10 +36,18 @@ class pl_cell(ctypes.Structure):
                 ("replicates", ctypes.c_int64), ("cell_id", ctypes.c_uint64)]
 
 
+class pl_counter_info(ctypes.Structure):
+    _fields_ = [("newton_capped", ctypes.c_uint64), ("tail_draws", ctypes.c_uint64),
+                ("global_sorts", ctypes.c_uint64), ("fit_fallbacks", ctypes.c_uint64),
+                ("resampled", ctypes.c_uint64)]
+
+
 class pl_trace_info(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("law_ms", ctypes.c_float),
                 ("replicate_ms", ctypes.c_float), ("select_ms", ctypes.c_float),
-                ("total_ms", ctypes.c_float)]
+                ("total_ms", ctypes.c_float), ("sample_ms", ctypes.c_float),
+                ("finish_ms", ctypes.c_float), ("waves", ctypes.c_uint32),
+                ("draws", ctypes.c_uint64)]
 
 
 _vp = ctypes.c_void_p
@@ -52,7 +60,7 @@ _lib.pl_destroy.restype = None
 _lib.pl_last_error.argtypes = [_vp]
 _lib.pl_last_error.restype = ctypes.c_char_p
 _lib.pl_sync.argtypes = [_vp, _vp]
-_lib.pl_counters.argtypes = [_vp, _vp, _u64p, _u64p, _u64p, _u64p]
+_lib.pl_counters.argtypes = [_vp, _vp, ctypes.POINTER(pl_counter_info)]
 _lib.pl_set_tracing.argtypes = [_vp, ctypes.c_int]
 _lib.pl_trace.argtypes = [_vp, _vp, ctypes.POINTER(pl_trace_info)]
 _lib.pl_sample.argtypes = [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
@@ -134,11 +142,9 @@ class Context:
         self._check(_lib.pl_sync(self._h, _stream_ptr(stream)))
 
     def pl_counters(self, stream=None) -> dict:
-        a, b, c, d = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
-        self._check(_lib.pl_counters(self._h, _stream_ptr(stream), ctypes.byref(a), ctypes.byref(b),
-                                     ctypes.byref(c), ctypes.byref(d)))
-        return {"newton_capped": a.value, "tail_draws": b.value, "global_sorts": c.value,
-                "fit_fallbacks": d.value}
+        c = pl_counter_info()
+        self._check(_lib.pl_counters(self._h, _stream_ptr(stream), ctypes.byref(c)))
+        return {k: getattr(c, k) for k, _ in pl_counter_info._fields_}
 
     def pl_set_tracing(self, on: bool = True):
         self._check(_lib.pl_set_tracing(self._h, 1 if on else 0))
@@ -146,8 +152,7 @@ class Context:
     def pl_trace(self, stream=None) -> dict:
         t = pl_trace_info()
         self._check(_lib.pl_trace(self._h, _stream_ptr(stream), ctypes.byref(t)))
-        return {"launches": t.launches, "law_ms": t.law_ms, "replicate_ms": t.replicate_ms,
-                "select_ms": t.select_ms, "total_ms": t.total_ms}
+        return {k: getattr(t, k) for k, _ in pl_trace_info._fields_}
 
     def pl_sample(self, alpha: float, xmin: int, seed: int, cell_id: int, purpose: int, rep0: int,
                   nrep: int, n: int, out, stream=None):

@@ -195,6 +195,43 @@ def test_cutoffs_device_output_and_batching_invariance(ctx, pl):
     assert cut_dev[1].item() == s[oracle.quantile_index(R, 0.9)].item()
 
 
+FALLBACK_CELLS = [(1.5, 1, 5000, 300, 1), (1.75, 1, 16384, 40, 5), (2.5, 1, 100, 700, 0),
+                  (3.0, 5, 20, 513, 4), (1.5, 1, 2000, 257, 9)]
+
+
+@pytest.mark.parametrize("env,counter", [
+    ({"PL_TEST_SPILL_SLOT": "1"}, "resampled"),     # record spill slots overflow: drawn again
+    ({"PL_TEST_TAIL_QUEUE": "1"}, None),            # tail queue overflows: finisher resolves
+    ({"PL_TEST_ARENA_BYTES": "1"}, None),           # arena fills: fit and KS run early
+])
+def test_fallback_paths_are_bit_identical(pl, monkeypatch, env, counter):
+    cells = [pl.Cell(*c) for c in FALLBACK_CELLS]
+    tot = sum(c.replicates for c in cells)
+
+    def run(prec, extra):
+        for k, v in extra.items():
+            monkeypatch.setenv(k, v)
+        c = pl.Context(0)
+        for k in extra:
+            monkeypatch.delenv(k)
+        D = torch.empty(tot, dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
+        A = torch.empty(tot, dtype=torch.float64, device="cuda")
+        cut = c.pl_ks_cutoffs(cells, 1, [0.9, 0.99], prec, D=D, alpha_hat=A)
+        c.pl_sync()
+        cnt = c.pl_counters()
+        c.close()
+        return D, A, cut, cnt
+
+    for prec in (0, 1):
+        D0, A0, cut0, _ = run(prec, {})
+        D1, A1, cut1, cnt = run(prec, env)
+        assert torch.equal(D0, D1)
+        assert torch.equal(A0, A1)
+        assert (cut0 == cut1).all()
+        if counter:
+            assert cnt[counter] > 0
+
+
 @pytest.mark.parametrize("bad", [
     dict(alpha=1.0), dict(alpha=0.5), dict(xmin=0), dict(n=0), dict(replicates=0),
     dict(cell_id=2**32), dict(q=[1.0]), dict(q=[0.0]),
