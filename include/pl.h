@@ -181,6 +181,28 @@ pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
                               double *alpha_hat, double *D, double *p,
                               void *stream);
 
+/* Fit and KS distance of one data set with no device allocation at all.
+ * The paper has no counterpart: this is an engineering variant of
+ * pl_fit_mle + pl_ks_stat for callers that cannot let a library call
+ * cudaMalloc -- runtimes that reserve all device memory up front for their
+ * own pool allocator, or loops that must never reach the allocator (its
+ * calls can synchronise the device).  Its scratch is a fixed device array
+ * inside the library (about 6.3 MB on every GPU that loads it, held until
+ * the process exits); no context is used.
+ * alpha: NaN or <= 0 fits the exponent (Eq. 2) and evaluates D there; a value
+ *   in (1, 64] evaluates D (Eq. 3) at that exponent.
+ * x_dev: device int32[n], 1 <= n <= 262144 (larger n: PL_EINVAL), values >= xmin.
+ * out_dev: device double[3], written in stream order: alpha (fitted or given),
+ *   D, zeta(alpha, xmin); all NaN if a value is below xmin.
+ * The first call on each device looks up the array's device address; make
+ * that first call before any stream capture.  All calls share the array,
+ * which keeps the last call's contents (each call clears what must start at
+ * zero); calls that overlap on the GPU race and must be serialised by the
+ * caller.  Errors: PL_EINVAL (arguments, n too large), PL_ECUDA. */
+pl_status pl_fit_ks_noalloc(const int32_t *x_dev, int64_t n, uint64_t xmin,
+                            double alpha, pl_precision prec, double *out_dev,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ _NAMES = {1: "PL_EINVAL", 2: "PL_ENOMEM", 3: "PL_ENOCONV", 4: "PL_ETIMEOUT", 5: 
 
 EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters", "pl_set_tracing",
            "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
-           "pl_bootstrap_pvalue"]
+           "pl_bootstrap_pvalue", "pl_fit_ks_noalloc"]
 
 
 class pl_cell(ctypes.Structure):
@@ -73,7 +73,9 @@ _lib.pl_ks_cutoffs.argtypes = [_vp, ctypes.POINTER(pl_cell), ctypes.c_int, ctype
 _lib.pl_bootstrap_pvalue.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64,
                                      ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _f64p, _f64p,
                                      _f64p, _vp]
-for _f in ["pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+_lib.pl_fit_ks_noalloc.argtypes = [_vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
+                                   _vp, _vp]
+for _f in ["pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -205,3 +207,14 @@ class Context:
                                              prec, ctypes.byref(a), ctypes.byref(d), ctypes.byref(p),
                                              _stream_ptr(stream)))
         return a.value, d.value, p.value
+
+
+def pl_fit_ks_noalloc(x, xmin: int, alpha: float, out, prec: int = PL_FP64, stream=None):
+    """Fit (alpha NaN) or evaluate D at alpha for one data set, with the library's
+    fixed scratch instead of a context (no device allocation by the library).
+    x: int32 device tensor (n <= 262144); out: float64 device tensor of 3 elements
+    receiving (alpha, D, zeta(alpha, xmin)) in stream order."""
+    assert out.numel() >= 3 and out.element_size() == 8
+    st = _lib.pl_fit_ks_noalloc(_ptr(x), x.numel(), xmin, alpha, prec, _ptr(out), _stream_ptr(stream))
+    if st != PL_OK:
+        raise PLError(st, "pl_fit_ks_noalloc failed")
