@@ -31,6 +31,7 @@ struct pl_ctx {
   int num_sms = 0;
   int finish_blocks_per_sm[2] = {0, 0};
   int sample_blocks_per_sm = 0;
+  int block_sampler_per_sm = 0;
   uint64_t launches = 0;
   // Capacity overrides for tests (environment, read at pl_create; 0 = off):
   // they only shrink buffers so that the overflow fallbacks run.
@@ -47,7 +48,9 @@ struct pl_ctx {
 
 namespace {
 
-constexpr int64_t kWarpNMax = 16384;  // warp form: n per replicate up to this
+constexpr int64_t kWarpNMax = 16384;     // warp form: n per replicate up to this
+constexpr int64_t kWideNMax = 1 << 21;   // block form: n up to this (16-bit lane counters)
+constexpr uint32_t kWideItemReps = 4;    // block form: replicates per work item
 
 pl_status fail(pl_ctx *ctx, pl_status s, const char *fmt, ...) {
   char buf[512];
@@ -183,6 +186,7 @@ uint64_t next_pow2(uint64_t v) {
 // Everything one batch of replicate cells needs on the device.
 struct Wave {
   size_t first, count;             // items [first, first + count)
+  size_t wide;                     // the first `wide` items are block-form cells
 };
 
 struct SimPlan {
@@ -196,6 +200,7 @@ struct SimPlan {
   size_t dense_elems = 0, spill_elems = 0, meta_elems = 0;  // largest wave
   int64_t total_R = 0;
   int64_t n_max = 0;
+  int64_t finisher_spill = 0;      // spills one finisher warp must hold for one replicate
 };
 
 pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpose, SimPlan &sp) {
@@ -210,8 +215,8 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
       return fail(ctx, PL_EINVAL, "cell %d: alpha must be in (1, 64]", c);
     if (x.xmin < 1 || x.xmin > (1ull << 40)) return fail(ctx, PL_EINVAL, "cell %d: xmin out of range", c);
     if (x.n < 1) return fail(ctx, PL_EINVAL, "cell %d: n < 1", c);
-    if (x.n > kWarpNMax)
-      return fail(ctx, PL_EINVAL, "cell %d: n = %lld exceeds %lld", c, (long long)x.n, (long long)kWarpNMax);
+    if (x.n > kWideNMax)
+      return fail(ctx, PL_EINVAL, "cell %d: n = %lld exceeds %lld", c, (long long)x.n, (long long)kWideNMax);
     if (x.replicates < 1 || x.replicates > (1ll << 31)) return fail(ctx, PL_EINVAL, "cell %d: replicates", c);
     if (x.cell_id >= (1ull << 32)) return fail(ctx, PL_EINVAL, "cell %d: cell_id >= 2^32", c);
     const auto key = std::make_pair(x.alpha, x.xmin);
@@ -233,7 +238,8 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     cd.R = x.replicates;
     cd.cell_id = (uint32_t)x.cell_id;
     cd.law = li;
-    cd.H = hist_bins(x.n);
+    cd.wide = x.n > kWarpNMax ? 1u : 0u;
+    cd.H = cd.wide ? (uint32_t)kHWide : hist_bins(x.n);
     cd.purpose = purpose;
     cd.out_off = sp.total_R;
     auto fi = fit_of.find(x.xmin);
@@ -244,23 +250,30 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     cd.fit = fi->second;
     cd.scap = spill_capacity(x.alpha, x.xmin, x.n, cd.H);
     if (ctx->dbg_spill_cap) cd.scap = std::min(cd.scap, ctx->dbg_spill_cap);
+    sp.finisher_spill = std::max<int64_t>(sp.finisher_spill, cd.wide ? 2 * (int64_t)cd.scap : x.n);
     sp.total_R += x.replicates;
     sp.n_max = std::max(sp.n_max, x.n);
     sp.consts[c] = cell_const(x.xmin);
   }
+  // The samplers histogram table indices below H and treat index L2 as
+  // "beyond the table", so every law's table must reach past H.
+  std::vector<uint32_t> law_hmax(sp.laws.size(), 0);
+  for (const Cell &cd : sp.cells) law_hmax[cd.law] = std::max(law_hmax[cd.law], cd.H);
   for (size_t l = 0; l < sp.laws.size(); ++l)
-    sp.laws[l].L2 = table_length(sp.laws[l].alpha, sp.laws[l].xmin, law_draws[l]);
+    sp.laws[l].L2 = std::max<uint32_t>(table_length(sp.laws[l].alpha, sp.laws[l].xmin, law_draws[l]),
+                                       (uint32_t)next_pow2(2 * (uint64_t)law_hmax[l]));
   // work items: cells grouped by law (the block keeps a law's table staged),
   // larger n first within a law
   std::vector<int> order(ncells);
   for (int c = 0; c < ncells; ++c) order[c] = c;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (sp.cells[a].wide != sp.cells[b].wide) return sp.cells[a].wide > sp.cells[b].wide;
     if (sp.cells[a].law != sp.cells[b].law) return sp.cells[a].law < sp.cells[b].law;
     return sp.cells[a].n > sp.cells[b].n;
   });
   // items, and waves whose replicate records fit the wave byte budget
   const size_t wave_budget = std::min<size_t>(ctx->budget / 4, (size_t)4 << 30);
-  size_t wd = 0, ws = 0, wm = 0, first = 0;
+  size_t wd = 0, ws = 0, wm = 0, first = 0, nwide = 0;
   double wt = 0.0;  // expected beyond-table draws of the wave
   auto close_tail = [&]() {
     const double cap = std::ceil(2.0 * wt + 10.0 * std::sqrt(wt) + 1024.0);
@@ -272,20 +285,23 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     const double xq = (double)lp.xmin;
     const double Zq = std::pow(xq, -lp.alpha) + std::pow(xq + 0.5, 1.0 - lp.alpha) / (lp.alpha - 1.0);
     const double q_tail = std::min(1.0, std::pow(xq + lp.L2 - 0.5, 1.0 - lp.alpha) / ((lp.alpha - 1.0) * Zq));
-    for (int64_t r0 = 0; r0 < cd.R; r0 += kItemReps) {
+    const int64_t per_item = cd.wide ? (int64_t)kWideItemReps : (int64_t)kItemReps;
+    for (int64_t r0 = 0; r0 < cd.R; r0 += per_item) {
       WorkItem it{};
       it.cell = (uint32_t)c;
       it.r0 = (uint32_t)r0;
-      it.nrep = (uint32_t)std::min<int64_t>(kItemReps, cd.R - r0);
-      const size_t d = (size_t)it.nrep * cd.H, sp_ = (size_t)it.nrep * cd.scap, m = it.nrep;
+      it.nrep = (uint32_t)std::min<int64_t>(per_item, cd.R - r0);
+      const size_t d = (size_t)it.nrep * cd.H * (cd.wide ? 2 : 1), sp_ = (size_t)it.nrep * cd.scap, m = it.nrep;
       const size_t bytes_after = (wd + d) * 2 + (ws + sp_) * 8 + (wm + m) * 8;
       if (sp.items.size() > first && bytes_after > wave_budget) {
-        sp.waves.push_back({first, sp.items.size() - first});
+        sp.waves.push_back({first, sp.items.size() - first, nwide});
         close_tail();
         first = sp.items.size();
         wd = ws = wm = 0;
+        nwide = 0;
         wt = 0.0;
       }
+      if (cd.wide) ++nwide;
       wt += (double)it.nrep * (double)cd.n * q_tail;
       it.dense_off = wd;
       it.spill_off = ws;
@@ -299,7 +315,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
       sp.items.push_back(it);
     }
   }
-  sp.waves.push_back({first, sp.items.size() - first});
+  sp.waves.push_back({first, sp.items.size() - first, nwide});
   close_tail();
   if (ctx->dbg_tail_cap) sp.tail_cap = std::min(sp.tail_cap, ctx->dbg_tail_cap);
   return PL_OK;
@@ -319,11 +335,12 @@ struct SimBuffers {
   unsigned int *tq_count;
   uint8_t *scratch;
   size_t spill_cap, arena_bytes;
-  int blocks, sample_blocks;
+  int blocks, sample_blocks, block_sampler_blocks;
 };
 
 // Lay out (or size) the device buffers of a simulation plan.
-void carve_sim(Carver &cv, const SimPlan &sp, int blocks, int sample_blocks, SimBuffers &b, size_t arena_override) {
+void carve_sim(Carver &cv, const SimPlan &sp, int blocks, int sample_blocks, SimBuffers &b, size_t arena_override,
+               int block_sampler_blocks) {
   b.fits_host.clear();
   for (uint64_t xm : sp.fit_xmins) b.fits_host.push_back(make_fit_table(cv, xm));
   b.fits_dev = cv.take<FitTable>(sp.fit_xmins.size());
@@ -339,11 +356,12 @@ void carve_sim(Carver &cv, const SimPlan &sp, int blocks, int sample_blocks, Sim
   b.tq_pos = cv.take<uint64_t>(sp.tail_cap);
   b.tq_law = cv.take<uint32_t>(sp.tail_cap);
   b.tq_count = cv.take<unsigned int>(1);
-  b.spill_cap = next_pow2((uint64_t)std::max<int64_t>(sp.n_max, kSortSmem));
-  b.arena_bytes = ((16 * (size_t)sp.n_max + 16) + (size_t)32 * 2048 + 255) & ~(size_t)255;
-  if (arena_override) b.arena_bytes = std::max<size_t>(16 * (size_t)sp.n_max + 16, arena_override);
+  b.spill_cap = next_pow2((uint64_t)std::max<int64_t>(sp.finisher_spill, kSortSmem));
+  b.arena_bytes = ((16 * (size_t)sp.finisher_spill + 16) + (size_t)32 * 2048 + 255) & ~(size_t)255;
+  if (arena_override) b.arena_bytes = std::max<size_t>(16 * (size_t)sp.finisher_spill + 16, arena_override);
   b.blocks = blocks;
   b.sample_blocks = sample_blocks;
+  b.block_sampler_blocks = block_sampler_blocks;
   b.scratch = cv.take<uint8_t>((size_t)blocks * kWarps * (b.spill_cap * 8 + b.arena_bytes));
 }
 
@@ -383,12 +401,9 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
     SampleLaunch sl{};
     sl.cells = b.cells;
     sl.laws = b.laws_dev;
-    sl.items = b.items + w.first;
-    sl.nitems = (uint32_t)w.count;
     sl.rk = rk;
     sl.rec = b.rec;
     sl.ctr = ctx->ctr;
-    sl.blocks = (int)std::min<size_t>((size_t)b.sample_blocks, w.count);
     sl.tq_pos = b.tq_pos;
     sl.tq_law = b.tq_law;
     sl.tq_count = b.tq_count;
@@ -396,7 +411,21 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
     PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
     PL_CUDA(cudaMemsetAsync(b.tq_count, 0, sizeof(unsigned int), st));
     if (wev) PL_CUDA(cudaEventRecord(wev[0], st));
-    PL_CUDA(launch_sample_hist(sl, st));
+    if (w.wide) {  // block form items come first in the wave
+      sl.items = b.items + w.first;
+      sl.nitems = (uint32_t)w.wide;
+      sl.blocks = (int)std::min<size_t>((size_t)b.block_sampler_blocks, w.wide);
+      PL_CUDA(launch_sample_block(sl, st));
+      ctx->launches += 1;
+    }
+    if (w.count > w.wide) {
+      if (w.wide) PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
+      sl.items = b.items + w.first + w.wide;
+      sl.nitems = (uint32_t)(w.count - w.wide);
+      sl.blocks = (int)std::min<size_t>((size_t)b.sample_blocks, w.count - w.wide);
+      PL_CUDA(launch_sample_hist(sl, st));
+      ctx->launches += 1;
+    }
     if (wev) PL_CUDA(cudaEventRecord(wev[1], st));
     PL_CUDA(launch_tail_queue_raw(b.laws_dev, b.tq_pos, b.tq_law, b.tq_count, sp.tail_cap, b.rec.spill, ctx->ctr,
                                   ctx->num_sms, st));
@@ -420,7 +449,7 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
     if (wev) PL_CUDA(cudaEventRecord(wev[2], st));
     PL_CUDA(launch_finish(fl, f32, st));
     if (wev) PL_CUDA(cudaEventRecord(wev[3], st));
-    ctx->launches += 3;
+    ctx->launches += 2;
   }
   return PL_OK;
 }
@@ -485,6 +514,7 @@ pl_status pl_create(pl_ctx **out, int device, size_t mem_budget_bytes) {
   ctx->finish_blocks_per_sm[0] = finish_kernel_blocks_per_sm(false);
   ctx->finish_blocks_per_sm[1] = finish_kernel_blocks_per_sm(true);
   ctx->sample_blocks_per_sm = sample_kernel_blocks_per_sm();
+  ctx->block_sampler_per_sm = block_sampler_blocks_per_sm();
   cudaGetLastError();
   *out = ctx;
   return PL_OK;
@@ -651,9 +681,10 @@ pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells, uint64_t 
   if (pl_status s = plan_cells(ctx, cells, ncells, 0u, sp)) return s;
   const bool host_out = !is_device_ptr(cutoffs);
   const size_t dsz = f32 ? 4 : 8;
-  const int blocks = sim_blocks(ctx, f32), sblocks = sample_blocks(ctx);
+  const int blocks = sim_blocks(ctx, f32), sblocks = sample_blocks(ctx),
+            bsblocks = ctx->num_sms * std::max(1, ctx->block_sampler_per_sm);
   auto lay = [&](Carver &cv, SimBuffers &b, void *&D, int64_t *&off, int64_t *&Rs, int64_t *&rank, double *&cut) {
-    carve_sim(cv, sp, blocks, sblocks, b, ctx->dbg_arena);
+    carve_sim(cv, sp, blocks, sblocks, b, ctx->dbg_arena, bsblocks);
     D = D_dev_opt ? D_dev_opt : (void *)cv.take<uint8_t>((size_t)sp.total_R * dsz);
     off = cv.take<int64_t>(ncells);
     Rs = cv.take<int64_t>(ncells);
@@ -711,9 +742,10 @@ pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint
   pl_cell cell{obs[0], xmin, n, B, request_id};
   SimPlan sp;
   if (pl_status s = plan_cells(ctx, &cell, 1, 1u, sp)) return s;
-  const int blocks = sim_blocks(ctx, f32), sblocks = sample_blocks(ctx);
+  const int blocks = sim_blocks(ctx, f32), sblocks = sample_blocks(ctx),
+            bsblocks = ctx->num_sms * std::max(1, ctx->block_sampler_per_sm);
   auto lay = [&](Carver &cv, SimBuffers &b, void *&Db, double *&dobs, double *&pd) {
-    carve_sim(cv, sp, blocks, sblocks, b, ctx->dbg_arena);
+    carve_sim(cv, sp, blocks, sblocks, b, ctx->dbg_arena, bsblocks);
     Db = cv.take<uint8_t>((size_t)B * (f32 ? 4 : 8));
     dobs = cv.take<double>(1);
     pd = cv.take<double>(1);

@@ -25,6 +25,7 @@ constexpr int kL1 = PL_L1_ENTRIES;          // thresholds staged in shared memor
 constexpr int kGuideBits = 11;              // guide table: 2^11 buckets of m
 constexpr int kGuide = 1 << kGuideBits;
 constexpr int kHMax = 1024;                 // dense histogram bins per warp
+constexpr int kHWide = 8192;                // dense histogram bins per block (block form)
 constexpr int kWarps = 8;                   // warps per block, warp form
 constexpr int kSortSmem = kHMax / 2;        // spills sorted on chip up to this count
 constexpr int kLnTable = 16384;             // ln(xmin + i) tables, i < kLnTable
@@ -33,7 +34,7 @@ constexpr int kNewtonCap = 200;             // Newton iteration cap
 // Device status word bits (latched; read by pl_sync).
 constexpr uint32_t kErrTimeout = 1u;        // a bounded mbarrier wait ran out
 constexpr uint32_t kErrData = 2u;           // a data value below xmin
-constexpr uint32_t kErrArena = 4u;          // per-warp arena too small (host bug)
+constexpr uint32_t kErrArena = 4u;          // a replicate's spills exceeded every buffer
 
 struct Counters {
   unsigned long long newton_capped;
@@ -77,6 +78,8 @@ struct Cell {
   int64_t out_off;        // offset of replicate 0 in the per-replicate outputs
   uint32_t fit;           // index into the fit-table array (one per xmin)
   uint32_t scap;          // spill slot capacity of a replicate record
+  uint32_t wide;          // block form: 32-bit dense counts, H = kHWide
+  uint32_t pad;
 };
 
 // A block-sized batch of replicates of one cell, with the offsets of its

@@ -692,6 +692,119 @@ __global__ void __launch_bounds__(kAWarps * 32, 3) sample_hist_kernel(SampleLaun
   }
 }
 
+// Block form (large n): a block per replicate, kHWide 32-bit bins in shared
+// memory, per-thread register counters for bins 0..3 (at most n/1024 + 2
+// draws per thread and bin; the host keeps n <= 2^25).
+constexpr int kBlkThreads = 512;
+
+__global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaunch a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
+  uint32_t *sG = reinterpret_cast<uint32_t *>(smem + kL1 * 8);
+  uint32_t *hist = reinterpret_cast<uint32_t *>(smem + kL1 * 8 + kGuide * 4);
+  int *s_spill = reinterpret_cast<int *>(hist + kHWide);
+  uint32_t *s_item = reinterpret_cast<uint32_t *>(s_spill + 1);
+  int *s_tmax = reinterpret_cast<int *>(s_item + 1);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(s_tmax + 2);
+  StagedLaw staged{sT, sG, mbar};
+  const int lane = threadIdx.x & 31;
+  const TailQueue tq{a.tq_pos, a.tq_law, a.tq_count, a.tq_cap};
+  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  __syncthreads();
+  uint32_t phase = 0, loaded = 0xffffffffu;
+  for (;;) {
+    if (threadIdx.x == 0) *s_item = atomicAdd(&a.ctr->work_next, 1u);
+    __syncthreads();
+    const uint32_t item = *s_item;
+    if (item >= a.nitems) break;
+    const WorkItem wi = a.items[item];
+    const Cell cell = a.cells[wi.cell];
+    const Law law = a.laws[cell.law];
+    if (cell.law != loaded) {
+      if (!stage_law(staged, law, phase, a.ctr)) return;
+      loaded = cell.law;
+    }
+    const uint32_t H = cell.H;
+    const int64_t n = cell.n;
+    for (uint32_t j = 0; j < wi.nrep; ++j) {
+      const uint32_t rep = wi.r0 + j;
+      for (uint32_t i = threadIdx.x; i < H; i += kBlkThreads) hist[i] = 0;
+      if (threadIdx.x == 0) {
+        *s_spill = 0;
+        *s_tmax = -1;
+      }
+      __syncthreads();
+      const uint64_t pos0 = wi.spill_off + (uint64_t)j * cell.scap;
+      uint64_t *spill = a.rec.spill + pos0;
+      uint64_t packed = 0;
+      const int64_t npairs = (n + 1) >> 1;
+      for (int64_t p = threadIdx.x; p < npairs; p += kBlkThreads) {
+        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), a.rk);
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          if (2 * p + jj < n) {
+            const uint64_t m = draw_bits(jj ? w.z : w.x, jj ? w.w : w.y);
+            const uint32_t b = lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m);
+            if (b < 4) {
+              packed += 1ull << (16 * b);
+            } else if (b < H) {
+              atomicAdd(&hist[b], 1u);
+            } else {
+              const int slot = atomicAdd(s_spill, 1);
+              if (slot < (int64_t)cell.scap) {
+                if (b < law.L2) {
+                  spill[slot] = cell.xmin + b;
+                } else {
+                  spill[slot] = kTailTag | m;
+                  const unsigned q = atomicAdd(tq.count, 1u);
+                  if (q < tq.cap) {
+                    tq.pos[q] = pos0 + (uint64_t)slot;
+                    tq.law[q] = cell.law;
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)((packed >> (16 * q)) & 0xffffu));
+        if (lane == 0 && c) atomicAdd(&hist[q], c);
+      }
+      __syncthreads();
+      int tm = -1;
+      for (uint32_t i = threadIdx.x; i < H; i += kBlkThreads)
+        if (hist[i]) tm = (int)i;
+      tm = (int)__reduce_max_sync(0xffffffffu, (unsigned)(tm + 1)) - 1;
+      if (lane == 0 && tm >= 0) atomicMax(s_tmax, tm);
+      __syncthreads();
+      const int tmax = *s_tmax;
+      uint32_t *dense = reinterpret_cast<uint32_t *>(a.rec.dense + wi.dense_off + (uint64_t)j * 2 * H);
+      for (int i = threadIdx.x; i <= tmax; i += kBlkThreads) dense[i] = hist[i];
+      if (threadIdx.x == 0) a.rec.meta[wi.meta_off + j] = make_int2(tmax, *s_spill);
+      __syncthreads();
+    }
+  }
+}
+
+size_t block_sampler_smem_bytes() {
+  return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kHWide * 4 + 32 + 16;
+}
+
+int block_sampler_blocks_per_sm() {
+  int nb = 0;
+  const size_t smem = block_sampler_smem_bytes();
+  cudaFuncSetAttribute(sample_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_block_kernel, kBlkThreads, smem);
+  return nb;
+}
+
+cudaError_t launch_sample_block(const SampleLaunch &a, cudaStream_t st) {
+  sample_block_kernel<<<a.blocks, kBlkThreads, block_sampler_smem_bytes(), st>>>(a);
+  return cudaGetLastError();
+}
+
 // Beyond-table draws queued by the sampler: one thread per draw (full lanes),
 // binary64 inversion written back into the record.
 __global__ void __launch_bounds__(256) tail_queue_kernel(const Law *laws, TailQueue tq, uint64_t *spill,
@@ -795,9 +908,13 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
           const int64_t tm = __shfl_sync(0xffffffffu, my_tmax, r);
           const int64_t ns = __shfl_sync(0xffffffffu, my_nsd, r);
           const size_t off = __shfl_sync(0xffffffffu, my_off, r);
-          const uint16_t *dense = a.rec.dense + wi.dense_off + (uint64_t)(j0 + r) * cell.H;
-          const double D = ks_warp<F32, uint16_t>(dense, tm, reinterpret_cast<const uint64_t *>(arena + off), ns,
-                                                  n, fr, law.lnT, law.lnT_hi, law.lnT_lo, lane);
+          const uint16_t *dense =
+              a.rec.dense + wi.dense_off + (uint64_t)(j0 + r) * (uint64_t)cell.H * (cell.wide ? 2 : 1);
+          const uint64_t *pr = reinterpret_cast<const uint64_t *>(arena + off);
+          const double D =
+              cell.wide ? ks_warp<F32, uint32_t>(reinterpret_cast<const uint32_t *>(dense), tm, pr, ns, n, fr,
+                                                 law.lnT, law.lnT_hi, law.lnT_lo, lane)
+                        : ks_warp<F32, uint16_t>(dense, tm, pr, ns, n, fr, law.lnT, law.lnT_hi, law.lnT_lo, lane);
           if (lane == r) myD = D;
         }
         PL_PHASE(4);
@@ -814,17 +931,29 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
         const int2 meta = a.rec.meta[wi.meta_off + j];
         int64_t tmax = meta.x;
         const int64_t s = meta.y;
-        uint16_t *dense = a.rec.dense + wi.dense_off + (uint64_t)j * cell.H;
+        const uint64_t dslot = (uint64_t)cell.H * (cell.wide ? 2 : 1);
+        uint16_t *dense = a.rec.dense + wi.dense_off + (uint64_t)j * dslot;
+        uint32_t *dense32 = cell.wide ? reinterpret_cast<uint32_t *>(dense) : nullptr;
         uint64_t *sp = a.rec.spill + wi.spill_off + (uint64_t)j * cell.scap;
         if (s > (int64_t)cell.scap) {
           // the record's spill slot overflowed: draw this replicate again with
-          // the warp's global spill buffer (same stream, same values)
+          // the warp's global spill buffer (same stream, same values); the
+          // block form's histogram is rebuilt in place in the record
           if (lane == 0) atomicAdd(&a.ctr->resampled, 1ull);
-          tmax = draw_replicate<false>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp], spill,
-                                       (int64_t)a.spill_cap, lane, nullptr, 0);
-          for (int64_t i = lane; i <= tmax; i += 32) dense[i] = (uint16_t)hist[i];
+          if (cell.wide) {
+            tmax = draw_replicate<false>(sT, sG, law, cell, wi.r0 + j, a.rk, dense32, &s_spill[warp], spill,
+                                         (int64_t)a.spill_cap, lane, nullptr, 0);
+          } else {
+            tmax = draw_replicate<false>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp], spill,
+                                         (int64_t)a.spill_cap, lane, nullptr, 0);
+            for (int64_t i = lane; i <= tmax; i += 32) dense[i] = (uint16_t)hist[i];
+          }
           __syncwarp();
           sp = spill;
+          if (s > (int64_t)a.spill_cap) {  // beyond every buffer: report, leave this batch
+            if (lane == 0) atomicOr(&a.ctr->status, kErrArena);
+            break;
+          }
         }
         PL_PHASE(0);
         // resolve the draws that fell beyond the threshold table (binary64 inversion)
@@ -840,13 +969,14 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
         double L;
         if (!F32) {
           double acc = 0.0;
-          for (int64_t i = lane; i <= tmax; i += 32) acc += (double)dense[i] * law.lnT[i];
+          for (int64_t i = lane; i <= tmax; i += 32)
+            acc += (double)(dense32 ? dense32[i] : (uint32_t)dense[i]) * law.lnT[i];
           for (int64_t k = lane; k < s; k += 32) acc += log((double)sp[k]);
           L = warp_sum(acc);
         } else {
           float h = 0.0f, l = 0.0f;
           for (int64_t i = lane; i <= tmax; i += 32) {
-            const float c = (float)dense[i];
+            const float c = (float)(dense32 ? dense32[i] : (uint32_t)dense[i]);
             const float ph = c * law.lnT_hi[i];
             const float pe = fmaf(c, law.lnT_hi[i], -ph) + c * law.lnT_lo[i];
             ff_add(h, l, ph, pe);
@@ -859,7 +989,7 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
           warp_sum_ff(h, l);
           L = (double)h + (double)l;
         }
-        if (tmax >= 0 && (int64_t)dense[0] == n) L += cc.ln_allmin;
+        if (tmax >= 0 && (int64_t)(dense32 ? dense32[0] : (uint32_t)dense[0]) == n) L += cc.ln_allmin;
         PL_PHASE(1);
         // arena space for this replicate's spill pairs; run phases 2-3 early if full
         const size_t need = (size_t)s * 16;

@@ -196,7 +196,57 @@ def test_cutoffs_device_output_and_batching_invariance(ctx, pl):
 
 
 FALLBACK_CELLS = [(1.5, 1, 5000, 300, 1), (1.75, 1, 16384, 40, 5), (2.5, 1, 100, 700, 0),
-                  (3.0, 5, 20, 513, 4), (1.5, 1, 2000, 257, 9)]
+                  (3.0, 5, 20, 513, 4), (1.5, 1, 2000, 257, 9), (2.0, 1, 40000, 9, 14)]
+
+# block form (n beyond the warp form), mixed with warp-form cells in one call
+WIDE_CELLS = [(2.0, 1, 20000, 24, 11), (1.75, 1, 50000, 8, 12), (2.5, 2, 100000, 5, 13),
+              (1.6, 5, 16385, 7, 15), (3.0, 1, 100, 300, 16)]
+
+
+@pytest.fixture(scope="module")
+def wide_oracle():
+    return _oracle_cells(WIDE_CELLS)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_block_form_matches_oracle(ctx, pl, wide_oracle, prec):
+    cells = [pl.Cell(*c) for c in WIDE_CELLS]
+    total = sum(c[3] for c in WIDE_CELLS)
+    D = torch.empty(total, dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
+    A = torch.empty(total, dtype=torch.float64, device="cuda")
+    q = [0.5, 0.9]
+    cut = ctx.pl_ks_cutoffs(cells, 1, q, prec, D=D, alpha_hat=A)
+    ctx.pl_sync()
+    atol_a, atol_d = TOL[prec]
+    off = 0
+    for ci, (a, xm, n, R, cid) in enumerate(WIDE_CELLS):
+        dg = D[off:off + R].double().cpu().numpy()
+        ag = A[off:off + R].cpu().numpy()
+        assert np.max(np.abs(ag / wide_oracle[1][ci] - 1)) < atol_a, ci
+        assert np.max(np.abs(dg - wide_oracle[0][ci])) < atol_d, ci
+        assert np.max(np.abs(cut[ci] - oracle.quantiles(wide_oracle[0][ci], q))) < atol_d + 1e-15
+        off += R
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_large_n_cell_full_size_sampled(ctx, pl, prec):
+    """alpha = 2, n = 1,000,000, 10,000 replicates: sampled replicates against the
+    oracle; cutoffs are the order statistics of the returned D."""
+    c = inputs.large_n_cell()[0]
+    D = torch.empty(c.replicates, dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
+    A = torch.empty(c.replicates, dtype=torch.float64, device="cuda")
+    q = [0.9, 0.95, 0.99]
+    cut = ctx.pl_ks_cutoffs([pl.Cell(c.alpha, c.xmin, c.n, c.replicates, c.cell_id)], 1, q, prec, D=D, alpha_hat=A)
+    ctx.pl_sync()
+    atol_a, atol_d = TOL[prec]
+    for r in [0, 4321, c.replicates - 1]:
+        a_or, d_or = oracle.replicate(c.alpha, c.xmin, c.n, 1, c.cell_id, r, 0)
+        assert abs(A[r].item() / a_or - 1) < atol_a
+        assert abs(D[r].item() - d_or) < atol_d
+    s = torch.sort(D).values.double()
+    for j, qq in enumerate(q):
+        assert cut[0, j] == s[oracle.quantile_index(c.replicates, qq)].item()
+    assert ctx.pl_counters()["newton_capped"] == 0
 
 
 @pytest.mark.parametrize("env,counter", [
