@@ -148,16 +148,32 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--replicates", type=int, default=100_000,
                     help="replicates per cell (smaller values for profiler captures only)")
+    ap.add_argument("--workload", choices=["sweep", "small", "large-n", "batched"], default="sweep",
+                    help="sweep: the 90-cell table (the benchmark line); small: alpha=2.5, n=100, "
+                         "10,000 replicates; large-n: alpha=2, n=1e6, 10,000 replicates; batched: "
+                         "4,096 uneven instances x 2,000 replicates in one graph-captured launch")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    sweep = inputs.cutoff_table_sweep(args.replicates)
+    if args.workload == "sweep":
+        sweep = inputs.cutoff_table_sweep(args.replicates)
+        wname = ("KS cutoff-table sweep: alpha in {1.5,...,3.5} (9) x n in {10,...,10000} (10), "
+                 f"xmin=1, {args.replicates:,} replicates per cell")
+    elif args.workload == "small":
+        sweep = inputs.cutoff_cell_small()
+        wname = "single cell: alpha=2.5, xmin=1, n=100, 10,000 replicates"
+    elif args.workload == "large-n":
+        sweep = inputs.large_n_cell()
+        wname = "large-n heavy tail: alpha=2.0, xmin=1, n=1,000,000, 10,000 replicates (block form)"
+    else:
+        sweep = inputs.batched_instances()
+        wname = ("batched uneven: 4,096 instances, n log-uniform [10,1e5], alpha U(1.6,3.2), "
+                 "xmin in {1,2,5}, 2,000 replicates each; one plan, graph-captured launch, autotuned split")
     total_R = sum(c.replicates for c in sweep)
     draws = sum(c.replicates * c.n for c in sweep)
-    config = {"workload": "KS cutoff-table sweep: alpha in {1.5,...,3.5} (9) x n in {10,...,10000} (10), "
-                          f"xmin=1, {args.replicates:,} replicates per cell",
+    config = {"workload": wname,
               "cells": len(sweep), "replicates_per_step": total_R, "draws_per_step": draws,
               "precision_form": args.precision, "seed": 1, "quantiles": Q,
               "l2": "256 MiB buffer written between timed steps (L2 flush)",
@@ -212,9 +228,34 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    ctx.pl_set_tracing(True)
+    graph = None
+    if args.workload == "batched":
+        # untimed set-up: autotuned warp/block split, plan (tables), graph capture
+        t0 = time.perf_counter()
+        split = ctx.pl_autotune()
+        plan = ctx.pl_plan_cutoffs(cells, Q, prec)
+        config["autotuned_split_n"] = split
+        config["plan_ms"] = (time.perf_counter() - t0) * 1e3
+        gstream = torch.cuda.Stream()
+        with torch.cuda.stream(gstream):
+            plan.run(seed, cut, stream=gstream)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        l0 = ctx.pl_trace()["launches"]
+        with torch.cuda.graph(graph, stream=gstream):
+            plan.run(seed, cut)
+        torch.cuda.synchronize()
+        kernels_per_replay = ctx.pl_trace()["launches"] - l0
+
+    def step():
+        if graph is not None:
+            graph.replay()
+        else:
+            ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=cut)
+
+    ctx.pl_set_tracing(graph is None)
     for _ in range(args.warmup):
-        ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=cut)
+        step()
     ctx.pl_sync()
     launches0 = ctx.pl_trace()["launches"]
 
@@ -227,16 +268,19 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=cut)
+        step()
         e1.record(stream)
         tr = ctx.pl_trace()  # synchronises; kernel time from events on the call's stream
         step_ms.append(e0.elapsed_time(e1))
-        kern_ms.append(tr["sample_ms"])
-        fin_ms.append(tr["finish_ms"])
-        waves = tr["waves"]
+        if graph is None:
+            kern_ms.append(tr["sample_ms"])
+            fin_ms.append(tr["finish_ms"])
+            waves = tr["waves"]
     barrier()
     clocks = sampler.stop()
     launches = ctx.pl_trace()["launches"] - launches0
+    if graph is not None:  # each replay launches the captured kernels
+        launches = kernels_per_replay * args.steps
     ctx.pl_sync()
     total_ms = sum(step_ms)
     if dist is not None:
@@ -255,6 +299,11 @@ def main():
         t0 = time.perf_counter()
         ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=host_cut)
         e2e_s.append(time.perf_counter() - t0)
+    if graph is not None:  # trace one plain call for the per-kernel times
+        ctx.pl_set_tracing(True)
+        ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=cut)
+        tr = ctx.pl_trace()
+        kern_ms, fin_ms, waves = [tr["sample_ms"]], [tr["finish_ms"]], tr["waves"]
     e2e_value = world * total_R / statistics.mean(e2e_s)
     h2d = len(cells) * 40 + len(Q) * 8
     d2h = host_cut.nbytes

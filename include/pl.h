@@ -30,8 +30,11 @@
  *   next pl_sync or by the next entry point with a host output.
  * - Randomness: draw i of replicate r is a pure function of
  *   (seed, cell_id, r, purpose, i) through Philox4x32-10 (counter
- *   (i/2, r, cell_id, purpose), key = seed); results never depend on launch
- *   shape, batching or precision form.  purpose: 0 = cutoff simulation,
+ *   (i/2, r, cell_id, purpose), key = seed).  Sampled values never depend on
+ *   launch shape, batching, the warp/block split or the precision form; for a
+ *   given split and precision form every result is bit-identical whether a
+ *   cell runs alone or with others.  Changing the split changes the rounding
+ *   of alpha-hat and D at the 1e-15 level.  purpose: 0 = cutoff simulation,
  *   1 = parametric bootstrap, 2 = test data.
  * - Heavy tail: simulated values are uint64 and saturate at 2^62.
  */
@@ -168,6 +171,37 @@ pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells,
                         uint64_t seed, const double *q, int nq,
                         pl_precision prec, double *cutoffs, void *D_dev_opt,
                         double *alpha_hat_dev_opt, void *stream);
+
+/* Autotuner of the warp/block split: replicates with n above the split use
+ * the block-per-replicate form, the others the warp-per-replicate form.  The
+ * split starts at 16384; pl_autotune times both forms on the context's GPU
+ * (alpha = 2, 4,096 replicates, n = 2^12 .. 2^16) and sets the split to the
+ * largest n bucket where the warp form is faster (results never depend on
+ * it).  Synchronises `stream`; *split_out (host, may be NULL) receives it.
+ * pl_set_split sets it directly (1 <= split <= 65535). */
+pl_status pl_autotune(pl_ctx *ctx, void *stream, int64_t *split_out);
+pl_status pl_set_split(pl_ctx *ctx, int64_t split);
+
+/* The same computation split in two, so that the simulation can be enqueued
+ * repeatedly (for example inside a captured CUDA graph).
+ * pl_plan_cutoffs validates the cells (as pl_ks_cutoffs), allocates the
+ * plan's own device memory (at most the context's byte budget), uploads its
+ * cell, law and work tables, builds the law and fit tables on `stream`, and
+ * synchronises `stream`.
+ * pl_plan_run enqueues the simulation and the order statistics for `seed` on
+ * `stream`: kernel launches and memsets only -- no allocation, no host
+ * copy, no synchronisation.  cutoffs_dev: device double[ncells * nq];
+ * D_dev_opt / alpha_hat_dev_opt as in pl_ks_cutoffs.  A plan uses its
+ * context's counters: do not run it concurrently with other work of the
+ * same context.
+ * Errors: as pl_ks_cutoffs; PL_ENOMEM if the plan exceeds the budget. */
+typedef struct pl_plan pl_plan;
+pl_status pl_plan_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells,
+                          const double *q, int nq, pl_precision prec,
+                          pl_plan **out, void *stream);
+pl_status pl_plan_run(pl_plan *plan, uint64_t seed, double *cutoffs_dev,
+                      void *D_dev_opt, double *alpha_hat_dev_opt, void *stream);
+void pl_plan_destroy(pl_plan *plan);
 
 /* Goodness of fit of a data set (Section 3's use of the tables, with the
  * bespoke cutoff computed by simulation): fit alpha-hat (Eq. 2), compute D

@@ -32,6 +32,7 @@ struct pl_ctx {
   int finish_blocks_per_sm[2] = {0, 0};
   int sample_blocks_per_sm = 0;
   int block_sampler_per_sm = 0;
+  int64_t warp_split = 16384;    // n above this: block form
   uint64_t launches = 0;
   // Capacity overrides for tests (environment, read at pl_create; 0 = off):
   // they only shrink buffers so that the overflow fallbacks run.
@@ -48,9 +49,9 @@ struct pl_ctx {
 
 namespace {
 
-constexpr int64_t kWarpNMax = 16384;     // warp form: n per replicate up to this
+constexpr int64_t kWarpNMax = 65535;     // warp form: n up to this (16-bit dense record counts)
 constexpr int64_t kWideNMax = 1 << 21;   // block form: n up to this (16-bit lane counters)
-constexpr uint32_t kWideItemReps = 4;    // block form: replicates per work item
+constexpr uint32_t kWideItemReps = 8;    // block form: replicates per work item
 
 pl_status fail(pl_ctx *ctx, pl_status s, const char *fmt, ...) {
   char buf[512];
@@ -105,17 +106,17 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Length of the inverse-CDF table: the smallest kL1 * 2^k whose last entry
-// leaves at most 1e-6 of the mass (or ~1000 expected draws) beyond it, at most
-// 2^20.  Sizing only: uses the continuous tail approximation.
+// Length of the inverse-CDF table: the smallest kL1 * 2^k (at most 2^20) at
+// which the binary64 tail inversions it leaves (draws * P(X beyond), each about
+// four times the cost of building one table entry) cost no more than the
+// table itself.  Sizing only: uses the continuous tail approximation.
 uint32_t table_length(double alpha, uint64_t xmin, double draws) {
   const double x = (double)xmin;
   const double Zapprox = std::pow(x, -alpha) + std::pow(x + 0.5, 1.0 - alpha) / (alpha - 1.0);
-  const double target = std::max(1e-6, draws > 0 ? 1000.0 / draws : 0.0);
   uint32_t L = kL1;
   while (L < (1u << 20)) {
     const double Q = std::pow(x + L - 0.5, 1.0 - alpha) / ((alpha - 1.0) * Zapprox);
-    if (Q <= target) break;
+    if (4.0 * draws * Q <= (double)L) break;
     L <<= 1;
   }
   return L;
@@ -238,7 +239,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     cd.R = x.replicates;
     cd.cell_id = (uint32_t)x.cell_id;
     cd.law = li;
-    cd.wide = x.n > kWarpNMax ? 1u : 0u;
+    cd.wide = x.n > std::min(kWarpNMax, ctx->warp_split) ? 1u : 0u;
     cd.H = cd.wide ? (uint32_t)kHWide : hist_bins(x.n);
     cd.purpose = purpose;
     cd.out_off = sp.total_R;
@@ -382,9 +383,10 @@ pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t
 }
 
 pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, bool f32, void *D,
-                  double *A, cudaStream_t st) {
+                  double *A, cudaStream_t st, bool trace = true) {
   const RoundKeys rk = round_keys(seed);
-  if (ctx->tracing) {
+  trace = trace && ctx->tracing;
+  if (trace) {
     while (ctx->wave_ev.size() < 4 * sp.waves.size()) {
       cudaEvent_t e;
       PL_CUDA(cudaEventCreate(&e));
@@ -396,7 +398,7 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
   }
   size_t wi_ = 0;
   for (const Wave &w : sp.waves) {
-    cudaEvent_t *wev = ctx->tracing ? &ctx->wave_ev[4 * wi_] : nullptr;
+    cudaEvent_t *wev = trace ? &ctx->wave_ev[4 * wi_] : nullptr;
     ++wi_;
     SampleLaunch sl{};
     sl.cells = b.cells;
@@ -726,6 +728,153 @@ pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells, uint64_t 
     return read_status(ctx, st);
   }
   return PL_OK;
+}
+
+}  // extern "C"
+
+struct pl_plan {
+  pl_ctx *ctx = nullptr;
+  SimPlan sp;
+  SimBuffers b;
+  uint8_t *mem = nullptr;
+  void *D = nullptr;
+  int64_t *off = nullptr, *Rs = nullptr, *rank = nullptr;
+  int ncells = 0, nq = 0;
+  bool f32 = false;
+};
+
+extern "C" {
+
+pl_status pl_set_split(pl_ctx *ctx, int64_t split) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (split < 1 || split > kWarpNMax) return fail(ctx, PL_EINVAL, "split must be in [1, %lld]", (long long)kWarpNMax);
+  ctx->warp_split = split;
+  return PL_OK;
+}
+
+pl_status pl_autotune(pl_ctx *ctx, void *stream, int64_t *split_out) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t saved = ctx->warp_split;
+  const bool saved_tracing = ctx->tracing;
+  if (pl_status s = pl_set_tracing(ctx, 1)) return s;
+  const double q = 0.9;
+  double cut = 0.0;
+  int64_t best = 1;
+  pl_status st_all = PL_OK;
+  for (int64_t n = 4096; n <= 65536; n *= 2) {
+    const int64_t nn = std::min(n, kWarpNMax);
+    pl_cell cell{2.0, 1, nn, 4096, 0};
+    float t[2] = {0.0f, 0.0f};
+    for (int form = 0; form < 2 && !st_all; ++form) {  // 0: warp, 1: block
+      ctx->warp_split = form == 0 ? kWarpNMax : 1;
+      for (int rep = 0; rep < 2 && !st_all; ++rep) {  // second run timed
+        st_all = pl_ks_cutoffs(ctx, &cell, 1, 1, &q, 1, PL_FP32_BULK, &cut, nullptr, nullptr, stream);
+        if (!st_all) {
+          pl_trace_info ti;
+          st_all = pl_trace(ctx, stream, &ti);
+          t[form] = ti.replicate_ms;
+        }
+      }
+    }
+    if (st_all) break;
+    if (t[0] <= t[1]) best = nn;
+    else break;
+  }
+  ctx->warp_split = st_all ? saved : best;
+  pl_set_tracing(ctx, saved_tracing ? 1 : 0);
+  PL_CUDA(cudaStreamSynchronize(st));
+  if (split_out) *split_out = ctx->warp_split;
+  return st_all;
+}
+
+pl_status pl_plan_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells, const double *q, int nq,
+                          pl_precision prec, pl_plan **out, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!out || !cells || ncells < 1 || !q || nq < 1) return fail(ctx, PL_EINVAL, "pl_plan_cutoffs: bad arguments");
+  *out = nullptr;
+  if (prec != PL_FP64 && prec != PL_FP32_BULK) return fail(ctx, PL_EINVAL, "unknown precision form");
+  for (int j = 0; j < nq; ++j)
+    if (!(q[j] > 0.0 && q[j] < 1.0)) return fail(ctx, PL_EINVAL, "quantile %d outside (0, 1)", j);
+  cudaStream_t st = (cudaStream_t)stream;
+  pl_plan *pp = new pl_plan();
+  pp->ctx = ctx;
+  pp->ncells = ncells;
+  pp->nq = nq;
+  pp->f32 = prec == PL_FP32_BULK;
+  if (pl_status s = plan_cells(ctx, cells, ncells, 0u, pp->sp)) {
+    delete pp;
+    return s;
+  }
+  const SimPlan &sp = pp->sp;
+  const int blocks = sim_blocks(ctx, pp->f32), sblocks = sample_blocks(ctx),
+            bsblocks = ctx->num_sms * std::max(1, ctx->block_sampler_per_sm);
+  auto lay = [&](Carver &cv) {
+    carve_sim(cv, sp, blocks, sblocks, pp->b, ctx->dbg_arena, bsblocks);
+    pp->D = cv.take<uint8_t>((size_t)sp.total_R * (pp->f32 ? 4 : 8));
+    pp->off = cv.take<int64_t>(ncells);
+    pp->Rs = cv.take<int64_t>(ncells);
+    pp->rank = cv.take<int64_t>((size_t)ncells * nq);
+  };
+  Carver cv;
+  lay(cv);
+  if (cv.off > ctx->budget) {
+    delete pp;
+    return fail(ctx, PL_ENOMEM, "plan of %zu bytes exceeds the budget of %zu", cv.off, ctx->budget);
+  }
+  if (cudaMalloc(&pp->mem, cv.off) != cudaSuccess) {
+    cudaGetLastError();
+    delete pp;
+    return fail(ctx, PL_ENOMEM, "plan allocation of %zu bytes failed", cv.off);
+  }
+  cv.base = pp->mem;
+  cv.off = 0;
+  lay(cv);
+  pl_status s = upload_sim(ctx, sp, pp->b, st);
+  std::vector<int64_t> h_off(ncells), h_R(ncells), h_rank((size_t)ncells * nq);
+  for (int c = 0; c < ncells; ++c) {
+    h_off[c] = sp.cells[c].out_off;
+    h_R[c] = sp.cells[c].R;
+    for (int j = 0; j < nq; ++j) {
+      int64_t i = (int64_t)std::floor((double)h_R[c] * q[j]);
+      h_rank[(size_t)c * nq + j] = std::min(std::max<int64_t>(i, 0), h_R[c] - 1);
+    }
+  }
+  if (!s && (cudaMemcpyAsync(pp->off, h_off.data(), sizeof(int64_t) * ncells, cudaMemcpyHostToDevice, st) ||
+             cudaMemcpyAsync(pp->Rs, h_R.data(), sizeof(int64_t) * ncells, cudaMemcpyHostToDevice, st) ||
+             cudaMemcpyAsync(pp->rank, h_rank.data(), sizeof(int64_t) * h_rank.size(), cudaMemcpyHostToDevice,
+                             st)))
+    s = fail(ctx, PL_ECUDA, "plan upload failed");
+  if (!s) s = read_status(ctx, st);
+  if (s) {
+    cudaFree(pp->mem);
+    delete pp;
+    return s;
+  }
+  *out = pp;
+  return PL_OK;
+}
+
+pl_status pl_plan_run(pl_plan *plan, uint64_t seed, double *cutoffs_dev, void *D_dev_opt,
+                      double *alpha_hat_dev_opt, void *stream) {
+  if (!plan) return PL_EINVAL;
+  pl_ctx *ctx = plan->ctx;
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!cutoffs_dev) return fail(ctx, PL_EINVAL, "pl_plan_run: null cutoffs");
+  cudaStream_t st = (cudaStream_t)stream;
+  void *D = D_dev_opt ? D_dev_opt : plan->D;
+  if (pl_status s = run_sim(ctx, plan->sp, plan->b, seed, plan->f32, D, alpha_hat_dev_opt, st, false)) return s;
+  PL_CUDA(launch_select(D, plan->f32, plan->off, plan->Rs, plan->rank, plan->ncells, plan->nq, cutoffs_dev, st));
+  ctx->launches += 1;
+  return PL_OK;
+}
+
+void pl_plan_destroy(pl_plan *plan) {
+  if (!plan) return;
+  cudaSetDevice(plan->ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(plan->mem);
+  delete plan;
 }
 
 pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint64_t xmin, int64_t B,

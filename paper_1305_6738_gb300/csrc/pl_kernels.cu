@@ -880,8 +880,10 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
       if (!stage_law(staged, law, phase, a.ctr)) return;
       loaded = cell.law;
     }
-    const int j0 = warp * kBRepsPerWarp;
-    const int nb = (int)min((int64_t)kBRepsPerWarp, (int64_t)wi.nrep - j0);
+    // the item's replicates spread evenly over the warps (at most 32 each)
+    const int per_warp = (int)((wi.nrep + kWarps - 1) / kWarps);
+    const int j0 = warp * per_warp;
+    const int nb = (int)min((int64_t)per_warp, (int64_t)wi.nrep - j0);
     if (nb > 0) {
       const int64_t n = cell.n;
       const uint64_t xmin = cell.xmin;
@@ -965,31 +967,26 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
           }
         }
         __syncwarp();
-        // log-sum  L = sum ln x_i  (+ ln((xmin+1)/xmin) if every x_i = xmin)
+        // log-sum  L = sum ln x_i  (+ ln((xmin+1)/xmin) if every x_i = xmin):
+        // dense part here, spill part after sorting (so that the summation
+        // order, and hence the rounding, never depends on the spill order)
         double L;
+        float Lh = 0.0f, Ll = 0.0f;
         if (!F32) {
           double acc = 0.0;
           for (int64_t i = lane; i <= tmax; i += 32)
             acc += (double)(dense32 ? dense32[i] : (uint32_t)dense[i]) * law.lnT[i];
-          for (int64_t k = lane; k < s; k += 32) acc += log((double)sp[k]);
           L = warp_sum(acc);
         } else {
-          float h = 0.0f, l = 0.0f;
           for (int64_t i = lane; i <= tmax; i += 32) {
             const float c = (float)(dense32 ? dense32[i] : (uint32_t)dense[i]);
             const float ph = c * law.lnT_hi[i];
             const float pe = fmaf(c, law.lnT_hi[i], -ph) + c * law.lnT_lo[i];
-            ff_add(h, l, ph, pe);
+            ff_add(Lh, Ll, ph, pe);
           }
-          for (int64_t k = lane; k < s; k += 32) {
-            float vh, vl;
-            ln_u64_ff(sp[k], vh, vl);
-            ff_add(h, l, vh, vl);
-          }
-          warp_sum_ff(h, l);
-          L = (double)h + (double)l;
+          L = 0.0;
         }
-        if (tmax >= 0 && (int64_t)(dense32 ? dense32[0] : (uint32_t)dense[0]) == n) L += cc.ln_allmin;
+        const bool allmin = tmax >= 0 && (int64_t)(dense32 ? dense32[0] : (uint32_t)dense[0]) == n;
         PL_PHASE(1);
         // arena space for this replicate's spill pairs; run phases 2-3 early if full
         const size_t need = (size_t)s * 16;
@@ -1009,6 +1006,22 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
         }
         uint64_t *pairs = reinterpret_cast<uint64_t *>(arena + arena_off);
         const int64_t nsd = spill_compact(sp, hist, s, pairs, lane, a.ctr);
+        if (!F32) {
+          double acc = 0.0;
+          for (int64_t k = lane; k < nsd; k += 32) acc += (double)pairs[2 * k + 1] * log((double)pairs[2 * k]);
+          L += warp_sum(acc);
+        } else {
+          for (int64_t k = lane; k < nsd; k += 32) {
+            float vh, vl;
+            ln_u64_ff(pairs[2 * k], vh, vl);
+            const float c = (float)pairs[2 * k + 1];
+            const float ph = c * vh;
+            ff_add(Lh, Ll, ph, fmaf(c, vh, -ph) + c * vl);
+          }
+          warp_sum_ff(Lh, Ll);
+          L = (double)Lh + (double)Ll;
+        }
+        if (allmin) L += cc.ln_allmin;
         if (lane == r) {
           myL = L;
           my_tmax = tmax;
@@ -1103,7 +1116,6 @@ __global__ void __launch_bounds__(1024) dataset_kernel(const int32_t *x, int64_t
   // log-sum (binary64 here: one data set, no bulk)
   double acc = 0.0;
   for (int64_t i = threadIdx.x; i <= tmax; i += blockDim.x) acc += (double)hist[i] * law.lnT[i];
-  for (int64_t k = threadIdx.x; k < s; k += blockDim.x) acc += log((double)spill[k]);
   acc = warp_sum(acc);
   if (lane == 0) s_red[warp] = acc;
   // sort the spills in global memory (block bitonic), padded to a power of two
@@ -1159,6 +1171,11 @@ __global__ void __launch_bounds__(1024) dataset_kernel(const int32_t *x, int64_t
       __syncwarp();
       if (k < base) pairs[2 * k + 1] = cnt;
       __syncwarp();
+    }
+    {  // spill part of the log-sum, over the sorted distinct values
+      double sacc = 0.0;
+      for (int64_t k = lane; k < base; k += 32) sacc += (double)pairs[2 * k + 1] * log((double)pairs[2 * k]);
+      L += warp_sum(sacc);
     }
     FitOut fo{};
     if (fit) {

@@ -28,7 +28,8 @@ _NAMES = {1: "PL_EINVAL", 2: "PL_ENOMEM", 3: "PL_ENOCONV", 4: "PL_ETIMEOUT", 5: 
 
 EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters", "pl_set_tracing",
            "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
-           "pl_bootstrap_pvalue", "pl_fit_ks_noalloc"]
+           "pl_bootstrap_pvalue", "pl_fit_ks_noalloc", "pl_plan_cutoffs", "pl_plan_run",
+           "pl_plan_destroy", "pl_autotune", "pl_set_split"]
 
 
 class pl_cell(ctypes.Structure):
@@ -73,9 +74,16 @@ _lib.pl_ks_cutoffs.argtypes = [_vp, ctypes.POINTER(pl_cell), ctypes.c_int, ctype
 _lib.pl_bootstrap_pvalue.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64,
                                      ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _f64p, _f64p,
                                      _f64p, _vp]
+_lib.pl_plan_cutoffs.argtypes = [_vp, ctypes.POINTER(pl_cell), ctypes.c_int, _f64p, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(_vp), _vp]
+_lib.pl_plan_run.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _vp, _vp]
+_lib.pl_autotune.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]
+_lib.pl_set_split.argtypes = [_vp, ctypes.c_int64]
+_lib.pl_plan_destroy.argtypes = [_vp]
+_lib.pl_plan_destroy.restype = None
 _lib.pl_fit_ks_noalloc.argtypes = [_vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
                                    _vp, _vp]
-for _f in ["pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+for _f in ["pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -200,6 +208,23 @@ class Context:
             return host.reshape(len(cells), qa.size)
         return cutoffs
 
+    def pl_autotune(self, stream=None) -> int:
+        v = ctypes.c_int64()
+        self._check(_lib.pl_autotune(self._h, _stream_ptr(stream), ctypes.byref(v)))
+        return v.value
+
+    def pl_set_split(self, split: int):
+        self._check(_lib.pl_set_split(self._h, split))
+
+    def pl_plan_cutoffs(self, cells, q, prec: int = PL_FP64, stream=None) -> "Plan":
+        arr = (pl_cell * len(cells))(*[pl_cell(c.alpha, c.xmin, c.n, c.replicates, c.cell_id)
+                                       for c in cells])
+        qa = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        h = _vp()
+        self._check(_lib.pl_plan_cutoffs(self._h, arr, len(cells), qa.ctypes.data_as(_f64p), qa.size,
+                                         prec, ctypes.byref(h), _stream_ptr(stream)))
+        return Plan(self, h)
+
     def pl_bootstrap_pvalue(self, x, xmin: int, B: int, seed: int, request_id: int,
                             prec: int = PL_FP64, stream=None):
         a, d, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
@@ -207,6 +232,29 @@ class Context:
                                              prec, ctypes.byref(a), ctypes.byref(d), ctypes.byref(p),
                                              _stream_ptr(stream)))
         return a.value, d.value, p.value
+
+
+class Plan:
+    """A planned cutoff computation (pl_plan_cutoffs); run() only enqueues kernels."""
+
+    def __init__(self, ctx: Context, h):
+        self._ctx = ctx
+        self._h = h
+
+    def run(self, seed: int, cutoffs, D=None, alpha_hat=None, stream=None):
+        self._ctx._check(_lib.pl_plan_run(self._h, seed, _ptr(cutoffs), _ptr(D), _ptr(alpha_hat),
+                                          _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pl_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pl_fit_ks_noalloc(x, xmin: int, alpha: float, out, prec: int = PL_FP64, stream=None):

@@ -282,6 +282,64 @@ def test_fallback_paths_are_bit_identical(pl, monkeypatch, env, counter):
             assert cnt[counter] > 0
 
 
+def test_plan_run_and_graph_capture(ctx, pl):
+    cells = [pl.Cell(*c) for c in SMALL_CELLS[:5]] + [pl.Cell(2.0, 2, 30000, 6, 21)]
+    tot = sum(c.replicates for c in cells)
+    q = [0.9, 0.99]
+    D_ref = torch.empty(tot, dtype=torch.float64, device="cuda")
+    cut_ref = ctx.pl_ks_cutoffs(cells, 7, q, 0, D=D_ref)
+    ctx.pl_sync()
+    plan = ctx.pl_plan_cutoffs(cells, q, 0)
+    cut1 = torch.empty(len(cells) * len(q), dtype=torch.float64, device="cuda")
+    D1 = torch.empty_like(D_ref)
+    plan.run(7, cut1, D=D1)
+    torch.cuda.synchronize()
+    assert torch.equal(D1, D_ref)
+    assert (cut1.cpu().numpy().reshape(len(cells), -1) == cut_ref).all()
+    s = torch.cuda.Stream()
+    cut2 = torch.zeros_like(cut1)
+    D2 = torch.zeros_like(D_ref)
+    with torch.cuda.stream(s):
+        plan.run(7, cut2, D=D2, stream=s)
+    torch.cuda.synchronize()
+    D2.zero_()
+    cut2.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(7, cut2, D=D2)
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(D2, D_ref)
+        assert torch.equal(cut2, cut1)
+    plan.close()
+
+
+def test_split_and_autotune_keep_parity(pl):
+    # the warp/block split changes which values are histogrammed and which are
+    # spilled, hence the summation order: results agree to the FP64 parity bars
+    c = pl.Context(0)
+    cells = [pl.Cell(2.0, 1, 3000, 64, 31), pl.Cell(1.75, 2, 20000, 16, 32)]
+    ref = None
+    for split in (1, 65535, 16384, 1, 65535):
+        c.pl_set_split(split)
+        D = torch.empty(80, dtype=torch.float64, device="cuda")
+        A = torch.empty(80, dtype=torch.float64, device="cuda")
+        c.pl_ks_cutoffs(cells, 3, [0.9], 0, D=D, alpha_hat=A)
+        c.pl_sync()
+        if ref is None:
+            ref = (D.clone(), A.clone())
+        assert torch.max(torch.abs(D - ref[0])).item() < 1e-12
+        assert torch.max(torch.abs(A / ref[1] - 1)).item() < 1e-10
+    split = c.pl_autotune()
+    assert 1 <= split <= 65535
+    D = torch.empty(80, dtype=torch.float64, device="cuda")
+    c.pl_ks_cutoffs(cells, 3, [0.9], 0, D=D)
+    c.pl_sync()
+    assert torch.max(torch.abs(D - ref[0])).item() < 1e-12
+    c.close()
+
+
 @pytest.mark.parametrize("bad", [
     dict(alpha=1.0), dict(alpha=0.5), dict(xmin=0), dict(n=0), dict(replicates=0),
     dict(cell_id=2**32), dict(q=[1.0]), dict(q=[0.0]),
@@ -362,3 +420,41 @@ def test_bootstrap_rejects_lognormal(ctx, pl):
     assert a == pytest.approx(a_or, rel=1e-10)
     assert abs(d - d_or) < 1e-6
     assert p == 0.0
+
+
+def test_batched_instances_full_size_graph(ctx, pl):
+    """4,096 uneven instances x 2,000 replicates, planned once and replayed from a
+    CUDA graph: sampled replicates (warp and block forms) against the oracle."""
+    inst = inputs.batched_instances()
+    cells = [pl.Cell(c.alpha, c.xmin, c.n, c.replicates, c.cell_id) for c in inst]
+    tot = sum(c.replicates for c in inst)
+    D = torch.empty(tot, dtype=torch.float32, device="cuda")
+    A = torch.empty(tot, dtype=torch.float64, device="cuda")
+    cut = torch.empty(len(cells) * 2, dtype=torch.float64, device="cuda")
+    plan = ctx.pl_plan_cutoffs(cells, [0.9, 0.99], 1)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.run(1, cut, D=D, alpha_hat=A, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(1, cut, D=D, alpha_hat=A)
+    D.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    offs = np.cumsum([0] + [c.replicates for c in inst])
+    rng = np.random.default_rng(5)
+    small = [i for i, c in enumerate(inst) if c.n <= 2000]
+    big = [i for i, c in enumerate(inst) if c.n > 16384 and c.n < 40000]
+    picks = list(rng.choice(small, 6, replace=False)) + list(rng.choice(big, 3, replace=False))
+    for i in picks:
+        c = inst[i]
+        r = int(rng.integers(c.replicates))
+        a_or, d_or = oracle.replicate(c.alpha, c.xmin, c.n, 1, c.cell_id, r, 0)
+        assert abs(A[offs[i] + r].item() / a_or - 1) < 1e-6
+        assert abs(D[offs[i] + r].item() - d_or) < 1e-6
+    cutc = cut.cpu().numpy().reshape(len(cells), 2)
+    for i in picks[:3]:
+        srt = torch.sort(D[offs[i]:offs[i + 1]]).values.double().cpu().numpy()
+        assert cutc[i, 0] == srt[oracle.quantile_index(inst[i].replicates, 0.9)]
+    plan.close()
