@@ -136,6 +136,177 @@ def cpu_oracle_rate(sample_reps: int, threads: int) -> dict:
                       f"timed per cell and extrapolated linearly to 100,000 replicates per cell"}
 
 
+# ----------------------------------------------------------------------------- serving
+SERVE_B = 2500
+SERVE_RATE = 200.0
+SERVE_BUDGET = 40 << 30
+
+
+def serving_config(args) -> dict:
+    return {"workload": (f"serving: Poisson arrivals at {SERVE_RATE:.0f} fit requests/s, n log-uniform "
+                         "[50, 1e6], alpha U(1.5, 3.5), xmin=1, 10% rounded-lognormal data; per request "
+                         f"MLE, D and a {SERVE_B:,}-replicate bootstrap p-value; 40 GB device budget"),
+            "rate_per_s": SERVE_RATE, "B": SERVE_B, "duration_s": args.duration,
+            "warmup_s": args.serve_warmup, "budget_bytes": SERVE_BUDGET, "workers": args.workers,
+            "precision_form": args.precision, "request_seed": 4, "bootstrap_seed": 1,
+            "l2": "inputs larger than L2 in aggregate (requests of up to 4 MB stream through)",
+            "parallelism": "one GPU, requests overlapped on per-worker streams"}
+
+
+def request_data_lognormal(r):
+    import numpy as np
+    return inputs.rounded_lognormal(np.random.default_rng((44, r.request_id)), r.n)
+
+
+def serving_cpu_baseline(reqs, threads: int) -> dict:
+    """The oracle's bootstrap on a bounded sample of the request stream: 32
+    requests spread evenly over it (their data drawn by the oracle's sampler, the same integers the
+    library's sampler gives), timed with b1 and b2 replicates and extrapolated
+    linearly to B (the data fit is the intercept)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    picks = reqs[::max(1, len(reqs) // 32)][:32]
+    b1, b2 = threads, 3 * threads
+    per = []
+    wall = 0.0
+    for r in picks:
+        if r.lognormal:
+            x = request_data_lognormal(r)
+        else:
+            x = inputs.as_request_data(oracle.sample(r.alpha, r.xmin, 4, r.request_id, 0,
+                                                     inputs.PURPOSE_TESTDATA, r.n))
+        t = []
+        for b in (b1, b2):
+            t0 = time.perf_counter()
+            oracle.bootstrap_pvalue(x, r.xmin, b, 1, r.request_id, threads)
+            t.append(time.perf_counter() - t0)
+        wall += sum(t)
+        slope = max(0.0, (t[1] - t[0]) / (b2 - b1))
+        per.append(t[0] + slope * (SERVE_B - b1))
+    return {"value": len(per) / sum(per), "p50_ms": 1e3 * statistics.median(per), "wall_s": wall,
+            "sample": (f"{len(per)} requests spread evenly over the stream, oracle bootstrap timed at B={b1} "
+                       f"and B={b2} and extrapolated linearly to B={SERVE_B}; requests served one at a time")}
+
+
+def serving_requests_and_data(args, pl, ctx, torch):
+    """Request schedule and host int32 data: power-law data from the library's
+    sampler (stream tag 2, cell id = request id, seed 4), lognormal data from
+    the input module; generated before the clock starts."""
+    reqs = inputs.serving_requests(args.serve_warmup + args.duration, SERVE_RATE, seed=4)
+    buf = torch.empty(max(r.n for r in reqs), dtype=torch.int64, device="cuda")
+    data = []
+    for r in reqs:
+        if r.lognormal:
+            data.append(request_data_lognormal(r))
+            continue
+        ctx.pl_sample(r.alpha, r.xmin, 4, r.request_id, inputs.PURPOSE_TESTDATA, 0, 1, r.n, buf)
+        data.append(buf[:r.n].clamp(max=inputs.INT32_MAX).to(torch.int32).cpu().numpy())
+    return reqs, data
+
+
+def run_serving(args):
+    import threading
+    import numpy as np
+    threads = os.cpu_count() or 1
+    config = serving_config(args)
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        reqs = inputs.serving_requests(args.serve_warmup + args.duration, SERVE_RATE, seed=4)
+        cb = serving_cpu_baseline([r for r in reqs if r.arrival_s >= args.serve_warmup], threads)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "requests/s",
+                "n_gpus": 0, "steps": len(reqs), "warmup": 0, "ms_per_step": 1e3 / cb["value"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic request stream", "config": config,
+                "cpu_baseline": {"value": cb["value"], "unit": "requests/s", "cores": threads,
+                                 "kind": "oracle", "sample": cb["sample"]},
+                "e2e": {"value": cb["value"], "unit": "requests/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1305_6738_gb300 import pl
+    ctx = pl.Context(local)
+    t0 = time.perf_counter()
+    reqs, data = serving_requests_and_data(args, pl, ctx, torch)
+    config["generate_s"] = time.perf_counter() - t0
+    ctx.close()
+    prec = pl.PL_FP32_BULK if args.precision == "fp32-bulk" else pl.PL_FP64
+    srv = pl.Server(local, SERVE_BUDGET, workers=args.workers, prec=prec, seed=1, B=SERVE_B)
+    base = srv.pl_server_now() + 0.2
+    lag = []
+
+    def submit_all():
+        for r, x in zip(reqs, data):
+            dt = base + r.arrival_s - srv.pl_server_now()
+            if dt > 0:
+                time.sleep(dt)
+            lag.append(srv.pl_server_now() - (base + r.arrival_s))
+            srv.pl_server_submit(r.request_id, x, r.xmin)
+
+    sampler = None
+    results = {}
+    th = threading.Thread(target=submit_all)
+    th.start()
+    max_queue = max_running = 0
+    max_reserved = 0
+    launches0 = None
+    while len(results) < len(reqs):
+        now = srv.pl_server_now()
+        if sampler is None and now >= base + args.serve_warmup:
+            sampler = ClockSampler(gpu_query_id(local))
+            launches0 = srv.pl_server_load()[3]
+        for res in srv.pl_server_poll(256, 0.01):
+            results[res["request_id"]] = res
+        q, run, rb, _ = srv.pl_server_load()
+        if sampler is not None:
+            max_queue, max_running, max_reserved = max(max_queue, q), max(max_running, run), max(max_reserved, rb)
+    th.join()
+    clocks = sampler.stop() if sampler else {}
+    launches = srv.pl_server_load()[3] - (launches0 or 0)
+    srv.close()
+
+    timed = [r for r in reqs if r.arrival_s >= args.serve_warmup]
+    bad = [results[r.request_id]["status"] for r in timed if results[r.request_id]["status"] != 0]
+    lat = np.array([results[r.request_id]["done_s"] - (base + r.arrival_s) for r in timed]) * 1e3
+    wait = np.array([results[r.request_id]["start_s"] - results[r.request_id]["submit_s"] for r in timed]) * 1e3
+    t_first = base + timed[0].arrival_s
+    t_last = max(results[r.request_id]["done_s"] for r in timed)
+    span = t_last - t_first
+    value = len(timed) / span
+    draws = sum(SERVE_B * r.n for r in timed)
+    h2d = statistics.mean(4 * r.n for r in timed)
+    big = np.array([r.n >= 100_000 for r in timed])
+    line = {"metric": METRIC, "value": value, "unit": "requests/s", "n_gpus": 1, "steps": len(timed),
+            "warmup": sum(1 for r in reqs if r.arrival_s < args.serve_warmup),
+            "ms_per_step": 1e3 * span / len(timed), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == pl.PL_FP32_BULK else "f64",
+            "data": "synthetic request stream (library sampler, stream tag 2; rounded lognormal)",
+            "config": config,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max()), "mean": float(lat.mean()),
+                           "p50_n_ge_1e5": float(np.percentile(lat[big], 50)) if big.any() else None,
+                           "p99_n_lt_1e5": float(np.percentile(lat[~big], 99)) if (~big).any() else None,
+                           "queue_wait_p99": float(np.percentile(wait, 99)),
+                           "submit_lag_p99": float(np.percentile(np.array(lag) * 1e3, 99))},
+            "draws_per_s": draws / span, "failed_requests": len(bad),
+            "load": {"max_queued": max_queue, "max_running": max_running, "max_reserved_bytes": max_reserved},
+            "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": 24,
+                    "note": "the serving value is end to end: host data in, host results out"},
+            "gpu_launches": launches, "clocks": clocks}
+    if not args.no_cpu_baseline:
+        cb = serving_cpu_baseline(timed, threads)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": "requests/s", "cores": threads,
+                                "kind": "oracle", "sample": cb["sample"], "p50_ms": cb["p50_ms"]}
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -148,11 +319,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--replicates", type=int, default=100_000,
                     help="replicates per cell (smaller values for profiler captures only)")
-    ap.add_argument("--workload", choices=["sweep", "small", "large-n", "batched"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "small", "large-n", "batched", "serving"],
+                    default="sweep",
                     help="sweep: the 90-cell table (the benchmark line); small: alpha=2.5, n=100, "
                          "10,000 replicates; large-n: alpha=2, n=1e6, 10,000 replicates; batched: "
-                         "4,096 uneven instances x 2,000 replicates in one graph-captured launch")
+                         "4,096 uneven instances x 2,000 replicates in one graph-captured launch; "
+                         "serving: Poisson fit requests at 200/s through the serving engine")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: measured seconds")
+    ap.add_argument("--serve-warmup", type=float, default=5.0, help="serving: warm-up seconds")
+    ap.add_argument("--workers", type=int, default=8, help="serving: engine worker slots")
     args = ap.parse_args()
+    if args.workload == "serving":
+        return run_serving(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

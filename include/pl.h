@@ -175,9 +175,9 @@ pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells,
 /* Autotuner of the warp/block split: replicates with n above the split use
  * the block-per-replicate form, the others the warp-per-replicate form.  The
  * split starts at 16384; pl_autotune times both forms on the context's GPU
- * (alpha = 2, 4,096 replicates, n = 2^12 .. 2^16) and sets the split to the
- * largest n bucket where the warp form is faster (results never depend on
- * it).  Synchronises `stream`; *split_out (host, may be NULL) receives it.
+ * (alpha = 2, 4,096 replicates, n = 2^9 .. 2^16) and sets the split to the
+ * largest n bucket up to which the warp form is faster (at least 256).  The
+ * split changes only rounding (see Randomness above).  Synchronises `stream`; *split_out (host, may be NULL) receives it.
  * pl_set_split sets it directly (1 <= split <= 65535). */
 pl_status pl_autotune(pl_ctx *ctx, void *stream, int64_t *split_out);
 pl_status pl_set_split(pl_ctx *ctx, int64_t split);
@@ -214,6 +214,53 @@ pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
                               uint64_t request_id, pl_precision prec,
                               double *alpha_hat, double *D, double *p,
                               void *stream);
+
+/* Serving engine: continuous batching of goodness-of-fit requests.  The
+ * paper has no serving layer; each request computes what pl_bootstrap_pvalue
+ * computes (Eq. 2, Eq. 3 and the bootstrap p-value at alpha-hat), and the
+ * engine only schedules them.
+ * `workers` host threads each own a context (with the fit tables of every
+ * xmin seen kept on the device) and a non-blocking stream, so up to `workers`
+ * requests run on the GPU at the same time.  A request is admitted, oldest
+ * first, when a worker is free and its planned device workspace fits in
+ * mem_budget_bytes (0 = 40 GiB) beside the requests already running; one
+ * request larger than the whole budget runs alone and fails with PL_ENOMEM.
+ * Results are the same numbers pl_bootstrap_pvalue gives for that request
+ * alone on a fresh context (seed, B, prec as given here; cell_id =
+ * request_id), bit for bit.
+ * pl_server_create: device as in pl_create; 1 <= workers <= 64; B >= 1.
+ *   Errors: PL_EINVAL, PL_ECUDA, PL_ENOMEM.
+ * pl_server_submit: x_host is host int32[n] (values >= xmin), copied before
+ *   the call returns; request_id < 2^32.  Never blocks on the GPU.
+ * pl_server_poll: moves up to max_results finished requests (host array
+ *   pl_result[max_results]) in finishing order and returns their number,
+ *   waiting up to wait_s seconds for the first one.
+ * pl_server_now: seconds since create on the clock of the result times.
+ * pl_server_load: queued requests, running requests, reserved bytes, and
+ *   kernels launched by the finished requests (each pointer may be NULL).
+ * pl_server_destroy: drops queued requests, waits for running ones, frees
+ *   everything. */
+typedef struct pl_server pl_server;
+typedef struct {
+  uint64_t request_id;
+  int32_t status; /* pl_status of this request */
+  int32_t pad;
+  int64_t n;
+  double alpha_hat, D, p;
+  double submit_s, start_s, done_s; /* pl_server_now at submit, start, finish */
+} pl_result;
+
+pl_status pl_server_create(pl_server **out, int device, size_t mem_budget_bytes,
+                           int workers, pl_precision prec, uint64_t seed,
+                           int64_t B);
+pl_status pl_server_submit(pl_server *srv, uint64_t request_id,
+                           const int32_t *x_host, int64_t n, uint64_t xmin);
+int pl_server_poll(pl_server *srv, pl_result *out, int max_results,
+                   double wait_s);
+double pl_server_now(const pl_server *srv);
+pl_status pl_server_load(pl_server *srv, int *queued, int *running,
+                         size_t *reserved_bytes, uint64_t *launches);
+void pl_server_destroy(pl_server *srv);
 
 /* Fit and KS distance of one data set with no device allocation at all.
  * The paper has no counterpart: this is an engineering variant of

@@ -1,6 +1,6 @@
 """Compile the sm_103a CUDA library (libpl.so) in-tree with nvcc.
 
-Two translation units are compiled in parallel for one target
+The translation units are compiled in parallel for one target
 (-gencode arch=compute_103a,code=sm_103a) and linked into a shared library
 with the CUDA runtime linked statically; the result lands in ``_build/``.
 """
@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpl.so")
-SOURCES = ["pl_kernels.cu", "pl_api.cu", "pl_noalloc.cu"]
+SOURCES = ["pl_kernels.cu", "pl_api.cu", "pl_noalloc.cu", "pl_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + ARCH
 

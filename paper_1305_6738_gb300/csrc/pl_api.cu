@@ -43,6 +43,10 @@ struct pl_ctx {
   bool traced = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> wave_ev;   // 4 per wave: sampler start/end, finisher start/end
+  // Fit tables depend only on xmin; a serving context keeps them.
+  bool cache_fits = false;
+  std::map<uint64_t, FitTable> fit_cache;   // complete host copies (pointers into fit_mem)
+  std::vector<void *> fit_mem;
   uint32_t traced_waves = 0;
   uint64_t traced_draws = 0;
 };
@@ -374,10 +378,37 @@ pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t
                           cudaMemcpyHostToDevice, st));
   PL_CUDA(cudaMemcpyAsync(b.items, sp.items.data(), sizeof(WorkItem) * sp.items.size(),
                           cudaMemcpyHostToDevice, st));
+  std::vector<size_t> fresh;  // fit tables to build
+  for (size_t i = 0; i < b.fits_host.size(); ++i) {
+    const uint64_t xm = b.fits_host[i].xmin;
+    if (ctx->cache_fits) {
+      auto it = ctx->fit_cache.find(xm);
+      if (it != ctx->fit_cache.end()) {
+        b.fits_host[i] = it->second;
+        continue;
+      }
+      void *mem = nullptr;
+      PL_CUDA(cudaMalloc(&mem, sizeof(FitNode) * kFitNodes + sizeof(int) * kFitGuides));
+      ctx->fit_mem.push_back(mem);
+      b.fits_host[i].node = reinterpret_cast<FitNode *>(mem);
+      b.fits_host[i].guide = reinterpret_cast<int *>(reinterpret_cast<FitNode *>(mem) + kFitNodes);
+    }
+    fresh.push_back(i);
+  }
   PL_CUDA(cudaMemcpyAsync(b.fits_dev, b.fits_host.data(), sizeof(FitTable) * b.fits_host.size(),
                           cudaMemcpyHostToDevice, st));
   PL_CUDA(launch_law_setup(b.laws_dev, (int)b.laws_host.size(), st));
-  PL_CUDA(launch_fit_tables(b.fits_dev, (int)b.fits_host.size(), st));
+  if (fresh.size() == b.fits_host.size()) {
+    PL_CUDA(launch_fit_tables(b.fits_dev, (int)b.fits_host.size(), st));
+  } else {
+    for (size_t i : fresh) PL_CUDA(launch_fit_tables(b.fits_dev + i, 1, st));
+  }
+  if (ctx->cache_fits && !fresh.empty()) {  // keep the completed tables (guide origin set on device)
+    PL_CUDA(cudaMemcpyAsync(b.fits_host.data(), b.fits_dev, sizeof(FitTable) * b.fits_host.size(),
+                            cudaMemcpyDeviceToHost, st));
+    PL_CUDA(cudaStreamSynchronize(st));
+    for (size_t i : fresh) ctx->fit_cache[b.fits_host[i].xmin] = b.fits_host[i];
+  }
   ctx->launches += 5;
   return PL_OK;
 }
@@ -491,6 +522,29 @@ pl_status read_status(pl_ctx *ctx, cudaStream_t st) {
 
 }  // namespace
 
+// Hooks for the serving engine (pl_server.cu).
+namespace pl {
+void ctx_enable_fit_cache(pl_ctx *ctx) { ctx->cache_fits = true; }
+uint64_t ctx_launches(const pl_ctx *ctx) { return ctx->launches; }
+
+// Device bytes a bootstrap request of n values and B replicates plans (the
+// data-set pass and the simulation; alpha taken as 2 for sizing).
+size_t ctx_bootstrap_bytes(pl_ctx *ctx, int64_t n, uint64_t xmin, int64_t B) {
+  pl_cell cell{2.0, xmin, n, B, 0};
+  SimPlan sp;
+  if (plan_cells(ctx, &cell, 1, 1u, sp) != PL_OK) return 0;
+  const int blocks = sim_blocks(ctx, true), sblocks = sample_blocks(ctx),
+            bsblocks = ctx->num_sms * std::max(1, ctx->block_sampler_per_sm);
+  Carver cv;
+  SimBuffers b;
+  carve_sim(cv, sp, blocks, sblocks, b, ctx->dbg_arena, bsblocks);
+  cv.take<uint8_t>((size_t)B * 8 + 16);
+  const size_t sim = cv.off;
+  const size_t data = (size_t)next_pow2((uint64_t)n) * 8 + (size_t)n * 16 + (1u << 20);
+  return std::max(sim, data);
+}
+}  // namespace pl
+
 // ===========================================================================
 extern "C" {
 
@@ -529,6 +583,7 @@ void pl_destroy(pl_ctx *ctx) {
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
   for (auto &e : ctx->wave_ev) cudaEventDestroy(e);
+  for (void *m : ctx->fit_mem) cudaFree(m);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->ctr) cudaFree(ctx->ctr);
   delete ctx;
@@ -760,9 +815,9 @@ pl_status pl_autotune(pl_ctx *ctx, void *stream, int64_t *split_out) {
   if (pl_status s = pl_set_tracing(ctx, 1)) return s;
   const double q = 0.9;
   double cut = 0.0;
-  int64_t best = 1;
+  int64_t best = 256;  // the warp form is kept below the smallest bucket tried
   pl_status st_all = PL_OK;
-  for (int64_t n = 4096; n <= 65536; n *= 2) {
+  for (int64_t n = 512; n <= 65536; n *= 2) {
     const int64_t nn = std::min(n, kWarpNMax);
     pl_cell cell{2.0, 1, nn, 4096, 0};
     float t[2] = {0.0f, 0.0f};

@@ -565,7 +565,6 @@ __device__ int64_t spill_compact(uint64_t *spill, uint32_t *onchip, int64_t s, u
 //   phase 3 (warp per replicate): KS distance.
 constexpr int kAWarps = 16;
 constexpr int kARepsPerWarp = kItemReps / kAWarps;
-constexpr int kBRepsPerWarp = kItemReps / kWarps;
 
 // Draws of one replicate into a histogram.  PACKED: two 16-bit bins per word
 // (hist holds H/2 words); otherwise one 32-bit bin per word.  Spills beyond the

@@ -103,3 +103,13 @@ def rounded_lognormal(rng: np.random.Generator, n: int, mu: float = 2.0, sigma: 
         out[filled:filled + v.size] = v.astype(np.int64)
         filled += v.size
     return out.astype(np.int32)
+
+
+INT32_MAX = 2**31 - 1
+
+
+def as_request_data(values) -> np.ndarray:
+    """Fit requests carry int32 data: sampled values above 2^31 - 1 (the far
+    tail at exponents near 1.5, a few per million draws) are clamped to it."""
+    v = np.asarray(values).view(np.uint64) if np.asarray(values).dtype == np.int64 else np.asarray(values)
+    return np.minimum(v.astype(np.uint64), np.uint64(INT32_MAX)).astype(np.int32)

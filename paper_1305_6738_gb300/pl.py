@@ -29,7 +29,8 @@ _NAMES = {1: "PL_EINVAL", 2: "PL_ENOMEM", 3: "PL_ENOCONV", 4: "PL_ETIMEOUT", 5: 
 EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters", "pl_set_tracing",
            "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue", "pl_fit_ks_noalloc", "pl_plan_cutoffs", "pl_plan_run",
-           "pl_plan_destroy", "pl_autotune", "pl_set_split"]
+           "pl_plan_destroy", "pl_autotune", "pl_set_split", "pl_server_create", "pl_server_submit",
+           "pl_server_poll", "pl_server_now", "pl_server_load", "pl_server_destroy"]
 
 
 class pl_cell(ctypes.Structure):
@@ -49,6 +50,13 @@ class pl_trace_info(ctypes.Structure):
                 ("total_ms", ctypes.c_float), ("sample_ms", ctypes.c_float),
                 ("finish_ms", ctypes.c_float), ("waves", ctypes.c_uint32),
                 ("draws", ctypes.c_uint64)]
+
+
+class pl_result(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("alpha_hat", ctypes.c_double), ("D", ctypes.c_double),
+                ("p", ctypes.c_double), ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
 
 
 _vp = ctypes.c_void_p
@@ -83,7 +91,18 @@ _lib.pl_plan_destroy.argtypes = [_vp]
 _lib.pl_plan_destroy.restype = None
 _lib.pl_fit_ks_noalloc.argtypes = [_vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
                                    _vp, _vp]
-for _f in ["pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+_lib.pl_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_uint64, ctypes.c_int64]
+_lib.pl_server_submit.argtypes = [_vp, ctypes.c_uint64, _vp, ctypes.c_int64, ctypes.c_uint64]
+_lib.pl_server_poll.argtypes = [_vp, ctypes.POINTER(pl_result), ctypes.c_int, ctypes.c_double]
+_lib.pl_server_poll.restype = ctypes.c_int
+_lib.pl_server_now.argtypes = [_vp]
+_lib.pl_server_now.restype = ctypes.c_double
+_lib.pl_server_load.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_size_t), _u64p]
+_lib.pl_server_destroy.argtypes = [_vp]
+_lib.pl_server_destroy.restype = None
+for _f in ["pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -266,3 +285,47 @@ def pl_fit_ks_noalloc(x, xmin: int, alpha: float, out, prec: int = PL_FP64, stre
     st = _lib.pl_fit_ks_noalloc(_ptr(x), x.numel(), xmin, alpha, prec, _ptr(out), _stream_ptr(stream))
     if st != PL_OK:
         raise PLError(st, "pl_fit_ks_noalloc failed")
+
+
+class Server:
+    """Continuous-batching engine of bootstrap fit requests (pl_server_*)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, workers: int = 4,
+                 prec: int = PL_FP32_BULK, seed: int = 1, B: int = 2500):
+        h = _vp()
+        st = _lib.pl_server_create(ctypes.byref(h), device, mem_budget_bytes, workers, prec, seed, B)
+        if st != PL_OK:
+            raise PLError(st, "pl_server_create failed")
+        self._h = h
+
+    def pl_server_submit(self, request_id: int, x: np.ndarray, xmin: int = 1):
+        """x: host int32 array (copied by the call)."""
+        xa = np.ascontiguousarray(x, dtype=np.int32)
+        st = _lib.pl_server_submit(self._h, request_id, xa.ctypes.data, xa.size, xmin)
+        if st != PL_OK:
+            raise PLError(st, "pl_server_submit failed")
+
+    def pl_server_poll(self, max_results: int = 256, wait_s: float = 0.0) -> list[dict]:
+        buf = (pl_result * max_results)()
+        k = _lib.pl_server_poll(self._h, buf, max_results, wait_s)
+        return [{f: getattr(buf[i], f) for f, _ in pl_result._fields_ if f != "pad"} for i in range(k)]
+
+    def pl_server_now(self) -> float:
+        return _lib.pl_server_now(self._h)
+
+    def pl_server_load(self) -> tuple[int, int, int, int]:
+        """(queued, running, reserved bytes, kernels launched by finished requests)"""
+        q, r, b, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t(), ctypes.c_uint64()
+        _lib.pl_server_load(self._h, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b), ctypes.byref(k))
+        return q.value, r.value, b.value, k.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pl_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
