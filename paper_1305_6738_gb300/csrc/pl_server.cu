@@ -9,6 +9,7 @@
 // workspaces of the requests already running (the device budget).
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -81,8 +82,7 @@ void worker_loop(pl_server *srv, Worker *w) {
       // admission: the oldest request, once its workspace fits the budget
       srv->cv_work.wait(lock, [&] {
         return srv->stopping ||
-               (!srv->queue.empty() &&
-                (srv->reserved + srv->queue.front().bytes <= srv->budget || srv->reserved == 0));
+               (!srv->queue.empty() && srv->reserved + srv->queue.front().bytes <= srv->budget);
       });
       if (srv->stopping) return;  // queued requests are dropped
       req = std::move(srv->queue.front());
@@ -181,6 +181,20 @@ pl_status pl_server_submit(pl_server *srv, uint64_t request_id, const int32_t *x
   {
     std::lock_guard<std::mutex> lock(srv->sizer_mu);
     req.bytes = pl::ctx_bootstrap_bytes(srv->sizer, n, xmin, srv->B);
+  }
+  if (req.bytes > srv->budget) {  // can never be admitted: fails at once
+    pl_result res{};
+    res.request_id = req.id;
+    res.status = PL_ENOMEM;
+    res.n = n;
+    res.submit_s = res.start_s = res.done_s = req.submit_s;
+    res.alpha_hat = res.D = res.p = std::nan("");
+    {
+      std::lock_guard<std::mutex> lock(srv->mu);
+      srv->done.push_back(res);
+    }
+    srv->cv_done.notify_all();
+    return PL_OK;
   }
   {
     std::lock_guard<std::mutex> lock(srv->mu);
