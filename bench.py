@@ -271,6 +271,15 @@ def run_serving(args):
     launches = srv.pl_server_load()[3] - (launches0 or 0)
     srv.close()
 
+    if args.serve_log:
+        with open(args.serve_log, "w") as f:
+            for r in reqs:
+                res = results[r.request_id]
+                f.write(json.dumps({"id": r.request_id, "n": r.n, "alpha": r.alpha, "lognormal": r.lognormal,
+                                    "arrival_s": base + r.arrival_s, "submit_s": res["submit_s"],
+                                    "start_s": res["start_s"], "done_s": res["done_s"],
+                                    "status": res["status"], "alpha_hat": res["alpha_hat"],
+                                    "p": res["p"]}) + "\n")
     timed = [r for r in reqs if r.arrival_s >= args.serve_warmup]
     bad = [results[r.request_id]["status"] for r in timed if results[r.request_id]["status"] != 0]
     lat = np.array([results[r.request_id]["done_s"] - (base + r.arrival_s) for r in timed]) * 1e3
@@ -328,6 +337,7 @@ def main():
     ap.add_argument("--duration", type=float, default=60.0, help="serving: measured seconds")
     ap.add_argument("--serve-warmup", type=float, default=5.0, help="serving: warm-up seconds")
     ap.add_argument("--workers", type=int, default=8, help="serving: engine worker slots")
+    ap.add_argument("--serve-log", default="", help="serving: write per-request results (JSON lines)")
     args = ap.parse_args()
     if args.workload == "serving":
         return run_serving(args)

@@ -175,7 +175,7 @@ pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells,
 /* Autotuner of the warp/block split: replicates with n above the split use
  * the block-per-replicate form, the others the warp-per-replicate form.  The
  * split starts at 16384; pl_autotune times both forms on the context's GPU
- * (alpha = 2, 4,096 replicates, n = 2^9 .. 2^16) and sets the split to the
+ * (alpha = 2, 65,536 replicates, n = 2^9 .. 2^16) and sets the split to the
  * largest n bucket up to which the warp form is faster (at least 256).  The
  * split changes only rounding (see Randomness above).  Synchronises `stream`; *split_out (host, may be NULL) receives it.
  * pl_set_split sets it directly (1 <= split <= 65535). */

@@ -278,6 +278,15 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
   });
   // items, and waves whose replicate records fit the wave byte budget
   const size_t wave_budget = std::min<size_t>(ctx->budget / 4, (size_t)4 << 30);
+  // Warp-form items hold up to kItemReps replicates; a small simulation gets
+  // smaller items (down to 32) so that there are at least two per resident
+  // sampler block.  Results do not depend on the item size.
+  int64_t warp_R = 0;
+  for (const Cell &cd : sp.cells)
+    if (!cd.wide) warp_R += cd.R;
+  const int64_t fill = 2 * (int64_t)ctx->num_sms * std::max(1, ctx->sample_blocks_per_sm);
+  int64_t warp_item = kItemReps;
+  while (warp_item > 32 && warp_R / warp_item < fill) warp_item /= 2;
   size_t wd = 0, ws = 0, wm = 0, first = 0, nwide = 0;
   double wt = 0.0;  // expected beyond-table draws of the wave
   auto close_tail = [&]() {
@@ -290,7 +299,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     const double xq = (double)lp.xmin;
     const double Zq = std::pow(xq, -lp.alpha) + std::pow(xq + 0.5, 1.0 - lp.alpha) / (lp.alpha - 1.0);
     const double q_tail = std::min(1.0, std::pow(xq + lp.L2 - 0.5, 1.0 - lp.alpha) / ((lp.alpha - 1.0) * Zq));
-    const int64_t per_item = cd.wide ? (int64_t)kWideItemReps : (int64_t)kItemReps;
+    const int64_t per_item = cd.wide ? (int64_t)kWideItemReps : warp_item;
     for (int64_t r0 = 0; r0 < cd.R; r0 += per_item) {
       WorkItem it{};
       it.cell = (uint32_t)c;
@@ -819,7 +828,7 @@ pl_status pl_autotune(pl_ctx *ctx, void *stream, int64_t *split_out) {
   pl_status st_all = PL_OK;
   for (int64_t n = 512; n <= 65536; n *= 2) {
     const int64_t nn = std::min(n, kWarpNMax);
-    pl_cell cell{2.0, 1, nn, 4096, 0};
+    pl_cell cell{2.0, 1, nn, 65536, 0};
     float t[2] = {0.0f, 0.0f};
     for (int form = 0; form < 2 && !st_all; ++form) {  // 0: warp, 1: block
       ctx->warp_split = form == 0 ? kWarpNMax : 1;

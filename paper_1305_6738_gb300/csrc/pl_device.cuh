@@ -300,7 +300,7 @@ __device__ __forceinline__ void polish_direct_term(double t, double lk, double &
   z2 += lk * lk * t;
 }
 
-// zeta(s, a), zeta', zeta'' with the warp-uniform shift Nw >= polish_shift_n(s, a).
+// zeta(s, a), zeta', zeta'' with the shift Nw >= polish_shift_n(s, a).
 __device__ __forceinline__ void hurwitz_polish(double s, uint64_t a, int Nw, const double *lnT,
                                                double *z) {
   double z0 = 0.0, z1 = 0.0, z2 = 0.0;

@@ -325,9 +325,10 @@ __device__ __forceinline__ FitOut fit_lanes(double L, int64_t n, uint64_t xmin, 
       }
     }
   }
-  const int Nw = __reduce_max_sync(0xffffffffu, (unsigned)polish_shift_n(a0, xmin));
+  // the shift is the lane's own (not a warp maximum), so a replicate's result
+  // does not depend on which replicates share its warp
   double z[3];
-  hurwitz_polish(a0, xmin, Nw, lnT, z);
+  hurwitz_polish(a0, xmin, polish_shift_n(a0, xmin), lnT, z);
   FitOut o;
   if (ok) {
     const double inv = 1.0 / z[0];
@@ -677,7 +678,7 @@ __global__ void __launch_bounds__(kAWarps * 32, 3) sample_hist_kernel(SampleLaun
       loaded = cell.law;
     }
     for (int jj = 0; jj < kARepsPerWarp; ++jj) {
-      const uint32_t j = warp * kARepsPerWarp + jj;
+      const uint32_t j = warp + jj * kAWarps;  // strided: small items still use every warp
       if (j >= wi.nrep) break;
       const uint64_t pos0 = wi.spill_off + (uint64_t)j * cell.scap;
       const int64_t tmax = draw_replicate<true>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp],
