@@ -497,25 +497,98 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
 }
 
 // ===========================================================================
-// Sort the s spill values of one replicate (bitonic, on chip when they fit,
-// else in the warp's global buffer) and run-length encode them into
-// interleaved (value, count) pairs.  Returns the number of distinct values.
+// Stable LSD radix sort of s uint64 keys by one warp, 8-bit digits of
+// (key - smallest key), only as many digits as the key range needs.  Keys
+// move between a and b (global memory, s entries each) and end in a; cnt is
+// 256 words of the warp's shared memory.  A pass: digit counts (shared
+// atomics), exclusive scan, then a stable scatter of 32 keys at a time (equal
+// digits ranked among the warp's lanes with match.any).
+__device__ void warp_radix_sort(uint64_t *a, uint64_t *b, int64_t s, uint32_t *cnt, int lane) {
+  uint64_t lo = ~0ull, hi = 0;
+  for (int64_t i = lane; i < s; i += 32) {
+    const uint64_t x = a[i];
+    lo = x < lo ? x : lo;
+    hi = x > hi ? x : hi;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  const uint64_t span = hi - lo;
+  const int passes = span ? (71 - __clzll((long long)span)) / 8 : 0;  // ceil(bits / 8)
+  uint64_t *src = a, *dst = b;
+  for (int p = 0; p < passes; ++p) {
+    const int sh = 8 * p;
+    for (int d = lane; d < 256; d += 32) cnt[d] = 0;
+    __syncwarp();
+    for (int64_t i = lane; i < s; i += 32) atomicAdd(&cnt[(uint32_t)((src[i] - lo) >> sh) & 255u], 1u);
+    __syncwarp();
+    uint32_t v[8], t = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v[k] = cnt[lane * 8 + k];
+      t += v[k];
+    }
+    uint32_t incl = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t run = incl - t;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      cnt[lane * 8 + k] = run;
+      run += v[k];
+    }
+    __syncwarp();
+    for (int64_t i0 = 0; i0 < s; i0 += 32) {
+      const int64_t i = i0 + lane;
+      const bool ok = i < s;
+      const uint64_t x = ok ? src[i] : 0;
+      const uint32_t d = ok ? ((uint32_t)((x - lo) >> sh) & 255u) : 256u + (uint32_t)lane;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      const uint32_t base = ok ? cnt[d] : 0u;
+      __syncwarp();
+      if (ok) {
+        dst[base + rank] = x;
+        if (rank == 0) cnt[d] = base + __popc(peers);
+      }
+      __syncwarp();
+    }
+    uint64_t *t2 = src;
+    src = dst;
+    dst = t2;
+  }
+  if (src != a) {
+    for (int64_t i = lane; i < s; i += 32) a[i] = src[i];
+    __syncwarp();
+  }
+}
+
+// Sort the s spill values of one replicate (bitonic on chip when they fit,
+// else radix in global memory with `pairs` as the second buffer) and
+// run-length encode them into interleaved (value, count) pairs at `pairs`
+// (room for 2 s entries).  Returns the number of distinct values.
 __device__ int64_t spill_compact(uint64_t *spill, uint32_t *onchip, int64_t s, uint64_t *pairs,
                                  int lane, Counters *ctr) {
   if (s <= 0) return 0;
-  uint32_t P = 1;
-  while ((int64_t)P < s) P <<= 1;
   uint64_t *buf;
   if (s <= kSortSmem) {
+    uint32_t P = 1;
+    while ((int64_t)P < s) P <<= 1;
     buf = reinterpret_cast<uint64_t *>(onchip);
     for (uint32_t i = lane; i < P; i += 32) buf[i] = (int64_t)i < s ? spill[i] : ~0ull;
+    __syncwarp();
+    warp_bitonic_sort(buf, P, lane);
   } else {
     buf = spill;
-    for (uint32_t i = (uint32_t)s + lane; i < P; i += 32) buf[i] = ~0ull;
     if (lane == 0) atomicAdd(&ctr->global_sorts, 1ull);
+    warp_radix_sort(spill, pairs, s, onchip, lane);
   }
-  __syncwarp();
-  warp_bitonic_sort(buf, P, lane);
   int64_t base = 0;
   for (int64_t i0 = 0; i0 < s; i0 += 32) {
     const int64_t i = i0 + lane;

@@ -198,9 +198,12 @@ def test_cutoffs_device_output_and_batching_invariance(ctx, pl):
 FALLBACK_CELLS = [(1.5, 1, 5000, 300, 1), (1.75, 1, 16384, 40, 5), (2.5, 1, 100, 700, 0),
                   (3.0, 5, 20, 513, 4), (1.5, 1, 2000, 257, 9), (2.0, 1, 40000, 9, 14)]
 
-# block form (n beyond the warp form), mixed with warp-form cells in one call
+# block form (n beyond the warp form), mixed with warp-form cells in one call; the
+# alpha = 1.4 cells spill more values than fit on chip (radix sort in global memory),
+# the first in the warp form, the second in the block form
 WIDE_CELLS = [(2.0, 1, 20000, 24, 11), (1.75, 1, 50000, 8, 12), (2.5, 2, 100000, 5, 13),
-              (1.6, 5, 16385, 7, 15), (3.0, 1, 100, 300, 16)]
+              (1.6, 5, 16385, 7, 15), (3.0, 1, 100, 300, 16), (1.4, 1, 16384, 6, 17),
+              (1.4, 1, 100000, 3, 18)]
 
 
 @pytest.fixture(scope="module")
@@ -215,8 +218,10 @@ def test_block_form_matches_oracle(ctx, pl, wide_oracle, prec):
     D = torch.empty(total, dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
     A = torch.empty(total, dtype=torch.float64, device="cuda")
     q = [0.5, 0.9]
+    sorts0 = ctx.pl_counters()["global_sorts"]
     cut = ctx.pl_ks_cutoffs(cells, 1, q, prec, D=D, alpha_hat=A)
     ctx.pl_sync()
+    assert ctx.pl_counters()["global_sorts"] - sorts0 >= 9
     atol_a, atol_d = TOL[prec]
     off = 0
     for ci, (a, xm, n, R, cid) in enumerate(WIDE_CELLS):
