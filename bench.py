@@ -41,9 +41,11 @@ METRIC = "KS replicates/sec and samples/sec per (alpha,n) vs roofline; p50/p99 f
 MUL_PER_DRAW = 10
 MUL_LANES_PER_SM = 32
 
-# DRAM traffic of the replicate kernel from one ncu capture, keyed by the hash
-# of the kernel sources it was taken on (reported as null once they change).
-TRAFFIC = {}
+# DRAM bytes per replicate of the sampler from one ncu capture (sweep at 4,000
+# replicates per cell: 136.9 MB over 360,000 replicates), keyed by the hash of
+# the kernel sources it was taken on (reported as null once they change).  The
+# bench scales it to a launch by the replicates one launch processes.
+TRAFFIC_PER_REPLICATE = {"1e25c3dd9f0ca573": 136.893440e6 / 360000}
 
 
 def kernel_source_hash() -> str:
@@ -506,8 +508,13 @@ def main():
     achieved = MUL_PER_DRAW * draws / (kmean / 1000.0) / 1e9
     h = kernel_source_hash()
     roofline = {"bound": "alu", "achieved": achieved, "peak": mul_peak, "unit": "Gmul/s (32x32->64)",
-                "frac": achieved / mul_peak, "traffic": TRAFFIC.get(h),
-                "kernel": "sample_hist_kernel", "kernel_ms_per_step": kmean, "launches_per_step": waves,
+                "frac": achieved / mul_peak,
+                "traffic": (TRAFFIC_PER_REPLICATE[h] * total_R / max(1, waves)
+                            if h in TRAFFIC_PER_REPLICATE and args.workload == "sweep" else None),
+                "kernel": ("sample_block_kernel" if args.workload == "large-n"
+                           else "sample_hist_kernel + sample_block_kernel" if args.workload == "batched"
+                           else "sample_hist_kernel"),
+                "kernel_ms_per_step": kmean, "launches_per_step": waves,
                 "finisher_ms_per_step": statistics.mean(fin_ms),
                 "peak_basis": f"{props.multi_processor_count} SMs x {MUL_LANES_PER_SM} multiply lanes x "
                               f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json); "
