@@ -369,9 +369,14 @@ __device__ __forceinline__ void hurwitz_polish(double s, uint64_t a, int Nw, con
 // 1/(u_next - u)) from one Euler-Maclaurin evaluation.  A guide table over a
 // uniform u grid points to the node at or below each bin start.  Lookup:
 // guide, a short forward scan, cubic Hermite interpolation in u.
+// Node of the inverse of the MLE equation, at u = ln(mean ln x - ln xmin):
+// alpha(u), its slope, ln zeta(alpha, xmin) and its slope in u.
 struct FitNode {
-  double u, alpha, dadu, inv_du;
+  double u, alpha, dadu, inv_du, lnZ, dlnZdu;
 };
+// Below this exponent the fit table's interpolation is accurate to ~1e-11
+// (alpha and zeta) for every xmin; the binary32 form takes it as the fit.
+constexpr double kFitTableOnlyMax = 16.0;
 struct FitTable {
   uint64_t xmin;
   int nodes;

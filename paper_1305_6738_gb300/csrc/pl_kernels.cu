@@ -211,6 +211,8 @@ __global__ void fit_nodes_kernel(FitTable *fts) {
   nd.u = log(h);
   nd.alpha = a;
   nd.dadu = -h / var;
+  nd.lnZ = log(z[0]);
+  nd.dlnZdu = g * nd.dadu;  // d ln zeta / d alpha = zeta'/zeta
 }
 
 // inv_du of each interval, and the guide: guide[b] = max{k : u_k <= ug0 + b du_g}.
@@ -296,19 +298,21 @@ __device__ __forceinline__ FitOut fit_from_logsum(double L, int64_t n, uint64_t 
 }
 
 // Lane-parallel fit (one replicate per lane; every lane of the warp calls it,
-// lanes without a replicate pass a harmless log-sum).  The Newton start comes
-// from the fit table's cubic Hermite interpolation (error ~1e-12), so one
-// Euler-Maclaurin evaluation at the start gives the FP64 root (the step's
-// error is quadratic in the start's), and zeta(alpha-hat) follows from the
-// same evaluation by a second-order Taylor step.  A start outside the table
-// or a step larger than 1e-8 alpha falls back to the full iteration.
+// lanes without a replicate pass a harmless log-sum).  The fit table's cubic
+// Hermite interpolation gives alpha-hat and ln zeta(alpha-hat) to ~1e-11
+// below kFitTableOnlyMax: the binary32 form (tolerance 1e-6) takes them as
+// they are.  The binary64 form polishes: one Euler-Maclaurin evaluation at
+// the interpolated start gives the FP64 root (the step's error is quadratic
+// in the start's), and zeta(alpha-hat) follows from the same evaluation by a
+// second-order Taylor step.  A start outside the table or a step larger than
+// 1e-8 alpha falls back to the full iteration.
 __device__ __forceinline__ FitOut fit_lanes(double L, int64_t n, uint64_t xmin, const CellConst &cc,
                                             const FitTable &ft, const double *lnT, bool f32,
                                             Counters *ctr) {
   const double mbar = L / (double)n;
   const double h = mbar - cc.ln_xmin;
   bool ok = false;
-  double a0 = 1.2;
+  double a0 = 1.2, lz0 = 0.0;
   if (h > 0.0) {
     const double u = log(h);
     const double pos = (u - ft.ug0) * ft.inv_dug;
@@ -319,11 +323,24 @@ __device__ __forceinline__ FitOut fit_lanes(double L, int64_t n, uint64_t xmin, 
       if (u >= A.u && u <= B.u) {
         const double du = B.u - A.u;
         const double t = (u - A.u) * A.inv_du, t2 = t * t, t3 = t2 * t;
-        a0 = (2.0 * t3 - 3.0 * t2 + 1.0) * A.alpha + (t3 - 2.0 * t2 + t) * du * A.dadu +
-             (3.0 * t2 - 2.0 * t3) * B.alpha + (t3 - t2) * du * B.dadu;
+        const double h00 = 2.0 * t3 - 3.0 * t2 + 1.0, h10 = (t3 - 2.0 * t2 + t) * du,
+                     h01 = 3.0 * t2 - 2.0 * t3, h11 = (t3 - t2) * du;
+        a0 = h00 * A.alpha + h10 * A.dadu + h01 * B.alpha + h11 * B.dadu;
+        lz0 = h00 * A.lnZ + h10 * A.dlnZdu + h01 * B.lnZ + h11 * B.dlnZdu;
         ok = true;
       }
     }
+  }
+  if (f32 && ok && a0 < kFitTableOnlyMax) {
+    FitOut o;
+    o.ahat = a0;
+    o.Z = exp(lz0);
+    o.a_hi = (float)a0;
+    o.a_lo = (float)(a0 - (double)o.a_hi);
+    o.invZ = (float)(1.0 / o.Z);
+    o.lnZ = (float)lz0;
+    o.lnc = logf((float)(a0 - 1.0)) + o.lnZ;
+    return o;
   }
   // the shift is the lane's own (not a warp maximum), so a replicate's result
   // does not depend on which replicates share its warp
