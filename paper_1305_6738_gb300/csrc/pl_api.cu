@@ -245,6 +245,9 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     cd.law = li;
     cd.wide = x.n > std::min(kWarpNMax, ctx->warp_split) ? 1u : 0u;
     cd.H = cd.wide ? (uint32_t)kHWide : hist_bins(x.n);
+    // batched table searches pay off once a replicate has many draws or the
+    // tail is heavy (measured crossover on GB300)
+    cd.defer = (x.n >= 512 || x.alpha < 1.6) ? 1u : 0u;
     cd.purpose = purpose;
     cd.out_off = sp.total_R;
     auto fi = fit_of.find(x.xmin);

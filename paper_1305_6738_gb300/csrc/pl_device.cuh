@@ -24,6 +24,9 @@ constexpr uint64_t kXCap = 1ull << 62;      // simulated values saturate here
 constexpr int kL1 = PL_L1_ENTRIES;          // thresholds staged in shared memory
 constexpr int kGuideBits = 11;              // guide table: 2^11 buckets of m
 constexpr int kGuide = 1 << kGuideBits;
+// A guide word holds the bucket's smallest answer index (low 31 bits) and, in
+// bit 31, whether the bucket holds more than one answer (a search is needed).
+constexpr uint32_t kGuideMulti = 0x80000000u, kGuideIndex = 0x7fffffffu;
 constexpr int kHMax = 1024;                 // dense histogram bins per warp
 constexpr int kHWide = 8192;                // dense histogram bins per block (block form)
 constexpr int kWarps = 8;                   // warps per block, warp form
@@ -60,7 +63,7 @@ struct Law {
   float tail_e;           // -1 / (alpha - 1)
   float xmin_f;           // xmin + 1/2, binary32
   uint64_t *T;            // T[i] = floor(Q(xmin+i) 2^53) + 1, Q(k) = P(X > k)
-  uint32_t *guide;        // guide[j] = min{i : T[i] <= (j+1) 2^(53-g)} (or L2)
+  uint32_t *guide;        // guide[j] = min{i : T[i] <= (j+1) 2^(53-g)} (or L2) | kGuideMulti flag
   double *lnT;            // ln(xmin + i), i < kLnTable
   float *lnT_hi;          // float split of lnT: hi + lo
   float *lnT_lo;
@@ -79,7 +82,7 @@ struct Cell {
   uint32_t fit;           // index into the fit-table array (one per xmin)
   uint32_t scap;          // spill slot capacity of a replicate record
   uint32_t wide;          // block form: 32-bit dense counts, H = kHWide
-  uint32_t pad;
+  uint32_t defer;         // warp form: batch the table searches (see kDeferCap)
 };
 
 // A block-sized batch of replicates of one cell, with the offsets of its
@@ -471,8 +474,8 @@ __device__ __forceinline__ uint32_t lookup_index(const uint64_t *sT, const uint3
                                                  const uint64_t *gT, uint32_t L2, float xmin_f,
                                                  float tail_c, float tail_e, uint64_t m) {
   const uint32_t j = (uint32_t)((m - 1ull) >> (53 - kGuideBits));
-  uint32_t lo = sG[j];
-  uint32_t hi = j ? sG[j - 1] : L2;
+  uint32_t lo = sG[j] & kGuideIndex;
+  uint32_t hi = j ? sG[j - 1] & kGuideIndex : L2;
   if (hi - lo > 8) {
     // v 2^32 from the top 32 of the 53 bits of m (tail_c carries the 2^-32)
     const float v32 = (float)(uint32_t)(m >> 21);

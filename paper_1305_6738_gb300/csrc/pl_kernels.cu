@@ -59,11 +59,10 @@ __global__ void law_fill_kernel(Law *laws) {
   }
 }
 
-// guide[j] = min{i < L2 : T[i] <= (j+1) 2^(53-g)}, or L2.
-__global__ void law_guide_kernel(Law *laws) {
-  const Law law = laws[blockIdx.y];
-  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= (uint32_t)kGuide) return;
+// guide[j] = min{i < L2 : T[i] <= (j+1) 2^(53-g)}, or L2, with kGuideMulti
+// set unless the bucket's answers [guide[j], guide[j-1]] (L2 above bucket 0)
+// are a single index.
+__device__ __forceinline__ uint32_t guide_bound(const Law &law, uint32_t j) {
   const uint64_t bound = (uint64_t)(j + 1) << (53 - kGuideBits);
   uint32_t lo = 0, hi = law.L2;
   while (lo < hi) {
@@ -71,7 +70,16 @@ __global__ void law_guide_kernel(Law *laws) {
     if (law.T[mid] <= bound) hi = mid;
     else lo = mid + 1;
   }
-  law.guide[j] = lo;
+  return lo;
+}
+
+__global__ void law_guide_kernel(Law *laws) {
+  const Law law = laws[blockIdx.y];
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= (uint32_t)kGuide) return;
+  const uint32_t lo = guide_bound(law, j);
+  const uint32_t hi = j ? guide_bound(law, j - 1) : law.L2;
+  law.guide[j] = lo | (hi != lo ? kGuideMulti : 0u);
 }
 
 cudaError_t launch_law_setup(Law *laws_dev, int nlaws, cudaStream_t st) {
@@ -670,12 +678,19 @@ struct TailQueue {
   uint32_t cap;
 };
 
-template <bool PACKED>
+// Per-warp queue of draws whose guide bucket holds more than one value: they
+// are searched 32 at a time, so the warp's lanes search together instead of
+// one divergent lane holding up the others (histogram counts and the later
+// sorted spills do not depend on the order draws are binned in).
+constexpr int kDeferCap = 64;
+
+template <bool PACKED, bool DEFER>
 __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint32_t *sG, const Law &law,
                                                   const Cell &cell, uint32_t rep, const RoundKeys &rk,
                                                   uint32_t *hist, int *s_count, uint64_t *spill,
                                                   int64_t spill_capacity, int lane,
-                                                  const TailQueue *tq, uint64_t spill_pos0) {
+                                                  const TailQueue *tq, uint64_t spill_pos0,
+                                                  uint64_t *defer_q) {
   const int64_t n = cell.n;
   const uint64_t xmin = cell.xmin;
   const uint32_t H = cell.H;
@@ -684,37 +699,81 @@ __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint
   if (lane == 0) *s_count = 0;
   __syncwarp();
   uint64_t packed = 0;  // 16-bit counters of bins 0..3
-  const int64_t npairs = (n + 1) >> 1;
-  for (int64_t p = lane; p < npairs; p += 32) {
-    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (2 * p + j < n) {
-        const uint64_t m = draw_bits(j ? w.z : w.x, j ? w.w : w.y);
-        const uint32_t b = lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m);
-        if (b < 4) {
-          packed += 1ull << (16 * b);
-        } else if (b < H) {
-          if (PACKED) atomicAdd(&hist[b >> 1], 1u << ((b & 1u) << 4));
-          else atomicAdd(&hist[b], 1u);
+  auto bin = [&](uint32_t b, uint64_t m) {
+    if (b < 4) {
+      packed += 1ull << (16 * b);
+    } else if (b < H) {
+      if (PACKED) atomicAdd(&hist[b >> 1], 1u << ((b & 1u) << 4));
+      else atomicAdd(&hist[b], 1u);
+    } else {
+      const int slot = atomicAdd(s_count, 1);
+      if (slot < spill_capacity) {
+        if (b < law.L2) {
+          spill[slot] = xmin + b;
         } else {
-          const int slot = atomicAdd(s_count, 1);
-          if (slot < spill_capacity) {
-            if (b < law.L2) {
-              spill[slot] = xmin + b;
-            } else {
-              spill[slot] = kTailTag | m;
-              if (tq) {
-                const unsigned q = atomicAdd(tq->count, 1u);
-                if (q < tq->cap) {
-                  tq->pos[q] = spill_pos0 + (uint64_t)slot;
-                  tq->law[q] = cell.law;
-                }
-              }
+          spill[slot] = kTailTag | m;
+          if (tq) {
+            const unsigned q = atomicAdd(tq->count, 1u);
+            if (q < tq->cap) {
+              tq->pos[q] = spill_pos0 + (uint64_t)slot;
+              tq->law[q] = cell.law;
             }
           }
         }
       }
+    }
+  };
+  int qn = 0;  // warp-uniform queue length (< 32 between draws)
+  const unsigned lt = (1u << lane) - 1u;
+  // One draw: the guide word answers directly unless its bucket holds several
+  // values; bins 0..3 go to the lane's registers without a branch.
+  auto draw = [&](uint32_t wlo, uint32_t whi, bool valid) {
+    if (DEFER) {
+      // guide bucket = top kGuideBits of m - 1 = top bits of the high word
+      const uint32_t gw = sG[whi >> (32 - kGuideBits)];
+      const bool direct = valid && !(gw & kGuideMulti);
+      packed += (direct && gw < 4) ? 1ull << (16 * (gw & 3u)) : 0ull;
+      if (direct && gw >= 4) bin(gw, draw_bits(wlo, whi));
+      const bool later = valid && (gw & kGuideMulti);
+      if (__any_sync(0xffffffffu, later)) {
+        const unsigned dm = __ballot_sync(0xffffffffu, later);
+        if (later) defer_q[qn + __popc(dm & lt)] = draw_bits(wlo, whi);
+        qn += __popc(dm);
+        if (qn >= 32) {
+          __syncwarp();
+          qn -= 32;
+          const uint64_t mq = defer_q[qn + lane];
+          __syncwarp();
+          bin(lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, mq), mq);
+        }
+      }
+    } else if (valid) {
+      const uint32_t gw = sG[whi >> (32 - kGuideBits)];
+      const uint64_t m = draw_bits(wlo, whi);
+      bin((gw & kGuideMulti) ? lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m)
+                             : gw,
+          m);
+    }
+  };
+  // full rounds (every lane has two valid draws: pairs below a multiple of 32
+  // that is at most n/2), then one ragged round for the at most 32 pairs left
+  const int64_t full = (n >> 1) & ~(int64_t)31;
+  int64_t p = lane;
+  for (; p < full; p += 32) {
+    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
+    draw(w.x, w.y, true);
+    draw(w.z, w.w, true);
+  }
+  if (2 * full < n) {
+    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
+    draw(w.x, w.y, 2 * p < n);
+    draw(w.z, w.w, 2 * p + 1 < n);
+  }
+  if (DEFER) {
+    __syncwarp();
+    if (lane < qn) {
+      const uint64_t mq = defer_q[lane];
+      bin(lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, mq), mq);
     }
   }
   __syncwarp();
@@ -748,6 +807,7 @@ __global__ void __launch_bounds__(kAWarps * 32, 3) sample_hist_kernel(SampleLaun
   int *s_spill = reinterpret_cast<int *>(smem + kL1 * 8 + kGuide * 4 + kAWarps * (kHMax / 2) * 4);
   uint32_t *s_item = reinterpret_cast<uint32_t *>(s_spill + kAWarps);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(s_item + 2);
+  uint64_t *s_defer = mbar + 2;  // kAWarps * kDeferCap draws
   StagedLaw staged{sT, sG, mbar};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t *hist = sH + warp * (kHMax / 2);
@@ -771,8 +831,12 @@ __global__ void __launch_bounds__(kAWarps * 32, 3) sample_hist_kernel(SampleLaun
       const uint32_t j = warp + jj * kAWarps;  // strided: small items still use every warp
       if (j >= wi.nrep) break;
       const uint64_t pos0 = wi.spill_off + (uint64_t)j * cell.scap;
-      const int64_t tmax = draw_replicate<true>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp],
-                                                a.rec.spill + pos0, cell.scap, lane, &tq, pos0);
+      const int64_t tmax =
+          cell.defer ? draw_replicate<true, true>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp],
+                                                  a.rec.spill + pos0, cell.scap, lane, &tq, pos0,
+                                                  s_defer + warp * kDeferCap)
+                     : draw_replicate<true, false>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp],
+                                                   a.rec.spill + pos0, cell.scap, lane, &tq, pos0, nullptr);
       uint32_t *dense = reinterpret_cast<uint32_t *>(a.rec.dense + wi.dense_off + (uint64_t)j * cell.H);
       for (int64_t i = lane; i <= (tmax >> 1); i += 32) dense[i] = hist[i];
       if (lane == 0) a.rec.meta[wi.meta_off + j] = make_int2((int)tmax, s_spill[warp]);
@@ -798,6 +862,8 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
   uint64_t *mbar = reinterpret_cast<uint64_t *>(s_tmax + 2);
   StagedLaw staged{sT, sG, mbar};
   const int lane = threadIdx.x & 31;
+  uint64_t *defer_q = mbar + 2 + (threadIdx.x >> 5) * kDeferCap;
+  const unsigned lt = (1u << lane) - 1u;
   const TailQueue tq{a.tq_pos, a.tq_law, a.tq_count, a.tq_cap};
   if (threadIdx.x == 0) mbar_init(mbar, 1);
   __syncthreads();
@@ -827,35 +893,57 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
       const uint64_t pos0 = wi.spill_off + (uint64_t)j * cell.scap;
       uint64_t *spill = a.rec.spill + pos0;
       uint64_t packed = 0;
-      const int64_t npairs = (n + 1) >> 1;
-      for (int64_t p = threadIdx.x; p < npairs; p += kBlkThreads) {
-        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), a.rk);
-#pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-          if (2 * p + jj < n) {
-            const uint64_t m = draw_bits(jj ? w.z : w.x, jj ? w.w : w.y);
-            const uint32_t b = lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m);
-            if (b < 4) {
-              packed += 1ull << (16 * b);
-            } else if (b < H) {
-              atomicAdd(&hist[b], 1u);
+      auto bin = [&](uint32_t b, uint64_t m) {
+        if (b < 4) {
+          packed += 1ull << (16 * b);
+        } else if (b < H) {
+          atomicAdd(&hist[b], 1u);
+        } else {
+          const int slot = atomicAdd(s_spill, 1);
+          if (slot < (int64_t)cell.scap) {
+            if (b < law.L2) {
+              spill[slot] = cell.xmin + b;
             } else {
-              const int slot = atomicAdd(s_spill, 1);
-              if (slot < (int64_t)cell.scap) {
-                if (b < law.L2) {
-                  spill[slot] = cell.xmin + b;
-                } else {
-                  spill[slot] = kTailTag | m;
-                  const unsigned q = atomicAdd(tq.count, 1u);
-                  if (q < tq.cap) {
-                    tq.pos[q] = pos0 + (uint64_t)slot;
-                    tq.law[q] = cell.law;
-                  }
-                }
+              spill[slot] = kTailTag | m;
+              const unsigned q = atomicAdd(tq.count, 1u);
+              if (q < tq.cap) {
+                tq.pos[q] = pos0 + (uint64_t)slot;
+                tq.law[q] = cell.law;
               }
             }
           }
         }
+      };
+      // direct answers from the guide; multi-valued buckets searched 32 at a
+      // time through the warp's queue (as in the warp form)
+      int qn = 0;
+      const int64_t npairs = (n + 1) >> 1;
+      for (int64_t p = threadIdx.x; p - lane < npairs; p += kBlkThreads) {
+        const bool pv = p < npairs;
+        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), a.rk);
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const bool valid = pv && 2 * p + jj < n;
+          const uint32_t wlo = jj ? w.z : w.x, whi = jj ? w.w : w.y;
+          const uint32_t gw = sG[whi >> (32 - kGuideBits)];
+          if (valid && !(gw & kGuideMulti)) bin(gw, draw_bits(wlo, whi));
+          const bool later = valid && (gw & kGuideMulti);
+          const unsigned dm = __ballot_sync(0xffffffffu, later);
+          if (later) defer_q[qn + __popc(dm & lt)] = draw_bits(wlo, whi);
+          qn += __popc(dm);
+          if (qn >= 32) {
+            __syncwarp();
+            qn -= 32;
+            const uint64_t mq = defer_q[qn + lane];
+            __syncwarp();
+            bin(lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, mq), mq);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane < qn) {
+        const uint64_t mq = defer_q[lane];
+        bin(lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, mq), mq);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -879,7 +967,7 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
 }
 
 size_t block_sampler_smem_bytes() {
-  return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kHWide * 4 + 32 + 16;
+  return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kHWide * 4 + 32 + 16 + (size_t)(kBlkThreads / 32) * kDeferCap * 8;
 }
 
 int block_sampler_blocks_per_sm() {
@@ -920,7 +1008,8 @@ cudaError_t launch_tail_queue_raw(const Law *laws, uint64_t *pos, uint32_t *law,
 }
 
 size_t sample_kernel_smem_bytes() {
-  return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kAWarps * (kHMax / 2) * 4 + kAWarps * 4 + 8 + 8 + 16;
+  return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kAWarps * (kHMax / 2) * 4 + kAWarps * 4 + 8 + 16 +
+         (size_t)kAWarps * kDeferCap * 8;
 }
 
 int sample_kernel_blocks_per_sm() {
@@ -1033,11 +1122,11 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
           // block form's histogram is rebuilt in place in the record
           if (lane == 0) atomicAdd(&a.ctr->resampled, 1ull);
           if (cell.wide) {
-            tmax = draw_replicate<false>(sT, sG, law, cell, wi.r0 + j, a.rk, dense32, &s_spill[warp], spill,
-                                         (int64_t)a.spill_cap, lane, nullptr, 0);
+            tmax = draw_replicate<false, false>(sT, sG, law, cell, wi.r0 + j, a.rk, dense32, &s_spill[warp], spill,
+                                                (int64_t)a.spill_cap, lane, nullptr, 0, nullptr);
           } else {
-            tmax = draw_replicate<false>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp], spill,
-                                         (int64_t)a.spill_cap, lane, nullptr, 0);
+            tmax = draw_replicate<false, false>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp], spill,
+                                                (int64_t)a.spill_cap, lane, nullptr, 0, nullptr);
             for (int64_t i = lane; i <= tmax; i += 32) dense[i] = (uint16_t)hist[i];
           }
           __syncwarp();
