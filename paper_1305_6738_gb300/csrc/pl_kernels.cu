@@ -917,17 +917,13 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
       // direct answers from the guide; multi-valued buckets searched 32 at a
       // time through the warp's queue (as in the warp form)
       int qn = 0;
-      const int64_t npairs = (n + 1) >> 1;
-      for (int64_t p = threadIdx.x; p - lane < npairs; p += kBlkThreads) {
-        const bool pv = p < npairs;
-        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), a.rk);
-#pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-          const bool valid = pv && 2 * p + jj < n;
-          const uint32_t wlo = jj ? w.z : w.x, whi = jj ? w.w : w.y;
-          const uint32_t gw = sG[whi >> (32 - kGuideBits)];
-          if (valid && !(gw & kGuideMulti)) bin(gw, draw_bits(wlo, whi));
-          const bool later = valid && (gw & kGuideMulti);
+      auto draw = [&](uint32_t wlo, uint32_t whi, bool valid) {
+        const uint32_t gw = sG[whi >> (32 - kGuideBits)];
+        const bool direct = valid && !(gw & kGuideMulti);
+        packed += (direct && gw < 4) ? 1ull << (16 * (gw & 3u)) : 0ull;
+        if (direct && gw >= 4) bin(gw, draw_bits(wlo, whi));
+        const bool later = valid && (gw & kGuideMulti);
+        if (__any_sync(0xffffffffu, later)) {
           const unsigned dm = __ballot_sync(0xffffffffu, later);
           if (later) defer_q[qn + __popc(dm & lt)] = draw_bits(wlo, whi);
           qn += __popc(dm);
@@ -939,6 +935,20 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
             bin(lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, mq), mq);
           }
         }
+      };
+      // full rounds of the block (every thread has two valid draws), then one
+      // ragged round for the fewer than kBlkThreads + 1 pairs left
+      const int64_t full = (n >> 1) / kBlkThreads * kBlkThreads;
+      int64_t p = threadIdx.x;
+      for (; p < full; p += kBlkThreads) {
+        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), a.rk);
+        draw(w.x, w.y, true);
+        draw(w.z, w.w, true);
+      }
+      for (; 2 * (p - lane) < n; p += kBlkThreads) {  // warp-uniform bound
+        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), a.rk);
+        draw(w.x, w.y, 2 * p < n);
+        draw(w.z, w.w, 2 * p + 1 < n);
       }
       __syncwarp();
       if (lane < qn) {
