@@ -97,7 +97,8 @@ pl_status pl_sync(pl_ctx *ctx, void *stream);
 typedef struct {
   uint64_t newton_capped;  /* Newton solves that hit the iteration cap */
   uint64_t tail_draws;     /* draws inverted in binary64 beyond the threshold table */
-  uint64_t global_sorts;   /* replicates whose spills were sorted in global memory */
+  uint64_t global_sorts;   /* replicates with more than 512 values beyond the
+                              dense histogram (large spill sorts) */
   uint64_t fit_fallbacks;  /* fits by the full Newton iteration instead of the
                               one-step polish from the interpolated start */
   uint64_t resampled;      /* replicates drawn a second time because their

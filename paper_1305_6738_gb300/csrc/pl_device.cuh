@@ -30,7 +30,7 @@ constexpr uint32_t kGuideMulti = 0x80000000u, kGuideIndex = 0x7fffffffu;
 constexpr int kHMax = 1024;                 // dense histogram bins per warp
 constexpr int kHWide = 8192;                // dense histogram bins per block (block form)
 constexpr int kWarps = 8;                   // warps per block, warp form
-constexpr int kSortSmem = kHMax / 2;        // spills sorted on chip up to this count
+constexpr int kSortSmem = kHMax / 2;        // replicates with more spills count as large sorts
 constexpr int kLnTable = 16384;             // ln(xmin + i) tables, i < kLnTable
 constexpr int kNewtonCap = 200;             // Newton iteration cap
 
@@ -607,27 +607,6 @@ __device__ __forceinline__ void warp_sum_ff(float &hi, float &lo) {
     const float yh = __shfl_xor_sync(0xffffffffu, hi, o);
     const float yl = __shfl_xor_sync(0xffffffffu, lo, o);
     ff_add(hi, lo, yh, yl);
-  }
-}
-
-// Bitonic sort of P (power of two, <= 32 * 2^k) uint64 keys at `a` by one warp.
-// Works on shared or global memory (generic pointer).
-__device__ __forceinline__ void warp_bitonic_sort(uint64_t *a, uint32_t P, int lane) {
-  for (uint32_t k = 2; k <= P; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = lane; i < P; i += 32) {
-        const uint32_t l = i ^ j;
-        if (l > i) {
-          const uint64_t x = a[i], y = a[l];
-          const bool up = (i & k) == 0;
-          if ((x > y) == up) {
-            a[i] = y;
-            a[l] = x;
-          }
-        }
-      }
-      __syncwarp();
-    }
   }
 }
 

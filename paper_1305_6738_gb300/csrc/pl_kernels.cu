@@ -594,26 +594,41 @@ __device__ void warp_radix_sort(uint64_t *a, uint64_t *b, int64_t s, uint32_t *c
   }
 }
 
-// Sort the s spill values of one replicate (bitonic on chip when they fit,
-// else radix in global memory with `pairs` as the second buffer) and
-// run-length encode them into interleaved (value, count) pairs at `pairs`
-// (room for 2 s entries).  Returns the number of distinct values.
+// Sort the s spill values of one replicate, in place (up to 32: a bitonic
+// network across the lanes' registers; more: the warp radix sort with `pairs`
+// as the second buffer) and run-length encode them into interleaved
+// (value, count) pairs at `pairs` (room for 2 s entries).  Returns the number
+// of distinct values.
 __device__ int64_t spill_compact(uint64_t *spill, uint32_t *onchip, int64_t s, uint64_t *pairs,
                                  int lane, Counters *ctr) {
   if (s <= 0) return 0;
-  uint64_t *buf;
-  if (s <= kSortSmem) {
-    uint32_t P = 1;
-    while ((int64_t)P < s) P <<= 1;
-    buf = reinterpret_cast<uint64_t *>(onchip);
-    for (uint32_t i = lane; i < P; i += 32) buf[i] = (int64_t)i < s ? spill[i] : ~0ull;
+  if (s <= 32) {
+    uint64_t x = lane < s ? spill[lane] : ~0ull;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+        x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
+      }
+    }
+    const uint64_t prev = __shfl_up_sync(0xffffffffu, x, 1);
+    const bool start = lane < s && (lane == 0 || prev != x);
+    const unsigned bal = __ballot_sync(0xffffffffu, start);
+    const unsigned after = bal & ~((2u << lane) - 1u);  // run starts beyond this lane
+    const int next = after ? __ffs((int)after) - 1 : (int)s;
+    if (start) {
+      const int rank = __popc(bal & ((1u << lane) - 1u));
+      pairs[2 * rank] = x;
+      pairs[2 * rank + 1] = (uint64_t)(next - lane);
+    }
     __syncwarp();
-    warp_bitonic_sort(buf, P, lane);
-  } else {
-    buf = spill;
-    if (lane == 0) atomicAdd(&ctr->global_sorts, 1ull);
-    warp_radix_sort(spill, pairs, s, onchip, lane);
+    return __popc(bal);
   }
+  if (s > kSortSmem && lane == 0) atomicAdd(&ctr->global_sorts, 1ull);
+  warp_radix_sort(spill, pairs, s, onchip, lane);
+  const uint64_t *buf = spill;
   int64_t base = 0;
   for (int64_t i0 = 0; i0 < s; i0 += 32) {
     const int64_t i = i0 + lane;
@@ -1187,11 +1202,6 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
             if (lane == 0) atomicOr(&a.ctr->status, kErrArena);
             break;                     // leave this batch; the block barrier below still meets
           }
-        }
-        if (s > kSortSmem && sp != spill) {  // sorted in the warp's buffer (power-of-two room)
-          for (int64_t k = lane; k < s; k += 32) spill[k] = sp[k];
-          __syncwarp();
-          sp = spill;
         }
         uint64_t *pairs = reinterpret_cast<uint64_t *>(arena + arena_off);
         const int64_t nsd = spill_compact(sp, hist, s, pairs, lane, a.ctr);
