@@ -342,11 +342,11 @@ __device__ __forceinline__ FitOut fit_lanes(double L, int64_t n, uint64_t xmin, 
   if (f32 && ok && a0 < kFitTableOnlyMax) {
     FitOut o;
     o.ahat = a0;
-    o.Z = exp(lz0);
+    o.Z = 0.0;  // the binary32 form reads invZ, lnZ and lnc only
     o.a_hi = (float)a0;
     o.a_lo = (float)(a0 - (double)o.a_hi);
-    o.invZ = (float)(1.0 / o.Z);
     o.lnZ = (float)lz0;
+    o.invZ = expf(-o.lnZ);
     o.lnc = logf((float)(a0 - 1.0)) + o.lnZ;
     return o;
   }
@@ -484,8 +484,8 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
         const int64_t Cb = Ca - c;
         double q;
         hurwitz_em<0, false>(f.ahat, (double)v + 1.0, &q);
-        const float Q = (float)(q / f.Z);
-        const float pv = (float)(exp(-f.ahat * log((double)v)) / f.Z);
+        const float Q = (float)(q * (double)f.invZ);
+        const float pv = (float)(exp(-f.ahat * log((double)v)) * (double)f.invZ);
         const float Fv = 1.0f - Q;
         const float Fb = 1.0f - (Q + pv);
         best = fmaxf(best, fmaxf(fabsf(Fv - (float)Ca * inv_n), fabsf(Fb - (float)Cb * inv_n)));
@@ -1050,6 +1050,54 @@ cudaError_t launch_sample_hist(const SampleLaunch &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Small replicates (warp form, no spills, largest bin below kLaneBins) are
+// finished by one lane each: the log-sum and the KS scan run serially over the
+// replicate's dense counts, with no warp reductions.  Same arithmetic as the
+// warp-cooperative path, summed in bin order.
+constexpr int64_t kLaneBins = 128;
+
+template <bool F32>
+__device__ __forceinline__ double lane_logsum(const uint16_t *dense, int64_t tmax, const Law &law) {
+  if (!F32) {
+    double acc = 0.0;
+    for (int64_t i = 0; i <= tmax; ++i) acc += (double)dense[i] * law.lnT[i];
+    return acc;
+  }
+  float Lh = 0.0f, Ll = 0.0f;
+  for (int64_t i = 0; i <= tmax; ++i) {
+    const float c = (float)dense[i];
+    const float ph = c * law.lnT_hi[i];
+    const float pe = fmaf(c, law.lnT_hi[i], -ph) + c * law.lnT_lo[i];
+    ff_add(Lh, Ll, ph, pe);
+  }
+  return (double)Lh + (double)Ll;
+}
+
+template <bool F32>
+__device__ __forceinline__ double lane_ks(const uint16_t *dense, int64_t tmax, int64_t n, const FitOut &f,
+                                          const Law &law) {
+  if (!F32) {
+    const double invZ = 1.0 / f.Z, inv_n = 1.0 / (double)n;
+    double F = 0.0, best = 0.0;
+    int64_t C = 0;
+    for (int64_t i = 0; i <= tmax; ++i) {
+      F += exp(-f.ahat * law.lnT[i]) * invZ;
+      C += dense[i];
+      best = fmax(best, fabs(F - (double)C * inv_n));
+    }
+    return best;
+  }
+  const float inv_n = 1.0f / (float)n;
+  float Fh = 0.0f, Fl = 0.0f, best = 0.0f;
+  int64_t C = 0;
+  for (int64_t i = 0; i <= tmax; ++i) {
+    ff_add(Fh, Fl, exp_neg_prod(f.a_hi, f.a_lo, law.lnT_hi[i], law.lnT_lo[i]) * f.invZ, 0.0f);
+    C += dense[i];
+    best = fmaxf(best, fabsf(Fh - (float)C * inv_n));
+  }
+  return (double)best;
+}
+
 template <bool F32>
 __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel(FinishLaunch a) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -1101,6 +1149,19 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
 #ifdef PL_PHASE_TIMING
       long long pt_ = clock64();
 #endif
+      const uint64_t dslot = (uint64_t)cell.H * (cell.wide ? 2 : 1);
+      const uint16_t *my_dense = a.rec.dense + wi.dense_off + (uint64_t)(j0 + (lane < nb ? lane : 0)) * dslot;
+      bool simple = false;
+      if (!cell.wide && lane < nb) {
+        const int2 m = a.rec.meta[wi.meta_off + j0 + lane];
+        simple = m.y == 0 && m.x >= 0 && (int64_t)m.x < kLaneBins;
+        if (simple) {
+          my_tmax = m.x;
+          myL = lane_logsum<F32>(my_dense, my_tmax, law);
+          if ((int64_t)my_dense[0] == n) myL += cc.ln_allmin;
+        }
+      }
+      const unsigned smask = __ballot_sync(0xffffffffu, simple);
       auto finish = [&](int b0, int b1) {
         PL_PHASE(6);
         const bool mine = lane >= b0 && lane < b1;
@@ -1110,6 +1171,7 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
         PL_PHASE(3);
         double myD = 0.0;
         for (int r = b0; r < b1; ++r) {
+          if ((smask >> r) & 1u) continue;
           const FitOut fr = shfl_fit(fo, r);
           const int64_t tm = __shfl_sync(0xffffffffu, my_tmax, r);
           const int64_t ns = __shfl_sync(0xffffffffu, my_nsd, r);
@@ -1123,6 +1185,7 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
                         : ks_warp<F32, uint16_t>(dense, tm, pr, ns, n, fr, law.lnT, law.lnT_hi, law.lnT_lo, lane);
           if (lane == r) myD = D;
         }
+        if (mine && simple) myD = lane_ks<F32>(my_dense, my_tmax, n, fo, law);
         PL_PHASE(4);
         if (mine) {
           const int64_t o = cell.out_off + wi.r0 + j0 + lane;
@@ -1133,11 +1196,11 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
       };
 
       for (int r = 0; r < nb; ++r) {
+        if ((smask >> r) & 1u) continue;  // finished by its lane
         const uint32_t j = (uint32_t)(j0 + r);
         const int2 meta = a.rec.meta[wi.meta_off + j];
         int64_t tmax = meta.x;
         const int64_t s = meta.y;
-        const uint64_t dslot = (uint64_t)cell.H * (cell.wide ? 2 : 1);
         uint16_t *dense = a.rec.dense + wi.dense_off + (uint64_t)j * dslot;
         uint32_t *dense32 = cell.wide ? reinterpret_cast<uint32_t *>(dense) : nullptr;
         uint64_t *sp = a.rec.spill + wi.spill_off + (uint64_t)j * cell.scap;
