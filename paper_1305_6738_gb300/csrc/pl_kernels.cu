@@ -404,9 +404,28 @@ __device__ __forceinline__ FitOut shfl_fit(const FitOut &f, int src) {
 // FP64 form: everything binary64.  FP32 form: p and F in binary32 with
 // compensated (two-sum) prefix sums; Q(v) by a 4-term Euler-Maclaurin in
 // binary32 (v - xmin >= 32 keeps it below 1e-8 relative).
+// Q(a - 1) = zeta(s, a) / Z for a large argument a (a >= 10 + 1.5 s), binary32:
+//   a^(1-s)/((s-1) Z) * [1 + (s-1)/(2a) + sum_j B2j/(2j)! s(s+1)..(s+2j-2)(s-1) a^-2j],
+// with ln a = la_hi + la_lo and the product's rounding error carried.
+__device__ __forceinline__ float survival_em_f32(float af, float la_hi, float la_lo, const FitOut &f) {
+  const float s = f.a_hi, sm1 = (float)(f.ahat - 1.0);
+  const float ia = 1.0f / af, ia2 = ia * ia;
+  float P = s, br = 1.0f + 0.5f * sm1 * ia, w = ia2;
+  const float cj[4] = {1.0f / 12.0f, -1.0f / 720.0f, 1.0f / 30240.0f, -1.0f / 1209600.0f};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    br += cj[j] * P * sm1 * w;
+    P *= (s + (float)(2 * j + 1)) * (s + (float)(2 * j + 2));
+    w *= ia2;
+  }
+  const float prod = sm1 * la_hi;
+  const float perr = fmaf(sm1, la_hi, -prod) + sm1 * la_lo;
+  return expf(-prod - f.lnc) * (1.0f - perr) * br;
+}
+
 template <bool F32, typename DT>
 __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, int64_t nsd,
-                          int64_t n, const FitOut &f, const double *lnT, const float *lnT_hi,
+                          int64_t n, uint64_t xmin, const FitOut &f, const double *lnT, const float *lnT_hi,
                           const float *lnT_lo, int lane) {
   if (!F32) {
     const double invZ = 1.0 / f.Z;
@@ -447,32 +466,34 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
   } else {
     const float inv_n = 1.0f / (float)n;
     float best = 0.0f;
-    // dense part, one contiguous chunk of bins per lane: compensated chunk
-    // sums, one warp scan for the chunk offsets, then the running F and C
+    // dense part, one contiguous chunk of bins per lane.  The chunk's starting
+    // F = 1 - zeta(s, xmin + i0)/Z comes from the short Euler-Maclaurin series
+    // once the argument is large enough, else from the compensated sum of the
+    // bins below it; then one compensated pass over the chunk.
     const int64_t nbins = tmax + 1;
     const int64_t cs = (nbins + 31) >> 5;
     const int64_t i0 = (int64_t)lane * cs;
     const int64_t i1 = i0 + cs < nbins ? i0 + cs : nbins;
-    float sh = 0.0f, sl = 0.0f;
     int64_t sc = 0;
-    for (int64_t i = i0; i < i1; ++i) {
-      ff_add(sh, sl, exp_neg_prod(f.a_hi, f.a_lo, lnT_hi[i], lnT_lo[i]) * f.invZ, 0.0f);
-      sc += (int64_t)dense[i];
-    }
-    float eh = sh, el = sl;
-    warp_scan_ff(eh, el, lane);
+    for (int64_t i = i0; i < i1; ++i) sc += (int64_t)dense[i];
     const int64_t incC = warp_scan_i64(sc, lane);
-    float Fh = __shfl_up_sync(0xffffffffu, eh, 1), Fl = __shfl_up_sync(0xffffffffu, el, 1);
     int64_t C = incC - sc;
-    if (lane == 0) Fh = Fl = 0.0f;
+    float Fh = 0.0f, Fl = 0.0f;
+    if (i0 > 0 && i0 < nbins) {
+      const float af = (float)(xmin + (uint64_t)i0);
+      if (af >= 10.0f + 1.5f * f.a_hi) {
+        two_sum(1.0f, -survival_em_f32(af, lnT_hi[i0], lnT_lo[i0], f), Fh, Fl);
+      } else {
+        for (int64_t i = 0; i < i0; ++i)
+          ff_add(Fh, Fl, exp_neg_prod(f.a_hi, f.a_lo, lnT_hi[i], lnT_lo[i]) * f.invZ, 0.0f);
+      }
+    }
     for (int64_t i = i0; i < i1; ++i) {
       ff_add(Fh, Fl, exp_neg_prod(f.a_hi, f.a_lo, lnT_hi[i], lnT_lo[i]) * f.invZ, 0.0f);
       C += (int64_t)dense[i];
       best = fmaxf(best, fabsf(Fh - (float)C * inv_n));
     }
     int64_t carryC = __shfl_sync(0xffffffffu, incC, 31);
-    const float s = f.a_hi;          // exponent, binary32
-    const float sm1 = (float)(f.ahat - 1.0);
     for (int64_t k0 = 0; k0 < nsd; k0 += 32) {
       const int64_t k = k0 + lane;
       const bool ok = k < nsd;
@@ -494,22 +515,8 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
         float la_hi, la_lo, lv_hi, lv_lo;
         ln_u64_ff(v + 1ull, la_hi, la_lo);
         ln_u64_ff(v, lv_hi, lv_lo);
-        // Q(v) = zeta(s, a)/Z, a = v+1:  a^(1-s)/((s-1)Z) * [1 + (s-1)/(2a)
-        //        + sum_j B2j/(2j)! s(s+1)..(s+2j-2)(s-1) a^-2j]
-        const float af = (float)(v + 1ull);
-        const float ia = 1.0f / af, ia2 = ia * ia;
-        float P = s, br = 1.0f + 0.5f * sm1 * ia, w = ia2;
-        const float cj[4] = {1.0f / 12.0f, -1.0f / 720.0f, 1.0f / 30240.0f, -1.0f / 1209600.0f};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          br += cj[j] * P * sm1 * w;
-          P *= (s + (float)(2 * j + 1)) * (s + (float)(2 * j + 2));
-          w *= ia2;
-        }
-        // ln Q = (1-s) ln a - lnc, with the product's error carried
-        const float prod = sm1 * la_hi;
-        const float perr = fmaf(sm1, la_hi, -prod) + sm1 * la_lo;
-        const float Q = expf(-prod - f.lnc) * (1.0f - perr) * br;
+        // Q(v) = zeta(s, v + 1)/Z
+        const float Q = survival_em_f32((float)(v + 1ull), la_hi, la_lo, f);
         const float pv = exp_neg_prod(f.a_hi, f.a_lo, lv_hi, lv_lo) * f.invZ;
         const float Fv = 1.0f - Q;
         const float Fb = 1.0f - (Q + pv);
@@ -1180,9 +1187,10 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
               a.rec.dense + wi.dense_off + (uint64_t)(j0 + r) * (uint64_t)cell.H * (cell.wide ? 2 : 1);
           const uint64_t *pr = reinterpret_cast<const uint64_t *>(arena + off);
           const double D =
-              cell.wide ? ks_warp<F32, uint32_t>(reinterpret_cast<const uint32_t *>(dense), tm, pr, ns, n, fr,
+              cell.wide ? ks_warp<F32, uint32_t>(reinterpret_cast<const uint32_t *>(dense), tm, pr, ns, n, xmin, fr,
                                                  law.lnT, law.lnT_hi, law.lnT_lo, lane)
-                        : ks_warp<F32, uint16_t>(dense, tm, pr, ns, n, fr, law.lnT, law.lnT_hi, law.lnT_lo, lane);
+                        : ks_warp<F32, uint16_t>(dense, tm, pr, ns, n, xmin, fr, law.lnT, law.lnT_hi, law.lnT_lo,
+                                                 lane);
           if (lane == r) myD = D;
         }
         if (mine && simple) myD = lane_ks<F32>(my_dense, my_tmax, n, fo, law);
@@ -1457,7 +1465,8 @@ __global__ void __launch_bounds__(1024) dataset_kernel(const int32_t *x, int64_t
       }
       fo = shfl_fit(fo, 0);
     }
-    const double D = ks_warp<F32, uint32_t>(hist, tmax, pairs, base, n, fo, law.lnT, law.lnT_hi, law.lnT_lo, lane);
+    const double D =
+        ks_warp<F32, uint32_t>(hist, tmax, pairs, base, n, xmin, fo, law.lnT, law.lnT_hi, law.lnT_lo, lane);
     if (lane == 0) {
       out[0] = fo.ahat;
       out[1] = D;
