@@ -280,7 +280,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     return sp.cells[a].n > sp.cells[b].n;
   });
   // items, and waves whose replicate records fit the wave byte budget
-  const size_t wave_budget = std::min<size_t>(ctx->budget / 4, (size_t)4 << 30);
+  const size_t wave_budget = std::min<size_t>(ctx->budget / 4, (size_t)16 << 30);
   // Warp-form items hold up to kItemReps replicates; a small simulation gets
   // smaller items (down to 32) so that there are at least two per resident
   // sampler block.  Results do not depend on the item size.

@@ -136,10 +136,15 @@ __host__ __device__ inline RoundKeys round_keys(uint64_t seed) {
 __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const RoundKeys &rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
-    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
-    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k[2 * r], (uint32_t)p1,
-                   (uint32_t)(p0 >> 32) ^ c.w ^ rk.k[2 * r + 1], (uint32_t)p0);
+    // one 32x32->64 multiply per product, its halves unpacked in place
+    uint32_t h0, l0, h1, l1;
+    asm("{\n\t.reg .b64 t;\n\tmul.wide.u32 t, %2, 0xD2511F53;\n\tmov.b64 {%0, %1}, t;\n\t}"
+        : "=r"(l0), "=r"(h0)
+        : "r"(c.x));
+    asm("{\n\t.reg .b64 t;\n\tmul.wide.u32 t, %2, 0xCD9E8D57;\n\tmov.b64 {%0, %1}, t;\n\t}"
+        : "=r"(l1), "=r"(h1)
+        : "r"(c.z));
+    c = make_uint4(h1 ^ c.y ^ rk.k[2 * r], l1, h0 ^ c.w ^ rk.k[2 * r + 1], l0);
   }
   return c;
 }
