@@ -142,14 +142,15 @@ pl_status pl_sample(pl_ctx *ctx, double alpha, uint64_t xmin, uint64_t seed,
  * xmin the log-sum is increased by ln((xmin+1)/xmin) (one point counted as
  * xmin+1), as the paper's code does for xmin = 1.  x_dev: device, int32[n],
  * every value >= xmin.  alpha_hat_host: host double.  Synchronises `stream`.
- * Errors: PL_EINVAL (n < 1, xmin < 1, a value < xmin), PL_ENOCONV. */
+ * Errors: PL_EINVAL (n < 1, n > 2^31 - 1, xmin < 1, xmin > 2^31, a value
+ * < xmin), PL_ENOCONV. */
 pl_status pl_fit_mle(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
                      uint64_t xmin, double *alpha_hat_host, void *stream);
 
 /* KS distance (Eq. 3) between the empirical CDF of x and the law at
  * exponent alpha (alpha > 1; pass the fitted exponent to use the paper's
- * tables).  x_dev: device, int32[n], values >= xmin.  D_host: host double.
- * Synchronises `stream`.  Errors: PL_EINVAL. */
+ * tables).  x_dev: device, int32[n] (1 <= n <= 2^31 - 1), values >= xmin.
+ * D_host: host double.  Synchronises `stream`.  Errors: PL_EINVAL. */
 pl_status pl_ks_stat(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
                      uint64_t xmin, double alpha, pl_precision prec,
                      double *D_host, void *stream);

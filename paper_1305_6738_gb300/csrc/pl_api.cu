@@ -684,7 +684,8 @@ pl_status pl_sample(pl_ctx *ctx, double alpha, uint64_t xmin, uint64_t seed, uin
 namespace {
 pl_status run_dataset(pl_ctx *ctx, const int32_t *x, int64_t n, uint64_t xmin, bool fit, double alpha,
                       pl_precision prec, double out_host[3], cudaStream_t st, Carver *keep = nullptr) {
-  if (!x || n < 1 || xmin < 1 || xmin > (1ull << 31)) return fail(ctx, PL_EINVAL, "data set: bad arguments");
+  if (!x || n < 1 || n > INT32_MAX || xmin < 1 || xmin > (1ull << 31))
+    return fail(ctx, PL_EINVAL, "data set: bad arguments");
   if (!fit && (!(alpha > 1.0) || alpha > 64.0)) return fail(ctx, PL_EINVAL, "alpha must be in (1, 64]");
   LawPlan lp{fit ? 2.0 : alpha, xmin, kL1};
   const uint64_t cap = next_pow2((uint64_t)n);

@@ -272,6 +272,12 @@ __device__ __forceinline__ void ln_u64_ff(uint64_t a, float &hi, float &lo) {
   hi = s;
 }
 
+// uint64 to binary32 through 32-bit conversions (64-bit integer conversions run
+// on the slow binary64 unit); within one ulp.
+__device__ __forceinline__ float u64_to_f32(uint64_t v) {
+  return fmaf((float)(uint32_t)(v >> 32), 4294967296.0f, (float)(uint32_t)v);
+}
+
 // exp(-(a_hi + a_lo)(l_hi + l_lo)) in binary32, the product's rounding error
 // carried to first order.
 __device__ __forceinline__ float exp_neg_prod(float a_hi, float a_lo, float l_hi, float l_lo) {
@@ -464,7 +470,7 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
     }
     return warp_max(best);
   } else {
-    const float inv_n = 1.0f / (float)n;
+    const float inv_n = 1.0f / (float)(uint32_t)n;  // n < 2^31: 32-bit conversions only
     float best = 0.0f;
     // dense part, one contiguous chunk of bins per lane.  The chunk's starting
     // F = 1 - zeta(s, xmin + i0)/Z comes from the short Euler-Maclaurin series
@@ -480,7 +486,7 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
     int64_t C = incC - sc;
     float Fh = 0.0f, Fl = 0.0f;
     if (i0 > 0 && i0 < nbins) {
-      const float af = (float)(xmin + (uint64_t)i0);
+      const float af = u64_to_f32(xmin + (uint64_t)i0);
       if (af >= 10.0f + 1.5f * f.a_hi) {
         two_sum(1.0f, -survival_em_f32(af, lnT_hi[i0], lnT_lo[i0], f), Fh, Fl);
       } else {
@@ -491,7 +497,7 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
     for (int64_t i = i0; i < i1; ++i) {
       ff_add(Fh, Fl, exp_neg_prod(f.a_hi, f.a_lo, lnT_hi[i], lnT_lo[i]) * f.invZ, 0.0f);
       C += (int64_t)dense[i];
-      best = fmaxf(best, fabsf(Fh - (float)C * inv_n));
+      best = fmaxf(best, fabsf(Fh - (float)(uint32_t)C * inv_n));
     }
     int64_t carryC = __shfl_sync(0xffffffffu, incC, 31);
     for (int64_t k0 = 0; k0 < nsd; k0 += 32) {
@@ -500,7 +506,7 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
       const uint64_t v = ok ? pairs[2 * k] : 0;
       const int64_t c = ok ? (int64_t)pairs[2 * k + 1] : 0;
       const int64_t Ca = carryC + warp_scan_i64(c, lane);
-      if (ok && (float)(v + 1ull) < 10.0f + 1.5f * f.a_hi) {
+      if (ok && u64_to_f32(v + 1ull) < 10.0f + 1.5f * f.a_hi) {
         // exponent too large for the short binary32 series at this argument
         const int64_t Cb = Ca - c;
         double q;
@@ -509,18 +515,18 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
         const float pv = (float)(exp(-f.ahat * log((double)v)) * (double)f.invZ);
         const float Fv = 1.0f - Q;
         const float Fb = 1.0f - (Q + pv);
-        best = fmaxf(best, fmaxf(fabsf(Fv - (float)Ca * inv_n), fabsf(Fb - (float)Cb * inv_n)));
+        best = fmaxf(best, fmaxf(fabsf(Fv - (float)(uint32_t)Ca * inv_n), fabsf(Fb - (float)(uint32_t)Cb * inv_n)));
       } else if (ok) {
         const int64_t Cb = Ca - c;
         float la_hi, la_lo, lv_hi, lv_lo;
         ln_u64_ff(v + 1ull, la_hi, la_lo);
         ln_u64_ff(v, lv_hi, lv_lo);
         // Q(v) = zeta(s, v + 1)/Z
-        const float Q = survival_em_f32((float)(v + 1ull), la_hi, la_lo, f);
+        const float Q = survival_em_f32(u64_to_f32(v + 1ull), la_hi, la_lo, f);
         const float pv = exp_neg_prod(f.a_hi, f.a_lo, lv_hi, lv_lo) * f.invZ;
         const float Fv = 1.0f - Q;
         const float Fb = 1.0f - (Q + pv);
-        best = fmaxf(best, fmaxf(fabsf(Fv - (float)Ca * inv_n), fabsf(Fb - (float)Cb * inv_n)));
+        best = fmaxf(best, fmaxf(fabsf(Fv - (float)(uint32_t)Ca * inv_n), fabsf(Fb - (float)(uint32_t)Cb * inv_n)));
       }
       carryC = __shfl_sync(0xffffffffu, Ca, 31);
     }
@@ -1094,9 +1100,9 @@ __device__ __forceinline__ double lane_ks(const uint16_t *dense, int64_t tmax, i
     }
     return best;
   }
-  const float inv_n = 1.0f / (float)n;
+  const float inv_n = 1.0f / (float)(uint32_t)n;
   float Fh = 0.0f, Fl = 0.0f, best = 0.0f;
-  int64_t C = 0;
+  uint32_t C = 0;
   for (int64_t i = 0; i <= tmax; ++i) {
     ff_add(Fh, Fl, exp_neg_prod(f.a_hi, f.a_lo, law.lnT_hi[i], law.lnT_lo[i]) * f.invZ, 0.0f);
     C += dense[i];
@@ -1284,7 +1290,7 @@ __global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel
           for (int64_t k = lane; k < nsd; k += 32) {
             float vh, vl;
             ln_u64_ff(pairs[2 * k], vh, vl);
-            const float c = (float)pairs[2 * k + 1];
+            const float c = (float)(uint32_t)pairs[2 * k + 1];
             const float ph = c * vh;
             ff_add(Lh, Ll, ph, fmaf(c, vh, -ph) + c * vl);
           }
