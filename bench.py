@@ -318,6 +318,28 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- replicas
+def replica_seed(rank: int) -> int:
+    """Replicas (one process per GPU) draw independent Philox streams: the key
+    is the base seed plus the rank.  No data crosses ranks."""
+    return 1 + rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value (the job's time); x itself without a group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return world * units_per_rank / seconds
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -407,7 +429,7 @@ def main():
     from paper_1305_6738_gb300 import pl
     ctx = pl.Context(local)
     prec = pl.PL_FP32_BULK if args.precision == "fp32-bulk" else pl.PL_FP64
-    seed = 1 + rank
+    seed = replica_seed(rank)
     cells = [pl.Cell(c.alpha, c.xmin, c.n, c.replicates, c.cell_id) for c in sweep]
     cut = torch.empty(len(cells) * len(Q), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -472,13 +494,9 @@ def main():
     if graph is not None:  # each replay launches the captured kernels
         launches = kernels_per_replay * args.steps
     ctx.pl_sync()
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * total_R * args.steps / (total_ms / 1000.0)
-    sps = world * draws * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
+    value = job_rate(total_R * args.steps, world, total_ms / 1000.0)
+    sps = job_rate(draws * args.steps, world, total_ms / 1000.0)
 
     # end to end through the public call with host buffers: host cell table in,
     # host cutoffs out (the call copies and synchronises), wall clock
@@ -494,7 +512,7 @@ def main():
         ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=cut)
         tr = ctx.pl_trace()
         kern_ms, fin_ms, waves = [tr["sample_ms"]], [tr["finish_ms"]], tr["waves"]
-    e2e_value = world * total_R / statistics.mean(e2e_s)
+    e2e_value = job_rate(total_R, world, max_over_ranks(statistics.mean(e2e_s), dist, "cuda"))
     h2d = len(cells) * 40 + len(Q) * 8
     d2h = host_cut.nbytes
 
