@@ -18,8 +18,13 @@ constexpr uint64_t kXCap = 1ull << 62;      // simulated values saturate here
 #ifndef PL_L1_ENTRIES
 #define PL_L1_ENTRIES 2048
 #endif
-#ifndef PL_WARP_MIN_BLOCKS
-#define PL_WARP_MIN_BLOCKS 2
+// finisher blocks per SM the compiler must fit (binary32 form / binary64
+// form): three trade some register spills for occupancy in the binary32 form
+#ifndef PL_FIN_MIN_BLOCKS_F32
+#define PL_FIN_MIN_BLOCKS_F32 3
+#endif
+#ifndef PL_FIN_MIN_BLOCKS_F64
+#define PL_FIN_MIN_BLOCKS_F64 2
 #endif
 constexpr int kL1 = PL_L1_ENTRIES;          // thresholds staged in shared memory
 constexpr int kGuideBits = 11;              // guide table: 2^11 buckets of m
@@ -179,6 +184,41 @@ __device__ __forceinline__ int em_shift(double s, double a) {
   return a < nmin ? (int)ceil(nmin - a) : 0;
 }
 
+// The Euler-Maclaurin part beyond the direct terms, from N on:
+//   N^(1-s)/(s-1) + N^-s/2 + sum_{j=1..8} B_2j/(2j)! s(s+1)..(s+2j-2) N^(-s-2j+1)
+// and its first/second s-derivatives into z[0..ND].
+template <int ND, bool PRECISE>
+__device__ __forceinline__ void hurwitz_em_tail(double s, double N, double *z) {
+  const double L = log(N);
+  const double Ns = PRECISE ? pow(N, -s) : exp(-s * L);
+  const double u = 1.0 / (s - 1.0);
+  const double N1s = N * Ns;
+  double z0 = N1s * u + 0.5 * Ns;
+  double z1 = -N1s * (L * u + u * u) - 0.5 * L * Ns;
+  double z2 = N1s * (L * L * u + 2.0 * L * u * u + 2.0 * u * u * u) + 0.5 * L * L * Ns;
+  const double inv_n2 = 1.0 / (N * N);
+  double w = Ns / N;                           // N^(-s-1)
+  double P = s, dP = 1.0, d2P = 0.0;           // s(s+1)..(s+2j-2) and derivatives
+#pragma unroll
+  for (int j = 1; j <= 8; ++j) {
+    const double c = bern_coef(j) * w;
+    z0 += c * P;
+    if (ND >= 1) z1 += c * (dP - L * P);
+    if (ND >= 2) z2 += c * (d2P - 2.0 * L * dP + L * L * P);
+#pragma unroll
+    for (int f = 2 * j - 1; f <= 2 * j; ++f) {
+      const double g = s + (double)f;
+      if (ND >= 2) d2P = d2P * g + 2.0 * dP;
+      if (ND >= 1) dP = dP * g + P;
+      P *= g;
+    }
+    w *= inv_n2;
+  }
+  z[0] = z0;
+  if (ND >= 1) z[1] = z1;
+  if (ND >= 2) z[2] = z2;
+}
+
 // zeta(s, a) and, for ND >= 1/2, its first/second s-derivatives into z[0..ND].
 // PRECISE evaluates powers with pow(); otherwise with exp(-s ln x), the log
 // taken from lnx_table when x - a0 < table_len (table of ln(a0 + i)).
@@ -203,35 +243,11 @@ __device__ __forceinline__ void hurwitz_em(double s, double a, double *z,
     if (ND >= 1) z1 -= lx * t;
     if (ND >= 2) z2 += lx * lx * t;
   }
-  const double N = a + (double)M;
-  const double L = log(N);
-  const double Ns = PRECISE ? pow(N, -s) : exp(-s * L);
-  const double u = 1.0 / (s - 1.0);
-  const double N1s = N * Ns;
-  z0 += N1s * u + 0.5 * Ns;
-  if (ND >= 1) z1 += -N1s * (L * u + u * u) - 0.5 * L * Ns;
-  if (ND >= 2) z2 += N1s * (L * L * u + 2.0 * L * u * u + 2.0 * u * u * u) + 0.5 * L * L * Ns;
-  const double inv_n2 = 1.0 / (N * N);
-  double w = Ns / N;                           // N^(-s-1)
-  double P = s, dP = 1.0, d2P = 0.0;           // s(s+1)..(s+2j-2) and derivatives
-#pragma unroll
-  for (int j = 1; j <= 8; ++j) {
-    const double c = bern_coef(j) * w;
-    z0 += c * P;
-    if (ND >= 1) z1 += c * (dP - L * P);
-    if (ND >= 2) z2 += c * (d2P - 2.0 * L * dP + L * L * P);
-#pragma unroll
-    for (int f = 2 * j - 1; f <= 2 * j; ++f) {
-      const double g = s + (double)f;
-      if (ND >= 2) d2P = d2P * g + 2.0 * dP;
-      if (ND >= 1) dP = dP * g + P;
-      P *= g;
-    }
-    w *= inv_n2;
-  }
-  z[0] = z0;
-  if (ND >= 1) z[1] = z1;
-  if (ND >= 2) z[2] = z2;
+  double t[3];
+  hurwitz_em_tail<ND, PRECISE>(s, a + (double)M, t);
+  z[0] = z0 + t[0];
+  if (ND >= 1) z[1] = z1 + t[1];
+  if (ND >= 2) z[2] = z2 + t[2];
 }
 
 __device__ __forceinline__ double hurwitz_precise(double s, double a) {

@@ -202,16 +202,39 @@ __device__ int newton_mle(double mbar, uint64_t xmin, double ln_xmin_half, const
 
 // ---------------------------------------------------------------------------
 // Fit tables (one Euler-Maclaurin evaluation per node, pow-based).
-__global__ void fit_nodes_kernel(FitTable *fts) {
+// One warp per node: the lanes share the Euler-Maclaurin direct terms (the
+// largest exponents need ~100 of them), a fixed-shape warp reduction adds
+// them, and lane 0 adds the tail and writes the node.
+constexpr int kFitNodeWarps = 8;
+
+__global__ void __launch_bounds__(kFitNodeWarps * 32) fit_nodes_kernel(FitTable *fts) {
   const FitTable ft = fts[blockIdx.y];
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= ft.nodes) return;
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * kFitNodeWarps + (threadIdx.x >> 5);
+  if (k >= ft.nodes) return;  // warp-uniform
   const double t_hi = log(kFitAlphaHi - 1.0), t_lo = log(kFitAlphaLo - 1.0);
   const double t = t_hi - (t_hi - t_lo) * (double)k / (double)(ft.nodes - 1);
   const double a = 1.0 + exp(t);
   const double x0 = (double)ft.xmin;
+  const int M = em_shift(a, x0);
+  double z0 = 0.0, z1 = 0.0, z2 = 0.0;
+  for (int i = lane; i < M; i += 32) {
+    const double x = x0 + (double)i;
+    const double lx = log(x);
+    const double tt = pow(x, -a);
+    z0 += tt;
+    z1 -= lx * tt;
+    z2 += lx * lx * tt;
+  }
+  z0 = warp_sum(z0);
+  z1 = warp_sum(z1);
+  z2 = warp_sum(z2);
+  if (lane != 0) return;
   double z[3];
-  hurwitz_em<2, true>(a, x0, z);
+  hurwitz_em_tail<2, true>(a, x0 + (double)M, z);
+  z[0] += z0;
+  z[1] += z1;
+  z[2] += z2;
   const double g = z[1] / z[0];
   const double h = -g - log(x0);
   const double var = z[2] / z[0] - g * g;
@@ -249,7 +272,8 @@ __global__ void fit_guide_kernel(FitTable *fts) {
 
 cudaError_t launch_fit_tables(FitTable *fts_dev, int nfit, cudaStream_t st) {
   if (nfit <= 0) return cudaSuccess;
-  fit_nodes_kernel<<<dim3((kFitNodes + 127) / 128, nfit), 128, 0, st>>>(fts_dev);
+  fit_nodes_kernel<<<dim3((kFitNodes + kFitNodeWarps - 1) / kFitNodeWarps, nfit), kFitNodeWarps * 32, 0, st>>>(
+      fts_dev);
   const int n = kFitNodes > kFitGuides ? kFitNodes : kFitGuides;
   fit_guide_kernel<<<dim3((n + 127) / 128, nfit), 128, 0, st>>>(fts_dev);
   return cudaGetLastError();
@@ -1112,7 +1136,8 @@ __device__ __forceinline__ double lane_ks(const uint16_t *dense, int64_t tmax, i
 }
 
 template <bool F32>
-__global__ void __launch_bounds__(kWarps * 32, PL_WARP_MIN_BLOCKS) finish_kernel(FinishLaunch a) {
+__global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_FIN_MIN_BLOCKS_F64)
+    finish_kernel(FinishLaunch a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
   uint32_t *sG = reinterpret_cast<uint32_t *>(smem + kL1 * 8);
