@@ -224,8 +224,9 @@ pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
  * `workers` host threads each own a context (with the fit tables of every
  * xmin seen kept on the device) and a non-blocking stream, so up to `workers`
  * requests run on the GPU at the same time.  A request is admitted, oldest
- * first, when a worker is free and its planned device workspace fits in
- * mem_budget_bytes (0 = 40 GiB) beside the requests already running; a
+ * first, when a worker is free and its planned device workspace (sized at a
+ * fitted exponent of 1.4; each worker's context also keeps to the budget)
+ * fits in mem_budget_bytes (0 = 40 GiB) beside the requests already running; a
  * request whose planned workspace exceeds the whole budget is not run: its
  * result (status PL_ENOMEM, NaN outputs) is ready at once.
  * Results are the same numbers pl_bootstrap_pvalue gives for that request

@@ -376,10 +376,14 @@ void carve_sim(Carver &cv, const SimPlan &sp, int blocks, int sample_blocks, Sim
   b.spill_cap = next_pow2((uint64_t)std::max<int64_t>(sp.finisher_spill, kSortSmem));
   b.arena_bytes = ((16 * (size_t)sp.finisher_spill + 16) + (size_t)32 * 2048 + 255) & ~(size_t)255;
   if (arena_override) b.arena_bytes = std::max<size_t>(16 * (size_t)sp.finisher_spill + 16, arena_override);
-  b.blocks = blocks;
+  // finisher grid: no more blocks than the largest wave has items (each
+  // block's warps own a scratch slot)
+  size_t max_items = 1;
+  for (const Wave &w : sp.waves) max_items = std::max(max_items, w.count);
+  b.blocks = (int)std::min<size_t>((size_t)blocks, max_items);
   b.sample_blocks = sample_blocks;
   b.block_sampler_blocks = block_sampler_blocks;
-  b.scratch = cv.take<uint8_t>((size_t)blocks * kWarps * (b.spill_cap * 8 + b.arena_bytes));
+  b.scratch = cv.take<uint8_t>((size_t)b.blocks * kWarps * (b.spill_cap * 8 + b.arena_bytes));
 }
 
 pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t st) {
@@ -540,9 +544,11 @@ void ctx_enable_fit_cache(pl_ctx *ctx) { ctx->cache_fits = true; }
 uint64_t ctx_launches(const pl_ctx *ctx) { return ctx->launches; }
 
 // Device bytes a bootstrap request of n values and B replicates plans (the
-// data-set pass and the simulation; alpha taken as 2 for sizing).
+// data-set pass and the simulation), sized at exponent 1.4: the spill slots,
+// tail queue and tables grow as the fitted exponent falls, and 1.4 covers
+// power-law data with alpha >= 1.5 and the rounded-lognormal alternative.
 size_t ctx_bootstrap_bytes(pl_ctx *ctx, int64_t n, uint64_t xmin, int64_t B) {
-  pl_cell cell{2.0, xmin, n, B, 0};
+  pl_cell cell{1.4, xmin, n, B, 0};
   SimPlan sp;
   if (plan_cells(ctx, &cell, 1, 1u, sp) != PL_OK) return 0;
   const int blocks = sim_blocks(ctx, true), sblocks = sample_blocks(ctx),
