@@ -1087,6 +1087,19 @@ cudaError_t launch_sample_hist(const SampleLaunch &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Copy the dense counts 0..tmax of a warp-form record (16-byte aligned, H >= 32
+// bins) to the warp's shared memory with 16-byte loads, so that the scans
+// below read them on chip instead of one dependent global load per bin.
+__device__ __forceinline__ const uint16_t *stage_dense(const uint16_t *src, int64_t tmax, uint32_t *onchip,
+                                                       int lane) {
+  uint16_t *dst = reinterpret_cast<uint16_t *>(onchip);
+  const int64_t nvec = (tmax + 8) >> 3;
+  for (int64_t v = lane; v < nvec; v += 32)
+    reinterpret_cast<uint4 *>(dst)[v] = reinterpret_cast<const uint4 *>(src)[v];
+  __syncwarp();
+  return dst;
+}
+
 // Small replicates (warp form, no spills, largest bin below kLaneBins) are
 // finished by one lane each: the log-sum and the KS scan run serially over the
 // replicate's dense counts, with no warp reductions.  Same arithmetic as the
@@ -1217,11 +1230,15 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
           const uint16_t *dense =
               a.rec.dense + wi.dense_off + (uint64_t)(j0 + r) * (uint64_t)cell.H * (cell.wide ? 2 : 1);
           const uint64_t *pr = reinterpret_cast<const uint64_t *>(arena + off);
-          const double D =
-              cell.wide ? ks_warp<F32, uint32_t>(reinterpret_cast<const uint32_t *>(dense), tm, pr, ns, n, xmin, fr,
-                                                 law.lnT, law.lnT_hi, law.lnT_lo, lane)
-                        : ks_warp<F32, uint16_t>(dense, tm, pr, ns, n, xmin, fr, law.lnT, law.lnT_hi, law.lnT_lo,
-                                                 lane);
+          double D;
+          if (cell.wide) {
+            D = ks_warp<F32, uint32_t>(reinterpret_cast<const uint32_t *>(dense), tm, pr, ns, n, xmin, fr, law.lnT,
+                                       law.lnT_hi, law.lnT_lo, lane);
+          } else {
+            const uint16_t *sd = stage_dense(dense, tm, hist, lane);
+            D = ks_warp<F32, uint16_t>(sd, tm, pr, ns, n, xmin, fr, law.lnT, law.lnT_hi, law.lnT_lo, lane);
+            __syncwarp();
+          }
           if (lane == r) myD = D;
         }
         if (mine && simple) myD = lane_ks<F32>(my_dense, my_tmax, n, fo, law);
@@ -1278,21 +1295,23 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
         // order, and hence the rounding, never depends on the spill order)
         double L;
         float Lh = 0.0f, Ll = 0.0f;
+        const uint16_t *dsrc = dense32 ? dense : stage_dense(dense, tmax, hist, lane);
         if (!F32) {
           double acc = 0.0;
           for (int64_t i = lane; i <= tmax; i += 32)
-            acc += (double)(dense32 ? dense32[i] : (uint32_t)dense[i]) * law.lnT[i];
+            acc += (double)(dense32 ? dense32[i] : (uint32_t)dsrc[i]) * law.lnT[i];
           L = warp_sum(acc);
         } else {
           for (int64_t i = lane; i <= tmax; i += 32) {
-            const float c = (float)(dense32 ? dense32[i] : (uint32_t)dense[i]);
+            const float c = (float)(dense32 ? dense32[i] : (uint32_t)dsrc[i]);
             const float ph = c * law.lnT_hi[i];
             const float pe = fmaf(c, law.lnT_hi[i], -ph) + c * law.lnT_lo[i];
             ff_add(Lh, Ll, ph, pe);
           }
           L = 0.0;
         }
-        const bool allmin = tmax >= 0 && (int64_t)(dense32 ? dense32[0] : (uint32_t)dense[0]) == n;
+        const bool allmin = tmax >= 0 && (int64_t)(dense32 ? dense32[0] : (uint32_t)dsrc[0]) == n;
+        __syncwarp();  // the staged copy is overwritten by the spill sort below
         PL_PHASE(1);
         // arena space for this replicate's spill pairs; run phases 2-3 early if full
         const size_t need = (size_t)s * 16;
