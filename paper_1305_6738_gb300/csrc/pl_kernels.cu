@@ -316,7 +316,8 @@ struct FitOut {
   double ahat;
   double Z;
   // binary32 form only
-  float a_hi, a_lo, invZ, lnZ, lnc;   // lnc = ln((ahat - 1) Z)
+  float a_hi, a_lo, invZ, lnZ;
+  float lnc, lnc_lo;                  // ln((ahat - 1) Z) as an unevaluated float pair
 };
 
 __device__ __forceinline__ FitOut fit_from_logsum(double L, int64_t n, uint64_t xmin,
@@ -330,7 +331,9 @@ __device__ __forceinline__ FitOut fit_from_logsum(double L, int64_t n, uint64_t 
     o.a_lo = (float)(o.ahat - (double)o.a_hi);
     o.invZ = (float)(1.0 / o.Z);
     o.lnZ = (float)log(o.Z);
-    o.lnc = (float)log((o.ahat - 1.0) * o.Z);
+    const double lncd = log((o.ahat - 1.0) * o.Z);
+    o.lnc = (float)lncd;
+    o.lnc_lo = (float)(lncd - (double)o.lnc);
   }
   return o;
 }
@@ -375,9 +378,14 @@ __device__ __forceinline__ FitOut fit_lanes(double L, int64_t n, uint64_t xmin, 
     o.Z = 0.0;  // the binary32 form reads invZ, lnZ and lnc only
     o.a_hi = (float)a0;
     o.a_lo = (float)(a0 - (double)o.a_hi);
+    // ln zeta as a float pair: 1/zeta and the survival's constant keep the
+    // pair's low part (ln zeta reaches -60 for large xmin)
     o.lnZ = (float)lz0;
-    o.invZ = expf(-o.lnZ);
-    o.lnc = logf((float)(a0 - 1.0)) + o.lnZ;
+    const float lz_lo = (float)(lz0 - (double)o.lnZ);
+    o.invZ = expf(-o.lnZ) * (1.0f - lz_lo);
+    float e;
+    two_sum(logf((float)(a0 - 1.0)), o.lnZ, o.lnc, e);
+    o.lnc_lo = e + lz_lo;
     return o;
   }
   // the shift is the lane's own (not a warp maximum), so a replicate's result
@@ -406,7 +414,9 @@ __device__ __forceinline__ FitOut fit_lanes(double L, int64_t n, uint64_t xmin, 
     o.a_lo = (float)(o.ahat - (double)o.a_hi);
     o.invZ = (float)(1.0 / o.Z);
     o.lnZ = logf((float)o.Z);
-    o.lnc = logf((float)((o.ahat - 1.0) * o.Z));
+    const double lncd = log((o.ahat - 1.0) * o.Z);
+    o.lnc = (float)lncd;
+    o.lnc_lo = (float)(lncd - (double)o.lnc);
   }
   return o;
 }
@@ -420,6 +430,7 @@ __device__ __forceinline__ FitOut shfl_fit(const FitOut &f, int src) {
   o.invZ = __shfl_sync(0xffffffffu, f.invZ, src);
   o.lnZ = __shfl_sync(0xffffffffu, f.lnZ, src);
   o.lnc = __shfl_sync(0xffffffffu, f.lnc, src);
+  o.lnc_lo = __shfl_sync(0xffffffffu, f.lnc_lo, src);
   return o;
 }
 
@@ -450,7 +461,7 @@ __device__ __forceinline__ float survival_em_f32(float af, float la_hi, float la
   }
   const float prod = sm1 * la_hi;
   const float perr = fmaf(sm1, la_hi, -prod) + sm1 * la_lo;
-  return expf(-prod - f.lnc) * (1.0f - perr) * br;
+  return expf(-prod - f.lnc) * (1.0f - perr - f.lnc_lo) * br;
 }
 
 template <bool F32, typename DT>
@@ -1511,7 +1522,9 @@ __global__ void __launch_bounds__(1024) dataset_kernel(const int32_t *x, int64_t
         fo.a_lo = (float)(alpha_in - (double)fo.a_hi);
         fo.invZ = (float)(1.0 / z0);
         fo.lnZ = (float)log(z0);
-        fo.lnc = (float)log((alpha_in - 1.0) * z0);
+        const double lncd = log((alpha_in - 1.0) * z0);
+        fo.lnc = (float)lncd;
+        fo.lnc_lo = (float)(lncd - (double)fo.lnc);
       }
       fo = shfl_fit(fo, 0);
     }

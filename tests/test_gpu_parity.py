@@ -485,3 +485,31 @@ def test_waves_do_not_change_results(pl):
     assert torch.equal(out[0][0], out[1][0])
     assert torch.equal(out[0][1], out[1][1])
     assert (out[0][2] == out[1][2]).all()
+
+
+# exponents near 1 (values saturating at 2^62, fits near the lower end of the
+# fit table or below it) and large exponents (samples almost all at xmin)
+EXTREME_CELLS = [(1.1, 1, 200, 40, 21), (1.02, 1, 50, 30, 22), (8.0, 1, 10, 300, 23), (6.0, 100, 500, 40, 24)]
+
+
+@pytest.fixture(scope="module")
+def extreme_oracle():
+    return _oracle_cells(EXTREME_CELLS)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_extreme_exponents_match_oracle(ctx, pl, extreme_oracle, prec):
+    cells = [pl.Cell(*c) for c in EXTREME_CELLS]
+    total = sum(c[3] for c in EXTREME_CELLS)
+    D = torch.empty(total, dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
+    A = torch.empty(total, dtype=torch.float64, device="cuda")
+    ctx.pl_ks_cutoffs(cells, 1, [0.5, 0.9], prec, D=D, alpha_hat=A)
+    ctx.pl_sync()
+    atol_a, atol_d = TOL[prec]
+    off = 0
+    for ci, (a, xm, n, R, cid) in enumerate(EXTREME_CELLS):
+        dg = D[off:off + R].double().cpu().numpy()
+        ag = A[off:off + R].cpu().numpy()
+        assert np.max(np.abs(ag / extreme_oracle[1][ci] - 1)) < atol_a, (ci, ag, extreme_oracle[1][ci])
+        assert np.max(np.abs(dg - extreme_oracle[0][ci])) < atol_d, ci
+        off += R
