@@ -489,7 +489,10 @@ def test_waves_do_not_change_results(pl):
 
 # exponents near 1 (values saturating at 2^62, fits near the lower end of the
 # fit table or below it) and large exponents (samples almost all at xmin)
-EXTREME_CELLS = [(1.1, 1, 200, 40, 21), (1.02, 1, 50, 30, 22), (8.0, 1, 10, 300, 23), (6.0, 100, 500, 40, 24)]
+EXTREME_CELLS = [(1.1, 1, 200, 40, 21), (1.02, 1, 50, 30, 22), (8.0, 1, 10, 300, 23), (6.0, 100, 500, 40, 24),
+                 # large lower ends, and the largest n of the warp form
+                 (2.5, 10**6, 200, 50, 31), (1.8, 2**31 - 5, 100, 30, 32), (3.0, 1000, 5000, 20, 33),
+                 (2.0, 7, 65535, 3, 34)]
 
 
 @pytest.fixture(scope="module")
