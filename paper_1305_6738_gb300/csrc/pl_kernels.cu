@@ -449,7 +449,8 @@ __device__ __forceinline__ FitOut shfl_fit(const FitOut &f, int src) {
 //   a^(1-s)/((s-1) Z) * [1 + (s-1)/(2a) + sum_j B2j/(2j)! s(s+1)..(s+2j-2)(s-1) a^-2j],
 // with ln a = la_hi + la_lo and the product's rounding error carried.
 __device__ __forceinline__ float survival_em_f32(float af, float la_hi, float la_lo, const FitOut &f) {
-  const float s = f.a_hi, sm1 = (float)(f.ahat - 1.0);
+  // s - 1 = (a_hi - 1) + a_lo, the first part exact in binary32 (a_hi >= 1)
+  const float s = f.a_hi, sm1 = f.a_hi - 1.0f;
   const float ia = 1.0f / af, ia2 = ia * ia;
   float P = s, br = 1.0f + 0.5f * sm1 * ia, w = ia2;
   const float cj[4] = {1.0f / 12.0f, -1.0f / 720.0f, 1.0f / 30240.0f, -1.0f / 1209600.0f};
@@ -460,7 +461,7 @@ __device__ __forceinline__ float survival_em_f32(float af, float la_hi, float la
     w *= ia2;
   }
   const float prod = sm1 * la_hi;
-  const float perr = fmaf(sm1, la_hi, -prod) + sm1 * la_lo;
+  const float perr = fmaf(sm1, la_hi, -prod) + fmaf(sm1, la_lo, f.a_lo * la_hi);
   return expf(-prod - f.lnc) * (1.0f - perr - f.lnc_lo) * br;
 }
 
