@@ -27,16 +27,23 @@ namespace pl {
 // ===========================================================================
 // Law tables.
 
+// Z = zeta(alpha, xmin), one warp per law: the lanes share the direct terms.
 __global__ void law_z_kernel(Law *laws, int nlaws) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nlaws) {
-    const double a = laws[i].alpha;
-    const double Z = hurwitz_precise(a, (double)laws[i].xmin);
-    laws[i].Z = Z;
-    laws[i].tail_c = (float)((a - 1.0) * Z * 0x1p-32);
-    laws[i].tail_e = (float)(-1.0 / (a - 1.0));
-    laws[i].xmin_f = (float)((double)laws[i].xmin + 0.5);
-  }
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= nlaws) return;  // warp-uniform
+  const double a = laws[i].alpha, x0 = (double)laws[i].xmin;
+  const int M = em_shift(a, x0);
+  double z = 0.0;
+  for (int k = lane; k < M; k += 32) z += pow(x0 + (double)k, -a);
+  z = warp_sum(z);
+  if (lane != 0) return;
+  double t;
+  hurwitz_em_tail<0, true>(a, x0 + (double)M, &t);
+  const double Z = z + t;
+  laws[i].Z = Z;
+  laws[i].tail_c = (float)((a - 1.0) * Z * 0x1p-32);
+  laws[i].tail_e = (float)(-1.0 / (a - 1.0));
+  laws[i].xmin_f = (float)(x0 + 0.5);
 }
 
 // T[i] = floor(Q(xmin+i) 2^53) + 1 and the log tables of xmin + i.
@@ -84,7 +91,7 @@ __global__ void law_guide_kernel(Law *laws) {
 
 cudaError_t launch_law_setup(Law *laws_dev, int nlaws, cudaStream_t st) {
   if (nlaws <= 0) return cudaSuccess;
-  law_z_kernel<<<(nlaws + 63) / 64, 64, 0, st>>>(laws_dev, nlaws);
+  law_z_kernel<<<(nlaws + 1) / 2, 64, 0, st>>>(laws_dev, nlaws);
   law_fill_kernel<<<dim3(256, nlaws), 256, 0, st>>>(laws_dev);
   law_guide_kernel<<<dim3(kGuide / 256, nlaws), 256, 0, st>>>(laws_dev);
   return cudaGetLastError();
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(kFitNodeWarps * 32) fit_nodes_kernel(FitTable 
   for (int i = lane; i < M; i += 32) {
     const double x = x0 + (double)i;
     const double lx = log(x);
-    const double tt = pow(x, -a);
+    const double tt = exp(-a * lx);  // node accuracy needs ~1e-13, not pow's last bit
     z0 += tt;
     z1 -= lx * tt;
     z2 += lx * lx * tt;
