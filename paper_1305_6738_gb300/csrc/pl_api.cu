@@ -49,6 +49,11 @@ struct pl_ctx {
   std::vector<void *> fit_mem;
   uint32_t traced_waves = 0;
   uint64_t traced_draws = 0;
+  // pinned staging of the host-written tables and the event of its last copy
+  void *staging = nullptr;
+  size_t staging_size = 0;
+  cudaEvent_t staging_ev = nullptr;
+  bool staged = false;
 };
 
 namespace {
@@ -339,6 +344,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
 }
 
 struct SimBuffers {
+  size_t host_bytes;      // laws_dev .. end of items: the host-written block
   FitTable *fits_dev;
   std::vector<FitTable> fits_host;
   Law *laws_dev;
@@ -358,15 +364,18 @@ struct SimBuffers {
 // Lay out (or size) the device buffers of a simulation plan.
 void carve_sim(Carver &cv, const SimPlan &sp, int blocks, int sample_blocks, SimBuffers &b, size_t arena_override,
                int block_sampler_blocks) {
-  b.fits_host.clear();
-  for (uint64_t xm : sp.fit_xmins) b.fits_host.push_back(make_fit_table(cv, xm));
-  b.fits_dev = cv.take<FitTable>(sp.fit_xmins.size());
-  b.laws_host.clear();
-  for (const auto &lp : sp.laws) b.laws_host.push_back(carve_law(cv, lp));
+  // the small tables written from the host, contiguous: one copy uploads them
   b.laws_dev = cv.take<Law>(sp.laws.size());
+  b.fits_dev = cv.take<FitTable>(sp.fit_xmins.size());
   b.cells = cv.take<Cell>(sp.cells.size());
   b.consts = cv.take<CellConst>(sp.consts.size());
   b.items = cv.take<WorkItem>(sp.items.size());
+  b.host_bytes = (size_t)(reinterpret_cast<uint8_t *>(b.items + sp.items.size()) -
+                          reinterpret_cast<uint8_t *>(b.laws_dev));
+  b.fits_host.clear();
+  for (uint64_t xm : sp.fit_xmins) b.fits_host.push_back(make_fit_table(cv, xm));
+  b.laws_host.clear();
+  for (const auto &lp : sp.laws) b.laws_host.push_back(carve_law(cv, lp));
   b.rec.dense = cv.take<uint16_t>(sp.dense_elems);
   b.rec.spill = cv.take<uint64_t>(sp.spill_elems);
   b.rec.meta = cv.take<int2>(sp.meta_elems);
@@ -386,14 +395,23 @@ void carve_sim(Carver &cv, const SimPlan &sp, int blocks, int sample_blocks, Sim
   b.scratch = cv.take<uint8_t>((size_t)b.blocks * kWarps * (b.spill_cap * 8 + b.arena_bytes));
 }
 
+// Pinned staging of the host-written tables, reused across calls; the copy
+// of the previous call must have left it before it is rewritten.
+pl_status staging(pl_ctx *ctx, size_t bytes, uint8_t **out) {
+  if (ctx->staged) PL_CUDA(cudaEventSynchronize(ctx->staging_ev));
+  if (bytes > ctx->staging_size) {
+    if (ctx->staging) PL_CUDA(cudaFreeHost(ctx->staging));
+    ctx->staging = nullptr;
+    ctx->staging_size = 0;
+    PL_CUDA(cudaMallocHost(&ctx->staging, std::max<size_t>(bytes, 1 << 16)));
+    ctx->staging_size = std::max<size_t>(bytes, 1 << 16);
+  }
+  if (!ctx->staging_ev) PL_CUDA(cudaEventCreateWithFlags(&ctx->staging_ev, cudaEventDisableTiming));
+  *out = static_cast<uint8_t *>(ctx->staging);
+  return PL_OK;
+}
+
 pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t st) {
-  PL_CUDA(cudaMemcpyAsync(b.laws_dev, b.laws_host.data(), sizeof(Law) * b.laws_host.size(),
-                          cudaMemcpyHostToDevice, st));
-  PL_CUDA(cudaMemcpyAsync(b.cells, sp.cells.data(), sizeof(Cell) * sp.cells.size(), cudaMemcpyHostToDevice, st));
-  PL_CUDA(cudaMemcpyAsync(b.consts, sp.consts.data(), sizeof(CellConst) * sp.consts.size(),
-                          cudaMemcpyHostToDevice, st));
-  PL_CUDA(cudaMemcpyAsync(b.items, sp.items.data(), sizeof(WorkItem) * sp.items.size(),
-                          cudaMemcpyHostToDevice, st));
   std::vector<size_t> fresh;  // fit tables to build
   for (size_t i = 0; i < b.fits_host.size(); ++i) {
     const uint64_t xm = b.fits_host[i].xmin;
@@ -411,8 +429,20 @@ pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t
     }
     fresh.push_back(i);
   }
-  PL_CUDA(cudaMemcpyAsync(b.fits_dev, b.fits_host.data(), sizeof(FitTable) * b.fits_host.size(),
-                          cudaMemcpyHostToDevice, st));
+  uint8_t *img = nullptr;
+  if (pl_status e = staging(ctx, b.host_bytes, &img)) return e;
+  const uint8_t *base = reinterpret_cast<const uint8_t *>(b.laws_dev);
+  auto put = [&](const void *dev, const void *src, size_t bytes) {
+    if (bytes) std::memcpy(img + (reinterpret_cast<const uint8_t *>(dev) - base), src, bytes);
+  };
+  put(b.laws_dev, b.laws_host.data(), sizeof(Law) * b.laws_host.size());
+  put(b.fits_dev, b.fits_host.data(), sizeof(FitTable) * b.fits_host.size());
+  put(b.cells, sp.cells.data(), sizeof(Cell) * sp.cells.size());
+  put(b.consts, sp.consts.data(), sizeof(CellConst) * sp.consts.size());
+  put(b.items, sp.items.data(), sizeof(WorkItem) * sp.items.size());
+  PL_CUDA(cudaMemcpyAsync(b.laws_dev, img, b.host_bytes, cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaEventRecord(ctx->staging_ev, st));
+  ctx->staged = true;
   PL_CUDA(launch_law_setup(b.laws_dev, (int)b.laws_host.size(), st));
   if (fresh.size() == b.fits_host.size()) {
     PL_CUDA(launch_fit_tables(b.fits_dev, (int)b.fits_host.size(), st));
@@ -601,6 +631,8 @@ void pl_destroy(pl_ctx *ctx) {
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
   for (auto &e : ctx->wave_ev) cudaEventDestroy(e);
+  if (ctx->staging_ev) cudaEventDestroy(ctx->staging_ev);
+  if (ctx->staging) cudaFreeHost(ctx->staging);
   for (void *m : ctx->fit_mem) cudaFree(m);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->ctr) cudaFree(ctx->ctr);
