@@ -429,6 +429,18 @@ pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t
     }
     fresh.push_back(i);
   }
+  // fresh fit tables read ln(xmin + i) from a law of the same xmin (filled by
+  // the law set-up, which runs first)
+  for (size_t i : fresh) {
+    b.fits_host[i].lnx = nullptr;
+    for (const Law &l : b.laws_host)
+      if (l.xmin == b.fits_host[i].xmin) {
+        b.fits_host[i].lnx = l.lnT;
+        break;
+      }
+    if (!b.fits_host[i].lnx) return fail(ctx, PL_ECUDA, "internal: no law for fit table xmin %llu",
+                                         (unsigned long long)b.fits_host[i].xmin);
+  }
   uint8_t *img = nullptr;
   if (pl_status e = staging(ctx, b.host_bytes, &img)) return e;
   const uint8_t *base = reinterpret_cast<const uint8_t *>(b.laws_dev);
@@ -444,10 +456,13 @@ pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t
   PL_CUDA(cudaEventRecord(ctx->staging_ev, st));
   ctx->staged = true;
   PL_CUDA(launch_law_setup(b.laws_dev, (int)b.laws_host.size(), st));
+  ctx->launches += b.laws_host.empty() ? 0 : 4;
   if (fresh.size() == b.fits_host.size()) {
     PL_CUDA(launch_fit_tables(b.fits_dev, (int)b.fits_host.size(), st));
+    ctx->launches += b.fits_host.empty() ? 0 : 3;
   } else {
     for (size_t i : fresh) PL_CUDA(launch_fit_tables(b.fits_dev + i, 1, st));
+    ctx->launches += 3 * fresh.size();
   }
   if (ctx->cache_fits && !fresh.empty()) {  // keep the completed tables (guide origin set on device)
     PL_CUDA(cudaMemcpyAsync(b.fits_host.data(), b.fits_dev, sizeof(FitTable) * b.fits_host.size(),
@@ -455,7 +470,6 @@ pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t
     PL_CUDA(cudaStreamSynchronize(st));
     for (size_t i : fresh) ctx->fit_cache[b.fits_host[i].xmin] = b.fits_host[i];
   }
-  ctx->launches += 5;
   return PL_OK;
 }
 
@@ -712,7 +726,7 @@ pl_status pl_sample(pl_ctx *ctx, double alpha, uint64_t xmin, uint64_t seed, uin
   ld = cv.take<Law>(1);
   PL_CUDA(cudaMemcpyAsync(ld, &lh, sizeof lh, cudaMemcpyHostToDevice, st));
   PL_CUDA(launch_law_setup(ld, 1, st));
-  ctx->launches += 4;
+  ctx->launches += 5;  // four law set-up kernels and the sampler
   PL_CUDA(launch_sample(ld, seed, (uint32_t)cell_id, purpose, (uint32_t)rep0, nrep, n, out_dev, ctx->ctr,
                         ctx->num_sms, st));
   return PL_OK;
@@ -746,7 +760,7 @@ pl_status run_dataset(pl_ctx *ctx, const int32_t *x, int64_t n, uint64_t xmin, b
   lay(cv, lh, ld, spill, pairs, out);
   PL_CUDA(cudaMemcpyAsync(ld, &lh, sizeof lh, cudaMemcpyHostToDevice, st));
   PL_CUDA(launch_law_setup(ld, 1, st));
-  ctx->launches += 4;
+  ctx->launches += 5;  // four law set-up kernels and the data-set kernel
   PL_CUDA(launch_dataset(x, n, xmin, fit, alpha, ld, cell_const(xmin), prec == PL_FP32_BULK, spill, pairs, out,
                          ctx->ctr, st));
   PL_CUDA(cudaMemcpyAsync(out_host, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));

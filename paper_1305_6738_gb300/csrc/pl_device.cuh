@@ -408,6 +408,7 @@ struct FitTable {
   double ug0, inv_dug;     // guide grid: bin b starts at ug0 + b / inv_dug
   FitNode *node;
   int *guide;
+  const double *lnx;       // ln(xmin + i), i < kLnTable: read while the table is built
 };
 constexpr int kFitNodes = 4096;
 constexpr int kFitGuides = 4096;

@@ -47,12 +47,18 @@ __global__ void law_z_kernel(Law *laws, int nlaws) {
 }
 
 // T[i] = floor(Q(xmin+i) 2^53) + 1 and the log tables of xmin + i.
+// Entries whose survival needs Euler-Maclaurin direct terms (argument below
+// 10 + 1.5 alpha, at most ~100 entries) are left to law_fill_em_kernel.
+__device__ __forceinline__ bool survival_needs_terms(const Law &law, uint32_t i) {
+  return (double)(law.xmin + i) + 1.0 < 10.0 + 1.5 * law.alpha;
+}
+
 __global__ void law_fill_kernel(Law *laws) {
   const Law law = laws[blockIdx.y];
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < law.L2 || i < (uint32_t)kLnTable;
        i += stride) {
-    if (i < law.L2) {
+    if (i < law.L2 && !survival_needs_terms(law, i)) {
       const double Q = survival(law.alpha, law.Z, law.xmin + i);
       law.T[i] = (uint64_t)(Q * 0x1p53) + 1ull;
     }
@@ -63,6 +69,27 @@ __global__ void law_fill_kernel(Law *laws) {
       law.lnT_hi[i] = hi;
       law.lnT_lo[i] = (float)(l - (double)hi);
     }
+  }
+}
+
+// The first thresholds (survival with direct terms): one warp per entry, the
+// lanes share the terms, a fixed-shape warp reduction adds them.
+constexpr int kFillEmWarps = 8;
+
+__global__ void __launch_bounds__(kFillEmWarps * 32) law_fill_em_kernel(Law *laws) {
+  const Law law = laws[blockIdx.y];
+  const uint32_t i = blockIdx.x * kFillEmWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= law.L2 || !survival_needs_terms(law, i)) return;  // warp-uniform
+  const double a = (double)(law.xmin + i) + 1.0;
+  const int M = em_shift(law.alpha, a);
+  double z = 0.0;
+  for (int k = lane; k < M; k += 32) z += pow(a + (double)k, -law.alpha);
+  z = warp_sum(z);
+  if (lane == 0) {
+    double t;
+    hurwitz_em_tail<0, true>(law.alpha, a + (double)M, &t);
+    law.T[i] = (uint64_t)((z + t) / law.Z * 0x1p53) + 1ull;
   }
 }
 
@@ -93,6 +120,8 @@ cudaError_t launch_law_setup(Law *laws_dev, int nlaws, cudaStream_t st) {
   if (nlaws <= 0) return cudaSuccess;
   law_z_kernel<<<(nlaws + 1) / 2, 64, 0, st>>>(laws_dev, nlaws);
   law_fill_kernel<<<dim3(256, nlaws), 256, 0, st>>>(laws_dev);
+  // entries with direct terms: xmin + i + 1 < 10 + 1.5 alpha, i < 105 for alpha <= 64
+  law_fill_em_kernel<<<dim3(128 / kFillEmWarps, nlaws), kFillEmWarps * 32, 0, st>>>(laws_dev);
   law_guide_kernel<<<dim3(kGuide / 256, nlaws), 256, 0, st>>>(laws_dev);
   return cudaGetLastError();
 }
@@ -209,25 +238,28 @@ __device__ int newton_mle(double mbar, uint64_t xmin, double ln_xmin_half, const
 
 // ---------------------------------------------------------------------------
 // Fit tables (one Euler-Maclaurin evaluation per node, pow-based).
-// One warp per node: the lanes share the Euler-Maclaurin direct terms (the
-// largest exponents need ~100 of them), a fixed-shape warp reduction adds
-// them, and lane 0 adds the tail and writes the node.
+// Fit-table nodes in two passes.  First one warp per node sums the
+// Euler-Maclaurin direct terms (the largest exponents need ~100 of them; the
+// lanes share them, a fixed-shape warp reduction adds them) into the node's
+// storage; then one thread per node adds the tail and forms the node, so the
+// binary64 tail work runs on full warps.
 constexpr int kFitNodeWarps = 8;
 
-__global__ void __launch_bounds__(kFitNodeWarps * 32) fit_nodes_kernel(FitTable *fts) {
+__device__ __forceinline__ double fit_node_alpha(const FitTable &ft, int k) {
+  const double t_hi = log(kFitAlphaHi - 1.0), t_lo = log(kFitAlphaLo - 1.0);
+  return 1.0 + exp(t_hi - (t_hi - t_lo) * (double)k / (double)(ft.nodes - 1));
+}
+
+__global__ void __launch_bounds__(kFitNodeWarps * 32) fit_sums_kernel(FitTable *fts) {
   const FitTable ft = fts[blockIdx.y];
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x * kFitNodeWarps + (threadIdx.x >> 5);
   if (k >= ft.nodes) return;  // warp-uniform
-  const double t_hi = log(kFitAlphaHi - 1.0), t_lo = log(kFitAlphaLo - 1.0);
-  const double t = t_hi - (t_hi - t_lo) * (double)k / (double)(ft.nodes - 1);
-  const double a = 1.0 + exp(t);
-  const double x0 = (double)ft.xmin;
-  const int M = em_shift(a, x0);
+  const double a = fit_node_alpha(ft, k);
+  const int M = em_shift(a, (double)ft.xmin);  // <= 100 < kLnTable
   double z0 = 0.0, z1 = 0.0, z2 = 0.0;
   for (int i = lane; i < M; i += 32) {
-    const double x = x0 + (double)i;
-    const double lx = log(x);
+    const double lx = ft.lnx[i];
     const double tt = exp(-a * lx);  // node accuracy needs ~1e-13, not pow's last bit
     z0 += tt;
     z1 -= lx * tt;
@@ -236,16 +268,29 @@ __global__ void __launch_bounds__(kFitNodeWarps * 32) fit_nodes_kernel(FitTable 
   z0 = warp_sum(z0);
   z1 = warp_sum(z1);
   z2 = warp_sum(z2);
-  if (lane != 0) return;
+  if (lane == 0) {  // partial sums parked in the node until the second pass
+    FitNode &nd = ft.node[k];
+    nd.u = z0;
+    nd.alpha = z1;
+    nd.dadu = z2;
+  }
+}
+
+__global__ void fit_nodes_kernel(FitTable *fts) {
+  const FitTable ft = fts[blockIdx.y];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ft.nodes) return;
+  const double a = fit_node_alpha(ft, k);
+  const double x0 = (double)ft.xmin;
+  FitNode &nd = ft.node[k];
   double z[3];
-  hurwitz_em_tail<2, true>(a, x0 + (double)M, z);
-  z[0] += z0;
-  z[1] += z1;
-  z[2] += z2;
+  hurwitz_em_tail<2, false>(a, x0 + (double)em_shift(a, x0), z);
+  z[0] += nd.u;
+  z[1] += nd.alpha;
+  z[2] += nd.dadu;
   const double g = z[1] / z[0];
   const double h = -g - log(x0);
   const double var = z[2] / z[0] - g * g;
-  FitNode &nd = ft.node[k];
   nd.u = log(h);
   nd.alpha = a;
   nd.dadu = -h / var;
@@ -279,8 +324,9 @@ __global__ void fit_guide_kernel(FitTable *fts) {
 
 cudaError_t launch_fit_tables(FitTable *fts_dev, int nfit, cudaStream_t st) {
   if (nfit <= 0) return cudaSuccess;
-  fit_nodes_kernel<<<dim3((kFitNodes + kFitNodeWarps - 1) / kFitNodeWarps, nfit), kFitNodeWarps * 32, 0, st>>>(
+  fit_sums_kernel<<<dim3((kFitNodes + kFitNodeWarps - 1) / kFitNodeWarps, nfit), kFitNodeWarps * 32, 0, st>>>(
       fts_dev);
+  fit_nodes_kernel<<<dim3((kFitNodes + 127) / 128, nfit), 128, 0, st>>>(fts_dev);
   const int n = kFitNodes > kFitGuides ? kFitNodes : kFitGuides;
   fit_guide_kernel<<<dim3((n + 127) / 128, nfit), 128, 0, st>>>(fts_dev);
   return cudaGetLastError();
