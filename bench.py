@@ -42,10 +42,10 @@ MUL_PER_DRAW = 10
 MUL_LANES_PER_SM = 32
 
 # DRAM bytes per replicate of the sampler from one ncu capture (sweep at 4,000
-# replicates per cell: 136.1 MB over 360,000 replicates), keyed by the hash of
+# replicates per cell: 136.6 MB over 360,000 replicates), keyed by the hash of
 # the kernel sources it was taken on (reported as null once they change).  The
 # bench scales it to a launch by the replicates one launch processes.
-TRAFFIC_PER_REPLICATE = {"2f92acd6a8e19566": 136.075776e6 / 360000}
+TRAFFIC_PER_REPLICATE = {"718eab3d07945042": 136.565248e6 / 360000}
 
 
 def kernel_source_hash() -> str:
