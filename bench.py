@@ -352,12 +352,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--replicates", type=int, default=100_000,
                     help="replicates per cell (smaller values for profiler captures only)")
-    ap.add_argument("--workload", choices=["sweep", "small", "large-n", "batched", "serving"],
+    ap.add_argument("--workload", choices=["sweep", "small", "large-n", "batched", "serving", "table1"],
                     default="sweep",
                     help="sweep: the 90-cell table (the benchmark line); small: alpha=2.5, n=100, "
                          "10,000 replicates; large-n: alpha=2, n=1e6, 10,000 replicates; batched: "
                          "4,096 uneven instances x 2,000 replicates in one graph-captured launch; "
-                         "serving: Poisson fit requests at 200/s through the serving engine")
+                         "serving: Poisson fit requests at 200/s through the serving engine; "
+                         "table1: one run of the paper's Table 1 (120 cells x 50,000 replicates)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: measured seconds")
     ap.add_argument("--serve-warmup", type=float, default=5.0, help="serving: warm-up seconds")
     ap.add_argument("--workers", type=int, default=8, help="serving: engine worker slots")
@@ -376,6 +377,10 @@ def main():
     elif args.workload == "small":
         sweep = inputs.cutoff_cell_small()
         wname = "single cell: alpha=2.5, xmin=1, n=100, 10,000 replicates"
+    elif args.workload == "table1":
+        sweep = inputs.table1_cells()
+        wname = ("Table 1 run: gamma in {1.25,...,4.0} (8) x N in {10,...,50000} (15), xmin=1, "
+                 "50,000 replicates per cell, quantiles 0.9/0.95/0.99/0.999")
     elif args.workload == "large-n":
         sweep = inputs.large_n_cell()
         wname = "large-n heavy tail: alpha=2.0, xmin=1, n=1,000,000, 10,000 replicates (block form)"
@@ -383,11 +388,12 @@ def main():
         sweep = inputs.batched_instances()
         wname = ("batched uneven: 4,096 instances, n log-uniform [10,1e5], alpha U(1.6,3.2), "
                  "xmin in {1,2,5}, 2,000 replicates each; one plan, graph-captured launch, autotuned split")
+    QS = list(inputs.TABLE1_QUANTILES) if args.workload == "table1" else Q
     total_R = sum(c.replicates for c in sweep)
     draws = sum(c.replicates * c.n for c in sweep)
     config = {"workload": wname,
               "cells": len(sweep), "replicates_per_step": total_R, "draws_per_step": draws,
-              "precision_form": args.precision, "seed": 1, "quantiles": Q,
+              "precision_form": args.precision, "seed": 1, "quantiles": QS,
               "l2": "256 MiB buffer written between timed steps (L2 flush)",
               "parallelism": f"replicas x{args.gpus}"}
     threads = os.cpu_count() or 1
@@ -431,7 +437,7 @@ def main():
     prec = pl.PL_FP32_BULK if args.precision == "fp32-bulk" else pl.PL_FP64
     seed = replica_seed(rank)
     cells = [pl.Cell(c.alpha, c.xmin, c.n, c.replicates, c.cell_id) for c in sweep]
-    cut = torch.empty(len(cells) * len(Q), dtype=torch.float64, device="cuda")
+    cut = torch.empty(len(cells) * len(QS), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -445,7 +451,7 @@ def main():
         # untimed set-up: autotuned warp/block split, plan (tables), graph capture
         t0 = time.perf_counter()
         split = ctx.pl_autotune()
-        plan = ctx.pl_plan_cutoffs(cells, Q, prec)
+        plan = ctx.pl_plan_cutoffs(cells, QS, prec)
         config["autotuned_split_n"] = split
         config["plan_ms"] = (time.perf_counter() - t0) * 1e3
         gstream = torch.cuda.Stream()
@@ -463,7 +469,7 @@ def main():
         if graph is not None:
             graph.replay()
         else:
-            ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=cut)
+            ctx.pl_ks_cutoffs(cells, seed, QS, prec, cutoffs=cut)
 
     ctx.pl_set_tracing(graph is None)
     for _ in range(args.warmup):
@@ -501,19 +507,19 @@ def main():
     # end to end through the public call with host buffers: host cell table in,
     # host cutoffs out (the call copies and synchronises), wall clock
     e2e_s = []
-    host_cut = np.zeros(len(cells) * len(Q))
+    host_cut = np.zeros(len(cells) * len(QS))
     for _ in range(max(2, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=host_cut)
+        ctx.pl_ks_cutoffs(cells, seed, QS, prec, cutoffs=host_cut)
         e2e_s.append(time.perf_counter() - t0)
     if graph is not None:  # trace one plain call for the per-kernel times
         ctx.pl_set_tracing(True)
-        ctx.pl_ks_cutoffs(cells, seed, Q, prec, cutoffs=cut)
+        ctx.pl_ks_cutoffs(cells, seed, QS, prec, cutoffs=cut)
         tr = ctx.pl_trace()
         kern_ms, fin_ms, waves = [tr["sample_ms"]], [tr["finish_ms"]], tr["waves"]
     e2e_value = job_rate(total_R, world, max_over_ranks(statistics.mean(e2e_s), dist, "cuda"))
-    h2d = len(cells) * 40 + len(Q) * 8
+    h2d = len(cells) * 40 + len(QS) * 8
     d2h = host_cut.nbytes
 
     # roofline of the sampler kernel (wide-multiply bound), from its CUDA-event

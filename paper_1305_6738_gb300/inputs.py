@@ -113,3 +113,18 @@ def as_request_data(values) -> np.ndarray:
     tail at exponents near 1.5, a few per million draws) are clamped to it."""
     v = np.asarray(values).view(np.uint64) if np.asarray(values).dtype == np.int64 else np.asarray(values)
     return np.minimum(v.astype(np.uint64), np.uint64(INT32_MAX)).astype(np.int32)
+
+
+# Table 1 of the paper: 8 exponents x 15 sample sizes, xmin = 1, 50,000
+# replicates per run, each cell the mean of 10 runs; quantiles 0.9 ... 0.999.
+TABLE1_GAMMAS = (1.25, 1.5, 1.75, 2.0, 2.5, 3.0, 3.5, 4.0)
+TABLE1_NS = (10, 20, 30, 40, 50, 100, 500, 1000, 2000, 3000, 4000, 5000, 10000, 20000, 50000)
+TABLE1_QUANTILES = (0.9, 0.95, 0.99, 0.999)
+TABLE1_RUNS = 10
+
+
+def table1_cells(replicates: int = 50_000) -> list[Cell]:
+    """One run of Table 1: every (gamma, N) cell; cell id = 100 * (gamma
+    index) + (N index).  Runs differ by seed (run r uses seed r + 1)."""
+    return [Cell(g, 1, n, replicates, 100 * i + j)
+            for i, g in enumerate(TABLE1_GAMMAS) for j, n in enumerate(TABLE1_NS)]
