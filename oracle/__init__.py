@@ -86,6 +86,18 @@ def _load():
         lib.or_bootstrap_pvalue.argtypes = [_i32p, c.c_int64, c.c_uint64, c.c_int64, c.c_uint64,
                                             c.c_uint32, c.c_int, _f64p, _f64p, _f64p, _f64p]
         lib.or_max_threads.restype = c.c_int
+        lib.or_tz_survival_table.restype = c.c_double
+        lib.or_tz_survival_table.argtypes = [c.c_double, c.c_int64, _f64p]
+        lib.or_tz_invert.restype = c.c_int64
+        lib.or_tz_invert.argtypes = [_f64p, c.c_int64, c.c_uint64]
+        lib.or_tz_sample.argtypes = [c.c_double, c.c_int64, c.c_uint64, c.c_uint32, c.c_uint32,
+                                     c.c_uint32, c.c_int64, _u64p]
+        lib.or_tz_mle_from_logsum.argtypes = [c.c_double, c.c_int64, c.c_int64, _f64p]
+        lib.or_tz_ks.argtypes = [_u64p, c.c_int64, c.c_int64, c.c_double, _f64p]
+        lib.or_tz_replicate.argtypes = [c.c_double, c.c_int64, c.c_int64, c.c_uint64, c.c_uint32,
+                                        c.c_uint32, c.c_uint32, _f64p, _f64p]
+        lib.or_tz_cell.argtypes = [c.c_double, c.c_int64, c.c_int64, c.c_uint64, c.c_uint32,
+                                   c.c_uint32, c.c_uint32, c.c_int64, c.c_int, _f64p, _f64p, _i64p]
         _lib = lib
         return lib
 
@@ -235,3 +247,52 @@ def bootstrap_pvalue(data: np.ndarray, xmin: int, B: int, seed: int, request_id:
 
 def max_threads() -> int:
     return int(_load().or_max_threads())
+
+
+# ---------------------------------------------------------------- truncated law
+def tz_survival(gamma: float, K: int):
+    """(Q[0..K], zeta_K): survival of the truncated law on 1..K."""
+    Q = np.zeros(K + 1)
+    z = _load().or_tz_survival_table(gamma, K, _ptr(Q, _f64p))
+    return Q, float(z)
+
+
+def tz_invert(Q: np.ndarray, K: int, m: int) -> int:
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    return int(_load().or_tz_invert(_ptr(Q, _f64p), K, m))
+
+
+def tz_sample(gamma: float, K: int, seed: int, cell: int, rep: int, purpose: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.uint64)
+    _load().or_tz_sample(gamma, K, seed, cell, rep, purpose, n, _ptr(out, _u64p))
+    return out
+
+
+def tz_mle(x: np.ndarray, K: int) -> float:
+    g = ctypes.c_double()
+    _check(_load().or_tz_mle_from_logsum(log_sum(x, 1), len(x), K, ctypes.byref(g)), "tz_mle")
+    return g.value
+
+
+def tz_mle_from_logsum(L: float, n: int, K: int) -> float:
+    g = ctypes.c_double()
+    _check(_load().or_tz_mle_from_logsum(L, n, K, ctypes.byref(g)), "tz_mle")
+    return g.value
+
+
+def tz_ks(x: np.ndarray, K: int, gamma: float) -> float:
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    d = ctypes.c_double()
+    _check(_load().or_tz_ks(_ptr(x, _u64p), x.size, K, gamma, ctypes.byref(d)), "tz_ks")
+    return d.value
+
+
+def tz_cell(gamma: float, K: int, n: int, R: int, seed: int, cell_id: int, purpose: int = 0,
+            rep0: int = 0, threads: int = 0):
+    """D and gamma-hat for replicates rep0..rep0+R-1 of one truncated cell."""
+    D = np.zeros(R)
+    A = np.zeros(R)
+    nc = ctypes.c_int64()
+    _check(_load().or_tz_cell(gamma, K, n, seed, cell_id, purpose, rep0, R, threads,
+                              _ptr(D, _f64p), _ptr(A, _f64p), ctypes.byref(nc)), "tz_cell")
+    return D, A, int(nc.value)

@@ -33,6 +33,10 @@
  *   or_quantile .......... pinned (integer index rule, Table 1 cells)
  *   or_bootstrap_pvalue .. pinned (uniformity of p under the null, power
  *                          against lognormal data)
+ *   or_tz_* (truncated) .. pinned (zeta_K closed forms and mpmath,
+ *                          linear-search inverse CDF, chi-square of draws,
+ *                          log-likelihood argmax, uniform data -> 0,
+ *                          D by definition, Tables 2-6 cells, K=20 atom)
  */
 #include <math.h>
 #include <stdint.h>
@@ -495,4 +499,168 @@ int or_max_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* ======================================================================== */
+/* Truncated Zipf law (Section 1's second version): support k = 1 .. K,
+ * p(k) = k^-gamma / zeta_K(gamma), zeta_K(gamma) = sum_{k=1}^{K} k^-gamma,
+ * any gamma > 0 (the MLE itself may fall anywhere on the real line).  The
+ * same method: inverse-CDF draws, the MLE of Eq. 2 with the finite scaling
+ * factor, and D of Eq. 3 against the fitted truncated law.
+ * Sums run from k = K down to the smallest index (small terms first).     */
+
+/* Survival Q(k) = P(X > k) = sum_{j=k+1}^{K} j^-gamma / zeta_K for k = 0..K
+ * into Q[0..K] (Q[0] = 1 up to rounding, Q[K] = 0); returns zeta_K. */
+double or_tz_survival_table(double gamma, int64_t K, double *Q) {
+  double s = 0.0;
+  Q[K] = 0.0;
+  for (int64_t k = K; k >= 1; --k) {
+    s += pow((double)k, -gamma);
+    Q[k - 1] = s;
+  }
+  for (int64_t k = 0; k < K; ++k) Q[k] /= s;
+  return s;
+}
+
+/* Inverse CDF on the finite support: X = min{k in 1..K : Q(k) < v},
+ * v = m 2^-53, by bisection on the table (Q(K) = 0 < v always). */
+int64_t or_tz_invert(const double *Q, int64_t K, uint64_t m) {
+  const double v = ldexp((double)m, -53);
+  int64_t lo = 1, hi = K; /* answer in [lo, hi] */
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (Q[mid] < v)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+void or_tz_sample(double gamma, int64_t K, uint64_t seed, uint32_t cell, uint32_t rep,
+                  uint32_t purpose, int64_t n, uint64_t *out) {
+  double *Q = (double *)malloc((size_t)(K + 1) * sizeof(double));
+  if (!Q) return;
+  or_tz_survival_table(gamma, K, Q);
+  for (int64_t i = 0; i < n; ++i) out[i] = (uint64_t)or_tz_invert(Q, K, or_draw_m(seed, cell, rep, purpose, (uint64_t)i));
+  free(Q);
+}
+
+/* zeta_K and its first two gamma-derivatives: sums of k^-g, -ln k k^-g,
+ * ln^2 k k^-g (small terms first). */
+static void or_tz_sums(double g, int64_t K, double z[3]) {
+  double z0 = 0.0, z1 = 0.0, z2 = 0.0;
+  for (int64_t k = K; k >= 1; --k) {
+    double l = log((double)k), t = pow((double)k, -g);
+    z0 += t;
+    z1 -= l * t;
+    z2 += l * l * t;
+  }
+  z[0] = z0;
+  z[1] = z1;
+  z[2] = z2;
+}
+
+/* MLE (Eq. 2 with the finite scaling factor): the root of
+ * h(g) = zeta_K'(g)/zeta_K(g) + mbar, decreasing in g (h' = Var(ln X) > 0
+ * with the sign convention z1 = zeta_K'), i.e. E_g[ln X] = mbar.  The root
+ * exists for 0 < mbar < ln K; it is searched on [-64, 64] by
+ * bisection-safeguarded Newton from g = 1 and clamped to that interval
+ * (reading: the paper states gamma > 0 for the law; the estimate is the
+ * unconstrained root, bounded for the rare samples whose mean log reaches
+ * an end of the range).  The all-equal rule as in the untruncated case: a
+ * sample of only ones gets ln 2 added to its log-sum.                      */
+int or_tz_mle_from_logsum(double L, int64_t n, int64_t K, double *gamma_hat) {
+  if (n < 1 || K < 2) return OR_EINVAL;
+  const double mbar = L / (double)n;
+  double lo = -64.0, hi = 64.0, g = 1.0;
+  for (int it = 1; it <= 400; ++it) {
+    double z[3];
+    or_tz_sums(g, K, z);
+    double e = -z[1] / z[0];                  /* E_g[ln X] */
+    double var = z[2] / z[0] - e * e;         /* Var_g[ln X] */
+    double f = e - mbar;                      /* decreasing in g */
+    if (f > 0.0)
+      lo = g;
+    else
+      hi = g;
+    double next = g + f / var;
+    if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+    double step = fabs(next - g);
+    g = next;
+    double tol = 4.0 * ldexp(1.0, ilogb(fabs(g) > 1.0 ? g : 1.0) - 52);
+    if (step <= tol || hi - lo <= tol) {
+      *gamma_hat = g;
+      return OR_OK;
+    }
+  }
+  *gamma_hat = g;
+  return OR_ENOCONV;
+}
+
+/* D (Eq. 3) against the truncated law at gamma: every t in 1..K. */
+int or_tz_ks(const uint64_t *x, int64_t n, int64_t K, double gamma, double *D) {
+  if (n < 1 || K < 2) return OR_EINVAL;
+  double *Q = (double *)malloc((size_t)(K + 1) * sizeof(double));
+  int64_t *cnt = (int64_t *)calloc((size_t)(K + 1), sizeof(int64_t));
+  if (!Q || !cnt) {
+    free(Q);
+    free(cnt);
+    return OR_ENOMEM;
+  }
+  or_tz_survival_table(gamma, K, Q);
+  for (int64_t i = 0; i < n; ++i) {
+    if (x[i] < 1 || (int64_t)x[i] > K) {
+      free(Q);
+      free(cnt);
+      return OR_EINVAL;
+    }
+    cnt[x[i]] += 1;
+  }
+  double best = 0.0;
+  int64_t below = 0;
+  for (int64_t t = 1; t <= K; ++t) {
+    below += cnt[t];
+    double d = fabs((1.0 - Q[t]) - (double)below / (double)n);
+    if (d > best) best = d;
+  }
+  free(Q);
+  free(cnt);
+  *D = best;
+  return OR_OK;
+}
+
+int or_tz_replicate(double gamma, int64_t K, int64_t n, uint64_t seed, uint32_t cell, uint32_t rep,
+                    uint32_t purpose, double *gamma_hat, double *D) {
+  uint64_t *x = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+  if (!x) return OR_ENOMEM;
+  or_tz_sample(gamma, K, seed, cell, rep, purpose, n, x);
+  int st = or_tz_mle_from_logsum(or_log_sum(x, n, 1), n, K, gamma_hat);
+  if (st == OR_OK || st == OR_ENOCONV) {
+    int st2 = or_tz_ks(x, n, K, *gamma_hat, D);
+    if (st2 != OR_OK) st = st2;
+  }
+  free(x);
+  return st;
+}
+
+int or_tz_cell(double gamma, int64_t K, int64_t n, uint64_t seed, uint32_t cell, uint32_t purpose,
+               uint32_t rep0, int64_t R, int nthreads, double *D, double *gamma_hat, int64_t *nonconv) {
+  if (n < 1 || R < 1 || K < 2 || !(gamma > 0.0)) return OR_EINVAL;
+  int64_t bad = 0, fails = 0;
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : bad, fails)
+#endif
+  for (int64_t r = 0; r < R; ++r) {
+    double gh = 0.0, d = 0.0;
+    int st = or_tz_replicate(gamma, K, n, seed, cell, rep0 + (uint32_t)r, purpose, &gh, &d);
+    if (st == OR_ENOCONV) bad += 1;
+    else if (st != OR_OK) fails += 1;
+    D[r] = d;
+    if (gamma_hat) gamma_hat[r] = gh;
+  }
+  if (nonconv) *nonconv = bad;
+  (void)nthreads;
+  return fails ? OR_ENOMEM : OR_OK;
 }
