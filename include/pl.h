@@ -266,6 +266,49 @@ pl_status pl_server_load(pl_server *srv, int *queued, int *running,
                          size_t *reserved_bytes, uint64_t *launches);
 void pl_server_destroy(pl_server *srv);
 
+/* Truncated law (Section 1's second version of the power law; the cutoffs
+ * of Tables 2-6): support k = 1..K,
+ *     p(k) = k^-gamma / zeta_K(gamma),  zeta_K(gamma) = sum_{k=1}^{K} k^-gamma,
+ * with 0 < gamma <= 64 and 2 <= K <= 1024.  The method is the untruncated
+ * one with the finite scaling factor: inverse-CDF draws
+ * X = min{k in 1..K : P(X > k) < v} (v = m 2^-53, the same Philox streams),
+ * the MLE of Eq. 2 (the root of E_g[ln X] = mean of ln x, searched on the
+ * whole real line and bounded to [-64, 64]; a sample of only ones counts one
+ * point as 2, as in the untruncated case), and D of Eq. 3 over every
+ * t = 1..K.  The form of Eq. 2 is the same in both precision forms; in
+ * PL_FP32_BULK the CDF prefix sums and D comparisons are binary32 with
+ * compensated accumulation. */
+typedef struct {
+  double gamma;
+  uint64_t K;
+  int64_t n;
+  int64_t replicates;
+  uint64_t cell_id;
+} pl_tcell;
+
+/* Draws from the truncated law, nrep rows of n (row r = replicate rep0 + r)
+ * at out_dev[r * n]; out_dev: device, uint64[nrep * n].  Errors: PL_EINVAL
+ * (gamma outside (0, 64], K outside [2, 1024], n < 1, n > 2^33, nrep < 1,
+ * cell_id >= 2^32, rep0 + nrep > 2^32). */
+pl_status pl_sample_truncated(pl_ctx *ctx, double gamma, uint64_t K,
+                              uint64_t seed, uint64_t cell_id,
+                              uint32_t purpose, uint64_t rep0, int64_t nrep,
+                              int64_t n, uint64_t *out_dev, void *stream);
+
+/* Cutoff tables of the truncated law (Tables 2-6): as pl_ks_cutoffs, for
+ * pl_tcell cells (1 <= n <= 65535).  gamma_hat_dev_opt: NULL or device
+ * double, per-replicate fitted exponents (cells concatenated); D_dev_opt:
+ * NULL or device, per-replicate D (double for PL_FP64, float for
+ * PL_FP32_BULK).  Fits whose Newton solve hits its cap are counted in
+ * newton_capped.  Errors: PL_EINVAL (ncells < 1, nq < 1, q outside (0, 1),
+ * a cell outside the ranges above, replicates outside [1, 2^32],
+ * cell_id >= 2^32), PL_ENOMEM. */
+pl_status pl_ks_cutoffs_truncated(pl_ctx *ctx, const pl_tcell *cells,
+                                  int ncells, uint64_t seed, const double *q,
+                                  int nq, pl_precision prec, double *cutoffs,
+                                  void *D_dev_opt, double *gamma_hat_dev_opt,
+                                  void *stream);
+
 /* Fit and KS distance of one data set with no device allocation at all.
  * The paper has no counterpart: this is an engineering variant of
  * pl_fit_mle + pl_ks_stat for callers that cannot let a library call

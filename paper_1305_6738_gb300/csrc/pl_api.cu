@@ -18,6 +18,7 @@
 
 #include "pl.h"
 #include "pl_kernels.cuh"
+#include "pl_truncated.cuh"
 
 using namespace pl;
 
@@ -729,6 +730,249 @@ pl_status pl_sample(pl_ctx *ctx, double alpha, uint64_t xmin, uint64_t seed, uin
   ctx->launches += 5;  // four law set-up kernels and the sampler
   PL_CUDA(launch_sample(ld, seed, (uint32_t)cell_id, purpose, (uint32_t)rep0, nrep, n, out_dev, ctx->ctr,
                         ctx->num_sms, st));
+  return PL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Truncated law on 1..K (Tables 2-6).
+namespace {
+
+struct TzPlan {
+  std::vector<TzCell> cells;
+  std::vector<TzLaw> laws;      // one per distinct (gamma, K)
+  std::vector<TzTable> tables;  // one per distinct K
+  std::vector<TzItem> items;
+  int64_t total_R = 0;
+};
+
+struct TzBuffers {
+  TzLaw *laws = nullptr;
+  TzTable *tables = nullptr;
+  TzCell *cells = nullptr;
+  TzItem *items = nullptr;
+  size_t host_bytes = 0;  // laws .. items, written from the host in one copy
+};
+
+pl_status tz_check_law(pl_ctx *ctx, double gamma, uint64_t K) {
+  if (!(gamma > 0.0 && gamma <= 64.0)) return fail(ctx, PL_EINVAL, "truncated law: gamma must be in (0, 64]");
+  if (K < 2 || K > kTzKMax) return fail(ctx, PL_EINVAL, "truncated law: K must be in [2, %u]", kTzKMax);
+  return PL_OK;
+}
+
+uint32_t tz_law_index(TzPlan &tp, double gamma, uint32_t K, std::map<std::pair<double, uint32_t>, uint32_t> &ids) {
+  auto key = std::make_pair(gamma, K);
+  auto it = ids.find(key);
+  if (it != ids.end()) return it->second;
+  uint32_t tab = 0;
+  while (tab < tp.tables.size() && tp.tables[tab].K != K) ++tab;
+  if (tab == tp.tables.size()) {
+    TzTable t{};
+    t.K = K;
+    t.lnK = std::log((double)K);
+    tp.tables.push_back(t);
+  }
+  TzLaw l{};
+  l.gamma = gamma;
+  l.K = K;
+  l.table = tab;
+  tp.laws.push_back(l);
+  ids[key] = (uint32_t)tp.laws.size() - 1;
+  return (uint32_t)tp.laws.size() - 1;
+}
+
+// Cells, laws, tables and work items.  A work item is a block of kTzWarps
+// warps, each taking a run of replicates of one cell; runs are sized by a
+// replicate's cost (draws, support points and the fit) so that items of
+// different cells cost about the same, and shrink when the call is too small
+// to give every SM four items.  Costlier cells' items come first.
+pl_status tz_plan(pl_ctx *ctx, const pl_tcell *in, int ncells, uint32_t purpose, TzPlan &tp) {
+  std::map<std::pair<double, uint32_t>, uint32_t> ids;
+  std::vector<double> cost(ncells);
+  double work = 0.0;
+  for (int i = 0; i < ncells; ++i) {
+    const pl_tcell &c = in[i];
+    if (pl_status s = tz_check_law(ctx, c.gamma, c.K)) return s;
+    if (c.n < 1 || c.n > kTzNMax || c.replicates < 1 || c.replicates > (1ll << 32) || c.cell_id >= (1ull << 32))
+      return fail(ctx, PL_EINVAL, "truncated cell %d: n must be in [1, %lld], replicates in [1, 2^32], cell_id < 2^32",
+                  i, (long long)kTzNMax);
+    TzCell tc{};
+    tc.gamma = c.gamma;
+    tc.n = c.n;
+    tc.R = c.replicates;
+    tc.out_off = tp.total_R;
+    tc.cell_id = (uint32_t)c.cell_id;
+    tc.law = tz_law_index(tp, c.gamma, (uint32_t)c.K, ids);
+    tc.purpose = purpose;
+    tp.cells.push_back(tc);
+    tp.total_R += c.replicates;
+    cost[i] = (double)c.n + 16.0 * (double)c.K + 1024.0;
+    work += cost[i] * (double)c.replicates;
+  }
+  std::vector<int> order(ncells);
+  for (int i = 0; i < ncells; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  int64_t cap = 64;  // replicates per warp, at most
+  const int64_t want = 4 * (int64_t)ctx->num_sms;
+  while (cap > 1 && work / (32768.0 * kTzWarps) < (double)want) cap >>= 1;
+  for (int i : order) {
+    const TzCell &c = tp.cells[i];
+    const int64_t rpw = std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)(32768.0 / cost[i])));
+    const int64_t per = rpw * kTzWarps;
+    for (int64_t r0 = 0; r0 < c.R; r0 += per)
+      tp.items.push_back({(uint32_t)i, (uint32_t)r0, (uint32_t)std::min<int64_t>(per, c.R - r0), 0u});
+  }
+  if (tp.items.size() > 0x7fffffffull) return fail(ctx, PL_ENOMEM, "truncated cutoffs: too many work items");
+  return PL_OK;
+}
+
+void carve_tz(Carver &cv, TzPlan &tp, TzBuffers &b) {
+  b.laws = cv.take<TzLaw>(tp.laws.size());
+  b.tables = cv.take<TzTable>(tp.tables.size());
+  b.cells = cv.take<TzCell>(tp.cells.size());
+  b.items = cv.take<TzItem>(tp.items.size());
+  b.host_bytes = (size_t)(reinterpret_cast<uint8_t *>(b.items + tp.items.size()) - reinterpret_cast<uint8_t *>(b.laws));
+  for (TzLaw &l : tp.laws) {
+    l.T = cv.take<uint64_t>(l.K + 1);
+    l.guide = cv.take<uint16_t>(kTzGuide);
+  }
+  for (TzTable &t : tp.tables) {
+    t.lnk = cv.take<double>(t.K + 1);
+    t.lnk_hi = cv.take<float>(t.K + 1);
+    t.lnk_lo = cv.take<float>(t.K + 1);
+    t.lnq_hi = cv.take<float>(t.K + 1);
+    t.lnq_lo = cv.take<float>(t.K + 1);
+    t.node = cv.take<double>((size_t)kTzNodes * kTzNodeStride);
+    t.E = cv.take<double>(kTzNodes);
+  }
+}
+
+// Stage the host-written structures in one copy, then build the laws' and
+// tables' contents on the device.
+pl_status upload_tz(pl_ctx *ctx, const TzPlan &tp, const TzBuffers &b, cudaStream_t st) {
+  uint8_t *img = nullptr;
+  if (pl_status e = staging(ctx, b.host_bytes, &img)) return e;
+  const uint8_t *base = reinterpret_cast<const uint8_t *>(b.laws);
+  auto put = [&](const void *dev, const void *src, size_t bytes) {
+    if (bytes) std::memcpy(img + (reinterpret_cast<const uint8_t *>(dev) - base), src, bytes);
+  };
+  put(b.laws, tp.laws.data(), sizeof(TzLaw) * tp.laws.size());
+  put(b.tables, tp.tables.data(), sizeof(TzTable) * tp.tables.size());
+  put(b.cells, tp.cells.data(), sizeof(TzCell) * tp.cells.size());
+  put(b.items, tp.items.data(), sizeof(TzItem) * tp.items.size());
+  PL_CUDA(cudaMemcpyAsync(b.laws, img, b.host_bytes, cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaEventRecord(ctx->staging_ev, st));
+  ctx->staged = true;
+  PL_CUDA(launch_tz_setup(b.laws, (int)tp.laws.size(), b.tables, (int)tp.tables.size(), st));
+  ctx->launches += 3;
+  return PL_OK;
+}
+
+}  // namespace
+
+pl_status pl_sample_truncated(pl_ctx *ctx, double gamma, uint64_t K, uint64_t seed, uint64_t cell_id,
+                              uint32_t purpose, uint64_t rep0, int64_t nrep, int64_t n, uint64_t *out_dev,
+                              void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (pl_status s = tz_check_law(ctx, gamma, K)) return s;
+  if (n < 1 || nrep < 1 || cell_id >= (1ull << 32) || rep0 + (uint64_t)nrep > (1ull << 32) || n > (1ll << 33) ||
+      !out_dev)
+    return fail(ctx, PL_EINVAL, "pl_sample_truncated: argument out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  TzLaw lh{};
+  lh.gamma = gamma;
+  lh.K = (uint32_t)K;
+  auto lay = [&](Carver &cv, TzLaw *&ld) {
+    ld = cv.take<TzLaw>(1);
+    lh.T = cv.take<uint64_t>(K + 1);
+    lh.guide = cv.take<uint16_t>(kTzGuide);
+  };
+  Carver cv;
+  TzLaw *ld = nullptr;
+  lay(cv, ld);
+  if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+  cv.base = ctx->ws;
+  cv.off = 0;
+  lay(cv, ld);
+  PL_CUDA(cudaMemcpyAsync(ld, &lh, sizeof lh, cudaMemcpyHostToDevice, st));
+  PL_CUDA(launch_tz_setup(ld, 1, nullptr, 0, st));
+  PL_CUDA(launch_tz_sample(ld, seed, (uint32_t)cell_id, purpose, (uint32_t)rep0, nrep, n, out_dev, st));
+  ctx->launches += 2;
+  return PL_OK;
+}
+
+pl_status pl_ks_cutoffs_truncated(pl_ctx *ctx, const pl_tcell *cells, int ncells, uint64_t seed, const double *q,
+                                  int nq, pl_precision prec, double *cutoffs, void *D_dev_opt,
+                                  double *gamma_hat_dev_opt, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!cells || ncells < 1 || !q || nq < 1 || !cutoffs)
+    return fail(ctx, PL_EINVAL, "pl_ks_cutoffs_truncated: bad arguments");
+  if (prec != PL_FP64 && prec != PL_FP32_BULK) return fail(ctx, PL_EINVAL, "unknown precision form");
+  for (int j = 0; j < nq; ++j)
+    if (!(q[j] > 0.0 && q[j] < 1.0)) return fail(ctx, PL_EINVAL, "quantile %d outside (0, 1)", j);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f32 = prec == PL_FP32_BULK;
+  TzPlan tp;
+  if (pl_status s = tz_plan(ctx, cells, ncells, 0u, tp)) return s;
+  const bool host_out = !is_device_ptr(cutoffs);
+  const size_t dsz = f32 ? 4 : 8;
+  TzBuffers b;
+  void *D = nullptr;
+  int64_t *off = nullptr, *Rs = nullptr, *rank = nullptr;
+  double *cut = nullptr;
+  auto lay = [&](Carver &cv) {
+    carve_tz(cv, tp, b);
+    D = D_dev_opt ? D_dev_opt : (void *)cv.take<uint8_t>((size_t)tp.total_R * dsz);
+    off = cv.take<int64_t>(ncells);
+    Rs = cv.take<int64_t>(ncells);
+    rank = cv.take<int64_t>((size_t)ncells * nq);
+    cut = host_out ? cv.take<double>((size_t)ncells * nq) : cutoffs;
+  };
+  Carver cv;
+  lay(cv);
+  if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+  cv.base = ctx->ws;
+  cv.off = 0;
+  lay(cv);
+  if (pl_status s = mark(ctx, 0, st)) return s;
+  if (pl_status s = upload_tz(ctx, tp, b, st)) return s;
+  std::vector<int64_t> h_off(ncells), h_R(ncells), h_rank((size_t)ncells * nq);
+  for (int c = 0; c < ncells; ++c) {
+    h_off[c] = tp.cells[c].out_off;
+    h_R[c] = tp.cells[c].R;
+    for (int j = 0; j < nq; ++j) {
+      int64_t i = (int64_t)std::floor((double)h_R[c] * q[j]);
+      h_rank[(size_t)c * nq + j] = std::min(std::max<int64_t>(i, 0), h_R[c] - 1);
+    }
+  }
+  PL_CUDA(cudaMemcpyAsync(off, h_off.data(), sizeof(int64_t) * ncells, cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(Rs, h_R.data(), sizeof(int64_t) * ncells, cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(rank, h_rank.data(), sizeof(int64_t) * h_rank.size(), cudaMemcpyHostToDevice, st));
+  if (pl_status s = mark(ctx, 1, st)) return s;
+  TzLaunch tl{};
+  tl.cells = b.cells;
+  tl.laws = b.laws;
+  tl.tables = b.tables;
+  tl.items = b.items;
+  tl.nitems = (uint32_t)tp.items.size();
+  tl.rk = round_keys(seed);
+  tl.D_out = D;
+  tl.A_out = gamma_hat_dev_opt;
+  tl.ctr = ctx->ctr;
+  PL_CUDA(launch_tz_replicates(tl, f32, st));
+  ctx->launches += 1;
+  if (ctx->tracing) {
+    ctx->traced_waves = 0;
+    ctx->traced_draws = 0;
+    for (const TzCell &c : tp.cells) ctx->traced_draws += (uint64_t)c.n * (uint64_t)c.R;
+  }
+  if (pl_status s = mark(ctx, 2, st)) return s;
+  PL_CUDA(launch_select(D, f32, off, Rs, rank, ncells, nq, cut, st));
+  ctx->launches += 1;
+  if (pl_status s = mark(ctx, 3, st)) return s;
+  if (host_out) {
+    PL_CUDA(cudaMemcpyAsync(cutoffs, cut, sizeof(double) * ncells * nq, cudaMemcpyDeviceToHost, st));
+    return read_status(ctx, st);
+  }
   return PL_OK;
 }
 

@@ -30,11 +30,17 @@ EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters",
            "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue", "pl_fit_ks_noalloc", "pl_plan_cutoffs", "pl_plan_run",
            "pl_plan_destroy", "pl_autotune", "pl_set_split", "pl_server_create", "pl_server_submit",
-           "pl_server_poll", "pl_server_now", "pl_server_load", "pl_server_destroy"]
+           "pl_server_poll", "pl_server_now", "pl_server_load", "pl_server_destroy",
+           "pl_sample_truncated", "pl_ks_cutoffs_truncated"]
 
 
 class pl_cell(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("xmin", ctypes.c_uint64), ("n", ctypes.c_int64),
+                ("replicates", ctypes.c_int64), ("cell_id", ctypes.c_uint64)]
+
+
+class pl_tcell(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("K", ctypes.c_uint64), ("n", ctypes.c_int64),
                 ("replicates", ctypes.c_int64), ("cell_id", ctypes.c_uint64)]
 
 
@@ -101,8 +107,12 @@ _lib.pl_server_now.restype = ctypes.c_double
 _lib.pl_server_load.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_size_t), _u64p]
 _lib.pl_server_destroy.argtypes = [_vp]
+_lib.pl_sample_truncated.argtypes = [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, _vp, _vp]
+_lib.pl_ks_cutoffs_truncated.argtypes = [_vp, ctypes.POINTER(pl_tcell), ctypes.c_int, ctypes.c_uint64, _f64p,
+                                         ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
 _lib.pl_server_destroy.restype = None
-for _f in ["pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+for _f in ["pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -135,6 +145,16 @@ def _ptr(t) -> int:
 class Cell:
     alpha: float
     xmin: int
+    n: int
+    replicates: int
+    cell_id: int
+
+
+@dataclass
+class TCell:
+    """A cell of the truncated law on 1..K (Tables 2-6)."""
+    gamma: float
+    K: int
     n: int
     replicates: int
     cell_id: int
@@ -223,6 +243,35 @@ class Context:
         self._check(_lib.pl_ks_cutoffs(self._h, arr, len(cells), seed,
                                        qa.ctypes.data_as(_f64p), qa.size, prec, out_ptr, _ptr(D),
                                        _ptr(alpha_hat), _stream_ptr(stream)))
+        if host is not None:
+            return host.reshape(len(cells), qa.size)
+        return cutoffs
+
+    def pl_sample_truncated(self, gamma: float, K: int, seed: int, cell_id: int, purpose: int, rep0: int,
+                            nrep: int, n: int, out, stream=None):
+        """out: 8-byte device tensor of nrep*n elements (values 1..K)."""
+        assert out.numel() >= nrep * n and out.element_size() == 8
+        self._check(_lib.pl_sample_truncated(self._h, gamma, K, seed, cell_id, purpose, rep0, nrep, n,
+                                             _ptr(out), _stream_ptr(stream)))
+
+    def pl_ks_cutoffs_truncated(self, cells, seed: int, q, prec: int = PL_FP64, cutoffs=None, D=None,
+                                gamma_hat=None, stream=None):
+        """As pl_ks_cutoffs for TCell cells; gamma_hat receives the per-replicate fits."""
+        arr = (pl_tcell * len(cells))(*[pl_tcell(c.gamma, c.K, c.n, c.replicates, c.cell_id)
+                                        for c in cells])
+        qa = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        host = None
+        if cutoffs is None:
+            host = np.zeros(len(cells) * qa.size)
+            out_ptr = host.ctypes.data
+        elif isinstance(cutoffs, np.ndarray):
+            host = cutoffs
+            out_ptr = cutoffs.ctypes.data
+        else:
+            out_ptr = _ptr(cutoffs)
+        self._check(_lib.pl_ks_cutoffs_truncated(self._h, arr, len(cells), seed,
+                                                 qa.ctypes.data_as(_f64p), qa.size, prec, out_ptr, _ptr(D),
+                                                 _ptr(gamma_hat), _stream_ptr(stream)))
         if host is not None:
             return host.reshape(len(cells), qa.size)
         return cutoffs
