@@ -319,6 +319,173 @@ def run_serving(args):
 
 
 # ----------------------------------------------------------------------------- replicas
+# ----------------------------------------------------------------------------- truncated law
+TZ_WORKLOAD = ("Tables 2-6 run: truncated law on 1..K, K in {20,50,100,500,1000} x gamma in "
+               "{0.25,...,4.0} (12) x N in {10,...,50000} (15), {R:,} replicates per cell, "
+               "quantiles 0.9/0.95/0.99/0.999")
+
+
+def tz_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ["pl_device.cuh", "pl_truncated.cuh", "pl_truncated.cu"]:
+        with open(os.path.join(ROOT, "paper_1305_6738_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes per replicate of the truncated replicate kernel from one ncu
+# capture, keyed by the hash of its sources (null once they change).
+TZ_TRAFFIC_PER_REPLICATE: dict = {}
+
+
+def tz_cpu_oracle_rate(cells, sample_reps: int, threads: int) -> dict:
+    """The oracle as it stands on sample_reps replicates of every truncated
+    cell, timed per cell and extrapolated linearly to the full replicate count."""
+    import oracle
+    oracle.build()
+    t_full = wall = 0.0
+    for c in cells:
+        t0 = time.perf_counter()
+        oracle.tz_cell(c.gamma, c.K, c.n, sample_reps, seed=1, cell_id=c.cell_id, threads=threads)
+        dt = time.perf_counter() - t0
+        wall += dt
+        t_full += dt / sample_reps * c.replicates
+    total_R = sum(c.replicates for c in cells)
+    draws = sum(c.replicates * c.n for c in cells)
+    return {"value": total_R / t_full, "samples_per_s": draws / t_full, "wall_s": wall,
+            "sample": f"{sample_reps} replicates of each of the {len(cells)} cells (draws, fit, KS, seed 1), "
+                      f"timed per cell and extrapolated linearly to {cells[0].replicates:,} replicates per cell"}
+
+
+def run_truncated(args):
+    """One run of Tables 2-6 per step through pl_ks_cutoffs_truncated."""
+    tcells = inputs.tables2to6_cells(args.tz_replicates)
+    QS = list(inputs.TZ_QUANTILES)
+    total_R = sum(c.replicates for c in tcells)
+    draws = sum(c.replicates * c.n for c in tcells)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    config = {"workload": TZ_WORKLOAD.replace("{R:,}", f"{args.tz_replicates:,}"), "cells": len(tcells), "replicates_per_step": total_R,
+              "draws_per_step": draws, "precision_form": args.precision, "seed": 1, "quantiles": QS,
+              "l2": "256 MiB buffer written between timed steps (L2 flush)",
+              "parallelism": f"replicas x{args.gpus}"}
+    threads = os.cpu_count() or 1
+    samp = max(1, threads)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        tz_cpu_oracle_rate(tcells[:15], 1, threads)
+        vals = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            vals.append(tz_cpu_oracle_rate(tcells, samp, threads))
+        wall = time.perf_counter() - t0
+        value = statistics.mean(v["value"] for v in vals)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "replicates/s",
+                "samples_per_s": statistics.mean(v["samples_per_s"] for v in vals), "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_R / value,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (Philox streams, seed 1)", "config": config,
+                "cpu_baseline": {"value": value, "unit": "replicates/s", "cores": threads, "kind": "oracle",
+                                 "sample": vals[0]["sample"]},
+                "e2e": {"value": value, "unit": "replicates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "wall_s": wall}
+        print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1305_6738_gb300 import pl
+    ctx = pl.Context(local)
+    prec = pl.PL_FP32_BULK if args.precision == "fp32-bulk" else pl.PL_FP64
+    seed = replica_seed(rank)
+    cells = [pl.TCell(c.gamma, c.K, c.n, c.replicates, c.cell_id) for c in tcells]
+    cut = torch.empty(len(cells) * len(QS), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step():
+        ctx.pl_ks_cutoffs_truncated(cells, seed, QS, prec, cutoffs=cut)
+
+    ctx.pl_set_tracing(True)
+    for _ in range(args.warmup):
+        step()
+    ctx.pl_sync()
+    launches0 = ctx.pl_trace()["launches"]
+    sampler = ClockSampler(gpu_query_id(local))
+    barrier()
+    step_ms, kern_ms, law_ms = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        tr = ctx.pl_trace()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(tr["replicate_ms"])
+        law_ms.append(tr["law_ms"])
+    barrier()
+    clocks = sampler.stop()
+    launches = ctx.pl_trace()["launches"] - launches0
+    ctx.pl_sync()
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
+    value = job_rate(total_R * args.steps, world, total_ms / 1000.0)
+    sps = job_rate(draws * args.steps, world, total_ms / 1000.0)
+    e2e_s = []
+    host_cut = np.zeros(len(cells) * len(QS))
+    for _ in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.pl_ks_cutoffs_truncated(cells, seed, QS, prec, cutoffs=host_cut)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_value = job_rate(total_R, world, max_over_ranks(statistics.mean(e2e_s), dist, "cuda"))
+    props = torch.cuda.get_device_properties(local)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    mul_peak = props.multi_processor_count * MUL_LANES_PER_SM * sm_max * 1e6 / 1e9
+    kmean = statistics.mean(kern_ms)
+    achieved = MUL_PER_DRAW * draws / (kmean / 1000.0) / 1e9
+    h = tz_source_hash()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": mul_peak, "unit": "Gmul/s (32x32->64)",
+                "frac": achieved / mul_peak,
+                "traffic": (TZ_TRAFFIC_PER_REPLICATE[h] * total_R if h in TZ_TRAFFIC_PER_REPLICATE else None),
+                "kernel": "tz_replicate_kernel", "kernel_ms_per_step": kmean, "launches_per_step": 1,
+                "setup_ms_per_step": statistics.mean(law_ms),
+                "peak_basis": f"{props.multi_processor_count} SMs x {MUL_LANES_PER_SM} multiply lanes x "
+                              f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json); "
+                              f"{MUL_PER_DRAW} multiplies per draw"}
+    line = {"metric": METRIC, "value": value, "unit": "replicates/s", "samples_per_s": sps,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == pl.PL_FP32_BULK else "f64",
+            "data": "synthetic (Philox streams, seed 1)", "config": config,
+            "e2e": {"value": e2e_value, "unit": "replicates/s", "h2d_bytes_per_step": len(cells) * 40 + len(QS) * 8,
+                    "d2h_bytes_per_step": host_cut.nbytes},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = tz_cpu_oracle_rate(tcells, samp, threads)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": "replicates/s", "cores": threads,
+                                "kind": "oracle", "sample": cb["sample"], "samples_per_s": cb["samples_per_s"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def replica_seed(rank: int) -> int:
     """Replicas (one process per GPU) draw independent Philox streams: the key
     is the base seed plus the rank.  No data crosses ranks."""
@@ -352,13 +519,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--replicates", type=int, default=100_000,
                     help="replicates per cell (smaller values for profiler captures only)")
-    ap.add_argument("--workload", choices=["sweep", "small", "large-n", "batched", "serving", "table1"],
+    ap.add_argument("--workload", choices=["sweep", "small", "large-n", "batched", "serving", "table1",
+                                           "truncated"],
                     default="sweep",
                     help="sweep: the 90-cell table (the benchmark line); small: alpha=2.5, n=100, "
                          "10,000 replicates; large-n: alpha=2, n=1e6, 10,000 replicates; batched: "
                          "4,096 uneven instances x 2,000 replicates in one graph-captured launch; "
                          "serving: Poisson fit requests at 200/s through the serving engine; "
-                         "table1: one run of the paper's Table 1 (120 cells x 50,000 replicates)")
+                         "table1: one run of the paper's Table 1 (120 cells x 50,000 replicates); "
+                         "truncated: one run of Tables 2-6 (truncated law, 900 cells x 50,000 replicates)")
+    ap.add_argument("--tz-replicates", type=int, default=50_000,
+                    help="truncated: replicates per cell (smaller values for profiler captures only)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: measured seconds")
     ap.add_argument("--serve-warmup", type=float, default=5.0, help="serving: warm-up seconds")
     ap.add_argument("--workers", type=int, default=8, help="serving: engine worker slots")
@@ -366,6 +537,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "truncated":
+        return run_truncated(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

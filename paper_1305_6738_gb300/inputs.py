@@ -128,3 +128,30 @@ def table1_cells(replicates: int = 50_000) -> list[Cell]:
     index) + (N index).  Runs differ by seed (run r uses seed r + 1)."""
     return [Cell(g, 1, n, replicates, 100 * i + j)
             for i, g in enumerate(TABLE1_GAMMAS) for j, n in enumerate(TABLE1_NS)]
+
+
+# Tables 2-6 of the paper (truncated law on 1..K): K = 20, 50, 100, 500, 1000,
+# 12 exponents x the 15 sample sizes of Table 1, 50,000 replicates per run,
+# each cell the mean of 10 runs; the same quantiles.
+TZ_KS = (20, 50, 100, 500, 1000)
+TZ_GAMMAS = (0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.75, 2.0, 2.5, 3.0, 3.5, 4.0)
+TZ_NS = TABLE1_NS
+TZ_QUANTILES = TABLE1_QUANTILES
+TZ_RUNS = 10
+
+
+@dataclass
+class TzCell:
+    gamma: float
+    K: int
+    n: int
+    replicates: int
+    cell_id: int
+
+
+def tables2to6_cells(replicates: int = 50_000, Ks=TZ_KS) -> list[TzCell]:
+    """One run of Tables 2-6: every (K, gamma, N) cell; cell id = 10000 * (K
+    index) + 100 * (gamma index) + (N index).  Runs differ by seed (run r uses
+    seed r + 1)."""
+    return [TzCell(g, K, n, replicates, 10000 * TZ_KS.index(K) + 100 * i + j)
+            for K in Ks for i, g in enumerate(TZ_GAMMAS) for j, n in enumerate(TZ_NS)]

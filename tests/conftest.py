@@ -30,3 +30,20 @@ def load_table1():
 @pytest.fixture(scope="session")
 def table1():
     return load_table1()
+
+
+def load_tables2to6():
+    """Tables 2-6 of the paper as {(K, gamma, N): (q90, q95, q99, q999)}."""
+    out = {}
+    with open(os.path.join(GOLDEN, "tables2to6_truncated.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            K, g, n, *q = line.split()
+            out[(int(K), float(g), int(n))] = tuple(float(v) for v in q)
+    return out
+
+
+@pytest.fixture(scope="session")
+def tables2to6():
+    return load_tables2to6()
