@@ -62,8 +62,9 @@ __global__ void tz_log_kernel(const TzTable *tables) {
 }
 
 // Fit nodes, one warp per node gamma_j: a_r = sum_k (-ln k)^r k^-gamma_j / r!,
-// r < kTzTerms (all terms of one a_r share a sign), E_j = -a_1 / a_0 (the
-// mean of ln X) and V_j = 2 a_2 / a_0 - E_j^2 (its variance).
+// r < kTzTerms (all terms of one a_r share a sign), stored as a_0 and
+// b_r = a_r / a_0; E_j = -b_1 (the mean of ln X) and V_j = 2 b_2 - b_1^2 (its
+// variance).
 __global__ void __launch_bounds__(256) tz_node_kernel(const TzTable *tables) {
   const TzTable &t = tables[blockIdx.y];
   const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
@@ -85,13 +86,32 @@ __global__ void __launch_bounds__(256) tz_node_kernel(const TzTable *tables) {
   for (int r = 0; r < kTzTerms; ++r) a[r] = warp_sum(a[r]);
   if (lane == 0) {
     double *nd = t.node + (size_t)j * kTzNodeStride;
+    const double inv = 1.0 / a[0];
+    nd[0] = a[0];
 #pragma unroll
-    for (int r = 0; r < kTzTerms; ++r) nd[r] = a[r];
-    const double E = -a[1] / a[0];
-    nd[kTzTerms] = E;
-    nd[kTzTerms + 1] = 2.0 * a[2] / a[0] - E * E;
+    for (int r = 1; r < kTzTerms; ++r) nd[r] = a[r] * inv;
+    const double E = -nd[1];
+    nd[kTzE] = E;
+    nd[kTzV] = 2.0 * nd[2] - E * E;
+    nd[kTzInvA0] = inv;
     t.E[j] = E;
   }
+}
+
+// The Hermite start terms of each node interval (after every node is built).
+__global__ void tz_node_interval_kernel(const TzTable *tables) {
+  const TzTable &t = tables[blockIdx.y];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= kTzNodes) return;
+  double *nd = t.node + (size_t)j * kTzNodeStride;
+  if (j == kTzNodes - 1) {
+    nd[kTzInvDE] = nd[kTzS0] = nd[kTzS1] = 0.0;
+    return;
+  }
+  const double dE = nd[kTzE] - nd[kTzNodeStride + kTzE];
+  nd[kTzInvDE] = 1.0 / dE;
+  nd[kTzS0] = dE / nd[kTzV];
+  nd[kTzS1] = dE / nd[kTzNodeStride + kTzV];
 }
 
 // Thresholds of one law, one block of 1024 threads: thread i holds the term
@@ -184,46 +204,60 @@ __device__ __forceinline__ uint32_t tz_bin(const uint32_t *h, uint32_t k) {
   return (h[k >> 1] >> ((k & 1u) << 4)) & 0xffffu;
 }
 
-// zeta_K and its first two gamma-derivatives at gamma_j + delta from node j's
-// polynomial (Horner with derivatives).
-__device__ __forceinline__ void tz_poly(const double *nd, double d, double &z0, double &z1, double &z2) {
-  double p = nd[kTzTerms - 1], dp = 0.0, ddp = 0.0;
+// The normalised scaling factor P(delta) = zeta_K(gamma_j + delta) / a_0 and
+// its first two derivatives from node j's polynomial (Horner with
+// derivatives; b_0 = 1).
+__device__ __forceinline__ void tz_poly(const double *nd, double d, double &p, double &dp, double &ddp) {
+  p = nd[kTzTerms - 1];
+  dp = 0.0;
+  ddp = 0.0;
 #pragma unroll
-  for (int r = kTzTerms - 2; r >= 0; --r) {
+  for (int r = kTzTerms - 2; r >= 1; --r) {
     ddp = fma(ddp, d, dp);
     dp = fma(dp, d, p);
     p = fma(p, d, nd[r]);
   }
-  z0 = p;
-  z1 = dp;
-  z2 = 2.0 * ddp;
+  ddp = fma(ddp, d, dp);
+  dp = fma(dp, d, p);
+  p = fma(p, d, 1.0);
+  ddp *= 2.0;
 }
-__device__ __forceinline__ double tz_poly0(const double *nd, double d) {
-  double p = nd[kTzTerms - 1];
-#pragma unroll
-  for (int r = kTzTerms - 2; r >= 0; --r) p = fma(p, d, nd[r]);
-  return p;
+
+// 1 / x for x in [2^-8, 2^8]: the binary32 reciprocal refined by two
+// binary64 Newton steps (relative error 1e-7 -> 1e-14 -> below 1 ulp).
+__device__ __forceinline__ double tz_rcp(double x) {
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
 }
 
 // MLE (Eq. 2 with the finite scaling factor): the root of
 // E_gamma[ln X] = mbar, E decreasing in gamma.  Every lane of the warp runs
 // the same steps.  The node bracket E_j >= mbar > E_{j+1} is found by a
 // 32-way search (three rounds of ballots over the node means), the start by
-// cubic Hermite interpolation of gamma(E) between the two nodes, and the
-// root by Newton on the node polynomial, safeguarded by bisection on
-// [gamma_j, gamma_j + 1/32] to 4 ulp of max(|gamma|, 1).  Means at or
-// beyond the ends of [-64, 64] give the end.  Returns the iterations
-// (kTzNewtonCap + 1 if the cap was hit); *Z = zeta_K(gamma-hat).
-__device__ __forceinline__ int tz_fit(const TzTable &tb, double mbar, int lane, double &g_out, double &Z) {
+// cubic Hermite interpolation of gamma(E) between the two nodes (its
+// interpolation error is of order 1e-8 or below), and the root by Newton on
+// the node polynomial with the slope -Var[ln X] rounded to binary32,
+// safeguarded by bisection on [gamma_j, gamma_j + 1/32].  A Newton step
+// below 2^-27 max(|gamma|, 1) is the last: the error left after it is below
+// the square of the step plus 1e-7 of it, under 1e-15.  Means at or beyond the
+// ends of [-64, 64] give the end.  Returns the number of polynomial
+// evaluations (kTzNewtonCap + 1 if the cap was hit); *Z = zeta_K(gamma-hat),
+// *invZ its reciprocal.
+__device__ __forceinline__ int tz_fit(const TzTable &tb, double mbar, int lane, double &g_out, double &Z,
+                                      double &invZ) {
   const double *E = tb.E;
   if (!(mbar < E[0])) {
     g_out = kTzGammaLo;
     Z = tb.node[0];
+    invZ = tb.node[kTzInvA0];
     return 0;
   }
   if (!(mbar > E[kTzNodes - 1])) {
+    const double *nd = tb.node + (size_t)(kTzNodes - 1) * kTzNodeStride;
     g_out = kTzGammaHi;
-    Z = tb.node[(size_t)(kTzNodes - 1) * kTzNodeStride];
+    Z = nd[0];
+    invZ = nd[kTzInvA0];
     return 0;
   }
   uint32_t base = 0;
@@ -243,35 +277,41 @@ __device__ __forceinline__ int tz_fit(const TzTable &tb, double mbar, int lane, 
   const double h = 1.0 / kTzNodeInv;
   const double gj = kTzGammaLo + (double)j * h;
   const double *nd = tb.node + (size_t)j * kTzNodeStride;
-  const double E0 = nd[kTzTerms], V0 = nd[kTzTerms + 1];
-  const double E1 = nd[kTzNodeStride + kTzTerms], V1 = nd[kTzNodeStride + kTzTerms + 1];
-  const double dE = E0 - E1;
-  const double t = (E0 - mbar) / dE;
+  const double t = (nd[kTzE] - mbar) * nd[kTzInvDE];
   const double t2 = t * t, t3 = t2 * t;
-  double d = (t3 - 2.0 * t2 + t) * (dE / V0) + (3.0 * t2 - 2.0 * t3) * h + (t3 - t2) * (dE / V1);
+  double d = (t3 - 2.0 * t2 + t) * nd[kTzS0] + (3.0 * t2 - 2.0 * t3) * h + (t3 - t2) * nd[kTzS1];
   if (!(d >= 0.0 && d <= h)) d = t * h;
-  const double tol = 4.0 * ldexp(1.0, ilogb(fmax(fabs(gj), 1.0)) - 52);
-  double lo = 0.0, hi = h;
+  const double scale = fmax(fabs(gj), 1.0);
+  const double small = 0x1p-27 * scale;
+  const double tol = 4.0 * 0x1p-52 * scale;
+  double lo = 0.0, hi = h, zr = 1.0, izr = 1.0;
   int it = 1;
   for (; it <= kTzNewtonCap; ++it) {
-    double z0, z1, z2;
-    tz_poly(nd, d, z0, z1, z2);
-    const double iz = 1.0 / z0;
-    const double e = -z1 * iz;
-    const double var = z2 * iz - e * e;
+    double p, dp, ddp;
+    tz_poly(nd, d, p, dp, ddp);
+    const double iz = tz_rcp(p);
+    const double e = -dp * iz;
+    const double var = fma(ddp, iz, -e * e);
     const double f = e - mbar;
     if (f > 0.0)
       lo = d;
     else
       hi = d;
-    double nx = d + f / var;
-    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
-    const double step = fabs(nx - d);
+    double nx = d + f * (double)__frcp_rn((float)var);
+    const bool newton = nx >= lo && nx <= hi;  // f = 0 gives a zero step
+    if (!newton) nx = 0.5 * (lo + hi);
+    const double step = nx - d;
     d = nx;
-    if (step <= tol || hi - lo <= tol) break;
+    // P and 1/P at the new point to second order in the step (the error left,
+    // of order E^3 step^3, is below 1e-16 for a final step)
+    zr = fma(fma(0.5 * ddp, step, dp), step, p);
+    const double u = (zr - p) * iz;
+    izr = iz * fma(u, u, 1.0 - u);
+    if ((newton && fabs(step) <= small) || hi - lo <= tol) break;
   }
   g_out = gj + d;
-  Z = tz_poly0(nd, d);
+  Z = nd[0] * zr;
+  invZ = nd[kTzInvA0] * izr;
   return it;
 }
 
@@ -281,12 +321,16 @@ __global__ void __launch_bounds__(kTzWarps * 32, 2) tz_replicate_kernel(TzLaunch
   __shared__ uint16_t sG[kTzGuide];
   __shared__ uint32_t sH[kTzWarps][kTzKMax / 2 + 4];
   const TzItem item = a.items[blockIdx.x];
-  const TzCell c = a.cells[item.cell];
-  const TzLaw law = a.laws[c.law];
-  const TzTable tb = a.tables[law.table];
+  const TzCell &c = a.cells[item.cell];
+  const TzLaw &law = a.laws[c.law];
+  const TzTable &tb = a.tables[law.table];
   const uint32_t K = law.K;
-  for (uint32_t i = threadIdx.x; i <= K; i += blockDim.x) sT[i] = law.T[i];
-  for (uint32_t i = threadIdx.x; i < (uint32_t)kTzGuide; i += blockDim.x) sG[i] = law.guide[i];
+  {
+    const uint64_t *T = law.T;
+    const uint16_t *G = law.guide;
+    for (uint32_t i = threadIdx.x; i <= K; i += blockDim.x) sT[i] = T[i];
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kTzGuide; i += blockDim.x) sG[i] = G[i];
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *h = sH[warp];
@@ -318,13 +362,12 @@ __global__ void __launch_bounds__(kTzWarps * 32, 2) tz_replicate_kernel(TzLaunch
     for (uint32_t k = 2 + lane; k <= K; k += 32) Ls += (double)tz_bin(h, k) * tb.lnk[k];
     Ls = warp_sum(Ls);
     if ((c12 & 0xffffu) == n) Ls += kLn2;
-    double g, Z;
-    const int its = tz_fit(tb, Ls * inv_n, lane, g, Z);
+    double g, Z, invZ;
+    const int its = tz_fit(tb, Ls * inv_n, lane, g, Z, invZ);
     if (its > kTzNewtonCap && lane == 0) atomicAdd(&a.ctr->newton_capped, 1ull);
     // D over the support, one chunk of 32 support points per step
     uint32_t carryC = 0;
     if (!F32) {
-      const double invZ = 1.0 / Z;
       double carryP = 0.0, best = 0.0;
       for (uint32_t k0 = 1; k0 <= K; k0 += 32) {
         const uint32_t k = k0 + lane;
@@ -344,8 +387,7 @@ __global__ void __launch_bounds__(kTzWarps * 32, 2) tz_replicate_kernel(TzLaunch
       const bool neg = g < 0.0;
       const float *lh = neg ? tb.lnq_hi : tb.lnk_hi, *ll = neg ? tb.lnq_lo : tb.lnk_lo;
       const float gh = (float)g, gl = (float)(g - (double)gh);
-      const double Zs = neg ? Z * exp(g * tb.lnK) : Z;
-      const float invZ = (float)(1.0 / Zs), invn = (float)inv_n;
+      const float invZf = neg ? (float)(invZ * exp(-g * tb.lnK)) : (float)invZ, invn = (float)inv_n;
       float ch = 0.0f, cl = 0.0f, best = 0.0f;
       for (uint32_t k0 = 1; k0 <= K; k0 += 32) {
         const uint32_t k = k0 + lane;
@@ -360,7 +402,7 @@ __global__ void __launch_bounds__(kTzWarps * 32, 2) tz_replicate_kernel(TzLaunch
         warp_scan_ff(th, tl, lane);
         ff_add(th, tl, ch, cl);
         const uint32_t C = warp_scan_u32(valid ? tz_bin(h, k) : 0u, lane) + carryC;
-        if (valid) best = fmaxf(best, fabsf(fmaf(th, invZ, tl * invZ) - (float)C * invn));
+        if (valid) best = fmaxf(best, fabsf(fmaf(th, invZf, tl * invZf) - (float)C * invn));
         ch = __shfl_sync(0xffffffffu, th, 31);
         cl = __shfl_sync(0xffffffffu, tl, 31);
         carryC = __shfl_sync(0xffffffffu, C, 31);
@@ -379,6 +421,7 @@ cudaError_t launch_tz_setup(TzLaw *laws, int nlaws, TzTable *tables, int ntables
   if (ntables > 0) {
     tz_log_kernel<<<dim3((kTzKMax + 1 + 255) / 256, ntables), 256, 0, st>>>(tables);
     tz_node_kernel<<<dim3((kTzNodes * 32 + 255) / 256, ntables), 256, 0, st>>>(tables);
+    tz_node_interval_kernel<<<dim3((kTzNodes + 255) / 256, ntables), 256, 0, st>>>(tables);
   }
   if (nlaws > 0) tz_law_kernel<<<nlaws, 1024, 0, st>>>(laws);
   return cudaGetLastError();

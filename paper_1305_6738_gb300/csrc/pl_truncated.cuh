@@ -22,16 +22,22 @@ constexpr int kTzGuide = 1 << kTzGuideBits;
 constexpr int kTzWarps = 16;                // warps per block of the replicate kernel
 // Fit nodes: gamma_j = -64 + j / 32, j = 0..4096.  Around each node the
 // scaling factor is a polynomial in delta = gamma - gamma_j:
-//   zeta_K(gamma_j + delta) = sum_r a_r delta^r,
-//   a_r = sum_k (-ln k)^r k^-gamma_j / r!,
+//   zeta_K(gamma_j + delta) = a_0 sum_r b_r delta^r,
+//   a_r = sum_k (-ln k)^r k^-gamma_j / r!,  b_r = a_r / a_0 (b_0 = 1),
 // exact as a series; kTzTerms terms leave a relative error below
 // (ln(1024) / 32)^14 / 14! < 1e-20 for delta in [0, 1/32], and below
-// 3e-17 in the second derivative.
+// 3e-17 in the second derivative.  The normalised polynomial stays in
+// [K^(-1/32), 1] on the interval, whatever the scale of a_0.
 constexpr int kTzNodeInv = 32;              // nodes per unit of gamma
 constexpr double kTzGammaLo = -64.0, kTzGammaHi = 64.0;
 constexpr int kTzNodes = 128 * kTzNodeInv + 1;
 constexpr int kTzTerms = 14;
-constexpr int kTzNodeStride = 16;           // doubles per node record: a_0..a_13, E, V
+// Node record (doubles): a_0, b_1..b_13, then E_j (mean of ln X at gamma_j),
+// V_j (its variance), 1 / (E_j - E_{j+1}), (E_j - E_{j+1}) / V_j,
+// (E_j - E_{j+1}) / V_{j+1} (the Hermite start on [gamma_j, gamma_{j+1}]),
+// 1 / a_0.
+constexpr int kTzNodeStride = 20;
+constexpr int kTzE = 14, kTzV = 15, kTzInvDE = 16, kTzS0 = 17, kTzS1 = 18, kTzInvA0 = 19;
 constexpr int kTzNewtonCap = 64;
 
 // One distinct (gamma, K): thresholds T[k] = floor(Q(k) 2^53) + 1 for
