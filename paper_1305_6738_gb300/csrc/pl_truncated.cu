@@ -315,11 +315,34 @@ __device__ __forceinline__ int tz_fit(const TzTable &tb, double mbar, int lane, 
   return it;
 }
 
+// Table-driven exponential (Tang, "Table-driven implementation of the
+// exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2),
+// 1989), in the form e^x = 2^(y/64) with y = 64 x / ln 2 passed in: m =
+// round(y) splits 2^(m/64) = 2^(m >> 6) tab[m & 63] (tab[i] = 2^(i/64)), and
+// the rest e^u, u = (y - m) ln 2 / 64, |u| <= ln 2 / 128, is its Taylor
+// polynomial of degree 5 (truncation below u^6 / 720 < 4e-17).  The scaling by
+// 2^(m >> 6) adds to the exponent field, exact for |y| < 64 * 1000.  The
+// error is a few ulps plus the rounding of y (|y| 2^-53 relative to e^x).
+__device__ __forceinline__ double tz_exp64(double y, const double *tab) {
+  const double magic = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer
+  const double md = y + magic;
+  const int m = (int)(uint32_t)__double_as_longlong(md);
+  const double u = (y - (md - magic)) * (0.69314718055994530942 / 64.0);
+  double p = fma(u, 1.0 / 120.0, 1.0 / 24.0);
+  p = fma(p, u, 1.0 / 6.0);
+  p = fma(p, u, 0.5);
+  p = fma(p, u, 1.0);
+  p = fma(p, u, 1.0);
+  const double v = tab[m & 63] * p;
+  return __longlong_as_double(__double_as_longlong(v) + ((long long)(m >> 6) << 52));
+}
+
 template <bool F32>
 __global__ void __launch_bounds__(kTzWarps * 32, 2) tz_replicate_kernel(TzLaunch a) {
   __shared__ uint64_t sT[kTzKMax + 1];
   __shared__ uint16_t sG[kTzGuide];
   __shared__ uint32_t sH[kTzWarps][kTzKMax / 2 + 4];
+  __shared__ double sX[64];  // 2^(i/64)
   const TzItem item = a.items[blockIdx.x];
   const TzCell &c = a.cells[item.cell];
   const TzLaw &law = a.laws[c.law];
@@ -331,6 +354,7 @@ __global__ void __launch_bounds__(kTzWarps * 32, 2) tz_replicate_kernel(TzLaunch
     for (uint32_t i = threadIdx.x; i <= K; i += blockDim.x) sT[i] = T[i];
     for (uint32_t i = threadIdx.x; i < (uint32_t)kTzGuide; i += blockDim.x) sG[i] = G[i];
   }
+  if (!F32 && threadIdx.x < 64) sX[threadIdx.x] = exp2((double)threadIdx.x / 64.0);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *h = sH[warp];
@@ -369,10 +393,12 @@ __global__ void __launch_bounds__(kTzWarps * 32, 2) tz_replicate_kernel(TzLaunch
     uint32_t carryC = 0;
     if (!F32) {
       double carryP = 0.0, best = 0.0;
+      const double cg = -g * (64.0 / 0.69314718055994530942);  // k^-g = 2^(cg ln k / 64)
+      const double *lnk = tb.lnk;
       for (uint32_t k0 = 1; k0 <= K; k0 += 32) {
         const uint32_t k = k0 + lane;
         const bool valid = k <= K;
-        const double t = valid ? exp(-g * tb.lnk[k]) : 0.0;
+        const double t = valid ? tz_exp64(cg * lnk[k], sX) : 0.0;
         const uint32_t C = warp_scan_u32(valid ? tz_bin(h, k) : 0u, lane) + carryC;
         const double P = warp_scan(t, lane) + carryP;
         if (valid) best = fmax(best, fabs(P * invZ - (double)C * inv_n));
