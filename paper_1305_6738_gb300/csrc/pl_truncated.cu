@@ -338,7 +338,7 @@ __device__ __forceinline__ double tz_exp64(double y, const double *tab) {
 }
 
 template <bool F32>
-__global__ void __launch_bounds__(kTzWarps * 32, 2) tz_replicate_kernel(TzLaunch a) {
+__global__ void __launch_bounds__(kTzWarps * 32, PL_TZ_MIN_BLOCKS) tz_replicate_kernel(TzLaunch a) {
   __shared__ uint64_t sT[kTzKMax + 1];
   __shared__ uint16_t sG[kTzGuide];
   __shared__ uint32_t sH[kTzWarps][kTzKMax / 2 + 4];

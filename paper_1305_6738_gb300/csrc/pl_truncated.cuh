@@ -19,7 +19,13 @@ constexpr uint32_t kTzKMax = 1024;          // largest support
 constexpr int64_t kTzNMax = 65535;          // largest sample (16-bit histogram counts)
 constexpr int kTzGuideBits = 11;            // guide: 2^11 buckets of m
 constexpr int kTzGuide = 1 << kTzGuideBits;
-constexpr int kTzWarps = 16;                // warps per block of the replicate kernel
+#ifndef PL_TZ_WARPS
+#define PL_TZ_WARPS 8
+#endif
+#ifndef PL_TZ_MIN_BLOCKS
+#define PL_TZ_MIN_BLOCKS 4
+#endif
+constexpr int kTzWarps = PL_TZ_WARPS;       // warps per block of the replicate kernel
 // Fit nodes: gamma_j = -64 + j / 32, j = 0..4096.  Around each node the
 // scaling factor is a polynomial in delta = gamma - gamma_j:
 //   zeta_K(gamma_j + delta) = a_0 sum_r b_r delta^r,
