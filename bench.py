@@ -333,9 +333,11 @@ def tz_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-# DRAM bytes per replicate of the truncated replicate kernel from one ncu
-# capture, keyed by the hash of its sources (null once they change).
-TZ_TRAFFIC_PER_REPLICATE: dict = {}
+# DRAM bytes per replicate of the truncated replicate kernel from one
+# one-pass ncu capture of a full Tables 2-6 launch (55.6 MB read + 147.1 MB
+# written for 45,000,000 replicates: the 4-byte D of each replicate plus the
+# tables), keyed by the hash of its sources (null once they change).
+TZ_TRAFFIC_PER_REPLICATE = {"324049b563c2cca9": (55621888 + 147120384) / 45e6}
 
 
 def tz_cpu_oracle_rate(cells, sample_reps: int, threads: int) -> dict:
