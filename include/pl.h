@@ -309,6 +309,63 @@ pl_status pl_ks_cutoffs_truncated(pl_ctx *ctx, const pl_tcell *cells,
                                   void *D_dev_opt, double *gamma_hat_dev_opt,
                                   void *stream);
 
+/* Fit and D of one data set of the truncated law (values 1..K, int32 on the
+ * device, 1 <= n <= 2^31 - 1, 2 <= K <= 1024).  gamma: NaN fits the exponent
+ * (Eq. 2 with the finite normaliser; the root on the real line, bounded to
+ * [-64, 64]) and evaluates D (Eq. 3, every t = 1..K) there; a value in
+ * [-64, 64] evaluates D at that exponent.  gamma_host, D_host: host doubles.
+ * Synchronises `stream`.  Errors: PL_EINVAL (arguments, a value outside
+ * 1..K). */
+pl_status pl_fit_ks_truncated(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
+                              uint64_t K, double gamma, pl_precision prec,
+                              double *gamma_host, double *D_host,
+                              void *stream);
+
+/* Bespoke cutoffs (Section 3: the cutoff for the exact N and fitted exponent
+ * of the sample, simulated): fit alpha-hat and D of the data set as
+ * pl_fit_mle / pl_ks_stat do, simulate R data sets of the same n at
+ * alpha-hat (purpose 1, cell_id = request_id; the same simulation as
+ * pl_bootstrap_pvalue with B = R), refit each, and return the order
+ * statistics D_(floor(R q_j)) of their D for the nq quantiles, and
+ * p = #{D_b >= D} / R.  The test rejects at level 1 - q_j when D exceeds
+ * cutoff j.  x_dev: device int32[n], values >= xmin.  alpha_hat, D, p: host
+ * doubles; cutoffs_host: host double[nq].  Synchronises `stream`.
+ * Errors: as pl_bootstrap_pvalue, and q outside (0, 1). */
+pl_status pl_bespoke_cutoffs(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
+                             uint64_t xmin, int64_t R, uint64_t seed,
+                             uint64_t request_id, const double *q, int nq,
+                             pl_precision prec, double *alpha_hat, double *D,
+                             double *p, double *cutoffs_host, void *stream);
+
+/* The same for the truncated law on 1..K (values 1..K, 1 <= n <= 65535):
+ * gamma-hat and D as pl_fit_ks_truncated, then R data sets of the same n at
+ * (gamma-hat, K) (any gamma-hat in [-64, 64]: the law on a finite support is
+ * defined for every real exponent), purpose 1, cell_id = request_id. */
+pl_status pl_bespoke_cutoffs_truncated(pl_ctx *ctx, const int32_t *x_dev,
+                                       int64_t n, uint64_t K, int64_t R,
+                                       uint64_t seed, uint64_t request_id,
+                                       const double *q, int nq,
+                                       pl_precision prec, double *gamma_hat,
+                                       double *D, double *p,
+                                       double *cutoffs_host, void *stream);
+
+/* Cutoffs at fitted exponents from a tabulated grid (Section 3: using the
+ * tables with a close value of the exponent).  The table holds nq cutoffs
+ * for each grid cell (grid_alpha[i], grid_n[k]) at row i * nn + k (the
+ * layout pl_ks_cutoffs returns for cells listed exponent-major).  For each
+ * query (alpha_dev[m], n_dev[m]) the result is bilinear in (alpha, ln n)
+ * between the four surrounding cells, clamped to the grid's edges (so equal
+ * to the cell's value at a grid point).  grid_alpha (host, strictly
+ * increasing, na >= 1), grid_n (host, strictly increasing, >= 1, nn >= 1);
+ * table_dev: device double[na * nn * nq]; alpha_dev, n_dev: device double /
+ * int64 [nquery]; out_dev: device double[nquery * nq], row per query.
+ * Stream ordered, no synchronisation.  Errors: PL_EINVAL. */
+pl_status pl_cutoff_lookup(pl_ctx *ctx, const double *grid_alpha, int na,
+                           const int64_t *grid_n, int nn,
+                           const double *table_dev, int nq,
+                           const double *alpha_dev, const int64_t *n_dev,
+                           int64_t nquery, double *out_dev, void *stream);
+
 /* Fit and KS distance of one data set with no device allocation at all.
  * The paper has no counterpart: this is an engineering variant of
  * pl_fit_mle + pl_ks_stat for callers that cannot let a library call

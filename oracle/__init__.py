@@ -296,3 +296,32 @@ def tz_cell(gamma: float, K: int, n: int, R: int, seed: int, cell_id: int, purpo
     _check(_load().or_tz_cell(gamma, K, n, seed, cell_id, purpose, rep0, R, threads,
                               _ptr(D, _f64p), _ptr(A, _f64p), ctypes.byref(nc)), "tz_cell")
     return D, A, int(nc.value)
+
+
+def cutoff_lookup(grid_alpha, grid_n, table: np.ndarray, alpha: float, n: int) -> np.ndarray:
+    """Cutoffs at (alpha, n) from a table on the grid (grid_alpha[i], grid_n[k])
+    (table[i, k, :]): bilinear in (alpha, ln n) between the four surrounding
+    grid cells, clamped to the grid's edges (the reading of Section 3's use of
+    the tables at a close value of the exponent)."""
+    import math
+
+    def bracket(g, v):
+        if len(g) == 1:
+            return 0, 0.0
+        i = 0
+        while i + 2 < len(g) and g[i + 1] <= v:
+            i += 1
+        t = (v - g[i]) / (g[i + 1] - g[i])
+        return i, min(max(t, 0.0), 1.0)
+
+    ia, wa = bracket([float(a) for a in grid_alpha], float(alpha))
+    ln = [math.log(float(v)) for v in grid_n]
+    k, wn = bracket(ln, math.log(float(n)))
+    ia1 = ia + 1 if len(grid_alpha) > 1 else ia
+    k1 = k + 1 if len(grid_n) > 1 else k
+    out = np.zeros(table.shape[2])
+    for j in range(table.shape[2]):
+        v00, v10 = table[ia, k, j], table[ia1, k, j]
+        v01, v11 = table[ia, k1, j], table[ia1, k1, j]
+        out[j] = (1.0 - wa) * ((1.0 - wn) * v00 + wn * v01) + wa * ((1.0 - wn) * v10 + wn * v11)
+    return out

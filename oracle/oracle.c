@@ -646,7 +646,10 @@ int or_tz_replicate(double gamma, int64_t K, int64_t n, uint64_t seed, uint32_t 
 
 int or_tz_cell(double gamma, int64_t K, int64_t n, uint64_t seed, uint32_t cell, uint32_t purpose,
                uint32_t rep0, int64_t R, int nthreads, double *D, double *gamma_hat, int64_t *nonconv) {
-  if (n < 1 || R < 1 || K < 2 || !(gamma > 0.0)) return OR_EINVAL;
+  /* the law on a finite support is normalisable for every real exponent;
+   * the cells of the tables have gamma > 0, bespoke cutoffs simulate at the
+   * fitted exponent, which may be negative */
+  if (n < 1 || R < 1 || K < 2 || !(gamma >= -64.0 && gamma <= 64.0)) return OR_EINVAL;
   int64_t bad = 0, fails = 0;
 #ifdef _OPENMP
   if (nthreads < 1) nthreads = omp_get_max_threads();

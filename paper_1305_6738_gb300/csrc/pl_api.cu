@@ -19,6 +19,7 @@
 #include "pl.h"
 #include "pl_kernels.cuh"
 #include "pl_truncated.cuh"
+#include "pl_lookup.cuh"
 
 using namespace pl;
 
@@ -601,7 +602,11 @@ size_t ctx_bootstrap_bytes(pl_ctx *ctx, int64_t n, uint64_t xmin, int64_t B) {
   Carver cv;
   SimBuffers b;
   carve_sim(cv, sp, blocks, sblocks, b, ctx->dbg_arena, bsblocks);
-  cv.take<uint8_t>((size_t)B * 8 + 16);
+  cv.take<uint8_t>((size_t)B * 8);  // as run_bootstrap lays out its buffers
+  cv.take<double>(1);
+  cv.take<double>(1);
+  cv.take<int64_t>(3);
+  cv.take<double>(1);
   const size_t sim = cv.off;
   const size_t data = (size_t)next_pow2((uint64_t)n) * 8 + (size_t)n * 16 + (1u << 20);
   return std::max(sim, data);
@@ -753,8 +758,9 @@ struct TzBuffers {
   size_t host_bytes = 0;  // laws .. items, written from the host in one copy
 };
 
-pl_status tz_check_law(pl_ctx *ctx, double gamma, uint64_t K) {
-  if (!(gamma > 0.0 && gamma <= 64.0)) return fail(ctx, PL_EINVAL, "truncated law: gamma must be in (0, 64]");
+pl_status tz_check_law(pl_ctx *ctx, double gamma, uint64_t K, bool any_sign = false) {
+  if (any_sign ? !(gamma >= -64.0 && gamma <= 64.0) : !(gamma > 0.0 && gamma <= 64.0))
+    return fail(ctx, PL_EINVAL, "truncated law: gamma must be in %s", any_sign ? "[-64, 64]" : "(0, 64]");
   if (K < 2 || K > kTzKMax) return fail(ctx, PL_EINVAL, "truncated law: K must be in [2, %u]", kTzKMax);
   return PL_OK;
 }
@@ -785,13 +791,13 @@ uint32_t tz_law_index(TzPlan &tp, double gamma, uint32_t K, std::map<std::pair<d
 // replicate's cost (draws, support points and the fit) so that items of
 // different cells cost about the same, and shrink when the call is too small
 // to give every SM four items.  Costlier cells' items come first.
-pl_status tz_plan(pl_ctx *ctx, const pl_tcell *in, int ncells, uint32_t purpose, TzPlan &tp) {
+pl_status tz_plan(pl_ctx *ctx, const pl_tcell *in, int ncells, uint32_t purpose, TzPlan &tp, bool any_sign = false) {
   std::map<std::pair<double, uint32_t>, uint32_t> ids;
   std::vector<double> cost(ncells);
   double work = 0.0;
   for (int i = 0; i < ncells; ++i) {
     const pl_tcell &c = in[i];
-    if (pl_status s = tz_check_law(ctx, c.gamma, c.K)) return s;
+    if (pl_status s = tz_check_law(ctx, c.gamma, c.K, any_sign)) return s;
     if (c.n < 1 || c.n > kTzNMax || c.replicates < 1 || c.replicates > (1ll << 32) || c.cell_id >= (1ull << 32))
       return fail(ctx, PL_EINVAL, "truncated cell %d: n must be in [1, %lld], replicates in [1, 2^32], cell_id < 2^32",
                   i, (long long)kTzNMax);
@@ -900,25 +906,22 @@ pl_status pl_sample_truncated(pl_ctx *ctx, double gamma, uint64_t K, uint64_t se
   return PL_OK;
 }
 
-pl_status pl_ks_cutoffs_truncated(pl_ctx *ctx, const pl_tcell *cells, int ncells, uint64_t seed, const double *q,
-                                  int nq, pl_precision prec, double *cutoffs, void *D_dev_opt,
-                                  double *gamma_hat_dev_opt, void *stream) {
-  if (pl_status s = check_ctx(ctx)) return s;
-  if (!cells || ncells < 1 || !q || nq < 1 || !cutoffs)
-    return fail(ctx, PL_EINVAL, "pl_ks_cutoffs_truncated: bad arguments");
-  if (prec != PL_FP64 && prec != PL_FP32_BULK) return fail(ctx, PL_EINVAL, "unknown precision form");
-  for (int j = 0; j < nq; ++j)
-    if (!(q[j] > 0.0 && q[j] < 1.0)) return fail(ctx, PL_EINVAL, "quantile %d outside (0, 1)", j);
-  cudaStream_t st = (cudaStream_t)stream;
-  const bool f32 = prec == PL_FP32_BULK;
+namespace {
+
+// Simulation of truncated cells (purpose 0: cutoff tables; 1: bespoke
+// cutoffs of a data set) and the order statistics of each cell's D; with
+// D_obs (device) also p = #{D >= D_obs} / R of the single cell.
+pl_status run_tz_cutoffs(pl_ctx *ctx, const pl_tcell *cells, int ncells, uint32_t purpose, bool any_sign,
+                         uint64_t seed, const double *q, int nq, bool f32, double *cutoffs, void *D_dev_opt,
+                         double *gamma_hat_dev_opt, const double *D_obs_host, double *p_host, cudaStream_t st) {
   TzPlan tp;
-  if (pl_status s = tz_plan(ctx, cells, ncells, 0u, tp)) return s;
+  if (pl_status s = tz_plan(ctx, cells, ncells, purpose, tp, any_sign)) return s;
   const bool host_out = !is_device_ptr(cutoffs);
   const size_t dsz = f32 ? 4 : 8;
   TzBuffers b;
   void *D = nullptr;
   int64_t *off = nullptr, *Rs = nullptr, *rank = nullptr;
-  double *cut = nullptr;
+  double *cut = nullptr, *dobs = nullptr, *pd = nullptr;
   auto lay = [&](Carver &cv) {
     carve_tz(cv, tp, b);
     D = D_dev_opt ? D_dev_opt : (void *)cv.take<uint8_t>((size_t)tp.total_R * dsz);
@@ -926,6 +929,8 @@ pl_status pl_ks_cutoffs_truncated(pl_ctx *ctx, const pl_tcell *cells, int ncells
     Rs = cv.take<int64_t>(ncells);
     rank = cv.take<int64_t>((size_t)ncells * nq);
     cut = host_out ? cv.take<double>((size_t)ncells * nq) : cutoffs;
+    dobs = cv.take<double>(1);
+    pd = cv.take<double>(1);
   };
   Carver cv;
   lay(cv);
@@ -947,6 +952,7 @@ pl_status pl_ks_cutoffs_truncated(pl_ctx *ctx, const pl_tcell *cells, int ncells
   PL_CUDA(cudaMemcpyAsync(off, h_off.data(), sizeof(int64_t) * ncells, cudaMemcpyHostToDevice, st));
   PL_CUDA(cudaMemcpyAsync(Rs, h_R.data(), sizeof(int64_t) * ncells, cudaMemcpyHostToDevice, st));
   PL_CUDA(cudaMemcpyAsync(rank, h_rank.data(), sizeof(int64_t) * h_rank.size(), cudaMemcpyHostToDevice, st));
+  if (D_obs_host) PL_CUDA(cudaMemcpyAsync(dobs, D_obs_host, sizeof(double), cudaMemcpyHostToDevice, st));
   if (pl_status s = mark(ctx, 1, st)) return s;
   TzLaunch tl{};
   tl.cells = b.cells;
@@ -968,11 +974,105 @@ pl_status pl_ks_cutoffs_truncated(pl_ctx *ctx, const pl_tcell *cells, int ncells
   if (pl_status s = mark(ctx, 2, st)) return s;
   PL_CUDA(launch_select(D, f32, off, Rs, rank, ncells, nq, cut, st));
   ctx->launches += 1;
-  if (pl_status s = mark(ctx, 3, st)) return s;
-  if (host_out) {
-    PL_CUDA(cudaMemcpyAsync(cutoffs, cut, sizeof(double) * ncells * nq, cudaMemcpyDeviceToHost, st));
-    return read_status(ctx, st);
+  if (D_obs_host) {
+    PL_CUDA(launch_count_ge(D, f32, tp.total_R, dobs, pd, st));
+    ctx->launches += 1;
   }
+  if (pl_status s = mark(ctx, 3, st)) return s;
+  if (host_out) PL_CUDA(cudaMemcpyAsync(cutoffs, cut, sizeof(double) * ncells * nq, cudaMemcpyDeviceToHost, st));
+  if (p_host) PL_CUDA(cudaMemcpyAsync(p_host, pd, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (host_out || p_host) return read_status(ctx, st);
+  return PL_OK;
+}
+
+// Fit and/or D of one truncated data set: out_host = (gamma, D, zeta_K(gamma)).
+pl_status run_tz_dataset(pl_ctx *ctx, const int32_t *x, int64_t n, uint64_t K, bool fit, double gamma, bool f32,
+                         double out_host[3], cudaStream_t st) {
+  if (!x || n < 1 || n > INT32_MAX) return fail(ctx, PL_EINVAL, "truncated data set: bad arguments");
+  if (pl_status s = tz_check_law(ctx, fit ? 1.0 : gamma, K, true)) return s;
+  TzTable th{};
+  th.K = (uint32_t)K;
+  th.lnK = std::log((double)K);
+  auto lay = [&](Carver &cv, TzTable *&td, double *&out) {
+    td = cv.take<TzTable>(1);
+    th.lnk = cv.take<double>(K + 1);
+    th.lnk_hi = cv.take<float>(K + 1);
+    th.lnk_lo = cv.take<float>(K + 1);
+    th.lnq_hi = cv.take<float>(K + 1);
+    th.lnq_lo = cv.take<float>(K + 1);
+    th.node = cv.take<double>((size_t)kTzNodes * kTzNodeStride);
+    th.E = cv.take<double>(kTzNodes);
+    out = cv.take<double>(4);
+  };
+  Carver cv;
+  TzTable *td = nullptr;
+  double *out = nullptr;
+  lay(cv, td, out);
+  if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+  cv.base = ctx->ws;
+  cv.off = 0;
+  lay(cv, td, out);
+  PL_CUDA(cudaMemcpyAsync(td, &th, sizeof th, cudaMemcpyHostToDevice, st));
+  PL_CUDA(launch_tz_setup(nullptr, 0, td, 1, st));
+  PL_CUDA(launch_tz_dataset(x, n, td, fit, gamma, f32, out, ctx->ctr, st));
+  ctx->launches += 4;
+  PL_CUDA(cudaMemcpyAsync(out_host, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return read_status(ctx, st);
+}
+
+}  // namespace
+
+pl_status pl_ks_cutoffs_truncated(pl_ctx *ctx, const pl_tcell *cells, int ncells, uint64_t seed, const double *q,
+                                  int nq, pl_precision prec, double *cutoffs, void *D_dev_opt,
+                                  double *gamma_hat_dev_opt, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!cells || ncells < 1 || !q || nq < 1 || !cutoffs)
+    return fail(ctx, PL_EINVAL, "pl_ks_cutoffs_truncated: bad arguments");
+  if (prec != PL_FP64 && prec != PL_FP32_BULK) return fail(ctx, PL_EINVAL, "unknown precision form");
+  for (int j = 0; j < nq; ++j)
+    if (!(q[j] > 0.0 && q[j] < 1.0)) return fail(ctx, PL_EINVAL, "quantile %d outside (0, 1)", j);
+  return run_tz_cutoffs(ctx, cells, ncells, 0u, false, seed, q, nq, prec == PL_FP32_BULK, cutoffs, D_dev_opt,
+                        gamma_hat_dev_opt, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+pl_status pl_fit_ks_truncated(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint64_t K, double gamma,
+                              pl_precision prec, double *gamma_host, double *D_host, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!gamma_host || !D_host) return fail(ctx, PL_EINVAL, "pl_fit_ks_truncated: null output");
+  if (prec != PL_FP64 && prec != PL_FP32_BULK) return fail(ctx, PL_EINVAL, "unknown precision form");
+  const bool fit = std::isnan(gamma);
+  double o[3];
+  if (pl_status s = run_tz_dataset(ctx, x_dev, n, K, fit, fit ? 0.0 : gamma, prec == PL_FP32_BULK, o,
+                                   (cudaStream_t)stream))
+    return s;
+  *gamma_host = o[0];
+  *D_host = o[1];
+  return PL_OK;
+}
+
+pl_status pl_bespoke_cutoffs_truncated(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint64_t K, int64_t R,
+                                       uint64_t seed, uint64_t request_id, const double *q, int nq,
+                                       pl_precision prec, double *gamma_hat, double *D, double *p,
+                                       double *cutoffs_host, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (R < 1 || R > (1ll << 32) || request_id >= (1ull << 32) || !gamma_hat || !D || !p || !q || nq < 1 ||
+      !cutoffs_host || n > kTzNMax)
+    return fail(ctx, PL_EINVAL, "pl_bespoke_cutoffs_truncated: bad arguments");
+  if (prec != PL_FP64 && prec != PL_FP32_BULK) return fail(ctx, PL_EINVAL, "unknown precision form");
+  for (int j = 0; j < nq; ++j)
+    if (!(q[j] > 0.0 && q[j] < 1.0)) return fail(ctx, PL_EINVAL, "quantile %d outside (0, 1)", j);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f32 = prec == PL_FP32_BULK;
+  double obs[3];
+  if (pl_status s = run_tz_dataset(ctx, x_dev, n, K, true, 0.0, f32, obs, st)) return s;
+  pl_tcell cell{obs[0], K, n, R, request_id};
+  double ph = 0.0;
+  if (pl_status s = run_tz_cutoffs(ctx, &cell, 1, 1u, true, seed, q, nq, f32, cutoffs_host, nullptr, nullptr,
+                                   &obs[1], &ph, st))
+    return s;
+  *gamma_hat = obs[0];
+  *D = obs[1];
+  *p = ph;
   return PL_OK;
 }
 
@@ -1241,14 +1341,20 @@ void pl_plan_destroy(pl_plan *plan) {
   delete plan;
 }
 
-pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint64_t xmin, int64_t B,
-                              uint64_t seed, uint64_t request_id, pl_precision prec, double *alpha_hat,
-                              double *D, double *p, void *stream) {
-  if (pl_status s = check_ctx(ctx)) return s;
-  if (B < 1 || B > (1ll << 31) || request_id >= (1ull << 32) || !alpha_hat || !D || !p)
-    return fail(ctx, PL_EINVAL, "pl_bootstrap_pvalue: bad arguments");
+namespace {
+// The parametric bootstrap of one data set: fit (Eq. 2) and D (Eq. 3), then B
+// data sets of the same n at alpha-hat (purpose 1, cell = request id), each
+// refitted; p = #{D_b >= D} / B and, for nq > 0, the order statistics of the
+// D_b at the quantiles q (the bespoke cutoffs).
+pl_status run_bootstrap(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint64_t xmin, int64_t B, uint64_t seed,
+                        uint64_t request_id, pl_precision prec, const double *q, int nq, double *alpha_hat,
+                        double *D, double *p, double *cut_host, cudaStream_t st) {
+  if (B < 1 || B > (1ll << 31) || request_id >= (1ull << 32) || !alpha_hat || !D || !p || nq < 0 ||
+      (nq > 0 && (!q || !cut_host)))
+    return fail(ctx, PL_EINVAL, "bootstrap: bad arguments");
   if (prec != PL_FP64 && prec != PL_FP32_BULK) return fail(ctx, PL_EINVAL, "unknown precision form");
-  cudaStream_t st = (cudaStream_t)stream;
+  for (int j = 0; j < nq; ++j)
+    if (!(q[j] > 0.0 && q[j] < 1.0)) return fail(ctx, PL_EINVAL, "quantile %d outside (0, 1)", j);
   const bool f32 = prec == PL_FP32_BULK;
   double obs[3];
   if (pl_status s = run_dataset(ctx, x_dev, n, xmin, true, 0.0, prec, obs, st)) return s;
@@ -1257,22 +1363,31 @@ pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint
   if (pl_status s = plan_cells(ctx, &cell, 1, 1u, sp)) return s;
   const int blocks = sim_blocks(ctx, f32), sblocks = sample_blocks(ctx),
             bsblocks = ctx->num_sms * std::max(1, ctx->block_sampler_per_sm);
-  auto lay = [&](Carver &cv, SimBuffers &b, void *&Db, double *&dobs, double *&pd) {
+  const int nsel = std::max(nq, 1);
+  auto lay = [&](Carver &cv, SimBuffers &b, void *&Db, double *&dobs, double *&pd, int64_t *&sel, double *&cut) {
     carve_sim(cv, sp, blocks, sblocks, b, ctx->dbg_arena, bsblocks);
     Db = cv.take<uint8_t>((size_t)B * (f32 ? 4 : 8));
     dobs = cv.take<double>(1);
     pd = cv.take<double>(1);
+    sel = cv.take<int64_t>(2 + (size_t)nsel);  // offset 0, R, then the ranks
+    cut = cv.take<double>(nsel);
   };
   Carver cv;
   SimBuffers b;
   void *Db;
-  double *dobs, *pd;
-  lay(cv, b, Db, dobs, pd);
+  double *dobs, *pd, *cut;
+  int64_t *sel;
+  lay(cv, b, Db, dobs, pd, sel, cut);
   if (pl_status s = ensure_ws(ctx, cv.off)) return s;
   cv.base = ctx->ws;
   cv.off = 0;
-  lay(cv, b, Db, dobs, pd);
+  lay(cv, b, Db, dobs, pd, sel, cut);
   PL_CUDA(cudaMemcpyAsync(dobs, &obs[1], sizeof(double), cudaMemcpyHostToDevice, st));
+  std::vector<int64_t> h_sel(2 + (size_t)nsel, 0);
+  h_sel[1] = B;
+  for (int j = 0; j < nq; ++j)
+    h_sel[2 + j] = std::min(std::max<int64_t>((int64_t)std::floor((double)B * q[j]), 0), B - 1);
+  if (nq > 0) PL_CUDA(cudaMemcpyAsync(sel, h_sel.data(), sizeof(int64_t) * h_sel.size(), cudaMemcpyHostToDevice, st));
   if (pl_status s = mark(ctx, 0, st)) return s;
   if (pl_status s = upload_sim(ctx, sp, b, st)) return s;
   if (pl_status s = mark(ctx, 1, st)) return s;
@@ -1280,13 +1395,69 @@ pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint
   if (pl_status s = mark(ctx, 2, st)) return s;
   PL_CUDA(launch_count_ge(Db, f32, B, dobs, pd, st));
   ctx->launches += 1;
+  if (nq > 0) {
+    PL_CUDA(launch_select(Db, f32, sel, sel + 1, sel + 2, 1, nq, cut, st));
+    ctx->launches += 1;
+  }
   if (pl_status s = mark(ctx, 3, st)) return s;
   double ph = 0.0;
   PL_CUDA(cudaMemcpyAsync(&ph, pd, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (nq > 0) PL_CUDA(cudaMemcpyAsync(cut_host, cut, sizeof(double) * nq, cudaMemcpyDeviceToHost, st));
   if (pl_status s = read_status(ctx, st)) return s;
   *alpha_hat = obs[0];
   *D = obs[1];
   *p = ph;
+  return PL_OK;
+}
+}  // namespace
+
+pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint64_t xmin, int64_t B,
+                              uint64_t seed, uint64_t request_id, pl_precision prec, double *alpha_hat,
+                              double *D, double *p, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  return run_bootstrap(ctx, x_dev, n, xmin, B, seed, request_id, prec, nullptr, 0, alpha_hat, D, p, nullptr,
+                       (cudaStream_t)stream);
+}
+
+pl_status pl_bespoke_cutoffs(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint64_t xmin, int64_t R, uint64_t seed,
+                             uint64_t request_id, const double *q, int nq, pl_precision prec, double *alpha_hat,
+                             double *D, double *p, double *cutoffs_host, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!q || nq < 1 || !cutoffs_host) return fail(ctx, PL_EINVAL, "pl_bespoke_cutoffs: bad arguments");
+  return run_bootstrap(ctx, x_dev, n, xmin, R, seed, request_id, prec, q, nq, alpha_hat, D, p, cutoffs_host,
+                       (cudaStream_t)stream);
+}
+
+pl_status pl_cutoff_lookup(pl_ctx *ctx, const double *grid_alpha, int na, const int64_t *grid_n, int nn,
+                           const double *table_dev, int nq, const double *alpha_dev, const int64_t *n_dev,
+                           int64_t nquery, double *out_dev, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!grid_alpha || !grid_n || na < 1 || nn < 1 || nq < 1 || nquery < 0 || !table_dev ||
+      (nquery > 0 && (!alpha_dev || !n_dev || !out_dev)))
+    return fail(ctx, PL_EINVAL, "pl_cutoff_lookup: bad arguments");
+  for (int i = 0; i < na; ++i)
+    if (!std::isfinite(grid_alpha[i]) || (i && !(grid_alpha[i] > grid_alpha[i - 1])))
+      return fail(ctx, PL_EINVAL, "pl_cutoff_lookup: exponent grid not strictly increasing");
+  for (int i = 0; i < nn; ++i)
+    if (grid_n[i] < 1 || (i && !(grid_n[i] > grid_n[i - 1])))
+      return fail(ctx, PL_EINVAL, "pl_cutoff_lookup: sample-size grid not strictly increasing from 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  auto lay = [&](Carver &cv, double *&ga, int64_t *&gn) {
+    ga = cv.take<double>(na);
+    gn = cv.take<int64_t>(nn);
+  };
+  Carver cv;
+  double *ga;
+  int64_t *gn;
+  lay(cv, ga, gn);
+  if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+  cv.base = ctx->ws;
+  cv.off = 0;
+  lay(cv, ga, gn);
+  PL_CUDA(cudaMemcpyAsync(ga, grid_alpha, sizeof(double) * na, cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(gn, grid_n, sizeof(int64_t) * nn, cudaMemcpyHostToDevice, st));
+  PL_CUDA(launch_lookup(ga, na, gn, nn, table_dev, nq, alpha_dev, n_dev, nquery, out_dev, st));
+  ctx->launches += nquery > 0 ? 1 : 0;
   return PL_OK;
 }
 

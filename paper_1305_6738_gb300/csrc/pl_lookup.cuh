@@ -1,0 +1,16 @@
+// pl_lookup.cuh -- launch wrapper of the cutoff-table lookup (host side).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pl {
+
+// out[q * nq + j] = the table's quantile j at (qa[q], qn[q]), bilinear in
+// (alpha, ln n) over the grid (galpha strictly increasing, na >= 1; gn
+// strictly increasing, nn >= 1), clamped to its edges.  table: cell
+// (alpha_i, n_k) at row i * nn + k, nq values per row.  All pointers device.
+cudaError_t launch_lookup(const double *galpha, int na, const int64_t *gn, int nn, const double *table, int nq,
+                          const double *qa, const int64_t *qn, int64_t nquery, double *out, cudaStream_t st);
+
+}  // namespace pl

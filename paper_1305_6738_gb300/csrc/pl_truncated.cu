@@ -337,6 +337,71 @@ __device__ __forceinline__ double tz_exp64(double y, const double *tab) {
   return __longlong_as_double(__double_as_longlong(v) + ((long long)(m >> 6) << 52));
 }
 
+// D (Eq. 3) over t = 1..K for the law at exponent g (invZ = 1 / zeta_K(g))
+// against the histogram read by bin(k), one chunk of 32 support points per
+// step, every lane of the warp taking part.  FP64 form: k^-g by the
+// table-driven exponential (sX = 2^(i/64)), prefix sums and comparisons in
+// binary64.  FP32-bulk form: terms scaled by K^g when g < 0 (so that every
+// term is at most 1), exponent g ln k as a float pair, t = exp(-p) (1 - corr),
+// compensated float-pair prefix sums, comparisons in binary32.
+template <bool F32, class Bin>
+__device__ __forceinline__ double tz_ks(const TzTable &tb, uint32_t K, double g, double invZ, double inv_n, int lane,
+                                        const double *sX, Bin bin) {
+  uint32_t carryC = 0;
+  if (!F32) {
+    double carryP = 0.0, best = 0.0;
+    const double cg = -g * (64.0 / 0.69314718055994530942);  // k^-g = 2^(cg ln k / 64)
+    const double *lnk = tb.lnk;
+    for (uint32_t k0 = 1; k0 <= K; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      const bool valid = k <= K;
+      const double t = valid ? tz_exp64(cg * lnk[k], sX) : 0.0;
+      const uint32_t C = warp_scan_u32(valid ? bin(k) : 0u, lane) + carryC;
+      const double P = warp_scan(t, lane) + carryP;
+      if (valid) best = fmax(best, fabs(P * invZ - (double)C * inv_n));
+      carryP = __shfl_sync(0xffffffffu, P, 31);
+      carryC = __shfl_sync(0xffffffffu, C, 31);
+    }
+    return warp_max(best);
+  }
+  const bool neg = g < 0.0;
+  const float *lh = neg ? tb.lnq_hi : tb.lnk_hi, *ll = neg ? tb.lnq_lo : tb.lnk_lo;
+  const float gh = (float)g, gl = (float)(g - (double)gh);
+  const float invZf = neg ? (float)(invZ * exp(-g * tb.lnK)) : (float)invZ, invn = (float)inv_n;
+  float ch = 0.0f, cl = 0.0f, best = 0.0f;
+  for (uint32_t k0 = 1; k0 <= K; k0 += 32) {
+    const uint32_t k = k0 + lane;
+    const bool valid = k <= K;
+    float th = 0.0f, tl = 0.0f;
+    if (valid) {
+      const float l_h = lh[k], l_l = ll[k];
+      const float p = gh * l_h;
+      const float corr = fmaf(gh, l_h, -p) + fmaf(gh, l_l, gl * l_h);
+      th = expf(-p) * (1.0f - corr);
+    }
+    warp_scan_ff(th, tl, lane);
+    ff_add(th, tl, ch, cl);
+    const uint32_t C = warp_scan_u32(valid ? bin(k) : 0u, lane) + carryC;
+    if (valid) best = fmaxf(best, fabsf(fmaf(th, invZf, tl * invZf) - (float)C * invn));
+    ch = __shfl_sync(0xffffffffu, th, 31);
+    cl = __shfl_sync(0xffffffffu, tl, 31);
+    carryC = __shfl_sync(0xffffffffu, C, 31);
+  }
+  return (double)warp_maxf(best);
+}
+
+// zeta_K(g) and its reciprocal at a given exponent in [-64, 64], from the
+// node polynomial of the node at or below g.
+__device__ __forceinline__ void tz_zeta_at(const TzTable &tb, double g, double &Z, double &invZ) {
+  int j = (int)floor((g - kTzGammaLo) * kTzNodeInv);
+  j = j < 0 ? 0 : (j > kTzNodes - 2 ? kTzNodes - 2 : j);
+  const double *nd = tb.node + (size_t)j * kTzNodeStride;
+  double p, dp, ddp;
+  tz_poly(nd, g - (kTzGammaLo + (double)j / kTzNodeInv), p, dp, ddp);
+  Z = nd[0] * p;
+  invZ = nd[kTzInvA0] * tz_rcp(p);
+}
+
 template <bool F32>
 __global__ void __launch_bounds__(kTzWarps * 32, PL_TZ_MIN_BLOCKS) tz_replicate_kernel(TzLaunch a) {
   __shared__ uint64_t sT[kTzKMax + 1];
@@ -389,59 +454,82 @@ __global__ void __launch_bounds__(kTzWarps * 32, PL_TZ_MIN_BLOCKS) tz_replicate_
     double g, Z, invZ;
     const int its = tz_fit(tb, Ls * inv_n, lane, g, Z, invZ);
     if (its > kTzNewtonCap && lane == 0) atomicAdd(&a.ctr->newton_capped, 1ull);
-    // D over the support, one chunk of 32 support points per step
-    uint32_t carryC = 0;
-    if (!F32) {
-      double carryP = 0.0, best = 0.0;
-      const double cg = -g * (64.0 / 0.69314718055994530942);  // k^-g = 2^(cg ln k / 64)
-      const double *lnk = tb.lnk;
-      for (uint32_t k0 = 1; k0 <= K; k0 += 32) {
-        const uint32_t k = k0 + lane;
-        const bool valid = k <= K;
-        const double t = valid ? tz_exp64(cg * lnk[k], sX) : 0.0;
-        const uint32_t C = warp_scan_u32(valid ? tz_bin(h, k) : 0u, lane) + carryC;
-        const double P = warp_scan(t, lane) + carryP;
-        if (valid) best = fmax(best, fabs(P * invZ - (double)C * inv_n));
-        carryP = __shfl_sync(0xffffffffu, P, 31);
-        carryC = __shfl_sync(0xffffffffu, C, 31);
-      }
-      best = warp_max(best);
-      if (lane == 0) static_cast<double *>(a.D_out)[c.out_off + r] = best;
-    } else {
-      // terms k^-g scaled by K^g when g < 0 (so that every term is at most 1),
-      // exponent g ln k as a float pair: t = exp(-p) (1 - corr)
-      const bool neg = g < 0.0;
-      const float *lh = neg ? tb.lnq_hi : tb.lnk_hi, *ll = neg ? tb.lnq_lo : tb.lnk_lo;
-      const float gh = (float)g, gl = (float)(g - (double)gh);
-      const float invZf = neg ? (float)(invZ * exp(-g * tb.lnK)) : (float)invZ, invn = (float)inv_n;
-      float ch = 0.0f, cl = 0.0f, best = 0.0f;
-      for (uint32_t k0 = 1; k0 <= K; k0 += 32) {
-        const uint32_t k = k0 + lane;
-        const bool valid = k <= K;
-        float th = 0.0f, tl = 0.0f;
-        if (valid) {
-          const float l_h = lh[k], l_l = ll[k];
-          const float p = gh * l_h;
-          const float corr = fmaf(gh, l_h, -p) + fmaf(gh, l_l, gl * l_h);
-          th = expf(-p) * (1.0f - corr);
-        }
-        warp_scan_ff(th, tl, lane);
-        ff_add(th, tl, ch, cl);
-        const uint32_t C = warp_scan_u32(valid ? tz_bin(h, k) : 0u, lane) + carryC;
-        if (valid) best = fmaxf(best, fabsf(fmaf(th, invZf, tl * invZf) - (float)C * invn));
-        ch = __shfl_sync(0xffffffffu, th, 31);
-        cl = __shfl_sync(0xffffffffu, tl, 31);
-        carryC = __shfl_sync(0xffffffffu, C, 31);
-      }
-      best = warp_maxf(best);
-      if (lane == 0) static_cast<float *>(a.D_out)[c.out_off + r] = best;
+    const double D = tz_ks<F32>(tb, K, g, invZ, inv_n, lane, sX, [&](uint32_t k) { return tz_bin(h, k); });
+    if (lane == 0) {
+      if (F32)
+        static_cast<float *>(a.D_out)[c.out_off + r] = (float)D;
+      else
+        static_cast<double *>(a.D_out)[c.out_off + r] = D;
     }
     if (lane == 0 && a.A_out) a.A_out[c.out_off + r] = g;
     __syncwarp();
   }
 }
 
+// One data set of the truncated law, one block of 1024 threads: histogram of
+// the values (1..K; any other value latches the data error and gives NaN
+// outputs), then the first warp takes the log-sum (with the all-ones rule),
+// the fit (or the given exponent) and D.  out = (gamma, D, zeta_K(gamma)).
+template <bool F32>
+__global__ void __launch_bounds__(1024) tz_dataset_kernel(const int32_t *x, int64_t n, const TzTable *tab, int fit,
+                                                          double gamma, double *out, Counters *ctr) {
+  __shared__ uint32_t sC[kTzKMax + 1];
+  __shared__ double sX[64];
+  __shared__ int s_bad;
+  const TzTable &tb = *tab;
+  const uint32_t K = tb.K;
+  for (uint32_t i = threadIdx.x; i <= K; i += blockDim.x) sC[i] = 0u;
+  if (threadIdx.x < 64) sX[threadIdx.x] = exp2((double)threadIdx.x / 64.0);
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int32_t v = x[i];
+    if (v < 1 || (uint32_t)v > K)
+      s_bad = 1;
+    else
+      atomicAdd(&sC[v], 1u);
+  }
+  __syncthreads();
+  if (s_bad) {
+    if (threadIdx.x == 0) {
+      atomicOr(&ctr->status, kErrData);
+      out[0] = out[1] = out[2] = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    return;
+  }
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const double inv_n = 1.0 / (double)n;
+  double Ls = 0.0;
+  for (uint32_t k = 2 + lane; k <= K; k += 32) Ls += (double)sC[k] * tb.lnk[k];
+  Ls = warp_sum(Ls);
+  if ((int64_t)sC[1] == n) Ls += kLn2;
+  double g, Z, invZ;
+  if (fit) {
+    const int its = tz_fit(tb, Ls * inv_n, lane, g, Z, invZ);
+    if (its > kTzNewtonCap && lane == 0) atomicAdd(&ctr->newton_capped, 1ull);
+  } else {
+    g = gamma;
+    tz_zeta_at(tb, g, Z, invZ);
+  }
+  const double D = tz_ks<F32>(tb, K, g, invZ, inv_n, lane, sX, [&](uint32_t k) { return sC[k]; });
+  if (lane == 0) {
+    out[0] = g;
+    out[1] = D;
+    out[2] = Z;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_tz_dataset(const int32_t *x, int64_t n, const TzTable *tab, bool fit, double gamma, bool f32,
+                              double *out, Counters *ctr, cudaStream_t st) {
+  if (f32)
+    tz_dataset_kernel<true><<<1, 1024, 0, st>>>(x, n, tab, fit ? 1 : 0, gamma, out, ctr);
+  else
+    tz_dataset_kernel<false><<<1, 1024, 0, st>>>(x, n, tab, fit ? 1 : 0, gamma, out, ctr);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tz_setup(TzLaw *laws, int nlaws, TzTable *tables, int ntables, cudaStream_t st) {
   if (ntables > 0) {

@@ -105,4 +105,10 @@ struct TzLaunch {
 };
 cudaError_t launch_tz_replicates(const TzLaunch &a, bool f32, cudaStream_t st);
 
+// Fit (or the given exponent) and D of one data set (values 1..K, int32):
+// out = (gamma, D, zeta_K(gamma)); a value outside 1..K latches the data
+// error and writes NaN.
+cudaError_t launch_tz_dataset(const int32_t *x, int64_t n, const TzTable *tab, bool fit, double gamma, bool f32,
+                              double *out, Counters *ctr, cudaStream_t st);
+
 }  // namespace pl

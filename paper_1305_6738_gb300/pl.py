@@ -31,7 +31,8 @@ EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters",
            "pl_bootstrap_pvalue", "pl_fit_ks_noalloc", "pl_plan_cutoffs", "pl_plan_run",
            "pl_plan_destroy", "pl_autotune", "pl_set_split", "pl_server_create", "pl_server_submit",
            "pl_server_poll", "pl_server_now", "pl_server_load", "pl_server_destroy",
-           "pl_sample_truncated", "pl_ks_cutoffs_truncated"]
+           "pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_fit_ks_truncated", "pl_bespoke_cutoffs",
+           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup"]
 
 
 class pl_cell(ctypes.Structure):
@@ -111,8 +112,19 @@ _lib.pl_sample_truncated.argtypes = [_vp, ctypes.c_double, ctypes.c_uint64, ctyp
                                      ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, _vp, _vp]
 _lib.pl_ks_cutoffs_truncated.argtypes = [_vp, ctypes.POINTER(pl_tcell), ctypes.c_int, ctypes.c_uint64, _f64p,
                                          ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+_lib.pl_fit_ks_truncated.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
+                                     _f64p, _f64p, _vp]
+_lib.pl_bespoke_cutoffs.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint64,
+                                    ctypes.c_uint64, _f64p, ctypes.c_int, ctypes.c_int, _f64p, _f64p, _f64p, _f64p,
+                                    _vp]
+_lib.pl_bespoke_cutoffs_truncated.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64,
+                                              ctypes.c_uint64, ctypes.c_uint64, _f64p, ctypes.c_int, ctypes.c_int,
+                                              _f64p, _f64p, _f64p, _f64p, _vp]
+_lib.pl_cutoff_lookup.argtypes = [_vp, _f64p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, _vp,
+                                  ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, _vp]
 _lib.pl_server_destroy.restype = None
-for _f in ["pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+for _f in ["pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_fit_ks_truncated", "pl_bespoke_cutoffs",
+           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -275,6 +287,47 @@ class Context:
         if host is not None:
             return host.reshape(len(cells), qa.size)
         return cutoffs
+
+    def pl_fit_ks_truncated(self, x, K: int, gamma: float = float("nan"), prec: int = PL_FP64, stream=None):
+        """x: torch.int32 device tensor (values 1..K).  Returns (gamma, D); gamma NaN fits it."""
+        g, d = ctypes.c_double(), ctypes.c_double()
+        self._check(_lib.pl_fit_ks_truncated(self._h, _ptr(x), x.numel(), K, gamma, prec, ctypes.byref(g),
+                                             ctypes.byref(d), _stream_ptr(stream)))
+        return g.value, d.value
+
+    def pl_bespoke_cutoffs(self, x, xmin: int, R: int, seed: int, request_id: int, q, prec: int = PL_FP64,
+                           stream=None):
+        """Returns (alpha_hat, D, p, cutoffs[nq])."""
+        qa = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        cut = np.zeros(qa.size)
+        a, d, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(_lib.pl_bespoke_cutoffs(self._h, _ptr(x), x.numel(), xmin, R, seed, request_id,
+                                            qa.ctypes.data_as(_f64p), qa.size, prec, ctypes.byref(a),
+                                            ctypes.byref(d), ctypes.byref(p), cut.ctypes.data_as(_f64p),
+                                            _stream_ptr(stream)))
+        return a.value, d.value, p.value, cut
+
+    def pl_bespoke_cutoffs_truncated(self, x, K: int, R: int, seed: int, request_id: int, q,
+                                     prec: int = PL_FP64, stream=None):
+        """Returns (gamma_hat, D, p, cutoffs[nq])."""
+        qa = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        cut = np.zeros(qa.size)
+        g, d, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(_lib.pl_bespoke_cutoffs_truncated(self._h, _ptr(x), x.numel(), K, R, seed, request_id,
+                                                      qa.ctypes.data_as(_f64p), qa.size, prec, ctypes.byref(g),
+                                                      ctypes.byref(d), ctypes.byref(p), cut.ctypes.data_as(_f64p),
+                                                      _stream_ptr(stream)))
+        return g.value, d.value, p.value, cut
+
+    def pl_cutoff_lookup(self, grid_alpha, grid_n, table, nq: int, alpha, n, out, stream=None):
+        """grid_alpha, grid_n: host sequences; table, alpha (float64), n (int64), out: device tensors."""
+        ga = np.ascontiguousarray(np.asarray(grid_alpha, dtype=np.float64))
+        gn = np.ascontiguousarray(np.asarray(grid_n, dtype=np.int64))
+        self._check(_lib.pl_cutoff_lookup(self._h, ga.ctypes.data_as(_f64p), ga.size,
+                                          gn.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), gn.size, _ptr(table),
+                                          nq, _ptr(alpha), _ptr(n), alpha.numel(), _ptr(out),
+                                          _stream_ptr(stream)))
+        return out
 
     def pl_autotune(self, stream=None) -> int:
         v = ctypes.c_int64()

@@ -145,3 +145,27 @@ def test_atom_k20_gamma4_n10():
     assert round(atom, 4) == 0.0821
     D, _, _ = oracle.tz_cell(4.0, 20, 10, 10_000, seed=1, cell_id=5)
     assert oracle.quantiles(D, [0.9])[0] == atom
+
+
+@pytest.mark.parametrize("K", [2, 20, 1000])
+def test_negative_exponents(K):
+    """On a finite support the law is defined for every real exponent (the
+    fitted exponent of a small sample can be negative): zeta_K(-1) and
+    zeta_K(-2) are the sums of k and k^2, and draws at gamma = -1 follow
+    p(k) = 2k / (K(K+1))."""
+    _, z1 = oracle.tz_survival(-1.0, K)
+    assert z1 == pytest.approx(K * (K + 1) / 2, rel=1e-14)
+    _, z2 = oracle.tz_survival(-2.0, K)
+    assert z2 == pytest.approx(K * (K + 1) * (2 * K + 1) / 6, rel=1e-14)
+    D, G, nc = oracle.tz_cell(-1.5, K, 50, 20, seed=1, cell_id=3)
+    assert nc == 0 and np.all(np.isfinite(D))
+
+
+def test_draws_at_negative_exponent_chi_square():
+    stats = pytest.importorskip("scipy.stats")
+    K, n = 12, 120_000
+    x = oracle.tz_sample(-1.0, K, 5, 1, 0, 1, n).astype(np.int64)
+    cnt = np.bincount(x, minlength=K + 1)[1:]
+    p = np.arange(1, K + 1) / (K * (K + 1) / 2)
+    chi2 = ((cnt - n * p) ** 2 / (n * p)).sum()
+    assert stats.chi2.sf(chi2, K - 1) > 1e-4
