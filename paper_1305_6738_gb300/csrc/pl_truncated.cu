@@ -241,13 +241,15 @@ __device__ __forceinline__ double tz_rcp(double x) {
 // safeguarded by bisection on [gamma_j, gamma_j + 1/32].  A Newton step
 // below 2^-27 max(|gamma|, 1) is the last: the error left after it is below
 // the square of the step plus 1e-7 of it, under 1e-15.  Means at or beyond the
-// ends of [-64, 64] give the end.  Returns the number of polynomial
+// ends of [-64, 64] give the end, and so does a sample of only K (all_top:
+// an integer test, since the equation then has no finite root and E is flat
+// to the last bit near -64 for small K).  Returns the number of polynomial
 // evaluations (kTzNewtonCap + 1 if the cap was hit); *Z = zeta_K(gamma-hat),
 // *invZ its reciprocal.
-__device__ __forceinline__ int tz_fit(const TzTable &tb, double mbar, int lane, double &g_out, double &Z,
-                                      double &invZ) {
+__device__ __forceinline__ int tz_fit(const TzTable &tb, double mbar, bool all_top, int lane, double &g_out,
+                                      double &Z, double &invZ) {
   const double *E = tb.E;
-  if (!(mbar < E[0])) {
+  if (all_top || !(mbar < E[0])) {
     g_out = kTzGammaLo;
     Z = tb.node[0];
     invZ = tb.node[kTzInvA0];
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(kTzWarps * 32, PL_TZ_MIN_BLOCKS) tz_replicate_
     Ls = warp_sum(Ls);
     if ((c12 & 0xffffu) == n) Ls += kLn2;
     double g, Z, invZ;
-    const int its = tz_fit(tb, Ls * inv_n, lane, g, Z, invZ);
+    const int its = tz_fit(tb, Ls * inv_n, tz_bin(h, K) == n, lane, g, Z, invZ);
     if (its > kTzNewtonCap && lane == 0) atomicAdd(&a.ctr->newton_capped, 1ull);
     const double D = tz_ks<F32>(tb, K, g, invZ, inv_n, lane, sX, [&](uint32_t k) { return tz_bin(h, k); });
     if (lane == 0) {
@@ -506,7 +508,7 @@ __global__ void __launch_bounds__(1024) tz_dataset_kernel(const int32_t *x, int6
   if ((int64_t)sC[1] == n) Ls += kLn2;
   double g, Z, invZ;
   if (fit) {
-    const int its = tz_fit(tb, Ls * inv_n, lane, g, Z, invZ);
+    const int its = tz_fit(tb, Ls * inv_n, (int64_t)sC[K] == n, lane, g, Z, invZ);
     if (its > kTzNewtonCap && lane == 0) atomicAdd(&ctr->newton_capped, 1ull);
   } else {
     g = gamma;
