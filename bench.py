@@ -488,6 +488,161 @@ def run_truncated(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- bespoke cutoffs
+BESPOKE_R = 10_000
+BESPOKE_Q = [0.90, 0.95, 0.99]
+LOOKUPS = 1_000_000
+
+
+def bespoke_cpu_baseline(reqs, data, sample_reps: int, threads: int) -> dict:
+    """The oracle composition per request (fit, D, the simulation at the
+    fitted exponent and its quantiles) on sample_reps replicates, extrapolated
+    linearly to BESPOKE_R replicates per request."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    t_full = wall = 0.0
+    for r, x in zip(reqs, data):
+        xu = np.asarray(x, dtype=np.uint64)
+        t0 = time.perf_counter()
+        if r.truncated:
+            g = oracle.tz_mle(xu, r.xmin_or_K)
+            oracle.tz_ks(xu, r.xmin_or_K, g)
+            t1 = time.perf_counter()
+            oracle.tz_cell(g, r.xmin_or_K, r.n, sample_reps, seed=1, cell_id=r.request_id, purpose=1,
+                           threads=threads)
+        else:
+            a = oracle.mle(xu, 1)
+            oracle.ks(xu, 1, a)
+            t1 = time.perf_counter()
+            oracle.cell(a, 1, r.n, sample_reps, seed=1, cell_id=r.request_id, purpose=1, threads=threads)
+        t2 = time.perf_counter()
+        wall += t2 - t0
+        t_full += (t1 - t0) + (t2 - t1) / sample_reps * BESPOKE_R
+    return {"value": len(reqs) / t_full, "wall_s": wall,
+            "sample": f"every request's fit and D, and {sample_reps} of its {BESPOKE_R:,} bespoke replicates "
+                      f"(extrapolated linearly)"}
+
+
+def run_bespoke(args):
+    """64 data sets per step, each through pl_bespoke_cutoffs(_truncated)."""
+    import numpy as np
+    import torch
+    from paper_1305_6738_gb300 import pl
+    reqs = inputs.bespoke_requests()
+    threads = os.cpu_count() or 1
+    config = {"workload": f"bespoke cutoffs: {len(reqs)} data sets (32 untruncated alpha~U(1.6,3), n in "
+                          f"[1e2,1e4]; 32 truncated K in {{20,100,1000}}, gamma~U(0.25,3), n in [10,1e4]), "
+                          f"{BESPOKE_R:,} simulated replicates each, q=0.9/0.95/0.99; plus {LOOKUPS:,} lookups "
+                          f"in the Table 1 grid",
+              "requests_per_step": len(reqs), "replicates_per_step": len(reqs) * BESPOKE_R,
+              "draws_per_step": sum(r.n for r in reqs) * BESPOKE_R, "precision_form": args.precision,
+              "l2": "inputs far below L2; calls synchronise (host outputs)", "parallelism": "one GPU"}
+    ctx = pl.Context(0)
+    prec = pl.PL_FP32_BULK if args.precision == "fp32-bulk" else pl.PL_FP64
+    buf = torch.empty(max(r.n for r in reqs), dtype=torch.int64, device="cuda")
+    data, dev = [], []
+    for r in reqs:
+        if r.truncated:
+            ctx.pl_sample_truncated(r.exponent, r.xmin_or_K, 4, r.request_id, inputs.PURPOSE_TESTDATA, 0, 1, r.n,
+                                    buf)
+        else:
+            ctx.pl_sample(r.exponent, 1, 4, r.request_id, inputs.PURPOSE_TESTDATA, 0, 1, r.n, buf)
+        x = buf[:r.n].clamp(max=inputs.INT32_MAX).to(torch.int32)
+        dev.append(x.clone())
+        data.append(x.cpu().numpy())
+    pinned = [torch.from_numpy(x).pin_memory() for x in data]
+
+    def one(r, x):
+        if r.truncated:
+            return ctx.pl_bespoke_cutoffs_truncated(x, r.xmin_or_K, BESPOKE_R, 1, r.request_id, BESPOKE_Q, prec)
+        return ctx.pl_bespoke_cutoffs(x, 1, BESPOKE_R, 1, r.request_id, BESPOKE_Q, prec)
+
+    for _ in range(args.warmup):
+        for r, x in zip(reqs, dev):
+            one(r, x)
+    launches0 = ctx.pl_trace()["launches"]
+    sampler = ClockSampler(gpu_query_id(0))
+    torch.cuda.synchronize()
+    step_s, lat = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for r, x in zip(reqs, dev):
+            t1 = time.perf_counter()
+            one(r, x)
+            lat.append(time.perf_counter() - t1)
+        step_s.append(time.perf_counter() - t0)
+    clocks = sampler.stop()
+    launches = ctx.pl_trace()["launches"] - launches0
+    total_s = sum(step_s)
+    value = len(reqs) * args.steps / total_s
+    draws = config["draws_per_step"]
+    # end to end: each request's data copied from pinned host memory inside the timed region
+    e2e = []
+    for _ in range(max(1, args.steps // 2)):
+        t0 = time.perf_counter()
+        for r, h in zip(reqs, pinned):
+            one(r, h.to("cuda", non_blocking=True))
+        e2e.append(time.perf_counter() - t0)
+    e2e_value = len(reqs) / statistics.mean(e2e)
+    # lookups in a tabulated grid (Table 1's exponents and sizes, 2,000 replicates per cell)
+    GA, GN = list(inputs.TABLE1_GAMMAS), list(inputs.TABLE1_NS)
+    cells = [pl.Cell(a, 1, n, 2000, 100 * i + k) for i, a in enumerate(GA) for k, n in enumerate(GN)]
+    table = torch.empty(len(cells) * len(BESPOKE_Q), dtype=torch.float64, device="cuda")
+    ctx.pl_ks_cutoffs(cells, 1, BESPOKE_Q, prec, cutoffs=table)
+    g = torch.Generator(device="cpu").manual_seed(8)
+    qa = (1.25 + 2.75 * torch.rand(LOOKUPS, generator=g, dtype=torch.float64)).cuda()
+    qn = torch.exp(math.log(10) + (math.log(50000) - math.log(10)) * torch.rand(LOOKUPS, generator=g,
+                                                                               dtype=torch.float64)).long().cuda()
+    out = torch.empty(LOOKUPS * len(BESPOKE_Q), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        ctx.pl_cutoff_lookup(GA, GN, table, len(BESPOKE_Q), qa, qn, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        ctx.pl_cutoff_lookup(GA, GN, table, len(BESPOKE_Q), qa, qn, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lk_ms = e0.elapsed_time(e1) / 10
+    lk_bytes = LOOKUPS * (8 + 8 + 8 * len(BESPOKE_Q))
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    props = torch.cuda.get_device_properties(0)
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    mul_peak = props.multi_processor_count * MUL_LANES_PER_SM * sm_max * 1e6 / 1e9
+    achieved = MUL_PER_DRAW * draws * args.steps / total_s / 1e9
+    lat.sort()
+    line = {"metric": METRIC, "value": value, "unit": "requests/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == pl.PL_FP32_BULK else "f64",
+            "data": "synthetic (power-law data from the method's sampler, stream tag 2)", "config": config,
+            "replicates_per_s": value * BESPOKE_R, "samples_per_s": draws * args.steps / total_s,
+            "latency_ms": {"p50": 1000 * lat[len(lat) // 2], "p99": 1000 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "max": 1000 * lat[-1]},
+            "e2e": {"value": e2e_value, "unit": "requests/s",
+                    "h2d_bytes_per_step": sum(4 * r.n for r in reqs),
+                    "d2h_bytes_per_step": len(reqs) * (3 + len(BESPOKE_Q)) * 8},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": mul_peak, "unit": "Gmul/s (32x32->64)",
+                         "frac": achieved / mul_peak, "traffic": None,
+                         "kernel": "whole step (sampler, finisher and truncated replicate kernels, host gaps included)",
+                         "peak_basis": f"{props.multi_processor_count} SMs x {MUL_LANES_PER_SM} multiply lanes x "
+                                       f"{sm_max:.0f} MHz; {MUL_PER_DRAW} multiplies per draw"},
+            "lookup": {"queries_per_s": LOOKUPS / (lk_ms / 1000), "kernel_ms": lk_ms,
+                       "roofline": {"bound": "hbm", "achieved": lk_bytes / (lk_ms / 1000) / 1e9, "peak": hbm,
+                                    "unit": "GB/s", "frac": lk_bytes / (lk_ms / 1000) / 1e9 / hbm,
+                                    "traffic": None,
+                                    "note": "algorithmic bytes: query (16 B) in, nq cutoffs out"}},
+            "clocks": clocks}
+    if not args.no_cpu_baseline:
+        cb = bespoke_cpu_baseline(reqs, data, max(1, threads), threads)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": "requests/s", "cores": threads, "kind": "oracle",
+                                "sample": cb["sample"]}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def replica_seed(rank: int) -> int:
     """Replicas (one process per GPU) draw independent Philox streams: the key
     is the base seed plus the rank.  No data crosses ranks."""
@@ -522,14 +677,16 @@ def main():
     ap.add_argument("--replicates", type=int, default=100_000,
                     help="replicates per cell (smaller values for profiler captures only)")
     ap.add_argument("--workload", choices=["sweep", "small", "large-n", "batched", "serving", "table1",
-                                           "truncated"],
+                                           "truncated", "bespoke"],
                     default="sweep",
                     help="sweep: the 90-cell table (the benchmark line); small: alpha=2.5, n=100, "
                          "10,000 replicates; large-n: alpha=2, n=1e6, 10,000 replicates; batched: "
                          "4,096 uneven instances x 2,000 replicates in one graph-captured launch; "
                          "serving: Poisson fit requests at 200/s through the serving engine; "
                          "table1: one run of the paper's Table 1 (120 cells x 50,000 replicates); "
-                         "truncated: one run of Tables 2-6 (truncated law, 900 cells x 50,000 replicates)")
+                         "truncated: one run of Tables 2-6 (truncated law, 900 cells x 50,000 replicates); "
+                         "bespoke: 64 data sets (both laws), each fitted with its own cutoffs from 10,000 "
+                         "simulated replicates, plus 10^6 lookups in a tabulated grid")
     ap.add_argument("--tz-replicates", type=int, default=50_000,
                     help="truncated: replicates per cell (smaller values for profiler captures only)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: measured seconds")
@@ -541,6 +698,8 @@ def main():
         return run_serving(args)
     if args.workload == "truncated":
         return run_truncated(args)
+    if args.workload == "bespoke":
+        return run_bespoke(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -9,6 +9,7 @@ drawn by the method's own sampler with stream tag 2 (test data).
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -155,3 +156,30 @@ def tables2to6_cells(replicates: int = 50_000, Ks=TZ_KS) -> list[TzCell]:
     seed r + 1)."""
     return [TzCell(g, K, n, replicates, 10000 * TZ_KS.index(K) + 100 * i + j)
             for K in Ks for i, g in enumerate(TZ_GAMMAS) for j, n in enumerate(TZ_NS)]
+
+
+@dataclass
+class BespokeRequest:
+    request_id: int
+    truncated: bool
+    exponent: float       # alpha (untruncated) or gamma (truncated) of the data's law
+    xmin_or_K: int        # xmin (untruncated) or K (truncated)
+    n: int
+
+
+def bespoke_requests(count: int = 64, seed: int = 7) -> list[BespokeRequest]:
+    """Data sets for the bespoke-cutoff workload: half from the untruncated law
+    (alpha ~ U(1.6, 3.0), xmin = 1, n log-uniform in [100, 10^4]), half from
+    the truncated law (K in {20, 100, 1000}, gamma ~ U(0.25, 3.0), n
+    log-uniform in [10, 10^4]); the data themselves are drawn by the method's
+    sampler with stream tag 2 (cell id = request id)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        if i % 2 == 0:
+            n = int(round(math.exp(rng.uniform(math.log(100), math.log(10_000)))))
+            out.append(BespokeRequest(i, False, float(rng.uniform(1.6, 3.0)), 1, n))
+        else:
+            n = int(round(math.exp(rng.uniform(math.log(10), math.log(10_000)))))
+            out.append(BespokeRequest(i, True, float(rng.uniform(0.25, 3.0)), int(rng.choice([20, 100, 1000])), n))
+    return out
