@@ -334,10 +334,10 @@ def tz_source_hash() -> str:
 
 
 # DRAM bytes per replicate of the truncated replicate kernel from one
-# one-pass ncu capture of a full Tables 2-6 launch (55.6 MB read + 147.1 MB
+# one-pass ncu capture of a full Tables 2-6 launch (57.2 MB read + 148.3 MB
 # written for 45,000,000 replicates: the 4-byte D of each replicate plus the
 # tables), keyed by the hash of its sources (null once they change).
-TZ_TRAFFIC_PER_REPLICATE = {"324049b563c2cca9": (55621888 + 147120384) / 45e6}
+TZ_TRAFFIC_PER_REPLICATE = {"bb5f053fedd20812": (57234944 + 148284928) / 45e6}
 
 
 def tz_cpu_oracle_rate(cells, sample_reps: int, threads: int) -> dict:

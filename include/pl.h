@@ -356,7 +356,8 @@ pl_status pl_bespoke_cutoffs_truncated(pl_ctx *ctx, const int32_t *x_dev,
  * query (alpha_dev[m], n_dev[m]) the result is bilinear in (alpha, ln n)
  * between the four surrounding cells, clamped to the grid's edges (so equal
  * to the cell's value at a grid point).  grid_alpha (host, strictly
- * increasing, na >= 1), grid_n (host, strictly increasing, >= 1, nn >= 1);
+ * increasing, 1 <= na <= 1024), grid_n (host, strictly increasing, >= 1,
+ * 1 <= nn <= 1024);
  * table_dev: device double[na * nn * nq]; alpha_dev, n_dev: device double /
  * int64 [nquery]; out_dev: device double[nquery * nq], row per query.
  * Stream ordered, no synchronisation.  Errors: PL_EINVAL. */

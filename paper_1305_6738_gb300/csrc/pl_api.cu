@@ -1432,7 +1432,8 @@ pl_status pl_cutoff_lookup(pl_ctx *ctx, const double *grid_alpha, int na, const 
                            const double *table_dev, int nq, const double *alpha_dev, const int64_t *n_dev,
                            int64_t nquery, double *out_dev, void *stream) {
   if (pl_status s = check_ctx(ctx)) return s;
-  if (!grid_alpha || !grid_n || na < 1 || nn < 1 || nq < 1 || nquery < 0 || !table_dev ||
+  if (!grid_alpha || !grid_n || na < 1 || nn < 1 || na > kLookupGridMax || nn > kLookupGridMax || nq < 1 ||
+      nquery < 0 || !table_dev ||
       (nquery > 0 && (!alpha_dev || !n_dev || !out_dev)))
     return fail(ctx, PL_EINVAL, "pl_cutoff_lookup: bad arguments");
   for (int i = 0; i < na; ++i)
