@@ -633,7 +633,9 @@ def run_bespoke(args):
                        "roofline": {"bound": "hbm", "achieved": lk_bytes / (lk_ms / 1000) / 1e9, "peak": hbm,
                                     "unit": "GB/s", "frac": lk_bytes / (lk_ms / 1000) / 1e9 / hbm,
                                     "traffic": None,
-                                    "note": "algorithmic bytes: query (16 B) in, nq cutoffs out"}},
+                                    "note": "algorithmic bytes: query (16 B) in, nq cutoffs out; the kernel is "
+                                            "bound by binary64 arithmetic (one log and two divisions per query), "
+                                            "not by memory"}},
             "clocks": clocks}
     if not args.no_cpu_baseline:
         cb = bespoke_cpu_baseline(reqs, data, max(1, threads), threads)
