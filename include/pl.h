@@ -367,6 +367,34 @@ pl_status pl_cutoff_lookup(pl_ctx *ctx, const double *grid_alpha, int na,
                            const double *alpha_dev, const int64_t *n_dev,
                            int64_t nquery, double *out_dev, void *stream);
 
+/* Lower end by KS minimisation (the procedure of Clauset, Shalizi & Newman
+ * with which the paper's tables are used, Section 3): every candidate x_min
+ * among the smallest max_candidates distinct values of the sample gets the
+ * MLE of its tail {x >= x_min} (Eq. 2 with the Hurwitz normaliser; the
+ * all-equal rule when the tail is one value) and the tail's D at that fit
+ * (Eq. 3); the estimate is the candidate of smallest D (the first on ties).
+ * Candidates with fewer than min_tail tail values get D = NaN and are not
+ * chosen.  x_dev: device int32[n] (values >= 1, 1 <= n <= 2^31 - 1).
+ * out_host: host pl_xmin_result (xmin = 0 and NaN fit if no candidate
+ * qualifies).  cand_*_dev: NULL or device arrays of max_candidates entries
+ * receiving each candidate's x_min (ascending), alpha-hat, D and tail size
+ * (entries beyond `candidates` untouched).  Synchronises `stream`.  The work
+ * grows as candidates x distinct values.  Errors: PL_EINVAL (arguments, a
+ * value < 1; 1 <= max_candidates <= 2^24, min_tail >= 1). */
+typedef struct {
+  uint64_t xmin;
+  double alpha_hat;
+  double D;
+  int64_t n_tail;
+  int64_t candidates;
+} pl_xmin_result;
+
+pl_status pl_estimate_xmin(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
+                           int64_t max_candidates, int64_t min_tail,
+                           pl_xmin_result *out_host, uint64_t *cand_xmin_dev,
+                           double *cand_alpha_dev, double *cand_D_dev,
+                           int64_t *cand_ntail_dev, void *stream);
+
 /* Fit and KS distance of one data set with no device allocation at all.
  * The paper has no counterpart: this is an engineering variant of
  * pl_fit_mle + pl_ks_stat for callers that cannot let a library call

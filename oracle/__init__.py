@@ -98,6 +98,8 @@ def _load():
                                         c.c_uint32, c.c_uint32, _f64p, _f64p]
         lib.or_tz_cell.argtypes = [c.c_double, c.c_int64, c.c_int64, c.c_uint64, c.c_uint32,
                                    c.c_uint32, c.c_uint32, c.c_int64, c.c_int, _f64p, _f64p, _i64p]
+        lib.or_estimate_xmin.argtypes = [_u64p, c.c_int64, c.c_int64, c.c_int64, c.c_int, _u64p, _f64p, _f64p,
+                                         _i64p, _i64p, _i64p]
         _lib = lib
         return lib
 
@@ -325,3 +327,19 @@ def cutoff_lookup(grid_alpha, grid_n, table: np.ndarray, alpha: float, n: int) -
         v01, v11 = table[ia, k1, j], table[ia1, k1, j]
         out[j] = (1.0 - wa) * ((1.0 - wn) * v00 + wn * v01) + wa * ((1.0 - wn) * v10 + wn * v11)
     return out
+
+
+def estimate_xmin(x: np.ndarray, max_candidates: int = 1000, min_tail: int = 10, threads: int = 0):
+    """Lower end by KS minimisation over the smallest max_candidates distinct
+    values: (best index or -1, xmin[], alpha_hat[], D[], n_tail[]) per candidate."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    xm = np.zeros(max_candidates, dtype=np.uint64)
+    a = np.zeros(max_candidates)
+    d = np.zeros(max_candidates)
+    nt = np.zeros(max_candidates, dtype=np.int64)
+    nc, best = ctypes.c_int64(), ctypes.c_int64()
+    _check(_load().or_estimate_xmin(_ptr(x, _u64p), x.size, max_candidates, min_tail, threads, _ptr(xm, _u64p),
+                                    _ptr(a, _f64p), _ptr(d, _f64p), _ptr(nt, _i64p), ctypes.byref(nc),
+                                    ctypes.byref(best)), "estimate_xmin")
+    m = nc.value
+    return best.value, xm[:m], a[:m], d[:m], nt[:m]

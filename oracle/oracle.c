@@ -667,3 +667,66 @@ int or_tz_cell(double gamma, int64_t K, int64_t n, uint64_t seed, uint32_t cell,
   (void)nthreads;
   return fails ? OR_ENOMEM : OR_OK;
 }
+
+/* ======================================================================== */
+/* Lower end by KS minimisation (the procedure of Clauset, Shalizi & Newman,
+ * which the paper's tables are used with, Section 3): for every candidate
+ * x_min among the sample's distinct values (the smallest max_candidates of
+ * them), fit alpha-hat on the tail {x >= x_min} (Eq. 2 with the Hurwitz
+ * normaliser) and compute D of the tail at its fit (Eq. 3); the estimate is
+ * the candidate of smallest D (the first on ties).  Candidates whose tail
+ * has fewer than min_tail values get D = NaN and are not chosen.
+ * Outputs per candidate (arrays of max_candidates): xmin, alpha-hat, D, tail
+ * size; *ncand the number of candidates, *best the chosen one (-1 if none). */
+int or_estimate_xmin(const uint64_t *x, int64_t n, int64_t max_candidates, int64_t min_tail, int nthreads,
+                     uint64_t *cand_xmin, double *cand_alpha, double *cand_D, int64_t *cand_ntail,
+                     int64_t *ncand, int64_t *best) {
+  if (n < 1 || max_candidates < 1 || min_tail < 1) return OR_EINVAL;
+  uint64_t *s = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+  int64_t *first = (int64_t *)malloc((size_t)max_candidates * sizeof(int64_t));
+  if (!s || !first) {
+    free(s);
+    free(first);
+    return OR_ENOMEM;
+  }
+  memcpy(s, x, (size_t)n * sizeof(uint64_t));
+  qsort(s, (size_t)n, sizeof(uint64_t), or_cmp_u64);
+  int64_t m = 0;
+  for (int64_t i = 0; i < n && m < max_candidates; ++i)
+    if (i == 0 || s[i] != s[i - 1]) first[m++] = i;
+  int fails = 0;
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : fails)
+#endif
+  for (int64_t j = 0; j < m; ++j) {
+    const uint64_t xm = s[first[j]];
+    const int64_t nt = n - first[j];
+    cand_xmin[j] = xm;
+    cand_ntail[j] = nt;
+    cand_alpha[j] = NAN;
+    cand_D[j] = NAN;
+    if (nt < min_tail) continue;
+    double a = 0.0, d = 0.0;
+    int st = or_mle(s + first[j], nt, xm, &a);
+    if (st != OR_OK && st != OR_ENOCONV) {
+      fails += 1;
+      continue;
+    }
+    if (or_ks(s + first[j], nt, xm, a, &d) != OR_OK) {
+      fails += 1;
+      continue;
+    }
+    cand_alpha[j] = a;
+    cand_D[j] = d;
+  }
+  (void)nthreads;
+  int64_t b = -1;
+  for (int64_t j = 0; j < m; ++j)
+    if (!isnan(cand_D[j]) && (b < 0 || cand_D[j] < cand_D[b])) b = j;
+  *ncand = m;
+  *best = b;
+  free(s);
+  free(first);
+  return fails ? OR_ENOMEM : OR_OK;
+}

@@ -20,6 +20,7 @@
 #include "pl_kernels.cuh"
 #include "pl_truncated.cuh"
 #include "pl_lookup.cuh"
+#include "pl_xmin.cuh"
 
 using namespace pl;
 
@@ -1459,6 +1460,54 @@ pl_status pl_cutoff_lookup(pl_ctx *ctx, const double *grid_alpha, int na, const 
   PL_CUDA(cudaMemcpyAsync(gn, grid_n, sizeof(int64_t) * nn, cudaMemcpyHostToDevice, st));
   PL_CUDA(launch_lookup(ga, na, gn, nn, table_dev, nq, alpha_dev, n_dev, nquery, out_dev, st));
   ctx->launches += nquery > 0 ? 1 : 0;
+  return PL_OK;
+}
+
+pl_status pl_estimate_xmin(pl_ctx *ctx, const int32_t *x_dev, int64_t n, int64_t max_candidates, int64_t min_tail,
+                           pl_xmin_result *out_host, uint64_t *cand_xmin_dev, double *cand_alpha_dev,
+                           double *cand_D_dev, int64_t *cand_ntail_dev, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!x_dev || n < 1 || n > INT32_MAX || max_candidates < 1 || max_candidates > (1ll << 24) || min_tail < 1 ||
+      !out_host)
+    return fail(ctx, PL_EINVAL, "pl_estimate_xmin: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t P = next_pow2((uint64_t)n);
+  auto lay = [&](Carver &cv, uint64_t *&spill, uint64_t *&vals, uint32_t *&cnts, int64_t *&S, double *&Lt,
+                 int64_t *&d, uint64_t *&cx, double *&ca, double *&cD, int64_t *&cn, XminOut *&out) {
+    spill = cv.take<uint64_t>(P);
+    vals = cv.take<uint64_t>(n);
+    cnts = cv.take<uint32_t>(n);
+    S = cv.take<int64_t>(n + 1);
+    Lt = cv.take<double>(n);
+    d = cv.take<int64_t>(1);
+    cx = cand_xmin_dev ? cand_xmin_dev : cv.take<uint64_t>(max_candidates);
+    ca = cand_alpha_dev ? cand_alpha_dev : cv.take<double>(max_candidates);
+    cD = cand_D_dev ? cand_D_dev : cv.take<double>(max_candidates);
+    cn = cand_ntail_dev ? cand_ntail_dev : cv.take<int64_t>(max_candidates);
+    out = cv.take<XminOut>(1);
+  };
+  Carver cv;
+  uint64_t *spill, *vals, *cx;
+  uint32_t *cnts;
+  int64_t *S, *d, *cn;
+  double *Lt, *ca, *cD;
+  XminOut *out;
+  lay(cv, spill, vals, cnts, S, Lt, d, cx, ca, cD, cn, out);
+  if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+  cv.base = ctx->ws;
+  cv.off = 0;
+  lay(cv, spill, vals, cnts, S, Lt, d, cx, ca, cD, cn, out);
+  PL_CUDA(launch_xmin(x_dev, n, spill, (uint32_t)std::min<uint64_t>(P, 0xffffffffull), vals, cnts, S, Lt, d,
+                      max_candidates, min_tail, cx, ca, cD, cn, out, ctx->ctr, st));
+  ctx->launches += 3;
+  XminOut o{};
+  PL_CUDA(cudaMemcpyAsync(&o, out, sizeof o, cudaMemcpyDeviceToHost, st));
+  if (pl_status s = read_status(ctx, st)) return s;
+  out_host->xmin = o.xmin;
+  out_host->alpha_hat = o.alpha_hat;
+  out_host->D = o.D;
+  out_host->n_tail = o.n_tail;
+  out_host->candidates = o.candidates;
   return PL_OK;
 }
 

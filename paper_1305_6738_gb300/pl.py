@@ -32,7 +32,7 @@ EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters",
            "pl_plan_destroy", "pl_autotune", "pl_set_split", "pl_server_create", "pl_server_submit",
            "pl_server_poll", "pl_server_now", "pl_server_load", "pl_server_destroy",
            "pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_fit_ks_truncated", "pl_bespoke_cutoffs",
-           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup"]
+           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin"]
 
 
 class pl_cell(ctypes.Structure):
@@ -43,6 +43,11 @@ class pl_cell(ctypes.Structure):
 class pl_tcell(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("K", ctypes.c_uint64), ("n", ctypes.c_int64),
                 ("replicates", ctypes.c_int64), ("cell_id", ctypes.c_uint64)]
+
+
+class pl_xmin_result(ctypes.Structure):
+    _fields_ = [("xmin", ctypes.c_uint64), ("alpha_hat", ctypes.c_double), ("D", ctypes.c_double),
+                ("n_tail", ctypes.c_int64), ("candidates", ctypes.c_int64)]
 
 
 class pl_counter_info(ctypes.Structure):
@@ -122,9 +127,11 @@ _lib.pl_bespoke_cutoffs_truncated.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c
                                               _f64p, _f64p, _f64p, _f64p, _vp]
 _lib.pl_cutoff_lookup.argtypes = [_vp, _f64p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, _vp,
                                   ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, _vp]
+_lib.pl_estimate_xmin.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.POINTER(pl_xmin_result), _vp, _vp, _vp, _vp, _vp]
 _lib.pl_server_destroy.restype = None
 for _f in ["pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_fit_ks_truncated", "pl_bespoke_cutoffs",
-           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -328,6 +335,16 @@ class Context:
                                           nq, _ptr(alpha), _ptr(n), alpha.numel(), _ptr(out),
                                           _stream_ptr(stream)))
         return out
+
+    def pl_estimate_xmin(self, x, max_candidates: int = 1000, min_tail: int = 10, cand_xmin=None,
+                         cand_alpha=None, cand_D=None, cand_ntail=None, stream=None) -> dict:
+        """x: torch.int32 device tensor.  Returns the pl_xmin_result fields; cand_* are
+        optional device tensors (uint64/int64, float64, float64, int64) of max_candidates."""
+        r = pl_xmin_result()
+        self._check(_lib.pl_estimate_xmin(self._h, _ptr(x), x.numel(), max_candidates, min_tail, ctypes.byref(r),
+                                          _ptr(cand_xmin), _ptr(cand_alpha), _ptr(cand_D), _ptr(cand_ntail),
+                                          _stream_ptr(stream)))
+        return {k: getattr(r, k) for k, _ in pl_xmin_result._fields_}
 
     def pl_autotune(self, stream=None) -> int:
         v = ctypes.c_int64()
