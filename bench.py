@@ -606,6 +606,30 @@ def run_bespoke(args):
     torch.cuda.synchronize()
     lk_ms = e0.elapsed_time(e1) / 10
     lk_bytes = LOOKUPS * (8 + 8 + 8 * len(BESPOKE_Q))
+    # lower end by KS minimisation on a large data set: a flat body below 10 and a
+    # power law (alpha = 2.5) from 10, 10^6 values, the smallest 1,000 distinct
+    # values as candidates
+    rngx = np.random.default_rng(12)
+    tail = torch.empty(700_000, dtype=torch.int64, device="cuda")
+    ctx.pl_sample(2.5, 10, 4, 9999, inputs.PURPOSE_TESTDATA, 0, 1, 700_000, tail)
+    xm_host = np.concatenate([rngx.integers(1, 10, 300_000),
+                              tail.clamp(max=inputs.INT32_MAX).cpu().numpy()]).astype(np.int32)
+    xm_dev = torch.from_numpy(xm_host).cuda()
+    ctx.pl_estimate_xmin(xm_dev, 1000, 10)
+    xm_s = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        xm_res = ctx.pl_estimate_xmin(xm_dev, 1000, 10)
+        xm_s.append(time.perf_counter() - t0)
+    xmin_line = {"n": int(xm_host.size), "candidates": xm_res["candidates"], "estimate": xm_res["xmin"],
+                 "alpha_hat": xm_res["alpha_hat"], "ms_per_estimate": 1000 * statistics.mean(xm_s)}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.estimate_xmin(xm_host.astype(np.uint64), 1000, 10, threads=threads)
+        xmin_line["cpu_baseline_ms"] = 1000 * (time.perf_counter() - t0)
+        xmin_line["cpu_cores"] = threads
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs") or 6800.0)
     props = torch.cuda.get_device_properties(0)
@@ -636,6 +660,7 @@ def run_bespoke(args):
                                     "note": "algorithmic bytes: query (16 B) in, nq cutoffs out; the kernel is "
                                             "bound by binary64 arithmetic (one log and two divisions per query), "
                                             "not by memory"}},
+            "xmin_estimate": xmin_line,
             "clocks": clocks}
     if not args.no_cpu_baseline:
         cb = bespoke_cpu_baseline(reqs, data, max(1, threads), threads)
@@ -688,7 +713,8 @@ def main():
                          "table1: one run of the paper's Table 1 (120 cells x 50,000 replicates); "
                          "truncated: one run of Tables 2-6 (truncated law, 900 cells x 50,000 replicates); "
                          "bespoke: 64 data sets (both laws), each fitted with its own cutoffs from 10,000 "
-                         "simulated replicates, plus 10^6 lookups in a tabulated grid")
+                         "simulated replicates, plus 10^6 lookups in a tabulated grid and one lower-end "
+                         "estimate on 10^6 values")
     ap.add_argument("--tz-replicates", type=int, default=50_000,
                     help="truncated: replicates per cell (smaller values for profiler captures only)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: measured seconds")
