@@ -262,7 +262,9 @@ __global__ void __launch_bounds__(kXWarps * 32) xmin_cand_kernel(const uint64_t 
     const uint64_t v = vals[i];
     const double F1 = 1.0 - survival(a, Z, v);
     best = fmax(best, fabs(F1 - (double)(nt - S[i + 1]) * inv_nt));
-    if (i > j) {
+    // t = v - 1 matters only after a gap: when the previous distinct value is
+    // v - 1 the check there is the previous value's own
+    if (i > j && vals[i - 1] != v - 1) {
       const double F0 = 1.0 - survival(a, Z, v - 1);
       best = fmax(best, fabs(F0 - (double)(nt - S[i]) * inv_nt));
     }
