@@ -1472,8 +1472,11 @@ pl_status pl_estimate_xmin(pl_ctx *ctx, const int32_t *x_dev, int64_t n, int64_t
     return fail(ctx, PL_EINVAL, "pl_estimate_xmin: bad arguments");
   cudaStream_t st = (cudaStream_t)stream;
   const uint64_t P = next_pow2((uint64_t)n);
-  auto lay = [&](Carver &cv, uint64_t *&spill, uint64_t *&vals, uint32_t *&cnts, int64_t *&S, double *&Lt,
-                 int64_t *&d, uint64_t *&cx, double *&ca, double *&cD, int64_t *&cn, XminOut *&out) {
+  auto lay = [&](Carver &cv, uint32_t *&ghist, unsigned long long *&nsp, uint64_t *&spill, uint64_t *&vals,
+                 uint32_t *&cnts, int64_t *&S, double *&Lt, int64_t *&d, uint64_t *&cx, double *&ca, double *&cD,
+                 int64_t *&cn, XminOut *&out) {
+    ghist = cv.take<uint32_t>(kXHistBins);
+    nsp = cv.take<unsigned long long>(1);
     spill = cv.take<uint64_t>(P);
     vals = cv.take<uint64_t>(n);
     cnts = cv.take<uint32_t>(n);
@@ -1487,19 +1490,21 @@ pl_status pl_estimate_xmin(pl_ctx *ctx, const int32_t *x_dev, int64_t n, int64_t
     out = cv.take<XminOut>(1);
   };
   Carver cv;
+  uint32_t *ghist;
+  unsigned long long *nsp;
   uint64_t *spill, *vals, *cx;
   uint32_t *cnts;
   int64_t *S, *d, *cn;
   double *Lt, *ca, *cD;
   XminOut *out;
-  lay(cv, spill, vals, cnts, S, Lt, d, cx, ca, cD, cn, out);
+  lay(cv, ghist, nsp, spill, vals, cnts, S, Lt, d, cx, ca, cD, cn, out);
   if (pl_status s = ensure_ws(ctx, cv.off)) return s;
   cv.base = ctx->ws;
   cv.off = 0;
-  lay(cv, spill, vals, cnts, S, Lt, d, cx, ca, cD, cn, out);
-  PL_CUDA(launch_xmin(x_dev, n, spill, (uint32_t)std::min<uint64_t>(P, 0xffffffffull), vals, cnts, S, Lt, d,
-                      max_candidates, min_tail, cx, ca, cD, cn, out, ctx->ctr, st));
-  ctx->launches += 3;
+  lay(cv, ghist, nsp, spill, vals, cnts, S, Lt, d, cx, ca, cD, cn, out);
+  PL_CUDA(launch_xmin(x_dev, n, ghist, nsp, spill, vals, cnts, S, Lt, d, max_candidates, min_tail, cx, ca, cD, cn,
+                      out, ctx->ctr, ctx->num_sms, st));
+  ctx->launches += 4;
   XminOut o{};
   PL_CUDA(cudaMemcpyAsync(&o, out, sizeof o, cudaMemcpyDeviceToHost, st));
   if (pl_status s = read_status(ctx, st)) return s;

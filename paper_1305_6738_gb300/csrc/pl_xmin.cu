@@ -4,9 +4,10 @@
 // the tail {x >= x_min} and D (Eq. 3) of the tail at its fit; the estimate is
 // the candidate of smallest D.
 //
-// xmin_prep_kernel (one block): the sorted distinct values with their counts
-// (a shared histogram of the values up to kXHist, the larger ones sorted in
-// global memory), then suffix sums of the counts and of c ln v.
+// xmin_hist_kernel (many blocks): a histogram of the values up to kXHist, the
+// larger ones collected; xmin_prep_kernel (one block): the sorted distinct
+// values with their counts (the collected ones sorted in global memory), then
+// suffix sums of the counts and of c ln v.
 // xmin_cand_kernel (a warp per candidate): the fit on lane 0 (safeguarded
 // Newton on the Euler-Maclaurin Hurwitz zeta), then D over the tail's distinct
 // values v and v - 1 on all lanes.  xmin_pick_kernel: the smallest D.
@@ -17,44 +18,53 @@
 namespace pl {
 namespace {
 
-constexpr int kXHist = 8192;   // values 1..kXHist counted in shared memory
+constexpr int kXHist = kXHistBins;  // values 1..kXHist counted in shared memory
 constexpr int kXWarps = 8;     // candidates per block of xmin_cand_kernel
 
-// One block of 1024 threads.  Writes the distinct values (ascending) and
-// counts, S[j] = tail count from j on (S[d] = 0), Lt[j] = sum_{i >= j} c_i ln v_i,
-// and d.  spill: scratch of P >= n uint64 (a power of two).
-__global__ void __launch_bounds__(1024) xmin_prep_kernel(const int32_t *x, int64_t n, uint64_t *spill, uint32_t P,
-                                                         uint64_t *vals, uint32_t *cnts, int64_t *S, double *Lt,
-                                                         int64_t *d_out, Counters *ctr) {
+// Histogram of the sample over many blocks: values 1..kXHist counted in a
+// shared histogram per block and added to the global one (ghist, zeroed
+// before), larger values appended to spill (counter *nspill, zeroed before);
+// a value below 1 latches the data error.
+__global__ void __launch_bounds__(256) xmin_hist_kernel(const int32_t *x, int64_t n, uint32_t *ghist,
+                                                        uint64_t *spill, unsigned long long *nspill,
+                                                        Counters *ctr) {
   __shared__ uint32_t hist[kXHist];
-  __shared__ unsigned long long s_cnt;
-  __shared__ int s_bad;
-  __shared__ int64_t s_part[33];
-  __shared__ double s_dpart[33];
   for (int i = threadIdx.x; i < kXHist; i += blockDim.x) hist[i] = 0;
-  if (threadIdx.x == 0) {
-    s_cnt = 0;
-    s_bad = 0;
-  }
   __syncthreads();
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = x[i];
     if (v < 1)
-      s_bad = 1;
+      bad = true;
     else if (v <= kXHist)
       atomicAdd(&hist[v - 1], 1u);
     else
-      spill[atomicAdd(&s_cnt, 1ull)] = (uint64_t)v;
+      spill[atomicAdd(nspill, 1ull)] = (uint64_t)v;
   }
+  if (bad) atomicOr(&ctr->status, kErrData);
   __syncthreads();
-  if (s_bad) {
-    if (threadIdx.x == 0) {
-      atomicOr(&ctr->status, kErrData);
-      *d_out = 0;
-    }
+  for (int i = threadIdx.x; i < kXHist; i += blockDim.x)
+    if (hist[i]) atomicAdd(&ghist[i], hist[i]);
+}
+
+// One block of 1024 threads, after xmin_hist_kernel.  Writes the distinct
+// values (ascending) and counts, S[j] = tail count from j on (S[d] = 0),
+// Lt[j] = sum_{i >= j} c_i ln v_i, and d.  spill: scratch of a power of two
+// >= n uint64 (the larger values, sorted here).
+__global__ void __launch_bounds__(1024) xmin_prep_kernel(const uint32_t *ghist, uint64_t *spill,
+                                                         const unsigned long long *nspill, uint64_t *vals,
+                                                         uint32_t *cnts, int64_t *S, double *Lt, int64_t *d_out,
+                                                         const Counters *ctr) {
+  __shared__ uint32_t hist[kXHist];
+  __shared__ int64_t s_part[33];
+  __shared__ double s_dpart[33];
+  if (ctr->status & kErrData) {
+    if (threadIdx.x == 0) *d_out = 0;
     return;
   }
-  const int64_t s = (int64_t)s_cnt;
+  for (int i = threadIdx.x; i < kXHist; i += blockDim.x) hist[i] = ghist[i];
+  __syncthreads();
+  const int64_t s = (int64_t)*nspill;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // sort the spills (block bitonic in global memory, padded to a power of two)
   uint32_t Q = 1;
@@ -330,11 +340,17 @@ __global__ void __launch_bounds__(1024) xmin_pick_kernel(const uint64_t *c_xmin,
 
 }  // namespace
 
-cudaError_t launch_xmin(const int32_t *x, int64_t n, uint64_t *spill, uint32_t P, uint64_t *vals, uint32_t *cnts,
-                        int64_t *S, double *Lt, int64_t *d, int64_t max_cand, int64_t min_tail, uint64_t *c_xmin,
-                        double *c_alpha, double *c_D, int64_t *c_nt, XminOut *out, Counters *ctr,
-                        cudaStream_t st) {
-  xmin_prep_kernel<<<1, 1024, 0, st>>>(x, n, spill, P, vals, cnts, S, Lt, d, ctr);
+cudaError_t launch_xmin(const int32_t *x, int64_t n, uint32_t *ghist, unsigned long long *nspill, uint64_t *spill,
+                        uint64_t *vals, uint32_t *cnts, int64_t *S, double *Lt, int64_t *d, int64_t max_cand,
+                        int64_t min_tail, uint64_t *c_xmin, double *c_alpha, double *c_D, int64_t *c_nt,
+                        XminOut *out, Counters *ctr, int num_sms, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * kXHist, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(nspill, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const int64_t want = (n + 256 * 16 - 1) / (256 * 16);
+  const int hblocks = (int)(want < 4 * num_sms ? (want < 1 ? 1 : want) : 4 * num_sms);
+  xmin_hist_kernel<<<hblocks, 256, 0, st>>>(x, n, ghist, spill, nspill, ctr);
+  xmin_prep_kernel<<<1, 1024, 0, st>>>(ghist, spill, nspill, vals, cnts, S, Lt, d, ctr);
   xmin_cand_kernel<<<(unsigned)((max_cand + kXWarps - 1) / kXWarps), kXWarps * 32, 0, st>>>(
       vals, cnts, S, Lt, d, max_cand, min_tail, c_xmin, c_alpha, c_D, c_nt, ctr);
   xmin_pick_kernel<<<1, 1024, 0, st>>>(c_xmin, c_alpha, c_D, c_nt, d, max_cand, out);
