@@ -98,6 +98,17 @@ def _load():
                                         c.c_uint32, c.c_uint32, _f64p, _f64p]
         lib.or_tz_cell.argtypes = [c.c_double, c.c_int64, c.c_int64, c.c_uint64, c.c_uint32,
                                    c.c_uint32, c.c_uint32, c.c_int64, c.c_int, _f64p, _f64p, _i64p]
+        lib.or_draw_bits64.restype = c.c_uint64
+        lib.or_draw_bits64.argtypes = [c.c_uint64, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64]
+        lib.or_binom_pmf.restype = c.c_double
+        lib.or_binom_pmf.argtypes = [c.c_int64, c.c_int64, c.c_double, c.c_double]
+        lib.or_binomial.restype = c.c_int64
+        lib.or_binomial.argtypes = [c.c_int64, c.c_double, c.c_double, c.c_double]
+        lib.or_thresholds.argtypes = [c.c_double, c.c_uint64, c.c_int64, _u64p]
+        lib.or_mn_sample.argtypes = [c.c_double, c.c_uint64, _u64p, c.c_uint64, c.c_uint32, c.c_uint32,
+                                     c.c_uint32, c.c_int64, _u64p]
+        lib.or_mn_cell.argtypes = [c.c_double, c.c_uint64, c.c_int64, c.c_uint64, c.c_uint32, c.c_uint32,
+                                   c.c_uint32, c.c_int64, c.c_int, _f64p, _f64p, _i64p]
         lib.or_estimate_xmin.argtypes = [_u64p, c.c_int64, c.c_int64, c.c_int64, c.c_int, _u64p, _f64p, _f64p,
                                          _i64p, _i64p, _i64p]
         _lib = lib
@@ -343,3 +354,46 @@ def estimate_xmin(x: np.ndarray, max_candidates: int = 1000, min_tail: int = 10,
                                     ctypes.byref(best)), "estimate_xmin")
     m = nc.value
     return best.value, xm[:m], a[:m], d[:m], nt[:m]
+
+
+MN_BINS = 2048
+PURPOSE_MULTINOMIAL = 3
+
+
+def draw_bits64(seed: int, cell: int, rep: int, purpose: int, i: int) -> int:
+    return int(_load().or_draw_bits64(seed, cell, rep, purpose, i))
+
+
+def binom_pmf(x: int, n: int, p: float, q: float | None = None) -> float:
+    return float(_load().or_binom_pmf(x, n, p, 1.0 - p if q is None else q))
+
+
+def binomial(n: int, p: float, u: float, q: float | None = None) -> int:
+    """Bin(n, p) from one uniform u in (0, 1] (inversion along a fixed order)."""
+    return int(_load().or_binomial(n, p, 1.0 - p if q is None else q, u))
+
+
+def thresholds(alpha: float, xmin: int, length: int = MN_BINS) -> np.ndarray:
+    T = np.zeros(length, dtype=np.uint64)
+    _load().or_thresholds(alpha, xmin, length, _ptr(T, _u64p))
+    return T
+
+
+def mn_sample(alpha: float, xmin: int, seed: int, cell: int, rep: int, purpose: int, n: int,
+              T: np.ndarray | None = None) -> np.ndarray:
+    """One replicate of n values by the multinomial (conditional binomial) sampler."""
+    T = thresholds(alpha, xmin) if T is None else np.ascontiguousarray(T, dtype=np.uint64)
+    out = np.zeros(n, dtype=np.uint64)
+    _load().or_mn_sample(alpha, xmin, _ptr(T, _u64p), seed, cell, rep, purpose, n, _ptr(out, _u64p))
+    return out
+
+
+def mn_cell(alpha: float, xmin: int, n: int, R: int, seed: int, cell_id: int, purpose: int = PURPOSE_MULTINOMIAL,
+            rep0: int = 0, threads: int = 0):
+    """D and alpha-hat for replicates rep0..rep0+R-1 drawn by the multinomial sampler."""
+    D = np.zeros(R)
+    A = np.zeros(R)
+    nc = ctypes.c_int64()
+    _check(_load().or_mn_cell(alpha, xmin, n, seed, cell_id, purpose, rep0, R, threads, _ptr(D, _f64p),
+                              _ptr(A, _f64p), ctypes.byref(nc)), "mn_cell")
+    return D, A, int(nc.value)

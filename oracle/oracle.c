@@ -37,6 +37,11 @@
  *                          linear-search inverse CDF, chi-square of draws,
  *                          log-likelihood argmax, uniform data -> 0,
  *                          D by definition, Tables 2-6 cells, K=20 atom)
+ *   or_estimate_xmin ..... pinned (planted lower ends, pure power law,
+ *                          candidates against the brute-force KS)
+ *   or_binomial/or_mn_* .. pinned (pmf against SciPy, chi-square of the
+ *                          binomial and of the bin counts, D distribution
+ *                          against the inverse-CDF sampler's)
  */
 #include <math.h>
 #include <stdint.h>
@@ -728,5 +733,191 @@ int or_estimate_xmin(const uint64_t *x, int64_t n, int64_t max_candidates, int64
   *best = b;
   free(s);
   free(first);
+  return fails ? OR_ENOMEM : OR_OK;
+}
+
+/* ======================================================================== */
+/* Multinomial histogram sampler (a large-n variant of the sampler, not in
+ * the paper): the histogram of a replicate drawn bin by bin by conditional
+ * binomials instead of one draw per value.  Same law as the inverse-CDF
+ * sampler (its integer thresholds), a different random stream.            */
+
+/* The 64 bits of draw i of stream (seed, cell, rep, purpose): the words
+ * (w[2j], w[2j+1]), j = i mod 2, of Philox block floor(i/2) as the low and
+ * high halves (the bits whose top 53 give or_draw_m). */
+uint64_t or_draw_bits64(uint64_t seed, uint32_t cell, uint32_t rep, uint32_t purpose, uint64_t i) {
+  uint32_t ctr[4] = {(uint32_t)(i >> 1), rep, cell, purpose};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t w[4];
+  or_philox4x32_10(ctr, key, w);
+  int j = (int)(i & 1);
+  return ((uint64_t)w[2 * j + 1] << 32) | (uint64_t)w[2 * j];
+}
+
+/* ln k! minus Stirling's formula (k + 1/2) ln k - k + ln sqrt(2 pi): for
+ * k > 15 the asymptotic series 1/(12k) - 1/(360k^3) + 1/(1260k^5)
+ * - 1/(1680k^7) + 1/(1188k^9) (Bernoulli numbers B_2j / (2j (2j-1))), next
+ * term below 1e-16; for smaller k the sum of logs. */
+static double or_stirling_err(double k) {
+  if (k > 15.0) {
+    const double r = 1.0 / (k * k);
+    return (1.0 / 12.0 - r * (1.0 / 360.0 - r * (1.0 / 1260.0 - r * (1.0 / 1680.0 - r / 1188.0)))) / k;
+  }
+  double lf = 0.0;
+  for (int i = 2; i <= (int)k; ++i) lf += log((double)i);
+  return lf - ((k + 0.5) * log(k) - k + 0.918938533204672741780329736406);
+}
+
+/* x ln(x / M) + M - x without cancellation: near x = M the series
+ * (x - M) v + 2x (v^3/3 + v^5/5 + ...), v = (x - M) / (x + M). */
+static double or_deviance(double x, double M) {
+  if (fabs(x - M) < 0.1 * (x + M)) {
+    double v = (x - M) / (x + M);
+    double s = (x - M) * v, e = 2.0 * x * v;
+    const double v2 = v * v;
+    for (int j = 1; j < 1000; ++j) {
+      e *= v2;
+      const double s1 = s + e / (double)(2 * j + 1);
+      if (s1 == s) return s1;
+      s = s1;
+    }
+    return s;
+  }
+  return x * log(x / M) + M - x;
+}
+
+/* P(Bin(n, p) = x), q = 1 - p given separately: the saddle-point form
+ * (Loader, "Fast and accurate computation of binomial probabilities", 2000)
+ *   exp(sterr(n) - sterr(x) - sterr(n-x) - dev(x, np) - dev(n-x, nq))
+ *   * sqrt(n / (2 pi x (n - x))),  0 < x < n. */
+double or_binom_pmf(int64_t x, int64_t n, double p, double q) {
+  if (x < 0 || x > n) return 0.0;
+  if (x == 0) return exp((double)n * (p < 0.5 ? log1p(-p) : log(q)));
+  if (x == n) return exp((double)n * (q < 0.5 ? log1p(-q) : log(p)));
+  const double dn = (double)n, dx = (double)x, dy = (double)(n - x);
+  const double lc = or_stirling_err(dn) - or_stirling_err(dx) - or_stirling_err(dy) - or_deviance(dx, dn * p) -
+                    or_deviance(dy, dn * q);
+  return exp(lc) * sqrt(dn / (6.283185307179586476925286766559 * dx * dy));
+}
+
+/* Bin(n, p) from one uniform u in (0, 1] by inversion along a fixed order of
+ * the outcomes (any order that lists every outcome once gives the law): for
+ * a mean below 30 the order 0, 1, 2, ... from P(0) = q^n; otherwise from the
+ * mode floor((n+1) p) outward, each step to the neighbour of larger
+ * probability (the upper on ties).  Probabilities by the ratio
+ * P(k+1)/P(k) = (n-k)/(k+1) p/q.  Once every remaining probability has
+ * underflowed, the last outcome taken is returned. */
+int64_t or_binomial(int64_t n, double p, double q, double u) {
+  if (n <= 0 || !(p > 0.0)) return 0;
+  if (!(q > 0.0)) return n;
+  const double r = p / q;
+  if ((double)n * p < 30.0) {
+    double f = or_binom_pmf(0, n, p, q), c = f;
+    int64_t k = 0;
+    while (c < u && k < n) {
+      f *= (double)(n - k) / (double)(k + 1) * r;
+      ++k;
+      c += f;
+      if (f == 0.0 && (double)k > (double)n * p) break;
+    }
+    return k;
+  }
+  int64_t M = (int64_t)floor((double)(n + 1) * p);
+  if (M > n) M = n;
+  const double fM = or_binom_pmf(M, n, p, q);
+  double rest = u - fM;
+  if (rest <= 0.0) return M;
+  int64_t lo = M - 1, hi = M + 1, last = M;
+  double flo = lo >= 0 ? fM * (double)M / ((double)(n - M + 1) * r) : 0.0;
+  double fhi = hi <= n ? fM * (double)(n - M) / (double)(M + 1) * r : 0.0;
+  while (flo > 0.0 || fhi > 0.0) {
+    if (fhi >= flo) {
+      rest -= fhi;
+      last = hi;
+      if (rest <= 0.0) return hi;
+      fhi = hi < n ? fhi * (double)(n - hi) / (double)(hi + 1) * r : 0.0;
+      ++hi;
+    } else {
+      rest -= flo;
+      last = lo;
+      if (rest <= 0.0) return lo;
+      flo = lo > 0 ? flo * (double)lo / ((double)(n - lo + 1) * r) : 0.0;
+      --lo;
+    }
+  }
+  return last;
+}
+
+/* Integer thresholds of the law for i = 0..len-1: T[i] = floor(Q(xmin+i)
+ * 2^53) + 1 (the inverse-CDF test Q(k) < m 2^-53 is T[k] <= m). */
+void or_thresholds(double alpha, uint64_t xmin, int64_t len, uint64_t *T) {
+  const double Z = or_hurwitz(alpha, (double)xmin);
+  for (int64_t i = 0; i < len; ++i)
+    T[i] = (uint64_t)floor(ldexp(or_survival(alpha, Z, xmin, xmin + (uint64_t)i), 53)) + 1;
+}
+
+/* One replicate by conditional binomials.  With T[-1] = 2^53 + 1, bin i
+ * (value xmin + i) gets Bin(n_rem, p_i) of the n_rem values not yet placed,
+ * p_i = (T[i-1] - T[i]) / (T[i-1] - 1) (the inverse-CDF law conditional on
+ * X >= xmin + i), for i = 0, 1, ... while i < OR_MN_BINS and n_rem p_i >= 1;
+ * the values left are drawn one by one conditional on X >= xmin + i: m'
+ * uniform on [1, T[i-1] - 1] (the multiply-high of a 64-bit random word by
+ * T[i-1] - 1, plus one) and X = min{k : Q(k) < m' 2^-53}.  Random words:
+ * draw index 0, 1, 2, ... of the stream in that order, u = m 2^-53 for a
+ * binomial, the full 64 bits for a single draw.  T: the thresholds of the
+ * first OR_MN_BINS values.  Writes the n values, bins first. */
+#define OR_MN_BINS 2048
+void or_mn_sample(double alpha, uint64_t xmin, const uint64_t *T, uint64_t seed, uint32_t cell, uint32_t rep,
+                  uint32_t purpose, int64_t n, uint64_t *out) {
+  const double Z = or_hurwitz(alpha, (double)xmin);
+  uint64_t Tprev = (1ull << 53) + 1, j = 0;
+  int64_t left = n, w = 0;
+  for (int64_t i = 0; i < OR_MN_BINS && left > 0; ++i) {
+    const double p = (double)(Tprev - T[i]) / (double)(Tprev - 1);
+    const double q = (double)(T[i] - 1) / (double)(Tprev - 1);
+    if ((double)left * p < 1.0) break;
+    const uint64_t m = (or_draw_bits64(seed, cell, rep, purpose, j++) >> 11) + 1;
+    const int64_t c = or_binomial(left, p, q, ldexp((double)m, -53));
+    for (int64_t t = 0; t < c; ++t) out[w++] = xmin + (uint64_t)i;
+    left -= c;
+    Tprev = T[i];
+  }
+  for (int64_t t = 0; t < left; ++t) {
+    const uint64_t bits = or_draw_bits64(seed, cell, rep, purpose, j++);
+    const uint64_t mp = (uint64_t)(((unsigned __int128)bits * (unsigned __int128)(Tprev - 1)) >> 64) + 1;
+    out[w++] = or_invert(alpha, Z, xmin, mp);
+  }
+}
+
+int or_mn_cell(double alpha, uint64_t xmin, int64_t n, uint64_t seed, uint32_t cell, uint32_t purpose,
+               uint32_t rep0, int64_t R, int nthreads, double *D, double *alpha_hat, int64_t *nonconv) {
+  if (n < 1 || R < 1 || !(alpha > 1.0) || xmin < 1) return OR_EINVAL;
+  uint64_t *T = (uint64_t *)malloc(OR_MN_BINS * sizeof(uint64_t));
+  if (!T) return OR_ENOMEM;
+  or_thresholds(alpha, xmin, OR_MN_BINS, T);
+  int64_t bad = 0, fails = 0;
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : bad, fails)
+#endif
+  for (int64_t r = 0; r < R; ++r) {
+    uint64_t *x = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    if (!x) {
+      fails += 1;
+      continue;
+    }
+    or_mn_sample(alpha, xmin, T, seed, cell, rep0 + (uint32_t)r, purpose, n, x);
+    double a = 0.0, d = 0.0;
+    int st = or_mle(x, n, xmin, &a);
+    if (st == OR_ENOCONV) bad += 1;
+    else if (st != OR_OK) fails += 1;
+    if (or_ks(x, n, xmin, a, &d) != OR_OK) fails += 1;
+    D[r] = d;
+    if (alpha_hat) alpha_hat[r] = a;
+    free(x);
+  }
+  free(T);
+  if (nonconv) *nonconv = bad;
+  (void)nthreads;
   return fails ? OR_ENOMEM : OR_OK;
 }
