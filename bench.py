@@ -715,6 +715,9 @@ def main():
                          "bespoke: 64 data sets (both laws), each fitted with its own cutoffs from 10,000 "
                          "simulated replicates, plus 10^6 lookups in a tabulated grid and one lower-end "
                          "estimate on 10^6 values")
+    ap.add_argument("--sampler", choices=["inverse-cdf", "multinomial"], default="inverse-cdf",
+                    help="sweep/small/large-n/table1: draw each value by the inverse CDF (default) or the "
+                         "histogram by conditional binomials (pl_ks_cutoffs_multinomial)")
     ap.add_argument("--tz-replicates", type=int, default=50_000,
                     help="truncated: replicates per cell (smaller values for profiler captures only)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: measured seconds")
@@ -827,11 +830,17 @@ def main():
         torch.cuda.synchronize()
         kernels_per_replay = ctx.pl_trace()["launches"] - l0
 
+    cutoffs_call = ctx.pl_ks_cutoffs_multinomial if args.sampler == "multinomial" else ctx.pl_ks_cutoffs
+    if args.sampler == "multinomial":
+        if args.workload == "batched":
+            raise SystemExit("--sampler multinomial: not for the batched workload")
+        config["sampler"] = "multinomial (conditional binomials, stream tag 3)"
+
     def step():
         if graph is not None:
             graph.replay()
         else:
-            ctx.pl_ks_cutoffs(cells, seed, QS, prec, cutoffs=cut)
+            cutoffs_call(cells, seed, QS, prec, cutoffs=cut)
 
     ctx.pl_set_tracing(graph is None)
     for _ in range(args.warmup):
@@ -873,7 +882,7 @@ def main():
     for _ in range(max(2, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.pl_ks_cutoffs(cells, seed, QS, prec, cutoffs=host_cut)
+        cutoffs_call(cells, seed, QS, prec, cutoffs=host_cut)
         e2e_s.append(time.perf_counter() - t0)
     if graph is not None:  # trace one plain call for the per-kernel times
         ctx.pl_set_tracing(True)
@@ -897,7 +906,8 @@ def main():
                 "frac": achieved / mul_peak,
                 "traffic": (TRAFFIC_PER_REPLICATE[h] * total_R / max(1, waves)
                             if h in TRAFFIC_PER_REPLICATE and args.workload == "sweep" else None),
-                "kernel": ("sample_block_kernel" if args.workload == "large-n"
+                "kernel": ("mn_sample_kernel" if args.sampler == "multinomial"
+                           else "sample_block_kernel" if args.workload == "large-n"
                            else "sample_hist_kernel + sample_block_kernel" if args.workload == "batched"
                            else "sample_hist_kernel"),
                 "kernel_ms_per_step": kmean, "launches_per_step": waves,

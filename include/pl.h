@@ -174,6 +174,25 @@ pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells,
                         pl_precision prec, double *cutoffs, void *D_dev_opt,
                         double *alpha_hat_dev_opt, void *stream);
 
+/* Cutoff table with the multinomial histogram sampler (a large-n variant;
+ * not in the paper): each replicate's histogram is drawn bin by bin by
+ * conditional binomials on the inverse-CDF sampler's law (its integer
+ * thresholds T: bin xmin + i gets Bin(n_rem, (T[i-1] - T[i]) / (T[i-1] - 1))
+ * of the n_rem values not yet placed, for i < 2048 while the expected count
+ * is at least one) and the values left one by one conditional on lying
+ * beyond, so the work grows with the occupied bins rather than with n
+ * (~780 binomials and ~780 single draws at alpha = 2, n = 10^6).  Same law
+ * as pl_ks_cutoffs, a different random stream (purpose 3: draw index j of
+ * the replicate's stream is the j-th binomial or single value), so results
+ * agree with pl_ks_cutoffs in distribution, not value by value.  Arguments,
+ * outputs and errors as pl_ks_cutoffs (every cell runs in the block form,
+ * n <= 2^21). */
+pl_status pl_ks_cutoffs_multinomial(pl_ctx *ctx, const pl_cell *cells,
+                                    int ncells, uint64_t seed, const double *q,
+                                    int nq, pl_precision prec, double *cutoffs,
+                                    void *D_dev_opt, double *alpha_hat_dev_opt,
+                                    void *stream);
+
 /* Autotuner of the warp/block split: replicates with n above the split use
  * the block-per-replicate form, the others the warp-per-replicate form.  The
  * split starts at 16384; pl_autotune times both forms on the context's GPU

@@ -21,6 +21,7 @@
 #include "pl_truncated.cuh"
 #include "pl_lookup.cuh"
 #include "pl_xmin.cuh"
+#include "pl_multinomial.cuh"
 
 using namespace pl;
 
@@ -61,9 +62,11 @@ struct pl_ctx {
 
 namespace {
 
+constexpr uint32_t kPurposeMultinomial = 3;  // stream tag of the multinomial sampler
 constexpr int64_t kWarpNMax = 65535;     // warp form: n up to this (16-bit dense record counts)
 constexpr int64_t kWideNMax = 1 << 21;   // block form: n up to this (16-bit lane counters)
 constexpr uint32_t kWideItemReps = 8;    // block form: replicates per work item
+static_assert(kWideItemReps == kWideReps, "block-form items as the multinomial sampler reads them");
 
 pl_status fail(pl_ctx *ctx, pl_status s, const char *fmt, ...) {
   char buf[512];
@@ -216,7 +219,8 @@ struct SimPlan {
   int64_t finisher_spill = 0;      // spills one finisher warp must hold for one replicate
 };
 
-pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpose, SimPlan &sp) {
+pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpose, SimPlan &sp,
+                     bool all_wide = false) {
   std::map<std::pair<double, uint64_t>, uint32_t> law_of;
   std::map<uint64_t, uint32_t> fit_of;
   std::vector<double> law_draws;
@@ -251,7 +255,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     cd.R = x.replicates;
     cd.cell_id = (uint32_t)x.cell_id;
     cd.law = li;
-    cd.wide = x.n > std::min(kWarpNMax, ctx->warp_split) ? 1u : 0u;
+    cd.wide = (all_wide || x.n > std::min(kWarpNMax, ctx->warp_split)) ? 1u : 0u;
     cd.H = cd.wide ? (uint32_t)kHWide : hist_bins(x.n);
     // batched table searches pay off once a replicate has many draws or the
     // tail is heavy (measured crossover on GB300)
@@ -525,6 +529,62 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
     if (wev) PL_CUDA(cudaEventRecord(wev[1], st));
     PL_CUDA(launch_tail_queue_raw(b.laws_dev, b.tq_pos, b.tq_law, b.tq_count, sp.tail_cap, b.rec.spill, ctx->ctr,
                                   ctx->num_sms, st));
+    FinishLaunch fl{};
+    fl.cells = b.cells;
+    fl.consts = b.consts;
+    fl.laws = b.laws_dev;
+    fl.fits = b.fits_dev;
+    fl.items = b.items + w.first;
+    fl.nitems = (uint32_t)w.count;
+    fl.rk = rk;
+    fl.rec = b.rec;
+    fl.D_out = D;
+    fl.A_out = A;
+    fl.scratch = b.scratch;
+    fl.spill_cap = b.spill_cap;
+    fl.arena_bytes = b.arena_bytes;
+    fl.ctr = ctx->ctr;
+    fl.blocks = (int)std::min<size_t>((size_t)b.blocks, w.count);
+    PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
+    if (wev) PL_CUDA(cudaEventRecord(wev[2], st));
+    PL_CUDA(launch_finish(fl, f32, st));
+    if (wev) PL_CUDA(cudaEventRecord(wev[3], st));
+    ctx->launches += 2;
+  }
+  return PL_OK;
+}
+
+// The same waves with the multinomial sampler in place of the samplers (every
+// cell in the block form, so each record has 32-bit counts for 8,192 values).
+pl_status run_sim_mn(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, bool f32, void *D, double *A,
+                     cudaStream_t st) {
+  const RoundKeys rk = round_keys(seed);
+  const bool trace = ctx->tracing;
+  if (trace) {
+    while (ctx->wave_ev.size() < 4 * sp.waves.size()) {
+      cudaEvent_t e;
+      PL_CUDA(cudaEventCreate(&e));
+      ctx->wave_ev.push_back(e);
+    }
+    ctx->traced_waves = (uint32_t)sp.waves.size();
+    ctx->traced_draws = 0;
+    for (const Cell &c : sp.cells) ctx->traced_draws += (uint64_t)c.n * (uint64_t)c.R;
+  }
+  size_t wi_ = 0;
+  for (const Wave &w : sp.waves) {
+    cudaEvent_t *wev = trace ? &ctx->wave_ev[4 * wi_] : nullptr;
+    ++wi_;
+    MnLaunch ml{};
+    ml.cells = b.cells;
+    ml.laws = b.laws_dev;
+    ml.items = b.items + w.first;
+    ml.nitems = (uint32_t)w.count;
+    ml.rk = rk;
+    ml.rec = b.rec;
+    ml.ctr = ctx->ctr;
+    if (wev) PL_CUDA(cudaEventRecord(wev[0], st));
+    PL_CUDA(launch_mn_sample(ml, st));
+    if (wev) PL_CUDA(cudaEventRecord(wev[1], st));
     FinishLaunch fl{};
     fl.cells = b.cells;
     fl.consts = b.consts;
@@ -1184,6 +1244,72 @@ pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells, uint64_t 
   PL_CUDA(cudaMemcpyAsync(rank, h_rank.data(), sizeof(int64_t) * h_rank.size(), cudaMemcpyHostToDevice, st));
   if (pl_status s = mark(ctx, 1, st)) return s;
   if (pl_status s = run_sim(ctx, sp, b, seed, f32, D, alpha_hat_dev_opt, st)) return s;
+  if (pl_status s = mark(ctx, 2, st)) return s;
+  PL_CUDA(launch_select(D, f32, off, Rs, rank, ncells, nq, cut, st));
+  ctx->launches += 1;
+  if (pl_status s = mark(ctx, 3, st)) return s;
+  if (host_out) {
+    PL_CUDA(cudaMemcpyAsync(cutoffs, cut, sizeof(double) * ncells * nq, cudaMemcpyDeviceToHost, st));
+    return read_status(ctx, st);
+  }
+  return PL_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+pl_status pl_ks_cutoffs_multinomial(pl_ctx *ctx, const pl_cell *cells, int ncells, uint64_t seed, const double *q,
+                                    int nq, pl_precision prec, double *cutoffs, void *D_dev_opt,
+                                    double *alpha_hat_dev_opt, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!cells || ncells < 1 || !q || nq < 1 || !cutoffs)
+    return fail(ctx, PL_EINVAL, "pl_ks_cutoffs_multinomial: bad arguments");
+  if (prec != PL_FP64 && prec != PL_FP32_BULK) return fail(ctx, PL_EINVAL, "unknown precision form");
+  for (int j = 0; j < nq; ++j)
+    if (!(q[j] > 0.0 && q[j] < 1.0)) return fail(ctx, PL_EINVAL, "quantile %d outside (0, 1)", j);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f32 = prec == PL_FP32_BULK;
+  SimPlan sp;
+  if (pl_status s = plan_cells(ctx, cells, ncells, kPurposeMultinomial, sp, true)) return s;
+  const bool host_out = !is_device_ptr(cutoffs);
+  const size_t dsz = f32 ? 4 : 8;
+  const int blocks = sim_blocks(ctx, f32), sblocks = sample_blocks(ctx),
+            bsblocks = ctx->num_sms * std::max(1, ctx->block_sampler_per_sm);
+  auto lay = [&](Carver &cv, SimBuffers &b, void *&D, int64_t *&off, int64_t *&Rs, int64_t *&rank, double *&cut) {
+    carve_sim(cv, sp, blocks, sblocks, b, ctx->dbg_arena, bsblocks);
+    D = D_dev_opt ? D_dev_opt : (void *)cv.take<uint8_t>((size_t)sp.total_R * dsz);
+    off = cv.take<int64_t>(ncells);
+    Rs = cv.take<int64_t>(ncells);
+    rank = cv.take<int64_t>((size_t)ncells * nq);
+    cut = host_out ? cv.take<double>((size_t)ncells * nq) : cutoffs;
+  };
+  Carver cv;
+  SimBuffers b;
+  void *D;
+  int64_t *off, *Rs, *rank;
+  double *cut;
+  lay(cv, b, D, off, Rs, rank, cut);
+  if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+  cv.base = ctx->ws;
+  cv.off = 0;
+  lay(cv, b, D, off, Rs, rank, cut);
+  if (pl_status s = mark(ctx, 0, st)) return s;
+  if (pl_status s = upload_sim(ctx, sp, b, st)) return s;
+  std::vector<int64_t> h_off(ncells), h_R(ncells), h_rank((size_t)ncells * nq);
+  for (int c = 0; c < ncells; ++c) {
+    h_off[c] = sp.cells[c].out_off;
+    h_R[c] = sp.cells[c].R;
+    for (int j = 0; j < nq; ++j) {
+      int64_t i = (int64_t)std::floor((double)h_R[c] * q[j]);
+      h_rank[(size_t)c * nq + j] = std::min(std::max<int64_t>(i, 0), h_R[c] - 1);
+    }
+  }
+  PL_CUDA(cudaMemcpyAsync(off, h_off.data(), sizeof(int64_t) * ncells, cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(Rs, h_R.data(), sizeof(int64_t) * ncells, cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(rank, h_rank.data(), sizeof(int64_t) * h_rank.size(), cudaMemcpyHostToDevice, st));
+  if (pl_status s = mark(ctx, 1, st)) return s;
+  if (pl_status s = run_sim_mn(ctx, sp, b, seed, f32, D, alpha_hat_dev_opt, st)) return s;
   if (pl_status s = mark(ctx, 2, st)) return s;
   PL_CUDA(launch_select(D, f32, off, Rs, rank, ncells, nq, cut, st));
   ctx->launches += 1;

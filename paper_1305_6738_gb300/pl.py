@@ -32,7 +32,8 @@ EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters",
            "pl_plan_destroy", "pl_autotune", "pl_set_split", "pl_server_create", "pl_server_submit",
            "pl_server_poll", "pl_server_now", "pl_server_load", "pl_server_destroy",
            "pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_fit_ks_truncated", "pl_bespoke_cutoffs",
-           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin"]
+           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin",
+           "pl_ks_cutoffs_multinomial"]
 
 
 class pl_cell(ctypes.Structure):
@@ -129,9 +130,11 @@ _lib.pl_cutoff_lookup.argtypes = [_vp, _f64p, ctypes.c_int, ctypes.POINTER(ctype
                                   ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, _vp]
 _lib.pl_estimate_xmin.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.POINTER(pl_xmin_result), _vp, _vp, _vp, _vp, _vp]
+_lib.pl_ks_cutoffs_multinomial.argtypes = [_vp, ctypes.POINTER(pl_cell), ctypes.c_int, ctypes.c_uint64, _f64p,
+                                           ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
 _lib.pl_server_destroy.restype = None
 for _f in ["pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_fit_ks_truncated", "pl_bespoke_cutoffs",
-           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin", "pl_ks_cutoffs_multinomial", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -345,6 +348,27 @@ class Context:
                                           _ptr(cand_xmin), _ptr(cand_alpha), _ptr(cand_D), _ptr(cand_ntail),
                                           _stream_ptr(stream)))
         return {k: getattr(r, k) for k, _ in pl_xmin_result._fields_}
+
+    def pl_ks_cutoffs_multinomial(self, cells, seed: int, q, prec: int = PL_FP64, cutoffs=None, D=None,
+                                  alpha_hat=None, stream=None):
+        """As pl_ks_cutoffs, with the multinomial histogram sampler (stream tag 3)."""
+        arr = (pl_cell * len(cells))(*[pl_cell(c.alpha, c.xmin, c.n, c.replicates, c.cell_id) for c in cells])
+        qa = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        host = None
+        if cutoffs is None:
+            host = np.zeros(len(cells) * qa.size)
+            out_ptr = host.ctypes.data
+        elif isinstance(cutoffs, np.ndarray):
+            host = cutoffs
+            out_ptr = cutoffs.ctypes.data
+        else:
+            out_ptr = _ptr(cutoffs)
+        self._check(_lib.pl_ks_cutoffs_multinomial(self._h, arr, len(cells), seed, qa.ctypes.data_as(_f64p),
+                                                   qa.size, prec, out_ptr, _ptr(D), _ptr(alpha_hat),
+                                                   _stream_ptr(stream)))
+        if host is not None:
+            return host.reshape(len(cells), qa.size)
+        return cutoffs
 
     def pl_autotune(self, stream=None) -> int:
         v = ctypes.c_int64()
