@@ -856,35 +856,57 @@ void or_thresholds(double alpha, uint64_t xmin, int64_t len, uint64_t *T) {
     T[i] = (uint64_t)floor(ldexp(or_survival(alpha, Z, xmin, xmin + (uint64_t)i), 53)) + 1;
 }
 
-/* One replicate by conditional binomials.  With T[-1] = 2^53 + 1, bin i
- * (value xmin + i) gets Bin(n_rem, p_i) of the n_rem values not yet placed,
- * p_i = (T[i-1] - T[i]) / (T[i-1] - 1) (the inverse-CDF law conditional on
- * X >= xmin + i), for i = 0, 1, ... while i < OR_MN_BINS and n_rem p_i >= 1;
- * the values left are drawn one by one conditional on X >= xmin + i: m'
- * uniform on [1, T[i-1] - 1] (the multiply-high of a 64-bit random word by
- * T[i-1] - 1, plus one) and X = min{k : Q(k) < m' 2^-53}.  Random words:
- * draw index 0, 1, 2, ... of the stream in that order, u = m 2^-53 for a
- * binomial, the full 64 bits for a single draw.  T: the thresholds of the
- * first OR_MN_BINS values.  Writes the n values, bins first. */
+/* One replicate by conditional binomials on a binary tree of the first
+ * OR_MN_BINS values.  With T[-1] = 2^53 + 1 the inverse-CDF law gives the
+ * index range [l, r) the mass (T[l-1] - T[r-1]) 2^-53.  First the count
+ * beyond the tree, Bin(n, (T[B-1] - 1) / 2^53) (B = OR_MN_BINS); then node 1
+ * (the range [0, B)) holds the rest, and node k of range [l, r) passes
+ * Bin(c_k, (T[l-1] - T[mid-1]) / (T[l-1] - T[r-1])) of its count to its
+ * left child 2k ([l, mid), mid = (l + r) / 2) and the others to its right
+ * child 2k+1; the leaves B..2B-1 are the values xmin .. xmin + B - 1.  The
+ * values beyond are drawn one by one conditional on X >= xmin + B: m' uniform
+ * on [1, T[B-1] - 1] (the multiply-high of a 64-bit random word by
+ * T[B-1] - 1, plus one) and X = min{k : Q(k) < m' 2^-53}.  Random words: draw
+ * index 0 for the count beyond, k for node k's binomial (u = m 2^-53), and
+ * 2B + t for the t-th value beyond (all 64 bits).  T: the thresholds of the
+ * first B values.  Writes the n values, the tree's first. */
 #define OR_MN_BINS 2048
+static uint64_t or_mn_tm1(const uint64_t *T, int64_t i) { return i == 0 ? (1ull << 53) + 1 : T[i - 1]; }
+
 void or_mn_sample(double alpha, uint64_t xmin, const uint64_t *T, uint64_t seed, uint32_t cell, uint32_t rep,
                   uint32_t purpose, int64_t n, uint64_t *out) {
+  const int64_t B = OR_MN_BINS;
   const double Z = or_hurwitz(alpha, (double)xmin);
-  uint64_t Tprev = (1ull << 53) + 1, j = 0;
-  int64_t left = n, w = 0;
-  for (int64_t i = 0; i < OR_MN_BINS && left > 0; ++i) {
-    const double p = (double)(Tprev - T[i]) / (double)(Tprev - 1);
-    const double q = (double)(T[i] - 1) / (double)(Tprev - 1);
-    if ((double)left * p < 1.0) break;
-    const uint64_t m = (or_draw_bits64(seed, cell, rep, purpose, j++) >> 11) + 1;
-    const int64_t c = or_binomial(left, p, q, ldexp((double)m, -53));
-    for (int64_t t = 0; t < c; ++t) out[w++] = xmin + (uint64_t)i;
-    left -= c;
-    Tprev = T[i];
+  const uint64_t TB = T[B - 1];
+  const double pb = ldexp((double)(TB - 1), -53), qb = ldexp((double)((1ull << 53) + 1 - TB), -53);
+  const uint64_t m0 = (or_draw_bits64(seed, cell, rep, purpose, 0) >> 11) + 1;
+  const int64_t beyond = or_binomial(n, pb, qb, ldexp((double)m0, -53));
+  int64_t *cnt = (int64_t *)calloc((size_t)(2 * B), sizeof(int64_t));
+  if (!cnt) return;
+  cnt[1] = n - beyond;
+  for (int64_t k = 1; k < B; ++k) {
+    const int64_t c = cnt[k];
+    if (c == 0) continue;
+    int level = 0;
+    while ((2ll << level) <= k) ++level;
+    const int64_t width = B >> level, l = (k - (1ll << level)) * width, r = l + width, mid = l + width / 2;
+    const uint64_t a = or_mn_tm1(T, l), b = or_mn_tm1(T, mid), e = or_mn_tm1(T, r);
+    int64_t cl = 0;
+    if (a > e) {
+      const double den = (double)(a - e);
+      const uint64_t m = (or_draw_bits64(seed, cell, rep, purpose, (uint64_t)k) >> 11) + 1;
+      cl = or_binomial(c, (double)(a - b) / den, (double)(b - e) / den, ldexp((double)m, -53));
+    }
+    cnt[2 * k] = cl;
+    cnt[2 * k + 1] = c - cl;
   }
-  for (int64_t t = 0; t < left; ++t) {
-    const uint64_t bits = or_draw_bits64(seed, cell, rep, purpose, j++);
-    const uint64_t mp = (uint64_t)(((unsigned __int128)bits * (unsigned __int128)(Tprev - 1)) >> 64) + 1;
+  int64_t w = 0;
+  for (int64_t i = 0; i < B; ++i)
+    for (int64_t t = 0; t < cnt[B + i]; ++t) out[w++] = xmin + (uint64_t)i;
+  free(cnt);
+  for (int64_t t = 0; t < beyond; ++t) {
+    const uint64_t bits = or_draw_bits64(seed, cell, rep, purpose, (uint64_t)(2 * B + t));
+    const uint64_t mp = (uint64_t)(((unsigned __int128)bits * (unsigned __int128)(TB - 1)) >> 64) + 1;
     out[w++] = or_invert(alpha, Z, xmin, mp);
   }
 }
