@@ -1,19 +1,23 @@
 // pl_multinomial.cu -- the multinomial histogram sampler (a large-n variant of
-// the sampler; not in the paper): a replicate's histogram drawn bin by bin by
-// conditional binomials, the few values of the tail one by one, written as a
-// block-form replicate record that the finisher fits and tests as usual.
+// the sampler; not in the paper): a replicate's histogram drawn by conditional
+// binomials on a binary tree of its first kMnBins values, the few values
+// beyond one by one, written as a block-form replicate record that the
+// finisher fits and tests as usual.
 //
 // Law: the inverse-CDF sampler's, through its integer thresholds T (with
-// T[-1] = 2^53 + 1, P(X = xmin + i) = (T[i-1] - T[i]) 2^-53).  Bin i gets
-// Bin(n_rem, p_i), p_i = (T[i-1] - T[i]) / (T[i-1] - 1), of the n_rem values
-// not yet placed, for i = 0, 1, ... while i < kMnBins and n_rem p_i >= 1; each
-// value left is drawn conditional on X >= xmin + i as the inverse CDF of m'
-// uniform on [1, T[i-1] - 1] (the multiply-high of a 64-bit random word).
-// Random words: draw index 0, 1, 2, ... of the replicate's stream in that
-// order (u = m 2^-53 for a binomial, all 64 bits for a single value).
+// T[-1] = 2^53 + 1 the index range [l, r) has mass (T[l-1] - T[r-1]) 2^-53).
+// The count beyond the tree is Bin(n, (T[B-1] - 1) 2^-53), B = kMnBins; node 1
+// (range [0, B)) holds the rest, and node k of range [l, r) passes
+// Bin(c_k, (T[l-1] - T[mid-1]) / (T[l-1] - T[r-1])) of its count to its left
+// child 2k ([l, mid)) and the others to 2k+1; leaves B..2B-1 are the values
+// xmin .. xmin + B - 1.  The values beyond are the inverse CDF of m' uniform
+// on [1, T[B-1] - 1] (the multiply-high of a 64-bit random word).  Random
+// words: draw index 0 for the count beyond, k for node k, 2B + t for the t-th
+// value beyond.
 //
-// One thread per replicate: the binomial chain is sequential, and its work
-// (binary64) grows with the number of occupied bins, not with n.
+// One warp per replicate: the binomials of a tree level are independent, so
+// the lanes take a level's nodes together; the work grows with the occupied
+// values, not with n.
 #include <cmath>
 
 #include "pl_multinomial.cuh"
@@ -21,7 +25,8 @@
 namespace pl {
 namespace {
 
-constexpr int kMnBins = 2048;
+constexpr int kMnBins = 2048;  // values in the binomial tree
+constexpr int kMnWarps = 4;     // replicates per block
 
 // ln k! minus Stirling's formula: the asymptotic series (Bernoulli numbers)
 // above 15, the sum of logs below.
@@ -107,87 +112,126 @@ __device__ int64_t mn_binomial(int64_t n, double p, double q, double u) {
   return last;
 }
 
-// The 64-bit random word i of a replicate's stream (two words of Philox block
-// i/2), one block cached.
-struct MnStream {
-  uint32_t rep, cell, purpose;
-  uint64_t blk;
-  uint4 w;
-  __device__ uint64_t word(uint64_t i, const RoundKeys &rk) {
-    if ((i >> 1) != blk) {
-      blk = i >> 1;
-      w = philox4x32_10_rk(make_uint4((uint32_t)blk, rep, cell, purpose), rk);
-    }
-    return (i & 1) ? ((uint64_t)w.w << 32) | w.z : ((uint64_t)w.y << 32) | w.x;
-  }
-};
+__device__ __forceinline__ uint64_t mn_word(uint64_t i, uint32_t rep, uint32_t cell, uint32_t purpose,
+                                            const RoundKeys &rk) {
+  const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)(i >> 1), rep, cell, purpose), rk);
+  return (i & 1) ? ((uint64_t)w.w << 32) | w.z : ((uint64_t)w.y << 32) | w.x;
+}
 
-__global__ void __launch_bounds__(128) mn_sample_kernel(MnLaunch a) {
-  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const uint64_t it = t / kWideReps, j = t % kWideReps;
-  if (it >= a.nitems) return;
+__device__ __forceinline__ uint64_t mn_tm1(const uint64_t *T, uint32_t i) {
+  return i == 0 ? (1ull << 53) + 1 : T[i - 1];
+}
+
+// One warp per replicate.  The tree's level L (nodes 2^L .. 2^(L+1) - 1) is
+// split by the lanes in parallel; internal counts wait in the record's dense
+// area above kMnScratch (cleared later where the finisher reads it), the
+// leaves are the dense counts of the first kMnBins values.
+constexpr uint32_t kMnScratch = 4096;
+static_assert(kMnScratch + kMnBins <= kHWide, "tree scratch inside the dense record");
+
+__global__ void __launch_bounds__(kMnWarps * 32) mn_sample_kernel(MnLaunch a) {
+  const uint64_t wid = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint64_t it = wid / kWideReps, j = wid % kWideReps;
+  if (it >= a.nitems) return;  // warp-uniform
   const WorkItem wi = a.items[it];
   if (j >= wi.nrep) return;
   const Cell &cell = a.cells[wi.cell];
   const Law &law = a.laws[cell.law];
   const uint32_t H = cell.H, L2 = law.L2;
   const int64_t n = cell.n;
+  const uint32_t rep = wi.r0 + (uint32_t)j;
   uint32_t *dense = reinterpret_cast<uint32_t *>(a.rec.dense + wi.dense_off + j * 2 * (uint64_t)H);
   uint64_t *spill = a.rec.spill + wi.spill_off + j * (uint64_t)cell.scap;
-  MnStream s{wi.r0 + (uint32_t)j, cell.cell_id, cell.purpose, ~0ull, make_uint4(0, 0, 0, 0)};
-  // head: conditional binomials
-  uint64_t Tprev = (1ull << 53) + 1, idx = 0;
-  int64_t left = n, tmax = -1;
-  uint32_t b = 0;
-  for (; b < (uint32_t)kMnBins && left > 0; ++b) {
-    const uint64_t Tb = law.T[b];
-    const double p = (double)(Tprev - Tb) / (double)(Tprev - 1);
-    const double q = (double)(Tb - 1) / (double)(Tprev - 1);
-    if ((double)left * p < 1.0) break;
-    const uint64_t m = (s.word(idx++, a.rk) >> 11) + 1;
-    const int64_t c = mn_binomial(left, p, q, (double)m * 0x1p-53);
-    dense[b] = (uint32_t)c;
-    if (c) tmax = b;
-    left -= c;
-    Tprev = Tb;
+  const uint64_t *T = law.T;
+  // the count beyond the tree, then the tree level by level
+  const uint64_t TB = T[kMnBins - 1];
+  int64_t beyond = 0;
+  if (lane == 0) {
+    const double pb = (double)(TB - 1) * 0x1p-53, qb = (double)((1ull << 53) + 1 - TB) * 0x1p-53;
+    const uint64_t m = (mn_word(0, rep, cell.cell_id, cell.purpose, a.rk) >> 11) + 1;
+    beyond = mn_binomial(n, pb, qb, (double)m * 0x1p-53);
+    dense[kMnScratch + 1] = (uint32_t)(n - beyond);
   }
-  // the values left, conditional on X >= xmin + b: first the largest
-  // histogram index they reach (to clear the bins from b to it), then counted
-  const uint64_t span = Tprev - 1;
-  auto index_of = [&](uint64_t w) {
-    const uint64_t mp = __umul64hi(w, span) + 1;
-    return lookup_index(law.T, law.guide, law.T, L2, law.xmin_f, law.tail_c, law.tail_e, mp);
-  };
-  int64_t top = -1;
-  for (int64_t k = 0; k < left; ++k) {
-    const uint32_t i = index_of(s.word(idx + (uint64_t)k, a.rk));
-    if (i < H && (int64_t)i > top) top = i;
-  }
-  for (int64_t i = b; i <= top; ++i) dense[i] = 0u;
-  int64_t ns = 0;
-  for (int64_t k = 0; k < left; ++k) {
-    const uint64_t w = s.word(idx + (uint64_t)k, a.rk);
-    const uint32_t i = index_of(w);
-    if (i < H) {
-      dense[i] += 1u;
-      if ((int64_t)i > tmax) tmax = i;
-    } else {
-      const uint64_t v = i < L2 ? cell.xmin + i : tail_invert(cell.alpha, law.Z, cell.xmin + L2,
-                                                              __umul64hi(w, span) + 1);
-      if (ns < (int64_t)cell.scap) spill[ns] = v;
-      ++ns;
+  beyond = __shfl_sync(0xffffffffu, beyond, 0);
+  __syncwarp();
+  uint32_t last = 0;  // 1 + the largest leaf with a count (this lane's)
+  for (uint32_t level = 0, first = 1; first < (uint32_t)kMnBins; ++level, first <<= 1) {
+    const uint32_t width = (uint32_t)kMnBins >> level;
+    for (uint32_t k = first + lane; k < 2 * first; k += 32) {
+      const int64_t c = dense[kMnScratch + k];
+      int64_t cl = 0;
+      const uint32_t l = (k - first) * width, r = l + width, mid = l + width / 2;
+      if (c > 0) {
+        const uint64_t A = mn_tm1(T, l), Bm = mn_tm1(T, mid), E = mn_tm1(T, r);
+        if (A > E) {
+          const double den = (double)(A - E);
+          const uint64_t m = (mn_word(k, rep, cell.cell_id, cell.purpose, a.rk) >> 11) + 1;
+          cl = mn_binomial(c, (double)(A - Bm) / den, (double)(Bm - E) / den, (double)m * 0x1p-53);
+        }
+      }
+      if (2 * first < (uint32_t)kMnBins) {
+        dense[kMnScratch + 2 * k] = (uint32_t)cl;
+        dense[kMnScratch + 2 * k + 1] = (uint32_t)(c - cl);
+      } else {  // the children are leaves: values l and l + 1
+        dense[l] = (uint32_t)cl;
+        dense[l + 1] = (uint32_t)(c - cl);
+        if (c - cl > 0) last = l + 2;
+        else if (cl > 0) last = l + 1;
+      }
     }
+    __syncwarp();
   }
-  if (ns > (int64_t)cell.scap) atomicOr(&a.ctr->status, kErrArena);  // the finisher must not redraw
-  a.rec.meta[wi.meta_off + j] = make_int2((int)tmax, (int)ns);
+  int64_t tmax = (int64_t)__reduce_max_sync(0xffffffffu, last) - 1;
+  // the values beyond the tree, conditional on X >= xmin + kMnBins: first the
+  // largest histogram index they reach (to clear the bins up to it), then counted
+  const uint64_t span = TB - 1;
+  auto draw = [&](int64_t t, uint64_t &mp) {
+    mp = __umul64hi(mn_word(2 * (uint64_t)kMnBins + (uint64_t)t, rep, cell.cell_id, cell.purpose, a.rk), span) + 1;
+    return lookup_index(T, law.guide, T, L2, law.xmin_f, law.tail_c, law.tail_e, mp);
+  };
+  uint32_t top = 0;
+  for (int64_t t = lane; t < beyond; t += 32) {
+    uint64_t mp;
+    const uint32_t i = draw(t, mp);
+    if (i < H && i + 1 > top) top = i + 1;
+  }
+  top = __reduce_max_sync(0xffffffffu, top);
+  for (uint32_t i = kMnBins + lane; i < top; i += 32) dense[i] = 0u;
+  __syncwarp();
+  uint32_t ns = 0;
+  for (int64_t t0 = 0; t0 < beyond; t0 += 32) {
+    const int64_t t = t0 + lane;
+    uint64_t v = 0;
+    bool sp = false;
+    if (t < beyond) {
+      uint64_t mp;
+      const uint32_t i = draw(t, mp);
+      if (i < H) {
+        atomicAdd(&dense[i], 1u);
+      } else {
+        sp = true;
+        v = i < L2 ? cell.xmin + i : tail_invert(cell.alpha, law.Z, cell.xmin + L2, mp);
+      }
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, sp);
+    const uint32_t slot = ns + __popc(b & ((1u << lane) - 1u));
+    if (sp && slot < cell.scap) spill[slot] = v;
+    ns += __popc(b);
+  }
+  if (top > 0) tmax = max(tmax, (int64_t)top - 1);
+  if (lane == 0) {
+    if (ns > cell.scap) atomicOr(&a.ctr->status, kErrArena);  // the finisher must not redraw
+    a.rec.meta[wi.meta_off + j] = make_int2((int)tmax, (int)ns);
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_mn_sample(const MnLaunch &a, cudaStream_t st) {
-  const uint64_t threads = (uint64_t)a.nitems * kWideReps;
-  if (threads == 0) return cudaSuccess;
-  mn_sample_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(a);
+  const uint64_t warps = (uint64_t)a.nitems * kWideReps;
+  if (warps == 0) return cudaSuccess;
+  mn_sample_kernel<<<(unsigned)((warps + kMnWarps - 1) / kMnWarps), kMnWarps * 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 
