@@ -103,7 +103,7 @@ def _load():
         lib.or_binom_pmf.restype = c.c_double
         lib.or_binom_pmf.argtypes = [c.c_int64, c.c_int64, c.c_double, c.c_double]
         lib.or_binomial.restype = c.c_int64
-        lib.or_binomial.argtypes = [c.c_int64, c.c_double, c.c_double, c.c_double]
+        lib.or_binomial.argtypes = [c.c_int64, c.c_uint64, c.c_uint64, c.c_double]
         lib.or_thresholds.argtypes = [c.c_double, c.c_uint64, c.c_int64, _u64p]
         lib.or_mn_sample.argtypes = [c.c_double, c.c_uint64, _u64p, c.c_uint64, c.c_uint32, c.c_uint32,
                                      c.c_uint32, c.c_int64, _u64p]
@@ -368,9 +368,9 @@ def binom_pmf(x: int, n: int, p: float, q: float | None = None) -> float:
     return float(_load().or_binom_pmf(x, n, p, 1.0 - p if q is None else q))
 
 
-def binomial(n: int, p: float, u: float, q: float | None = None) -> int:
-    """Bin(n, p) from one uniform u in (0, 1] (inversion along a fixed order)."""
-    return int(_load().or_binomial(n, p, 1.0 - p if q is None else q, u))
+def binomial(n: int, num: int, den: int, u: float) -> int:
+    """Bin(n, num/den) from one uniform u in (0, 1] (inversion along a fixed order)."""
+    return int(_load().or_binomial(n, num, den, u))
 
 
 def thresholds(alpha: float, xmin: int, length: int = MN_BINS) -> np.ndarray:

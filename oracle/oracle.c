@@ -800,18 +800,20 @@ double or_binom_pmf(int64_t x, int64_t n, double p, double q) {
   return exp(lc) * sqrt(dn / (6.283185307179586476925286766559 * dx * dy));
 }
 
-/* Bin(n, p) from one uniform u in (0, 1] by inversion along a fixed order of
- * the outcomes (any order that lists every outcome once gives the law): for
- * a mean below 30 the order 0, 1, 2, ... from P(0) = q^n; otherwise from the
- * mode floor((n+1) p) outward, each step to the neighbour of larger
- * probability (the upper on ties).  Probabilities by the ratio
- * P(k+1)/P(k) = (n-k)/(k+1) p/q.  Once every remaining probability has
- * underflowed, the last outcome taken is returned. */
-int64_t or_binomial(int64_t n, double p, double q, double u) {
-  if (n <= 0 || !(p > 0.0)) return 0;
-  if (!(q > 0.0)) return n;
+/* Bin(n, p), p = num / den (integers, num <= den), from one uniform u in
+ * (0, 1] by inversion along a fixed order of the outcomes (any order that
+ * lists every outcome once gives the law): for a mean n p below 30 the order
+ * 0, 1, 2, ... from P(0) = q^n; otherwise from the mode M = floor((n+1) p)
+ * outward, M+1, M-1, M+2, M-2, ... (one side alone once the other is
+ * exhausted or its probabilities have underflowed).  The branch and M come
+ * from exact integer arithmetic on num and den, so the order never depends
+ * on rounding.  Probabilities by the ratio P(k+1)/P(k) = (n-k)/(k+1) p/q. */
+int64_t or_binomial(int64_t n, uint64_t num, uint64_t den, double u) {
+  if (n <= 0 || num == 0) return 0;
+  if (num >= den) return n;
+  const double p = (double)num / (double)den, q = (double)(den - num) / (double)den;
   const double r = p / q;
-  if ((double)n * p < 30.0) {
+  if ((unsigned __int128)n * num < (unsigned __int128)30 * den) {
     double f = or_binom_pmf(0, n, p, q), c = f;
     int64_t k = 0;
     while (c < u && k < n) {
@@ -822,16 +824,16 @@ int64_t or_binomial(int64_t n, double p, double q, double u) {
     }
     return k;
   }
-  int64_t M = (int64_t)floor((double)(n + 1) * p);
-  if (M > n) M = n;
+  const int64_t M = (int64_t)(((unsigned __int128)(n + 1) * num) / den);
   const double fM = or_binom_pmf(M, n, p, q);
   double rest = u - fM;
   if (rest <= 0.0) return M;
   int64_t lo = M - 1, hi = M + 1, last = M;
   double flo = lo >= 0 ? fM * (double)M / ((double)(n - M + 1) * r) : 0.0;
   double fhi = hi <= n ? fM * (double)(n - M) / (double)(M + 1) * r : 0.0;
+  int up = 1;
   while (flo > 0.0 || fhi > 0.0) {
-    if (fhi >= flo) {
+    if (up ? fhi > 0.0 : !(flo > 0.0)) {
       rest -= fhi;
       last = hi;
       if (rest <= 0.0) return hi;
@@ -844,6 +846,7 @@ int64_t or_binomial(int64_t n, double p, double q, double u) {
       flo = lo > 0 ? flo * (double)lo / ((double)(n - lo + 1) * r) : 0.0;
       --lo;
     }
+    up = !up;
   }
   return last;
 }
@@ -878,9 +881,8 @@ void or_mn_sample(double alpha, uint64_t xmin, const uint64_t *T, uint64_t seed,
   const int64_t B = OR_MN_BINS;
   const double Z = or_hurwitz(alpha, (double)xmin);
   const uint64_t TB = T[B - 1];
-  const double pb = ldexp((double)(TB - 1), -53), qb = ldexp((double)((1ull << 53) + 1 - TB), -53);
   const uint64_t m0 = (or_draw_bits64(seed, cell, rep, purpose, 0) >> 11) + 1;
-  const int64_t beyond = or_binomial(n, pb, qb, ldexp((double)m0, -53));
+  const int64_t beyond = or_binomial(n, TB - 1, 1ull << 53, ldexp((double)m0, -53));
   int64_t *cnt = (int64_t *)calloc((size_t)(2 * B), sizeof(int64_t));
   if (!cnt) return;
   cnt[1] = n - beyond;
@@ -893,9 +895,8 @@ void or_mn_sample(double alpha, uint64_t xmin, const uint64_t *T, uint64_t seed,
     const uint64_t a = or_mn_tm1(T, l), b = or_mn_tm1(T, mid), e = or_mn_tm1(T, r);
     int64_t cl = 0;
     if (a > e) {
-      const double den = (double)(a - e);
       const uint64_t m = (or_draw_bits64(seed, cell, rep, purpose, (uint64_t)k) >> 11) + 1;
-      cl = or_binomial(c, (double)(a - b) / den, (double)(b - e) / den, ldexp((double)m, -53));
+      cl = or_binomial(c, a - b, a - e, ldexp((double)m, -53));
     }
     cnt[2 * k] = cl;
     cnt[2 * k + 1] = c - cl;

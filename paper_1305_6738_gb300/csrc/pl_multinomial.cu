@@ -68,14 +68,24 @@ __device__ double mn_binom_pmf(int64_t x, int64_t n, double p, double q) {
   return exp(lc) * sqrt(dn / (6.283185307179586476925286766559 * dx * dy));
 }
 
-// Bin(n, p) from one uniform u by inversion along a fixed order of the
-// outcomes: 0, 1, 2, ... for a mean below 30, else from the mode outward,
-// each step to the neighbour of larger probability (the upper on ties).
-__device__ int64_t mn_binomial(int64_t n, double p, double q, double u) {
-  if (n <= 0 || !(p > 0.0)) return 0;
-  if (!(q > 0.0)) return n;
+// a * b compared with c * d for 64-bit a, c and 64-bit b, d (128-bit products).
+__device__ __forceinline__ bool mn_mul_lt(uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+  const uint64_t h1 = __umul64hi(a, b), h2 = __umul64hi(c, d);
+  return h1 < h2 || (h1 == h2 && a * b < c * d);
+}
+
+// Bin(n, p), p = num / den (integers, num <= den), from one uniform u by
+// inversion along a fixed order of the outcomes: 0, 1, 2, ... for a mean
+// below 30, else from the mode M = floor((n+1) p) outward, M+1, M-1, M+2, ...
+// (one side alone once the other is exhausted or has underflowed).  The
+// branch and M are exact integer decisions, so the order never depends on
+// rounding.
+__device__ int64_t mn_binomial(int64_t n, uint64_t num, uint64_t den, double u) {
+  if (n <= 0 || num == 0) return 0;
+  if (num >= den) return n;
+  const double p = (double)num / (double)den, q = (double)(den - num) / (double)den;
   const double r = p / q;
-  if ((double)n * p < 30.0) {
+  if (mn_mul_lt((uint64_t)n, num, 30ull, den)) {
     double f = mn_binom_pmf(0, n, p, q), c = f;
     int64_t k = 0;
     while (c < u && k < n) {
@@ -86,16 +96,21 @@ __device__ int64_t mn_binomial(int64_t n, double p, double q, double u) {
     }
     return k;
   }
+  // M = floor((n+1) num / den): a binary64 estimate corrected by exact products
   int64_t M = (int64_t)floor((double)(n + 1) * p);
+  if (M < 0) M = 0;
   if (M > n) M = n;
+  while (M > 0 && mn_mul_lt((uint64_t)(n + 1), num, (uint64_t)M, den)) --M;
+  while (M < n && !mn_mul_lt((uint64_t)(n + 1), num, (uint64_t)(M + 1), den)) ++M;
   const double fM = mn_binom_pmf(M, n, p, q);
   double rest = u - fM;
   if (rest <= 0.0) return M;
   int64_t lo = M - 1, hi = M + 1, last = M;
   double flo = lo >= 0 ? fM * (double)M / ((double)(n - M + 1) * r) : 0.0;
   double fhi = hi <= n ? fM * (double)(n - M) / (double)(M + 1) * r : 0.0;
+  bool up = true;
   while (flo > 0.0 || fhi > 0.0) {
-    if (fhi >= flo) {
+    if (up ? fhi > 0.0 : !(flo > 0.0)) {
       rest -= fhi;
       last = hi;
       if (rest <= 0.0) return hi;
@@ -108,6 +123,7 @@ __device__ int64_t mn_binomial(int64_t n, double p, double q, double u) {
       flo = lo > 0 ? flo * (double)lo / ((double)(n - lo + 1) * r) : 0.0;
       --lo;
     }
+    up = !up;
   }
   return last;
 }
@@ -148,9 +164,8 @@ __global__ void __launch_bounds__(kMnWarps * 32) mn_sample_kernel(MnLaunch a) {
   const uint64_t TB = T[kMnBins - 1];
   int64_t beyond = 0;
   if (lane == 0) {
-    const double pb = (double)(TB - 1) * 0x1p-53, qb = (double)((1ull << 53) + 1 - TB) * 0x1p-53;
     const uint64_t m = (mn_word(0, rep, cell.cell_id, cell.purpose, a.rk) >> 11) + 1;
-    beyond = mn_binomial(n, pb, qb, (double)m * 0x1p-53);
+    beyond = mn_binomial(n, TB - 1, 1ull << 53, (double)m * 0x1p-53);
     dense[kMnScratch + 1] = (uint32_t)(n - beyond);
   }
   beyond = __shfl_sync(0xffffffffu, beyond, 0);
@@ -165,9 +180,8 @@ __global__ void __launch_bounds__(kMnWarps * 32) mn_sample_kernel(MnLaunch a) {
       if (c > 0) {
         const uint64_t A = mn_tm1(T, l), Bm = mn_tm1(T, mid), E = mn_tm1(T, r);
         if (A > E) {
-          const double den = (double)(A - E);
           const uint64_t m = (mn_word(k, rep, cell.cell_id, cell.purpose, a.rk) >> 11) + 1;
-          cl = mn_binomial(c, (double)(A - Bm) / den, (double)(Bm - E) / den, (double)m * 0x1p-53);
+          cl = mn_binomial(c, A - Bm, A - E, (double)m * 0x1p-53);
         }
       }
       if (2 * first < (uint32_t)kMnBins) {

@@ -5,7 +5,8 @@ bin counts by conditional binomials, the tail value by value).
 * The binomial sampler is an inversion along a fixed order of the outcomes,
   so a stratified grid of N uniforms gives every outcome N P(k) times to
   within one: checked against SciPy's pmf on both branches (from 0 and from
-  the mode), including p near 0 and near 1.
+  the mode), including p near 0 and near 1 and a mode (n+1) p that is an
+  integer (p = 64/113, n = 112).
 * The thresholds realise the inverse-CDF test: X(T[i]) <= xmin + i < X(T[i] - 1).
 * A replicate has n values >= xmin; pooled bin counts follow p(k) (chi-square);
   the distribution of D equals the inverse-CDF sampler's (two-sample KS test),
@@ -31,12 +32,14 @@ def test_binomial_pmf_against_scipy(n, p):
             assert oracle.binom_pmf(x, n, p) == pytest.approx(ref, rel=1e-12)
 
 
-@pytest.mark.parametrize("n,p,N", [(10, 0.3, 20000), (40, 0.7, 20000), (1000, 0.5, 20000), (10**6, 0.6, 4000),
-                                   (10**5, 1e-4, 20000), (50, 0.999, 20000), (7, 0.02, 20000)])
-def test_binomial_sampler_is_an_inversion(n, p, N):
+@pytest.mark.parametrize("n,num,den,N", [(10, 3, 10, 20000), (40, 7, 10, 20000), (1000, 1, 2, 20000),
+                                         (10**6, 3, 5, 4000), (10**5, 1, 10000, 20000), (50, 999, 1000, 20000),
+                                         (7, 1, 50, 20000), (112, 64, 113, 20000)])
+def test_binomial_sampler_is_an_inversion(n, num, den, N):
+    p = num / den
     counts = {}
     for i in range(N):
-        k = oracle.binomial(n, p, (i + 0.5) / N)
+        k = oracle.binomial(n, num, den, (i + 0.5) / N)
         assert 0 <= k <= n
         counts[k] = counts.get(k, 0) + 1
     for k, c in counts.items():
