@@ -803,17 +803,24 @@ double or_binom_pmf(int64_t x, int64_t n, double p, double q) {
 /* Bin(n, p), p = num / den (integers, num <= den), from one uniform u in
  * (0, 1] by inversion along a fixed order of the outcomes (any order that
  * lists every outcome once gives the law): for a mean n p below 30 the order
- * 0, 1, 2, ... from P(0) = q^n; otherwise from the mode M = floor((n+1) p)
- * outward, M+1, M-1, M+2, M-2, ... (one side alone once the other is
- * exhausted or its probabilities have underflowed).  The branch and M come
- * from exact integer arithmetic on num and den, so the order never depends
- * on rounding.  Probabilities by the ratio P(k+1)/P(k) = (n-k)/(k+1) p/q. */
+ * 0, 1, 2, ... from P(0) = q^n; otherwise from M = floor((n+1) p) (the mode,
+ * to within a part in 2^24 of p) outward, M+1, M-1, M+2, M-2, ... (one side
+ * alone once the other is exhausted or its probabilities have underflowed).
+ * The branch and M come from integer arithmetic on num and den cut to their
+ * top 24 bits, so the order depends neither on rounding nor on the last
+ * units of the thresholds.  Probabilities by the ratio P(k+1)/P(k) = (n-k)/(k+1) p/q. */
 int64_t or_binomial(int64_t n, uint64_t num, uint64_t den, double u) {
   if (n <= 0 || num == 0) return 0;
   if (num >= den) return n;
   const double p = (double)num / (double)den, q = (double)(den - num) / (double)den;
   const double r = p / q;
-  if ((unsigned __int128)n * num < (unsigned __int128)30 * den) {
+  /* the branch and the mode from num and den cut to their top 24 bits: the
+   * thresholds behind num and den are computed independently by each
+   * implementation and may differ in their last units, and p is often an
+   * exact ratio for which (n+1) p is an integer */
+  const int sh = 64 - __builtin_clzll(den) > 24 ? 64 - __builtin_clzll(den) - 24 : 0;
+  const uint64_t nc = num >> sh, dc = den >> sh;
+  if ((uint64_t)n * nc < 30ull * dc) {
     double f = or_binom_pmf(0, n, p, q), c = f;
     int64_t k = 0;
     while (c < u && k < n) {
@@ -824,7 +831,8 @@ int64_t or_binomial(int64_t n, uint64_t num, uint64_t den, double u) {
     }
     return k;
   }
-  const int64_t M = (int64_t)(((unsigned __int128)(n + 1) * num) / den);
+  int64_t M = (int64_t)(((uint64_t)(n + 1) * nc) / dc);
+  if (M > n) M = n;
   const double fM = or_binom_pmf(M, n, p, q);
   double rest = u - fM;
   if (rest <= 0.0) return M;

@@ -68,24 +68,23 @@ __device__ double mn_binom_pmf(int64_t x, int64_t n, double p, double q) {
   return exp(lc) * sqrt(dn / (6.283185307179586476925286766559 * dx * dy));
 }
 
-// a * b compared with c * d for 64-bit a, c and 64-bit b, d (128-bit products).
-__device__ __forceinline__ bool mn_mul_lt(uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
-  const uint64_t h1 = __umul64hi(a, b), h2 = __umul64hi(c, d);
-  return h1 < h2 || (h1 == h2 && a * b < c * d);
-}
-
 // Bin(n, p), p = num / den (integers, num <= den), from one uniform u by
 // inversion along a fixed order of the outcomes: 0, 1, 2, ... for a mean
-// below 30, else from the mode M = floor((n+1) p) outward, M+1, M-1, M+2, ...
-// (one side alone once the other is exhausted or has underflowed).  The
-// branch and M are exact integer decisions, so the order never depends on
-// rounding.
+// below 30, else from M = floor((n+1) p) (the mode to within a part in 2^24
+// of p) outward, M+1, M-1, M+2, ... (one side alone once the other is
+// exhausted or has underflowed).  The branch and M come from integer
+// arithmetic on num and den cut to their top 24 bits: the thresholds behind
+// them may differ from another implementation's in their last units, and p is
+// often an exact ratio for which (n+1) p is an integer.
 __device__ int64_t mn_binomial(int64_t n, uint64_t num, uint64_t den, double u) {
   if (n <= 0 || num == 0) return 0;
   if (num >= den) return n;
   const double p = (double)num / (double)den, q = (double)(den - num) / (double)den;
   const double r = p / q;
-  if (mn_mul_lt((uint64_t)n, num, 30ull, den)) {
+  const int bits = 64 - __clzll((long long)den);
+  const int sh = bits > 24 ? bits - 24 : 0;
+  const uint64_t nc = num >> sh, dc = den >> sh;
+  if ((uint64_t)n * nc < 30ull * dc) {
     double f = mn_binom_pmf(0, n, p, q), c = f;
     int64_t k = 0;
     while (c < u && k < n) {
@@ -96,12 +95,8 @@ __device__ int64_t mn_binomial(int64_t n, uint64_t num, uint64_t den, double u) 
     }
     return k;
   }
-  // M = floor((n+1) num / den): a binary64 estimate corrected by exact products
-  int64_t M = (int64_t)floor((double)(n + 1) * p);
-  if (M < 0) M = 0;
+  int64_t M = (int64_t)(((uint64_t)(n + 1) * nc) / dc);
   if (M > n) M = n;
-  while (M > 0 && mn_mul_lt((uint64_t)(n + 1), num, (uint64_t)M, den)) --M;
-  while (M < n && !mn_mul_lt((uint64_t)(n + 1), num, (uint64_t)(M + 1), den)) ++M;
   const double fM = mn_binom_pmf(M, n, p, q);
   double rest = u - fM;
   if (rest <= 0.0) return M;
