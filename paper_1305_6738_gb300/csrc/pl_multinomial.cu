@@ -40,20 +40,28 @@ __device__ double mn_stirling_err(double k) {
   return lf - ((k + 0.5) * log(k) - k + 0.918938533204672741780329736406);
 }
 
-// x ln(x/M) + M - x, by its series in v = (x - M)/(x + M) near x = M.
+// x ln(x/M) + M - x, by its series in v = (x - M)/(x + M) near x = M
+// (|v| < 0.1: the terms fall by 100 per step, so 9 of them reach 2^-53).
 __device__ double mn_deviance(double x, double M) {
   if (fabs(x - M) < 0.1 * (x + M)) {
     const double v = (x - M) / (x + M), v2 = v * v;
     double s = (x - M) * v, e = 2.0 * x * v;
-    for (int j = 1; j < 1000; ++j) {
+#pragma unroll
+    for (int j = 1; j <= 9; ++j) {
       e *= v2;
-      const double s1 = s + e / (double)(2 * j + 1);
-      if (s1 == s) return s1;
-      s = s1;
+      s += e * (1.0 / (double)(2 * j + 1));
     }
     return s;
   }
   return x * log(x / M) + M - x;
+}
+
+// 1 / x for x >= 1 (an integer-valued count): the binary32 reciprocal refined
+// by two binary64 Newton steps (relative error below 1 ulp).
+__device__ __forceinline__ double mn_rcp(double x) {
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
 }
 
 // P(Bin(n, p) = x) (q = 1 - p passed separately), saddle-point form
@@ -88,7 +96,7 @@ __device__ int64_t mn_binomial(int64_t n, uint64_t num, uint64_t den, double u) 
     double f = mn_binom_pmf(0, n, p, q), c = f;
     int64_t k = 0;
     while (c < u && k < n) {
-      f *= (double)(n - k) / (double)(k + 1) * r;
+      f *= (double)(n - k) * mn_rcp((double)(k + 1)) * r;
       ++k;
       c += f;
       if (f == 0.0 && (double)k > (double)n * p) break;
@@ -101,21 +109,22 @@ __device__ int64_t mn_binomial(int64_t n, uint64_t num, uint64_t den, double u) 
   double rest = u - fM;
   if (rest <= 0.0) return M;
   int64_t lo = M - 1, hi = M + 1, last = M;
-  double flo = lo >= 0 ? fM * (double)M / ((double)(n - M + 1) * r) : 0.0;
-  double fhi = hi <= n ? fM * (double)(n - M) / (double)(M + 1) * r : 0.0;
+  const double ir = q / p;
+  double flo = lo >= 0 ? fM * (double)M * mn_rcp((double)(n - M + 1)) * ir : 0.0;
+  double fhi = hi <= n ? fM * (double)(n - M) * mn_rcp((double)(M + 1)) * r : 0.0;
   bool up = true;
   while (flo > 0.0 || fhi > 0.0) {
     if (up ? fhi > 0.0 : !(flo > 0.0)) {
       rest -= fhi;
       last = hi;
       if (rest <= 0.0) return hi;
-      fhi = hi < n ? fhi * (double)(n - hi) / (double)(hi + 1) * r : 0.0;
+      fhi = hi < n ? fhi * (double)(n - hi) * mn_rcp((double)(hi + 1)) * r : 0.0;
       ++hi;
     } else {
       rest -= flo;
       last = lo;
       if (rest <= 0.0) return lo;
-      flo = lo > 0 ? flo * (double)lo / ((double)(n - lo + 1) * r) : 0.0;
+      flo = lo > 0 ? flo * (double)lo * mn_rcp((double)(n - lo + 1)) * ir : 0.0;
       --lo;
     }
     up = !up;
