@@ -93,7 +93,18 @@ __device__ int64_t mn_binomial(int64_t n, uint64_t num, uint64_t den, double u) 
   const int sh = bits > 24 ? bits - 24 : 0;
   const uint64_t nc = num >> sh, dc = den >> sh;
   if ((uint64_t)n * nc < 30ull * dc) {
-    double f = mn_binom_pmf(0, n, p, q), c = f;
+    double f;
+    if (n <= 64) {  // q^n by squaring (a few ulps) for the many small counts
+      double b = q;
+      f = 1.0;
+      for (int64_t e = n; e > 0; e >>= 1) {
+        if (e & 1) f *= b;
+        b *= b;
+      }
+    } else {
+      f = mn_binom_pmf(0, n, p, q);
+    }
+    double c = f;
     int64_t k = 0;
     while (c < u && k < n) {
       f *= (double)(n - k) * mn_rcp((double)(k + 1)) * r;
