@@ -715,6 +715,8 @@ def main():
                          "bespoke: 64 data sets (both laws), each fitted with its own cutoffs from 10,000 "
                          "simulated replicates, plus 10^6 lookups in a tabulated grid and one lower-end "
                          "estimate on 10^6 values")
+    ap.add_argument("--large-n-replicates", type=int, default=10_000,
+                    help="large-n: replicates (smaller values for profiler captures only)")
     ap.add_argument("--sampler", choices=["inverse-cdf", "multinomial"], default="inverse-cdf",
                     help="sweep/small/large-n/table1: draw each value by the inverse CDF (default) or the "
                          "histogram by conditional binomials (pl_ks_cutoffs_multinomial)")
@@ -747,8 +749,9 @@ def main():
         wname = ("Table 1 run: gamma in {1.25,...,4.0} (8) x N in {10,...,50000} (15), xmin=1, "
                  "50,000 replicates per cell, quantiles 0.9/0.95/0.99/0.999")
     elif args.workload == "large-n":
-        sweep = inputs.large_n_cell()
-        wname = "large-n heavy tail: alpha=2.0, xmin=1, n=1,000,000, 10,000 replicates (block form)"
+        sweep = inputs.large_n_cell(args.large_n_replicates)
+        wname = (f"large-n heavy tail: alpha=2.0, xmin=1, n=1,000,000, {args.large_n_replicates:,} replicates "
+                 "(block form)")
     else:
         sweep = inputs.batched_instances()
         wname = ("batched uneven: 4,096 instances, n log-uniform [10,1e5], alpha U(1.6,3.2), "
