@@ -524,13 +524,48 @@ def bespoke_cpu_baseline(reqs, data, sample_reps: int, threads: int) -> dict:
                       f"(extrapolated linearly)"}
 
 
+def bespoke_reference(args, reqs, threads):
+    """The reference arm: the oracle's composition per request on the same
+    data (the oracle's own samplers draw the identical values)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    data = []
+    for r in reqs:
+        if r.truncated:
+            x = oracle.tz_sample(r.exponent, r.xmin_or_K, 4, r.request_id, 0, inputs.PURPOSE_TESTDATA, r.n)
+        else:
+            x = oracle.sample(r.exponent, 1, 4, r.request_id, 0, inputs.PURPOSE_TESTDATA, r.n)
+        data.append(np.minimum(x, np.uint64(inputs.INT32_MAX)).astype(np.int64))
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(bespoke_cpu_baseline(reqs, data, max(1, threads), threads))
+    wall = time.perf_counter() - t0
+    value = statistics.mean(v["value"] for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "requests/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * len(reqs) / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (power-law data from the method's sampler, stream tag 2)",
+            "config": {"workload": f"bespoke cutoffs: {len(reqs)} data sets, {BESPOKE_R:,} replicates each"},
+            "cpu_baseline": {"value": value, "unit": "requests/s", "cores": threads, "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
 def run_bespoke(args):
     """64 data sets per step, each through pl_bespoke_cutoffs(_truncated)."""
+    reqs = inputs.bespoke_requests()
+    threads = os.cpu_count() or 1
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) == 0:
+            bespoke_reference(args, reqs, threads)
+        return
     import numpy as np
     import torch
     from paper_1305_6738_gb300 import pl
-    reqs = inputs.bespoke_requests()
-    threads = os.cpu_count() or 1
     config = {"workload": f"bespoke cutoffs: {len(reqs)} data sets (32 untruncated alpha~U(1.6,3), n in "
                           f"[1e2,1e4]; 32 truncated K in {{20,100,1000}}, gamma~U(0.25,3), n in [10,1e4]), "
                           f"{BESPOKE_R:,} simulated replicates each, q=0.9/0.95/0.99; plus {LOOKUPS:,} lookups "
