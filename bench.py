@@ -967,6 +967,9 @@ def main():
         line["cpu_baseline"] = {"value": cb["value"], "unit": "replicates/s", "cores": threads,
                                 "kind": "oracle", "sample": cb["sample"],
                                 "samples_per_s": cb["samples_per_s"]}
+        if args.workload == "sweep":  # the same oracle on one core, a smaller sample
+            c1 = cpu_oracle_rate(max(1, args.cpu_sample // 8), 1)
+            line["cpu_baseline"]["one_core"] = {"value": c1["value"], "cores": 1, "sample": c1["sample"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
