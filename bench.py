@@ -620,6 +620,17 @@ def run_bespoke(args):
             one(r, h.to("cuda", non_blocking=True))
         e2e.append(time.perf_counter() - t0)
     e2e_value = len(reqs) / statistics.mean(e2e)
+    # the untruncated requests again through one batched call (one simulation plan)
+    un = [(r, x) for r, x in zip(reqs, dev) if not r.truncated]
+    bx, bxm, bid = [x for _, x in un], [1] * len(un), [r.request_id for r, _ in un]
+    ctx.pl_bespoke_cutoffs_batch(bx, bxm, BESPOKE_R, 1, bid, BESPOKE_Q, prec)
+    batch_s = []
+    for _ in range(max(2, args.steps)):
+        t0 = time.perf_counter()
+        ctx.pl_bespoke_cutoffs_batch(bx, bxm, BESPOKE_R, 1, bid, BESPOKE_Q, prec)
+        batch_s.append(time.perf_counter() - t0)
+    batched_line = {"requests": len(un), "requests_per_s": len(un) / statistics.mean(batch_s),
+                    "ms_per_call": 1000 * statistics.mean(batch_s)}
     # lookups in a tabulated grid (Table 1's exponents and sizes, 2,000 replicates per cell)
     GA, GN = list(inputs.TABLE1_GAMMAS), list(inputs.TABLE1_NS)
     cells = [pl.Cell(a, 1, n, 2000, 100 * i + k) for i, a in enumerate(GA) for k, n in enumerate(GN)]
@@ -696,6 +707,7 @@ def run_bespoke(args):
                                             "bound by binary64 arithmetic (one log and two divisions per query), "
                                             "not by memory"}},
             "xmin_estimate": xmin_line,
+            "batched_untruncated": batched_line,
             "clocks": clocks}
     if not args.no_cpu_baseline:
         cb = bespoke_cpu_baseline(reqs, data, max(1, threads), threads)

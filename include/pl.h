@@ -356,6 +356,24 @@ pl_status pl_bespoke_cutoffs(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
                              pl_precision prec, double *alpha_hat, double *D,
                              double *p, double *cutoffs_host, void *stream);
 
+/* pl_bespoke_cutoffs for nsets data sets at once: every fit first (one
+ * synchronisation), then a single simulation plan holding one cell per data
+ * set (alpha-hat_i, xmin_i, n_i, R replicates, cell_id = request_id[i]), so
+ * many small requests share the GPU.  Each data set's results equal, bit for
+ * bit, those of pl_bespoke_cutoffs on it alone.  x_dev: host array of nsets
+ * device pointers (int32 data); n, xmin, request_id: host arrays[nsets].
+ * alpha_hat, D, p: host double[nsets]; cutoffs_host: host double[nsets * nq]
+ * (row per data set).  Synchronises `stream`.  Errors: as
+ * pl_bespoke_cutoffs (the data set at fault named in pl_last_error). */
+pl_status pl_bespoke_cutoffs_batch(pl_ctx *ctx, int nsets,
+                                   const int32_t *const *x_dev,
+                                   const int64_t *n, const uint64_t *xmin,
+                                   int64_t R, uint64_t seed,
+                                   const uint64_t *request_id, const double *q,
+                                   int nq, pl_precision prec, double *alpha_hat,
+                                   double *D, double *p, double *cutoffs_host,
+                                   void *stream);
+
 /* The same for the truncated law on 1..K (values 1..K, 1 <= n <= 65535):
  * gamma-hat and D as pl_fit_ks_truncated, then R data sets of the same n at
  * (gamma-hat, K) (any gamma-hat in [-64, 64]: the law on a finite support is

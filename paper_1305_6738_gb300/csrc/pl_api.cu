@@ -1555,6 +1555,129 @@ pl_status pl_bespoke_cutoffs(pl_ctx *ctx, const int32_t *x_dev, int64_t n, uint6
                        (cudaStream_t)stream);
 }
 
+pl_status pl_bespoke_cutoffs_batch(pl_ctx *ctx, int nsets, const int32_t *const *x_dev, const int64_t *n,
+                                   const uint64_t *xmin, int64_t R, uint64_t seed, const uint64_t *request_id,
+                                   const double *q, int nq, pl_precision prec, double *alpha_hat, double *D,
+                                   double *p, double *cutoffs_host, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (nsets < 1 || !x_dev || !n || !xmin || !request_id || !q || nq < 1 || !alpha_hat || !D || !p ||
+      !cutoffs_host || R < 1 || R > (1ll << 31))
+    return fail(ctx, PL_EINVAL, "pl_bespoke_cutoffs_batch: bad arguments");
+  if (prec != PL_FP64 && prec != PL_FP32_BULK) return fail(ctx, PL_EINVAL, "unknown precision form");
+  for (int j = 0; j < nq; ++j)
+    if (!(q[j] > 0.0 && q[j] < 1.0)) return fail(ctx, PL_EINVAL, "quantile %d outside (0, 1)", j);
+  for (int i = 0; i < nsets; ++i)
+    if (!x_dev[i] || n[i] < 1 || n[i] > INT32_MAX || xmin[i] < 1 || xmin[i] > (1ull << 31) ||
+        request_id[i] >= (1ull << 32))
+      return fail(ctx, PL_EINVAL, "pl_bespoke_cutoffs_batch: data set %d: bad arguments", i);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f32 = prec == PL_FP32_BULK;
+  // 1. every data set's fit and D (the data-set kernel, one log table per lower end), one synchronisation
+  std::map<uint64_t, int> law_of;
+  std::vector<LawPlan> lps;
+  for (int i = 0; i < nsets; ++i)
+    if (law_of.emplace(xmin[i], (int)lps.size()).second) lps.push_back({2.0, xmin[i], kL1});
+  std::vector<Law> lh(lps.size());
+  std::vector<Law *> ld(lps.size());
+  std::vector<uint64_t *> spill(nsets), pairs(nsets);
+  double *outs = nullptr;
+  auto lay_fit = [&](Carver &cv) {
+    for (size_t k = 0; k < lps.size(); ++k) {
+      lh[k] = carve_law(cv, lps[k]);
+      ld[k] = cv.take<Law>(1);
+    }
+    for (int i = 0; i < nsets; ++i) {
+      spill[i] = cv.take<uint64_t>(next_pow2((uint64_t)n[i]));
+      pairs[i] = cv.take<uint64_t>(2 * (size_t)n[i]);
+    }
+    outs = cv.take<double>(4 * (size_t)nsets);
+  };
+  {
+    Carver cv;
+    lay_fit(cv);
+    if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+    cv.base = ctx->ws;
+    cv.off = 0;
+    lay_fit(cv);
+  }
+  for (size_t k = 0; k < lps.size(); ++k) {
+    PL_CUDA(cudaMemcpyAsync(ld[k], &lh[k], sizeof(Law), cudaMemcpyHostToDevice, st));
+    PL_CUDA(launch_law_setup(ld[k], 1, st));
+    ctx->launches += 4;
+  }
+  for (int i = 0; i < nsets; ++i) {
+    PL_CUDA(launch_dataset(x_dev[i], n[i], xmin[i], true, 0.0, ld[law_of[xmin[i]]], cell_const(xmin[i]), f32,
+                           spill[i], pairs[i], outs + 4 * (size_t)i, ctx->ctr, st));
+    ctx->launches += 1;
+  }
+  std::vector<double> obs(4 * (size_t)nsets);
+  PL_CUDA(cudaMemcpyAsync(obs.data(), outs, sizeof(double) * obs.size(), cudaMemcpyDeviceToHost, st));
+  if (pl_status s = read_status(ctx, st)) return s;
+  // 2. one simulation of every data set's cell at its fit (purpose 1, cell = request id)
+  std::vector<pl_cell> cells(nsets);
+  for (int i = 0; i < nsets; ++i) cells[i] = pl_cell{obs[4 * (size_t)i], xmin[i], n[i], R, request_id[i]};
+  SimPlan sp;
+  if (pl_status s = plan_cells(ctx, cells.data(), nsets, 1u, sp)) return s;
+  const size_t dsz = f32 ? 4 : 8;
+  const int blocks = sim_blocks(ctx, f32), sblocks = sample_blocks(ctx),
+            bsblocks = ctx->num_sms * std::max(1, ctx->block_sampler_per_sm);
+  SimBuffers b;
+  uint8_t *Db = nullptr;
+  int64_t *off = nullptr, *Rs = nullptr, *rank = nullptr;
+  double *dobs = nullptr, *pd = nullptr, *cut = nullptr;
+  auto lay_sim = [&](Carver &cv) {
+    carve_sim(cv, sp, blocks, sblocks, b, ctx->dbg_arena, bsblocks);
+    Db = cv.take<uint8_t>((size_t)sp.total_R * dsz);
+    off = cv.take<int64_t>(nsets);
+    Rs = cv.take<int64_t>(nsets);
+    rank = cv.take<int64_t>((size_t)nsets * nq);
+    dobs = cv.take<double>(nsets);
+    pd = cv.take<double>(nsets);
+    cut = cv.take<double>((size_t)nsets * nq);
+  };
+  {
+    Carver cv;
+    lay_sim(cv);
+    if (pl_status s = ensure_ws(ctx, cv.off)) return s;
+    cv.base = ctx->ws;
+    cv.off = 0;
+    lay_sim(cv);
+  }
+  if (pl_status s = mark(ctx, 0, st)) return s;
+  if (pl_status s = upload_sim(ctx, sp, b, st)) return s;
+  std::vector<int64_t> h_off(nsets), h_R(nsets), h_rank((size_t)nsets * nq);
+  std::vector<double> h_dobs(nsets);
+  for (int c = 0; c < nsets; ++c) {
+    h_off[c] = sp.cells[c].out_off;
+    h_R[c] = sp.cells[c].R;
+    h_dobs[c] = obs[4 * (size_t)c + 1];
+    for (int j = 0; j < nq; ++j) {
+      const int64_t i = (int64_t)std::floor((double)h_R[c] * q[j]);
+      h_rank[(size_t)c * nq + j] = std::min(std::max<int64_t>(i, 0), h_R[c] - 1);
+    }
+  }
+  PL_CUDA(cudaMemcpyAsync(off, h_off.data(), sizeof(int64_t) * nsets, cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(Rs, h_R.data(), sizeof(int64_t) * nsets, cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(rank, h_rank.data(), sizeof(int64_t) * h_rank.size(), cudaMemcpyHostToDevice, st));
+  PL_CUDA(cudaMemcpyAsync(dobs, h_dobs.data(), sizeof(double) * nsets, cudaMemcpyHostToDevice, st));
+  if (pl_status s = mark(ctx, 1, st)) return s;
+  if (pl_status s = run_sim(ctx, sp, b, seed, f32, Db, nullptr, st)) return s;
+  if (pl_status s = mark(ctx, 2, st)) return s;
+  PL_CUDA(launch_select(Db, f32, off, Rs, rank, nsets, nq, cut, st));
+  for (int c = 0; c < nsets; ++c)
+    PL_CUDA(launch_count_ge(Db + (size_t)h_off[c] * dsz, f32, R, dobs + c, pd + c, st));
+  ctx->launches += 1 + (uint64_t)nsets;
+  if (pl_status s = mark(ctx, 3, st)) return s;
+  PL_CUDA(cudaMemcpyAsync(p, pd, sizeof(double) * nsets, cudaMemcpyDeviceToHost, st));
+  PL_CUDA(cudaMemcpyAsync(cutoffs_host, cut, sizeof(double) * nsets * nq, cudaMemcpyDeviceToHost, st));
+  if (pl_status s = read_status(ctx, st)) return s;
+  for (int i = 0; i < nsets; ++i) {
+    alpha_hat[i] = obs[4 * (size_t)i];
+    D[i] = obs[4 * (size_t)i + 1];
+  }
+  return PL_OK;
+}
+
 pl_status pl_cutoff_lookup(pl_ctx *ctx, const double *grid_alpha, int na, const int64_t *grid_n, int nn,
                            const double *table_dev, int nq, const double *alpha_dev, const int64_t *n_dev,
                            int64_t nquery, double *out_dev, void *stream) {

@@ -33,7 +33,7 @@ EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters",
            "pl_server_poll", "pl_server_now", "pl_server_load", "pl_server_destroy",
            "pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_fit_ks_truncated", "pl_bespoke_cutoffs",
            "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin",
-           "pl_ks_cutoffs_multinomial"]
+           "pl_ks_cutoffs_multinomial", "pl_bespoke_cutoffs_batch"]
 
 
 class pl_cell(ctypes.Structure):
@@ -132,9 +132,13 @@ _lib.pl_estimate_xmin.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int64, ctyp
                                   ctypes.POINTER(pl_xmin_result), _vp, _vp, _vp, _vp, _vp]
 _lib.pl_ks_cutoffs_multinomial.argtypes = [_vp, ctypes.POINTER(pl_cell), ctypes.c_int, ctypes.c_uint64, _f64p,
                                            ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+_lib.pl_bespoke_cutoffs_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint64),
+                                          ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _f64p,
+                                          ctypes.c_int, ctypes.c_int, _f64p, _f64p, _f64p, _f64p, _vp]
 _lib.pl_server_destroy.restype = None
 for _f in ["pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_fit_ks_truncated", "pl_bespoke_cutoffs",
-           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin", "pl_ks_cutoffs_multinomial", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin", "pl_ks_cutoffs_multinomial", "pl_bespoke_cutoffs_batch", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -316,6 +320,22 @@ class Context:
                                             ctypes.byref(d), ctypes.byref(p), cut.ctypes.data_as(_f64p),
                                             _stream_ptr(stream)))
         return a.value, d.value, p.value, cut
+
+    def pl_bespoke_cutoffs_batch(self, xs, xmins, R: int, seed: int, request_ids, q, prec: int = PL_FP64,
+                                 stream=None):
+        """xs: torch.int32 device tensors.  Returns (alpha_hat[], D[], p[], cutoffs[nsets, nq])."""
+        k = len(xs)
+        ptrs = (ctypes.c_void_p * k)(*[_ptr(x) for x in xs])
+        ns = (ctypes.c_int64 * k)(*[x.numel() for x in xs])
+        xm = (ctypes.c_uint64 * k)(*[int(v) for v in xmins])
+        rid = (ctypes.c_uint64 * k)(*[int(v) for v in request_ids])
+        qa = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        a, d, p, cut = np.zeros(k), np.zeros(k), np.zeros(k), np.zeros(k * qa.size)
+        self._check(_lib.pl_bespoke_cutoffs_batch(self._h, k, ptrs, ns, xm, R, seed, rid, qa.ctypes.data_as(_f64p),
+                                                  qa.size, prec, a.ctypes.data_as(_f64p), d.ctypes.data_as(_f64p),
+                                                  p.ctypes.data_as(_f64p), cut.ctypes.data_as(_f64p),
+                                                  _stream_ptr(stream)))
+        return a, d, p, cut.reshape(k, qa.size)
 
     def pl_bespoke_cutoffs_truncated(self, x, K: int, R: int, seed: int, request_id: int, q,
                                      prec: int = PL_FP64, stream=None):

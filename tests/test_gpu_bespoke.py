@@ -151,3 +151,23 @@ def test_cutoff_lookup_matches_oracle(ctx, pl):
     # grid points give the tabulated values exactly
     for i in range(len(GA)):
         assert np.array_equal(got[200 + i], tab[i, 1])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bespoke_batch_equals_single_calls(ctx, pl, prec):
+    specs = [(2.2, 1, 500), (1.8, 1, 3000), (2.6, 2, 50), (2.0, 1, 20000), (3.0, 1, 10), (2.4, 3, 1000)]
+    xs = [_dev(oracle.sample(a, xm, 5, 10 + i, 0, 2, n)) for i, (a, xm, n) in enumerate(specs)]
+    xmins = [xm for _, xm, _ in specs]
+    rids = [100 + i for i in range(len(specs))]
+    a, d, p, cut = ctx.pl_bespoke_cutoffs_batch(xs, xmins, 2000, 9, rids, Q, prec)
+    for i in range(len(specs)):
+        a1, d1, p1, c1 = ctx.pl_bespoke_cutoffs(xs[i], xmins[i], 2000, 9, rids[i], Q, prec)
+        assert (a[i], d[i], p[i]) == (a1, d1, p1), i
+        assert np.array_equal(cut[i], c1), i
+
+
+def test_bespoke_batch_rejects_bad_data(ctx, pl):
+    xs = [_dev([1, 2, 3]), _dev([3, 0, 2])]
+    with pytest.raises(pl.PLError) as e:
+        ctx.pl_bespoke_cutoffs_batch(xs, [1, 1], 100, 1, [0, 1], Q)
+    assert e.value.status == pl.PL_EINVAL
