@@ -58,6 +58,11 @@ struct pl_ctx {
   size_t staging_size = 0;
   cudaEvent_t staging_ev = nullptr;
   bool staged = false;
+  // side streams for independent small kernels inside one call (joined back
+  // to the call's stream by events before the call continues)
+  static constexpr int kAux = 8;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t aux_ev[kAux + 1] = {};
 };
 
 namespace {
@@ -715,6 +720,10 @@ void pl_destroy(pl_ctx *ctx) {
   if (ctx->staging_ev) cudaEventDestroy(ctx->staging_ev);
   if (ctx->staging) cudaFreeHost(ctx->staging);
   for (void *m : ctx->fit_mem) cudaFree(m);
+  for (auto &x : ctx->aux)
+    if (x) cudaStreamDestroy(x);
+  for (auto &e : ctx->aux_ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->ctr) cudaFree(ctx->ctr);
   delete ctx;
@@ -1605,10 +1614,22 @@ pl_status pl_bespoke_cutoffs_batch(pl_ctx *ctx, int nsets, const int32_t *const 
     PL_CUDA(launch_law_setup(ld[k], 1, st));
     ctx->launches += 4;
   }
+  // the fits are independent one-block kernels: spread over the side streams
+  const int naux = std::min(nsets, pl_ctx::kAux);
+  for (int k = 0; k < naux; ++k)
+    if (!ctx->aux[k]) PL_CUDA(cudaStreamCreateWithFlags(&ctx->aux[k], cudaStreamNonBlocking));
+  for (auto &e : ctx->aux_ev)
+    if (!e) PL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  PL_CUDA(cudaEventRecord(ctx->aux_ev[pl_ctx::kAux], st));
+  for (int k = 0; k < naux; ++k) PL_CUDA(cudaStreamWaitEvent(ctx->aux[k], ctx->aux_ev[pl_ctx::kAux], 0));
   for (int i = 0; i < nsets; ++i) {
     PL_CUDA(launch_dataset(x_dev[i], n[i], xmin[i], true, 0.0, ld[law_of[xmin[i]]], cell_const(xmin[i]), f32,
-                           spill[i], pairs[i], outs + 4 * (size_t)i, ctx->ctr, st));
+                           spill[i], pairs[i], outs + 4 * (size_t)i, ctx->ctr, ctx->aux[i % naux]));
     ctx->launches += 1;
+  }
+  for (int k = 0; k < naux; ++k) {
+    PL_CUDA(cudaEventRecord(ctx->aux_ev[k], ctx->aux[k]));
+    PL_CUDA(cudaStreamWaitEvent(st, ctx->aux_ev[k], 0));
   }
   std::vector<double> obs(4 * (size_t)nsets);
   PL_CUDA(cudaMemcpyAsync(obs.data(), outs, sizeof(double) * obs.size(), cudaMemcpyDeviceToHost, st));
