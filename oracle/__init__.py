@@ -5,7 +5,9 @@ CPU-baseline leg of ``bench.py`` may import this package.  It is the
 independent checker of the CUDA library and shares no code with it: the C
 source next to this file is compiled with gcc into ``_build/liboracle.so`` and
 called through ctypes.  See ``oracle.c`` for the paper passages each function
-follows and the parity status of each.
+follows and the parity status of each.  ``cutoff_lookup`` (plain Python) is
+pinned by exactness at grid points, exact reproduction of functions bilinear
+in (exponent, ln N), clamping at the grid's edges and single-row grids.
 """
 from __future__ import annotations
 
