@@ -397,7 +397,10 @@ pl_status pl_bespoke_cutoffs_truncated(pl_ctx *ctx, const int32_t *x_dev,
  * 1 <= nn <= 1024);
  * table_dev: device double[na * nn * nq]; alpha_dev, n_dev: device double /
  * int64 [nquery]; out_dev: device double[nquery * nq], row per query.
- * Stream ordered, no synchronisation.  Errors: PL_EINVAL. */
+ * The queries stay on the device and are not checked: an infinite exponent
+ * or n = 0 clamps to the grid's edge, a NaN exponent or n < 0 gives NaN.
+ * Stream ordered, no synchronisation.  Errors: PL_EINVAL (grids, sizes,
+ * null pointers). */
 pl_status pl_cutoff_lookup(pl_ctx *ctx, const double *grid_alpha, int na,
                            const int64_t *grid_n, int nn,
                            const double *table_dev, int nq,
