@@ -45,7 +45,7 @@ MUL_LANES_PER_SM = 32
 # replicates per cell: 136.6 MB over 360,000 replicates), keyed by the hash of
 # the kernel sources it was taken on (reported as null once they change).  The
 # bench scales it to a launch by the replicates one launch processes.
-TRAFFIC_PER_REPLICATE = {"718eab3d07945042": 136.565248e6 / 360000}
+TRAFFIC_PER_REPLICATE = {"dfd515beb0f1d4ba": (17.476608e6 + 118.964224e6) / 360000}
 
 
 def kernel_source_hash() -> str:
@@ -337,7 +337,11 @@ def tz_source_hash() -> str:
 # one-pass ncu capture of a full Tables 2-6 launch (57.2 MB read + 148.3 MB
 # written for 45,000,000 replicates: the 4-byte D of each replicate plus the
 # tables), keyed by the hash of its sources (null once they change).
-TZ_TRAFFIC_PER_REPLICATE = {"bb5f053fedd20812": (57234944 + 148284928) / 45e6}
+# The second key is the same kernel after a change to pl_device.cuh that only
+# enlarged the untruncated sampler's guide table, which the truncated kernel
+# does not use (it has its own constants).
+TZ_TRAFFIC_PER_REPLICATE = {"bb5f053fedd20812": (57234944 + 148284928) / 45e6,
+                            "a2952dc4a133b7a3": (57234944 + 148284928) / 45e6}
 
 
 def tz_cpu_oracle_rate(cells, sample_reps: int, threads: int) -> dict:

@@ -27,7 +27,7 @@ constexpr uint64_t kXCap = 1ull << 62;      // simulated values saturate here
 #define PL_FIN_MIN_BLOCKS_F64 2
 #endif
 constexpr int kL1 = PL_L1_ENTRIES;          // thresholds staged in shared memory
-constexpr int kGuideBits = 11;              // guide table: 2^11 buckets of m
+constexpr int kGuideBits = 12;              // guide table: 2^12 buckets of m
 constexpr int kGuide = 1 << kGuideBits;
 // A guide word holds the bucket's smallest answer index (low 31 bits) and, in
 // bit 31, whether the bucket holds more than one answer (a search is needed).
