@@ -33,12 +33,14 @@ Q = [0.90, 0.95, 0.99]
 METRIC = "KS replicates/sec and samples/sec per (alpha,n) vs roofline; p50/p99 fit-request latency"
 
 # Roofline of the dominant kernel (the sampler).  Algorithmic work per draw:
-# half a Philox4x32-10 block = 10 rounds x 2 products / 2 draws = 10 full
-# 32x32->64-bit multiplies (plus ~20 XOR/ADD ops on the wider ALU pipe).  The
-# binding unit is the wide-multiply pipe: 32 lanes per SM per clock on GB300
-# (a quarter of the 128 FP32/ALU lanes; measured with an issue-rate probe),
-# so the ceiling is SMs x 32 x clock / 10 draws per second.
-MUL_PER_DRAW = 10
+# a quarter of a Philox4x32-10 block (the draw's high word) = 10 rounds x 2
+# products / 4 draws = 5 full 32x32->64-bit multiplies (plus ~10 XOR/ADD ops
+# on the wider ALU pipe); the low word's block, drawn only for the rare draws
+# whose interval of m holds a threshold or that lie beyond the table, is not
+# counted.  The binding unit is the wide-multiply pipe: 32 lanes per SM per
+# clock on GB300 (a quarter of the 128 FP32/ALU lanes; measured with an
+# issue-rate probe), so the ceiling is SMs x 32 x clock / 5 draws per second.
+MUL_PER_DRAW = 5
 MUL_LANES_PER_SM = 32
 
 # DRAM bytes per replicate of the sampler from one ncu capture (sweep at 4,000
