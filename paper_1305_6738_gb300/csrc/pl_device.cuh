@@ -175,8 +175,8 @@ __device__ __forceinline__ uint64_t draw_m(uint32_t h, uint32_t l) {
 // m of draw i from its high word h (one Philox block of the low stream).  A
 // call, not inlined: the samplers take it rarely, and inlined its rounds
 // would claim registers in their draw loops.
-static __device__ __noinline__ uint64_t draw_m_full(uint32_t h, uint64_t i, uint32_t rep, uint32_t cell, uint32_t purpose,
-                                             uint32_t key_lo, uint32_t key_hi) {
+static __device__ __noinline__ uint64_t draw_m_full(uint32_t h, uint64_t i, uint32_t rep, uint32_t cell,
+                                                    uint32_t purpose, uint32_t key_lo, uint32_t key_hi) {
   const uint4 w = philox4x32_10(make_uint4((uint32_t)(i >> 2), rep, cell, purpose | kLowStream),
                                 make_uint2(key_lo, key_hi));
   return draw_m(h, quad_word(w, (uint32_t)i & 3u));

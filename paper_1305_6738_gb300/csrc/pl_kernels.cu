@@ -844,7 +844,9 @@ __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint
     }
   };
   // m of draw i from its high word h (a block of the low stream)
-  auto m_of = [&](uint32_t h, uint64_t i) { return draw_m_full(h, i, rep, cell.cell_id, cell.purpose, rk.k[0], rk.k[1]); };
+  auto m_of = [&](uint32_t h, uint64_t i) {
+    return draw_m_full(h, i, rep, cell.cell_id, cell.purpose, rk.k[0], rk.k[1]);
+  };
   // a draw of a multi-valued guide bucket: table search on its high word
   auto search = [&](uint32_t h, uint64_t i) {
     uint64_t m = 0;
@@ -1050,7 +1052,9 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
           }
         }
       };
-      auto m_of = [&](uint32_t h, uint64_t i) { return draw_m_full(h, i, rep, cell.cell_id, cell.purpose, a.rk.k[0], a.rk.k[1]); };
+      auto m_of = [&](uint32_t h, uint64_t i) {
+        return draw_m_full(h, i, rep, cell.cell_id, cell.purpose, a.rk.k[0], a.rk.k[1]);
+      };
       auto search = [&](uint32_t h, uint64_t i) {
         uint64_t m = 0;
         const uint32_t b = lookup_index_hi(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, h,

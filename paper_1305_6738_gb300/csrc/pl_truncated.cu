@@ -451,8 +451,8 @@ __global__ void __launch_bounds__(kTzWarps * 32, PL_TZ_MIN_BLOCKS) tz_replicate_
     // draw i's high word is word i mod 4 of block i / 4; its low word is
     // drawn only when a threshold lies inside its interval of m
     auto one = [&](uint32_t hw, uint32_t i) {
-      tz_count(tz_lookup_hi(sT, sG, hw, [&] { return draw_m_full(hw, i, r, c.cell_id, c.purpose, a.rk.k[0], a.rk.k[1]); }), h, c12,
-               c34);
+      auto m_full = [&] { return draw_m_full(hw, i, r, c.cell_id, c.purpose, a.rk.k[0], a.rk.k[1]); };
+      tz_count(tz_lookup_hi(sT, sG, hw, m_full), h, c12, c34);
     };
     for (uint32_t p = lane; p < nquads; p += 32) {
       const uint4 w = philox4x32_10_rk(make_uint4(p, r, c.cell_id, c.purpose), a.rk);
