@@ -4,7 +4,6 @@ the surrounding grid cells, clamped to the grid's edges."""
 import math
 
 import numpy as np
-import pytest
 
 import oracle
 

