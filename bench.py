@@ -33,12 +33,14 @@ Q = [0.90, 0.95, 0.99]
 METRIC = "KS replicates/sec and samples/sec per (alpha,n) vs roofline; p50/p99 fit-request latency"
 
 # Roofline of the dominant kernel (the sampler).  Algorithmic work per draw:
-# half a Philox4x32-10 block = 10 rounds x 2 products / 2 draws = 10 full
-# 32x32->64-bit multiplies (plus ~20 XOR/ADD ops on the wider ALU pipe).  The
-# binding unit is the wide-multiply pipe: 32 lanes per SM per clock on GB300
-# (a quarter of the 128 FP32/ALU lanes; measured with an issue-rate probe),
-# so the ceiling is SMs x 32 x clock / 10 draws per second.
-MUL_PER_DRAW = 10
+# a quarter of a Philox4x32-10 block (the draw's high word) = 10 rounds x 2
+# products / 4 draws = 5 full 32x32->64-bit multiplies (plus ~10 XOR/ADD ops
+# on the wider ALU pipe); the low word's block, drawn only for the rare draws
+# whose interval of m holds a threshold or that lie beyond the table, is not
+# counted.  The binding unit is the wide-multiply pipe: 32 lanes per SM per
+# clock on GB300 (a quarter of the 128 FP32/ALU lanes; measured with an
+# issue-rate probe), so the ceiling is SMs x 32 x clock / 5 draws per second.
+MUL_PER_DRAW = 5
 MUL_LANES_PER_SM = 32
 
 # DRAM bytes per replicate of the sampler from one ncu capture (sweep at 4,000
@@ -721,6 +723,48 @@ def run_bespoke(args):
     ctx.close()
 
 
+def cell_line(alpha: float, n: int, R: int, step_ms: float, sample_ms: float, finish_ms: float,
+              mul_peak_gmul: float) -> dict:
+    """One (alpha, n) cell run alone: replicates/s and samples/s over the
+    call's device time, the sampler's fraction of the multiply-pipe peak and
+    the finisher's time per replicate."""
+    draws = R * n
+    return {"alpha": alpha, "n": n, "replicates": R, "ms": step_ms,
+            "replicates_per_s": R / (step_ms / 1e3), "samples_per_s": draws / (step_ms / 1e3),
+            "sampler_ms": sample_ms, "finisher_ms": finish_ms,
+            "finisher_ns_per_replicate": finish_ms * 1e6 / R,
+            "sampler_frac": (MUL_PER_DRAW * draws / (sample_ms / 1e3) / 1e9 / mul_peak_gmul
+                             if sample_ms > 0 else None)}
+
+
+def per_cell_rates(ctx, cells, seed: int, qs, prec: int, mul_peak_gmul: float, flush, torch,
+                   reps: int = 3) -> list:
+    """Every cell of the sweep run alone (its own call, after one warm-up
+    call): the median over `reps` timed calls, each after an L2 flush, with
+    CUDA events on the call's stream and the library's per-kernel trace."""
+    stream = torch.cuda.current_stream()
+    one_cut = torch.empty(len(qs), dtype=torch.float64, device="cuda")
+    ctx.pl_set_tracing(True)
+    rows = []
+    for c in cells:
+        ctx.pl_ks_cutoffs([c], seed, qs, prec, cutoffs=one_cut)
+        ms, sm, fm = [], [], []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.pl_ks_cutoffs([c], seed, qs, prec, cutoffs=one_cut)
+            e1.record(stream)
+            tr = ctx.pl_trace()  # synchronises
+            ms.append(e0.elapsed_time(e1))
+            sm.append(tr["sample_ms"])
+            fm.append(tr["finish_ms"])
+        rows.append(cell_line(c.alpha, c.n, c.replicates, statistics.median(ms), statistics.median(sm),
+                              statistics.median(fm), mul_peak_gmul))
+    return rows
+
+
 def replica_seed(rank: int) -> int:
     """Replicas (one process per GPU) draw independent Philox streams: the key
     is the base seed plus the rank.  No data crosses ranks."""
@@ -766,6 +810,8 @@ def main():
                          "bespoke: 64 data sets (both laws), each fitted with its own cutoffs from 10,000 "
                          "simulated replicates, plus 10^6 lookups in a tabulated grid and one lower-end "
                          "estimate on 10^6 values")
+    ap.add_argument("--per-cell", action="store_true",
+                    help="sweep: also time every (alpha, n) cell alone and add a per_cell list to the line")
     ap.add_argument("--large-n-replicates", type=int, default=10_000,
                     help="large-n: replicates (smaller values for profiler captures only)")
     ap.add_argument("--sampler", choices=["inverse-cdf", "multinomial"], default="inverse-cdf",
@@ -986,6 +1032,8 @@ def main():
         if args.workload == "sweep":  # the same oracle on one core, a smaller sample
             c1 = cpu_oracle_rate(max(1, args.cpu_sample // 8), 1)
             line["cpu_baseline"]["one_core"] = {"value": c1["value"], "cores": 1, "sample": c1["sample"]}
+    if args.per_cell and args.workload == "sweep" and world == 1 and args.sampler == "inverse-cdf":
+        line["per_cell"] = per_cell_rates(ctx, cells, seed, QS, prec, mul_peak, flush, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -29,13 +29,16 @@
  *   ran out, bad data values) are latched in the context and reported by the
  *   next pl_sync or by the next entry point with a host output.
  * - Randomness: draw i of replicate r is a pure function of
- *   (seed, cell_id, r, purpose, i) through Philox4x32-10 (counter
- *   (i/2, r, cell_id, purpose), key = seed).  Sampled values never depend on
+ *   (seed, cell_id, r, purpose, i) through Philox4x32-10 (key = seed): the
+ *   high 32 of its 53 bits are word i mod 4 of the block with counter
+ *   (i/4, r, cell_id, purpose), the low 21 the top bits of the same word of
+ *   the block with counter (i/4, r, cell_id, purpose + 2^31), which the
+ *   samplers generate only when a draw needs them.  Sampled values never depend on
  *   launch shape, batching, the warp/block split or the precision form; for a
  *   given split and precision form every result is bit-identical whether a
  *   cell runs alone or with others.  Changing the split changes the rounding
- *   of alpha-hat and D at the 1e-15 level.  purpose: 0 = cutoff simulation,
- *   1 = parametric bootstrap, 2 = test data.
+ *   of alpha-hat and D at the 1e-15 level.  purpose (< 2^31): 0 = cutoff
+ *   simulation, 1 = parametric bootstrap, 2 = test data.
  * - Heavy tail: simulated values are uint64 and saturate at 2^62.
  */
 #ifndef PL_H_
@@ -133,7 +136,7 @@ pl_status pl_trace(pl_ctx *ctx, void *stream, pl_trace_info *out);
  * Writes nrep * n values, row r (replicate rep0 + r) at out_dev[r * n].
  * out_dev: device, uint64[nrep * n].  Errors: PL_EINVAL (alpha <= 1,
  * xmin < 1, n < 1, nrep < 1, cell_id >= 2^32, rep0 + nrep > 2^32,
- * n > 2^33). */
+ * n > 2^34, purpose >= 2^31). */
 pl_status pl_sample(pl_ctx *ctx, double alpha, uint64_t xmin, uint64_t seed,
                     uint64_t cell_id, uint32_t purpose, uint64_t rep0,
                     int64_t nrep, int64_t n, uint64_t *out_dev, void *stream);
@@ -307,8 +310,8 @@ typedef struct {
 
 /* Draws from the truncated law, nrep rows of n (row r = replicate rep0 + r)
  * at out_dev[r * n]; out_dev: device, uint64[nrep * n].  Errors: PL_EINVAL
- * (gamma outside (0, 64], K outside [2, 1024], n < 1, n > 2^33, nrep < 1,
- * cell_id >= 2^32, rep0 + nrep > 2^32). */
+ * (gamma outside (0, 64], K outside [2, 1024], n < 1, n > 2^34, nrep < 1,
+ * cell_id >= 2^32, rep0 + nrep > 2^32, purpose >= 2^31). */
 pl_status pl_sample_truncated(pl_ctx *ctx, double gamma, uint64_t K,
                               uint64_t seed, uint64_t cell_id,
                               uint32_t purpose, uint64_t rep0, int64_t nrep,

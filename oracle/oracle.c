@@ -86,21 +86,24 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* Draw i of stream (seed, cell, rep, purpose): Philox block with counter
- * (floor(i/2), rep, cell, purpose) and key (seed_lo, seed_hi); draw i takes
- * words (w[2j], w[2j+1]), j = i mod 2, as the low and high halves of a
- * 64-bit integer, keeps its top 53 bits and adds one, giving m in [1, 2^53].
- * The uniform is v = m * 2^-53 in (0, 1], the same half-open interval as the
+/* Draw i of stream (seed, cell, rep, purpose), key (seed_lo, seed_hi): its
+ * high word h is word j = i mod 4 of the Philox block with counter
+ * (floor(i/4), rep, cell, purpose), its low word l word j of the block with
+ * counter (floor(i/4), rep, cell, purpose + 2^31) (purposes are below 2^31).
+ * m = h 2^21 + floor(l / 2^11) + 1 lies in [1, 2^53] (53 random bits) and the
+ * uniform is v = m 2^-53 in (0, 1], the same half-open interval as the
  * double-precision uniform the paper's sampler consumes. */
+#define OR_LOW_STREAM 0x80000000u
 uint64_t or_draw_m(uint64_t seed, uint32_t cell, uint32_t rep,
                    uint32_t purpose, uint64_t i) {
-  uint32_t ctr[4] = {(uint32_t)(i >> 1), rep, cell, purpose};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-  uint32_t w[4];
-  or_philox4x32_10(ctr, key, w);
-  int j = (int)(i & 1);
-  uint64_t bits = ((uint64_t)w[2 * j + 1] << 32) | (uint64_t)w[2 * j];
-  return (bits >> 11) + 1;
+  uint32_t ctr_hi[4] = {(uint32_t)(i >> 2), rep, cell, purpose};
+  uint32_t ctr_lo[4] = {(uint32_t)(i >> 2), rep, cell, purpose | OR_LOW_STREAM};
+  uint32_t wh[4], wl[4];
+  or_philox4x32_10(ctr_hi, key, wh);
+  or_philox4x32_10(ctr_lo, key, wl);
+  int j = (int)(i & 3);
+  return (((uint64_t)wh[j] << 21) | (uint64_t)(wl[j] >> 11)) + 1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -742,9 +745,10 @@ int or_estimate_xmin(const uint64_t *x, int64_t n, int64_t max_candidates, int64
  * binomials instead of one draw per value.  Same law as the inverse-CDF
  * sampler (its integer thresholds), a different random stream.            */
 
-/* The 64 bits of draw i of stream (seed, cell, rep, purpose): the words
- * (w[2j], w[2j+1]), j = i mod 2, of Philox block floor(i/2) as the low and
- * high halves (the bits whose top 53 give or_draw_m). */
+/* Word i of 64 bits of stream (seed, cell, rep, purpose), the multinomial
+ * sampler's random numbers: the words (w[2j], w[2j+1]), j = i mod 2, of the
+ * Philox block with counter (floor(i/2), rep, cell, purpose) as the low and
+ * high halves. */
 uint64_t or_draw_bits64(uint64_t seed, uint32_t cell, uint32_t rep, uint32_t purpose, uint64_t i) {
   uint32_t ctr[4] = {(uint32_t)(i >> 1), rep, cell, purpose};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};

@@ -788,7 +788,8 @@ pl_status pl_sample(pl_ctx *ctx, double alpha, uint64_t xmin, uint64_t seed, uin
                     void *stream) {
   if (pl_status s = check_ctx(ctx)) return s;
   if (!(alpha > 1.0) || alpha > 64.0 || xmin < 1 || xmin > (1ull << 40) || n < 1 || nrep < 1 ||
-      cell_id >= (1ull << 32) || rep0 + (uint64_t)nrep > (1ull << 32) || n > (1ll << 33) || !out_dev)
+      cell_id >= (1ull << 32) || rep0 + (uint64_t)nrep > (1ull << 32) || n > (1ll << 34) || purpose >= kLowStream ||
+      !out_dev)
     return fail(ctx, PL_EINVAL, "pl_sample: argument out of range");
   cudaStream_t st = (cudaStream_t)stream;
   LawPlan lp{alpha, xmin, table_length(alpha, xmin, (double)n * (double)nrep)};
@@ -950,8 +951,8 @@ pl_status pl_sample_truncated(pl_ctx *ctx, double gamma, uint64_t K, uint64_t se
                               void *stream) {
   if (pl_status s = check_ctx(ctx)) return s;
   if (pl_status s = tz_check_law(ctx, gamma, K)) return s;
-  if (n < 1 || nrep < 1 || cell_id >= (1ull << 32) || rep0 + (uint64_t)nrep > (1ull << 32) || n > (1ll << 33) ||
-      !out_dev)
+  if (n < 1 || nrep < 1 || cell_id >= (1ull << 32) || rep0 + (uint64_t)nrep > (1ull << 32) || n > (1ll << 34) ||
+      purpose >= kLowStream || !out_dev)
     return fail(ctx, PL_EINVAL, "pl_sample_truncated: argument out of range");
   cudaStream_t st = (cudaStream_t)stream;
   TzLaw lh{};

@@ -154,10 +154,37 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const RoundKeys &rk) 
   return c;
 }
 
-// m in [1, 2^53] from the words (lo, hi) of one draw: top 53 bits plus one.
-__device__ __forceinline__ uint64_t draw_bits(uint32_t lo, uint32_t hi) {
-  return ((((uint64_t)hi << 32) | lo) >> 11) + 1ull;
+// Draw i of the stream (rep, cell, purpose): its high word h is word i mod 4
+// of the Philox block with counter (floor(i/4), rep, cell, purpose), its low
+// word l the same word of the block with counter (floor(i/4), rep, cell,
+// purpose | kLowStream); m = h 2^21 + floor(l / 2^11) + 1 in [1, 2^53].  Every
+// m of the interval [h 2^21 + 1, (h + 1) 2^21] has the same answer unless a
+// threshold lies inside it (at most one draw in 2^32 per threshold), so the
+// samplers take the low word only then, or for a draw beyond the table, whose
+// tail inversion needs m itself.
+constexpr uint32_t kLowStream = 0x80000000u;
+
+__device__ __forceinline__ uint32_t quad_word(const uint4 &w, uint32_t j) {
+  return j == 0 ? w.x : (j == 1 ? w.y : (j == 2 ? w.z : w.w));
 }
+
+__device__ __forceinline__ uint64_t draw_m(uint32_t h, uint32_t l) {
+  return (((uint64_t)h << 21) | (l >> 11)) + 1ull;
+}
+
+// m of draw i from its high word h (one Philox block of the low stream).  A
+// call, not inlined: the samplers take it rarely, and inlined its rounds
+// would claim registers in their draw loops.
+static __device__ __noinline__ uint64_t draw_m_full(uint32_t h, uint64_t i, uint32_t rep, uint32_t cell,
+                                                    uint32_t purpose, uint32_t key_lo, uint32_t key_hi) {
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)(i >> 2), rep, cell, purpose | kLowStream),
+                                make_uint2(key_lo, key_hi));
+  return draw_m(h, quad_word(w, (uint32_t)i & 3u));
+}
+
+// Smallest and largest m a high word allows.
+__device__ __forceinline__ uint64_t m_first(uint32_t h) { return ((uint64_t)h << 21) + 1ull; }
+__device__ __forceinline__ uint64_t m_last(uint32_t h) { return ((uint64_t)h + 1ull) << 21; }
 
 // ---------------------------------------------------------------------------
 // Euler-Maclaurin for the Hurwitz zeta (DLMF 2.10.1, 25.11):
@@ -533,6 +560,21 @@ __device__ __forceinline__ uint32_t lookup_index(const uint64_t *sT, const uint3
     else lo = mid + 1;
   }
   return lo;
+}
+
+// Index of a draw known by its high word h: the answer at m_first(h); the
+// low word (m_full(), which returns m) is drawn only when the answer at
+// m_last(h) may be smaller (T[i - 1] <= m_last) or the answer lies beyond the
+// table, and then *m receives m.  The answer is nonincreasing in m, so the
+// first case is exact.
+template <class MFull>
+__device__ __forceinline__ uint32_t lookup_index_hi(const uint64_t *sT, const uint32_t *sG, const uint64_t *gT,
+                                                    uint32_t L2, float xmin_f, float tail_c, float tail_e,
+                                                    uint32_t h, MFull m_full, uint64_t *m) {
+  const uint32_t i0 = lookup_index(sT, sG, gT, L2, xmin_f, tail_c, tail_e, m_first(h));
+  if (i0 < L2 && (i0 == 0 || table_at(sT, gT, i0 - 1) > m_last(h))) return i0;
+  *m = m_full();
+  return lookup_index(sT, sG, gT, L2, xmin_f, tail_c, tail_e, *m);
 }
 
 __device__ __forceinline__ uint64_t lookup_fast(const uint64_t *sT, const uint32_t *sG,

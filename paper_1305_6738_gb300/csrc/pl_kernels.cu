@@ -154,7 +154,8 @@ __device__ bool stage_law(const StagedLaw &s, const Law &law, uint32_t &phase, C
 }
 
 // ===========================================================================
-// Sampling only (pl_sample): one thread per pair of draws.
+// Sampling only (pl_sample): one thread per four draws, each m taken whole
+// (both words).
 __global__ void __launch_bounds__(256) sample_kernel(const Law *law_p, uint64_t seed,
                                                      uint32_t cell_id, uint32_t purpose,
                                                      uint32_t rep0, int64_t nrep, int64_t n,
@@ -167,18 +168,19 @@ __global__ void __launch_bounds__(256) sample_kernel(const Law *law_p, uint64_t 
   uint32_t phase = 0;
   if (!stage_law(s, law, phase, ctr)) return;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-  const int64_t npairs = (n + 1) >> 1;
-  const int64_t total = npairs * nrep;
+  const int64_t nquads = (n + 3) >> 2;
+  const int64_t total = nquads * nrep;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / npairs;
-    const int64_t p = idx - r * npairs;
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)p, rep0 + (uint32_t)r, cell_id, purpose), key);
+    const int64_t r = idx / nquads;
+    const int64_t p = idx - r * nquads;
+    const uint4 wh = philox4x32_10(make_uint4((uint32_t)p, rep0 + (uint32_t)r, cell_id, purpose), key);
+    const uint4 wl = philox4x32_10(make_uint4((uint32_t)p, rep0 + (uint32_t)r, cell_id, purpose | kLowStream), key);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int64_t i = 2 * p + j;
+    for (uint32_t j = 0; j < 4; ++j) {
+      const int64_t i = 4 * p + j;
       if (i < n) {
-        const uint64_t m = draw_bits(j ? w.z : w.x, j ? w.w : w.y);
+        const uint64_t m = draw_m(quad_word(wh, j), quad_word(wl, j));
         out[r * n + i] = lookup(s.sT, s.sG, law.T, law.L2, law.xmin, law.alpha, law.Z, law.xmin_f,
                                 law.tail_c, law.tail_e, m, &ctr->tail_draws);
       }
@@ -190,8 +192,8 @@ cudaError_t launch_sample(const Law *law_dev, uint64_t seed, uint32_t cell_id, u
                           uint32_t rep0, int64_t nrep, int64_t n, uint64_t *out, Counters *ctr,
                           int num_sms, cudaStream_t st) {
   const size_t smem = kL1 * 8 + kGuide * 4 + 16;
-  const int64_t pairs = ((n + 1) / 2) * nrep;
-  int64_t blocks = (pairs + 255) / 256;
+  const int64_t quads = ((n + 3) / 4) * nrep;
+  int64_t blocks = (quads + 255) / 256;
   const int64_t cap = (int64_t)num_sms * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
@@ -816,6 +818,7 @@ __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint
   if (lane == 0) *s_count = 0;
   __syncwarp();
   uint64_t packed = 0;  // 16-bit counters of bins 0..3
+  // b: the draw's table index; m: its m, needed (and given) only beyond the table
   auto bin = [&](uint32_t b, uint64_t m) {
     if (b < 4) {
       packed += 1ull << (16 * b);
@@ -840,57 +843,74 @@ __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint
       }
     }
   };
+  // m of draw i from its high word h (a block of the low stream)
+  auto m_of = [&](uint32_t h, uint64_t i) {
+    return draw_m_full(h, i, rep, cell.cell_id, cell.purpose, rk.k[0], rk.k[1]);
+  };
+  // a draw of a multi-valued guide bucket: table search on its high word
+  auto search = [&](uint32_t h, uint64_t i) {
+    uint64_t m = 0;
+    const uint32_t b = lookup_index_hi(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, h,
+                                       [&] { return m_of(h, i); }, &m);
+    bin(b, m);
+  };
   int qn = 0;  // warp-uniform queue length (< 32 between draws)
   const unsigned lt = (1u << lane) - 1u;
-  // One draw: the guide word answers directly unless its bucket holds several
-  // values; bins 0..3 go to the lane's registers without a branch.
-  auto draw = [&](uint32_t wlo, uint32_t whi, bool valid) {
+  // One draw (high word h, index i): the guide word answers directly unless
+  // its bucket holds several values; bins 0..3 go to the lane's registers
+  // without a branch.  Queued draws keep (i, h).
+  auto draw = [&](uint32_t h, uint64_t i, bool valid) {
+    const uint32_t gw = sG[h >> (32 - kGuideBits)];
     if (DEFER) {
-      // guide bucket = top kGuideBits of m - 1 = top bits of the high word
-      const uint32_t gw = sG[whi >> (32 - kGuideBits)];
       const bool direct = valid && !(gw & kGuideMulti);
       packed += (direct && gw < 4) ? 1ull << (16 * (gw & 3u)) : 0ull;
-      if (direct && gw >= 4) bin(gw, draw_bits(wlo, whi));
+      if (direct && gw >= 4) bin(gw, gw >= law.L2 ? m_of(h, i) : 0ull);
       const bool later = valid && (gw & kGuideMulti);
       if (__any_sync(0xffffffffu, later)) {
         const unsigned dm = __ballot_sync(0xffffffffu, later);
-        if (later) defer_q[qn + __popc(dm & lt)] = draw_bits(wlo, whi);
+        if (later) defer_q[qn + __popc(dm & lt)] = (i << 32) | h;
         qn += __popc(dm);
         if (qn >= 32) {
           __syncwarp();
           qn -= 32;
-          const uint64_t mq = defer_q[qn + lane];
+          const uint64_t q = defer_q[qn + lane];
           __syncwarp();
-          bin(lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, mq), mq);
+          search((uint32_t)q, q >> 32);
         }
       }
     } else if (valid) {
-      const uint32_t gw = sG[whi >> (32 - kGuideBits)];
-      const uint64_t m = draw_bits(wlo, whi);
-      bin((gw & kGuideMulti) ? lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m)
-                             : gw,
-          m);
+      if (gw & kGuideMulti)
+        search(h, i);
+      else
+        bin(gw, gw >= law.L2 ? m_of(h, i) : 0ull);
     }
   };
-  // full rounds (every lane has two valid draws: pairs below a multiple of 32
-  // that is at most n/2), then one ragged round for the at most 32 pairs left
-  const int64_t full = (n >> 1) & ~(int64_t)31;
+  // full rounds (every lane has four valid draws: blocks below a multiple of
+  // 32 that is at most n/4), then one ragged round for the at most 32 blocks
+  // left
+  const int64_t full = (n >> 2) & ~(int64_t)31;
   int64_t p = lane;
   for (; p < full; p += 32) {
     const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
-    draw(w.x, w.y, true);
-    draw(w.z, w.w, true);
+    const uint64_t i0 = 4 * (uint64_t)p;
+    draw(w.x, i0, true);
+    draw(w.y, i0 + 1, true);
+    draw(w.z, i0 + 2, true);
+    draw(w.w, i0 + 3, true);
   }
-  if (2 * full < n) {
+  if (4 * full < n) {
     const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
-    draw(w.x, w.y, 2 * p < n);
-    draw(w.z, w.w, 2 * p + 1 < n);
+    const int64_t i0 = 4 * p;
+    draw(w.x, (uint64_t)i0, i0 < n);
+    draw(w.y, (uint64_t)i0 + 1, i0 + 1 < n);
+    draw(w.z, (uint64_t)i0 + 2, i0 + 2 < n);
+    draw(w.w, (uint64_t)i0 + 3, i0 + 3 < n);
   }
   if (DEFER) {
     __syncwarp();
     if (lane < qn) {
-      const uint64_t mq = defer_q[lane];
-      bin(lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, mq), mq);
+      const uint64_t q = defer_q[lane];
+      search((uint32_t)q, q >> 32);
     }
   }
   __syncwarp();
@@ -1010,6 +1030,7 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
       const uint64_t pos0 = wi.spill_off + (uint64_t)j * cell.scap;
       uint64_t *spill = a.rec.spill + pos0;
       uint64_t packed = 0;
+      // b: the draw's table index; m: its m, needed (and given) only beyond the table
       auto bin = [&](uint32_t b, uint64_t m) {
         if (b < 4) {
           packed += 1ull << (16 * b);
@@ -1031,46 +1052,61 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
           }
         }
       };
+      auto m_of = [&](uint32_t h, uint64_t i) {
+        return draw_m_full(h, i, rep, cell.cell_id, cell.purpose, a.rk.k[0], a.rk.k[1]);
+      };
+      auto search = [&](uint32_t h, uint64_t i) {
+        uint64_t m = 0;
+        const uint32_t b = lookup_index_hi(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, h,
+                                           [&] { return m_of(h, i); }, &m);
+        bin(b, m);
+      };
       // direct answers from the guide; multi-valued buckets searched 32 at a
       // time through the warp's queue (as in the warp form)
       int qn = 0;
-      auto draw = [&](uint32_t wlo, uint32_t whi, bool valid) {
-        const uint32_t gw = sG[whi >> (32 - kGuideBits)];
+      auto draw = [&](uint32_t h, uint64_t i, bool valid) {
+        const uint32_t gw = sG[h >> (32 - kGuideBits)];
         const bool direct = valid && !(gw & kGuideMulti);
         packed += (direct && gw < 4) ? 1ull << (16 * (gw & 3u)) : 0ull;
-        if (direct && gw >= 4) bin(gw, draw_bits(wlo, whi));
+        if (direct && gw >= 4) bin(gw, gw >= law.L2 ? m_of(h, i) : 0ull);
         const bool later = valid && (gw & kGuideMulti);
         if (__any_sync(0xffffffffu, later)) {
           const unsigned dm = __ballot_sync(0xffffffffu, later);
-          if (later) defer_q[qn + __popc(dm & lt)] = draw_bits(wlo, whi);
+          if (later) defer_q[qn + __popc(dm & lt)] = (i << 32) | h;
           qn += __popc(dm);
           if (qn >= 32) {
             __syncwarp();
             qn -= 32;
-            const uint64_t mq = defer_q[qn + lane];
+            const uint64_t q = defer_q[qn + lane];
             __syncwarp();
-            bin(lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, mq), mq);
+            search((uint32_t)q, q >> 32);
           }
         }
       };
-      // full rounds of the block (every thread has two valid draws), then one
-      // ragged round for the fewer than kBlkThreads + 1 pairs left
-      const int64_t full = (n >> 1) / kBlkThreads * kBlkThreads;
+      // full rounds of the block (every thread has four valid draws), then
+      // ragged rounds for the fewer than 4 (kBlkThreads + 1) draws left
+      const int64_t full = (n >> 2) / kBlkThreads * kBlkThreads;
       int64_t p = threadIdx.x;
       for (; p < full; p += kBlkThreads) {
         const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), a.rk);
-        draw(w.x, w.y, true);
-        draw(w.z, w.w, true);
+        const uint64_t i0 = 4 * (uint64_t)p;
+        draw(w.x, i0, true);
+        draw(w.y, i0 + 1, true);
+        draw(w.z, i0 + 2, true);
+        draw(w.w, i0 + 3, true);
       }
-      for (; 2 * (p - lane) < n; p += kBlkThreads) {  // warp-uniform bound
+      for (; 4 * (p - lane) < n; p += kBlkThreads) {  // warp-uniform bound
         const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), a.rk);
-        draw(w.x, w.y, 2 * p < n);
-        draw(w.z, w.w, 2 * p + 1 < n);
+        const int64_t i0 = 4 * p;
+        draw(w.x, (uint64_t)i0, i0 < n);
+        draw(w.y, (uint64_t)i0 + 1, i0 + 1 < n);
+        draw(w.z, (uint64_t)i0 + 2, i0 + 2 < n);
+        draw(w.w, (uint64_t)i0 + 3, i0 + 3 < n);
       }
       __syncwarp();
       if (lane < qn) {
-        const uint64_t mq = defer_q[lane];
-        bin(lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, mq), mq);
+        const uint64_t q = defer_q[lane];
+        search((uint32_t)q, q >> 32);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {

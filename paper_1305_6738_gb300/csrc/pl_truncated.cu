@@ -175,15 +175,29 @@ __device__ __forceinline__ uint32_t tz_lookup(const uint64_t *T, const uint16_t 
   return k;
 }
 
+// X of a draw known by its high word h: the answer at m_first(h), or, when
+// the threshold above that answer lies inside the draw's interval of m
+// (T[X - 1] <= m_last(h)), the answer at m itself (m_full(), the low word's
+// block).  T[0] = 2^53 + 1 exceeds every m.
+template <class MFull>
+__device__ __forceinline__ uint32_t tz_lookup_hi(const uint64_t *T, const uint16_t *G, uint32_t h, MFull m_full) {
+  const uint32_t k = tz_lookup(T, G, m_first(h));
+  if (T[k - 1] > m_last(h)) return k;
+  return tz_lookup(T, G, m_full());
+}
+
+// Sampling only: one thread per draw, m taken whole (both words).
 __global__ void tz_sample_kernel(const TzLaw *law, RoundKeys rk, uint32_t cell_id, uint32_t purpose,
                                  uint32_t rep0, uint64_t nrep, uint64_t n, uint64_t *out) {
   const uint64_t total = nrep * n;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t r = i / n, d = i - r * n;
-    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)(d >> 1), rep0 + (uint32_t)r, cell_id, purpose), rk);
-    const uint64_t m = (d & 1) ? draw_bits(w.z, w.w) : draw_bits(w.x, w.y);
-    out[i] = tz_lookup(law->T, law->guide, m);
+    const uint4 wh = philox4x32_10_rk(make_uint4((uint32_t)(d >> 2), rep0 + (uint32_t)r, cell_id, purpose), rk);
+    const uint4 wl =
+        philox4x32_10_rk(make_uint4((uint32_t)(d >> 2), rep0 + (uint32_t)r, cell_id, purpose | kLowStream), rk);
+    const uint32_t j = (uint32_t)d & 3u;
+    out[i] = tz_lookup(law->T, law->guide, draw_m(quad_word(wh, j), quad_word(wl, j)));
   }
 }
 
@@ -427,17 +441,26 @@ __global__ void __launch_bounds__(kTzWarps * 32, PL_TZ_MIN_BLOCKS) tz_replicate_
   uint32_t *h = sH[warp];
   const uint32_t n = (uint32_t)c.n;
   const uint32_t nwords = (K >> 1) + 1;
-  const uint32_t npairs = (n + 1) >> 1;
+  const uint32_t nquads = (n + 3) >> 2;
   const double inv_n = 1.0 / (double)n;
   for (uint32_t rr = warp; rr < item.nrep; rr += kTzWarps) {
     const uint32_t r = item.r0 + rr;
     for (uint32_t i = lane; i < nwords; i += 32) h[i] = 0u;
     __syncwarp();
     uint32_t c12 = 0, c34 = 0;
-    for (uint32_t p = lane; p < npairs; p += 32) {
+    // draw i's high word is word i mod 4 of block i / 4; its low word is
+    // drawn only when a threshold lies inside its interval of m
+    auto one = [&](uint32_t hw, uint32_t i) {
+      auto m_full = [&] { return draw_m_full(hw, i, r, c.cell_id, c.purpose, a.rk.k[0], a.rk.k[1]); };
+      tz_count(tz_lookup_hi(sT, sG, hw, m_full), h, c12, c34);
+    };
+    for (uint32_t p = lane; p < nquads; p += 32) {
       const uint4 w = philox4x32_10_rk(make_uint4(p, r, c.cell_id, c.purpose), a.rk);
-      tz_count(tz_lookup(sT, sG, draw_bits(w.x, w.y)), h, c12, c34);
-      if (2 * p + 1 < n) tz_count(tz_lookup(sT, sG, draw_bits(w.z, w.w)), h, c12, c34);
+      const uint32_t i0 = 4 * p;
+      one(w.x, i0);
+      if (i0 + 1 < n) one(w.y, i0 + 1);
+      if (i0 + 2 < n) one(w.z, i0 + 2);
+      if (i0 + 3 < n) one(w.w, i0 + 3);
     }
     c12 = warp_sum_u32(c12);
     c34 = warp_sum_u32(c34);

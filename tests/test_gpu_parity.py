@@ -106,6 +106,17 @@ def test_fit_and_ks_match_oracle(ctx, pl, k):
     assert abs(ctx.pl_ks_stat(xt, xmin, 2.2, 0) - oracle.ks(xu, xmin, 2.2)) < 1e-12
 
 
+def test_sample_rejects_purposes_of_the_low_stream(ctx, pl):
+    # purposes at or above 2^31 would share the low words' stream
+    out = torch.empty(10, dtype=torch.int64, device="cuda")
+    with pytest.raises(pl.PLError) as e:
+        ctx.pl_sample(2.0, 1, 1, 0, 2**31, 0, 1, 10, out)
+    assert e.value.status == pl.PL_EINVAL
+    with pytest.raises(pl.PLError) as e:
+        ctx.pl_sample_truncated(2.0, 20, 1, 0, 2**31, 0, 1, 10, out)
+    assert e.value.status == pl.PL_EINVAL
+
+
 def test_data_below_xmin_is_rejected(ctx, pl):
     xt = torch.tensor([3, 4, 2, 9], dtype=torch.int32, device="cuda")
     with pytest.raises(pl.PLError) as e:

@@ -86,14 +86,26 @@ def test_philox_matches_curand_host_far_offsets(seed, offset):
 
 
 def test_draw_mapping_contract():
-    # draw i -> block (i>>1, rep, cell, purpose), words (2j, 2j+1), top 53 bits + 1
+    # draw i: high word j = i mod 4 of block (i>>2, rep, cell, purpose), low
+    # word j of block (i>>2, rep, cell, purpose + 2^31); m = h 2^21 + (l >> 11) + 1
     seed, cell, rep, purpose = 0xDEADBEEF12345678, 17, 99, 2
     key = [seed & 0xFFFFFFFF, seed >> 32]
-    for i in [0, 1, 2, 3, 1001, 2**33 - 1]:
-        w = oracle.philox4x32_10([i >> 1, rep, cell, purpose], key)
-        j = i & 1
-        bits = (int(w[2 * j + 1]) << 32) | int(w[2 * j])
-        assert oracle.draw_m(seed, cell, rep, purpose, i) == (bits >> 11) + 1
+    for i in [0, 1, 2, 3, 4, 1001, 2**34 - 1]:
+        wh = oracle.philox4x32_10([i >> 2, rep, cell, purpose], key)
+        wl = oracle.philox4x32_10([i >> 2, rep, cell, purpose + 2**31], key)
+        j = i & 3
+        assert oracle.draw_m(seed, cell, rep, purpose, i) == (int(wh[j]) << 21) + (int(wl[j]) >> 11) + 1
+
+
+def test_draw_low_bits_uniform():
+    # the 21 low bits of m - 1 come from the second stream: uniform too
+    n = 100_000
+    ms = np.array([oracle.draw_m(3, 1, r, 1, i) for r in range(10) for i in range(n // 10)], dtype=np.uint64)
+    low = ((ms - np.uint64(1)) & np.uint64(0xFF)).astype(np.int64)
+    counts = np.bincount(low, minlength=256)
+    exp = n / 256
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    assert chi2 < 255 + 6 * 22.6
 
 
 def test_draw_range_and_uniformity():
