@@ -32,6 +32,15 @@ constexpr int kGuide = 1 << kGuideBits;
 // A guide word holds the bucket's smallest answer index (low 31 bits) and, in
 // bit 31, whether the bucket holds more than one answer (a search is needed).
 constexpr uint32_t kGuideMulti = 0x80000000u, kGuideIndex = 0x7fffffffu;
+// Increment table of the warp-form sampler: 2^8 buckets of a draw's high
+// word.  A bucket whose draws all take one of the first four values holds
+// 1 << (8 b) (b = value - xmin), an increment of a lane's four 7-bit counter
+// fields; any other bucket holds kIncOther.  Stored with 32 copies of every
+// entry (bucket j, lane l at j * 32 + l) so that a warp's lookups never
+// share a shared-memory bank.
+constexpr int kIncBits = 8;
+constexpr int kIncBuckets = 1 << kIncBits;
+constexpr uint32_t kIncOther = 0x80000000u;
 constexpr int kHMax = 1024;                 // dense histogram bins per warp
 constexpr int kHWide = 8192;                // dense histogram bins per block (block form)
 constexpr int kWarps = 8;                   // warps per block, warp form
@@ -69,6 +78,7 @@ struct Law {
   float xmin_f;           // xmin + 1/2, binary32
   uint64_t *T;            // T[i] = floor(Q(xmin+i) 2^53) + 1, Q(k) = P(X > k)
   uint32_t *guide;        // guide[j] = min{i : T[i] <= (j+1) 2^(53-g)} (or L2) | kGuideMulti flag
+  uint32_t *inc;          // increment table (kIncBuckets x 32 copies)
   double *lnT;            // ln(xmin + i), i < kLnTable
   float *lnT_hi;          // float split of lnT: hi + lo
   float *lnT_lo;

@@ -116,6 +116,28 @@ __global__ void law_guide_kernel(Law *laws) {
   law.guide[j] = lo | (hi != lo ? kGuideMulti : 0u);
 }
 
+// Increment table: bucket j of the high word covers m in [j 2^45 + 1,
+// (j + 1) 2^45]; the answer index is nonincreasing in m, so it is one index
+// over the bucket exactly when the answers at the two ends agree.
+__device__ __forceinline__ uint32_t answer_at(const Law &law, uint64_t m) {
+  uint32_t lo = 0, hi = law.L2;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (law.T[mid] <= m) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+__global__ void law_inc_kernel(Law *laws) {
+  const Law law = laws[blockIdx.y];
+  const uint32_t j = blockIdx.x * 8 + (threadIdx.x >> 5), l = threadIdx.x & 31;
+  if (j >= (uint32_t)kIncBuckets) return;
+  const uint64_t m_lo = ((uint64_t)j << (53 - kIncBits)) + 1ull, m_hi = (uint64_t)(j + 1) << (53 - kIncBits);
+  const uint32_t a = answer_at(law, m_lo), b = answer_at(law, m_hi);
+  law.inc[j * 32 + l] = (a == b && a < 4) ? 1u << (8 * a) : kIncOther;
+}
+
 cudaError_t launch_law_setup(Law *laws_dev, int nlaws, cudaStream_t st) {
   if (nlaws <= 0) return cudaSuccess;
   law_z_kernel<<<(nlaws + 1) / 2, 64, 0, st>>>(laws_dev, nlaws);
@@ -123,6 +145,7 @@ cudaError_t launch_law_setup(Law *laws_dev, int nlaws, cudaStream_t st) {
   // entries with direct terms: xmin + i + 1 < 10 + 1.5 alpha, i < 105 for alpha <= 64
   law_fill_em_kernel<<<dim3(128 / kFillEmWarps, nlaws), kFillEmWarps * 32, 0, st>>>(laws_dev);
   law_guide_kernel<<<dim3(kGuide / 256, nlaws), 256, 0, st>>>(laws_dev);
+  law_inc_kernel<<<dim3(kIncBuckets / 8, nlaws), 256, 0, st>>>(laws_dev);
   return cudaGetLastError();
 }
 
@@ -134,13 +157,17 @@ struct StagedLaw {
   uint64_t *sT;
   uint32_t *sG;
   uint64_t *mbar;
+  uint32_t *sInc = nullptr;  // the increment table too, when given
 };
+
+constexpr uint32_t kIncBytes = (uint32_t)kIncBuckets * 32 * sizeof(uint32_t);
 
 __device__ bool stage_law(const StagedLaw &s, const Law &law, uint32_t &phase, Counters *ctr) {
   if (threadIdx.x == 0) {
-    mbar_expect_tx(s.mbar, (uint32_t)(kL1 * sizeof(uint64_t) + kGuide * sizeof(uint32_t)));
+    mbar_expect_tx(s.mbar, (uint32_t)(kL1 * sizeof(uint64_t) + kGuide * sizeof(uint32_t)) + (s.sInc ? kIncBytes : 0u));
     bulk_g2s(s.sT, law.T, (uint32_t)(kL1 * sizeof(uint64_t)), s.mbar);
     bulk_g2s(s.sG, law.guide, (uint32_t)(kGuide * sizeof(uint32_t)), s.mbar);
+    if (s.sInc) bulk_g2s(s.sInc, law.inc, kIncBytes, s.mbar);
   }
   const bool ok = mbar_wait_bounded(s.mbar, phase);
   const int any_fail = __syncthreads_or(!ok);
@@ -781,8 +808,15 @@ __device__ int64_t spill_compact(uint64_t *spill, uint32_t *onchip, int64_t s, u
 //           with a global spill buffer (same Philox stream, same values);
 //   phase 2 (lane per replicate): binary64 fit (interpolated start + polish);
 //   phase 3 (warp per replicate): KS distance.
-constexpr int kAWarps = 16;
+#ifndef PL_SAMPLER_WARPS
+#define PL_SAMPLER_WARPS 32
+#endif
+#ifndef PL_SAMPLER_QCAP
+#define PL_SAMPLER_QCAP 8
+#endif
+constexpr int kAWarps = PL_SAMPLER_WARPS;
 constexpr int kARepsPerWarp = kItemReps / kAWarps;
+constexpr int kABlocksPerSM = kAWarps >= 32 ? 1 : 2;
 
 // Draws of one replicate into a histogram.  PACKED: two 16-bit bins per word
 // (hist holds H/2 words); otherwise one 32-bit bin per word.  Spills beyond the
@@ -936,18 +970,157 @@ __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint
   return 2 * (int64_t)tw + ((hist[tw] >> 16) ? 1 : 0);
 }
 
-__global__ void __launch_bounds__(kAWarps * 32, 3) sample_hist_kernel(SampleLaunch a) {
+// Draws of one replicate for the warp-form sampler.  Every draw looks up its
+// high word in the increment table (the lane's own copy, so the warp's 32
+// loads touch 32 banks) and adds the entry to the lane's register `acc`:
+// draws of the first four values count in its four 7-bit fields, flushed to
+// 32-bit counters every kFlushBlocks Philox blocks (at most 124 increments).
+// Every other draw (a larger value, a bucket holding a threshold, a value
+// beyond the table) is appended to the lane's queue in shared memory (column
+// `lane`, kQCap entries) with no warp vote; once a lane's queue may not take
+// another block's four draws the warp drains all queues, each lane its own
+// entries: guide word, table search where the bucket holds several values,
+// then a shared atomic below H or a spill.  Counts do not depend on the order
+// draws are binned in, and spills are sorted later, so the record equals
+// draw_replicate's.  Returns tmax and leaves the spill count in *s_count.
+constexpr int kQCap = PL_SAMPLER_QCAP;
+constexpr int kFlushBlocks = 31;
+
+__device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const uint32_t *sG, const uint32_t *sInc,
+                                                    const Law &law, const Cell &cell, uint32_t rep,
+                                                    const RoundKeys &rk, uint32_t *hist, int *s_count,
+                                                    uint64_t *spill, int64_t spill_capacity, int lane,
+                                                    const TailQueue *tq, uint64_t spill_pos0, uint64_t *queue) {
+  const int64_t n = cell.n;
+  const uint64_t xmin = cell.xmin;
+  const uint32_t H = cell.H;
+  const int words = (int)(H / 2);
+  for (int i = lane; i < words; i += 32) hist[i] = 0;
+  if (lane == 0) *s_count = 0;
+  __syncwarp();
+  // any table index b: two 16-bit bins per shared word below H, else a spill
+  auto bin = [&](uint32_t b, uint64_t m) {
+    if (b < H) {
+      atomicAdd(&hist[b >> 1], 1u << ((b & 1u) << 4));
+    } else {
+      const int slot = atomicAdd(s_count, 1);
+      if (slot < spill_capacity) {
+        if (b < law.L2) {
+          spill[slot] = xmin + b;
+        } else {
+          spill[slot] = kTailTag | m;
+          const unsigned q = atomicAdd(tq->count, 1u);
+          if (q < tq->cap) {
+            tq->pos[q] = spill_pos0 + (uint64_t)slot;
+            tq->law[q] = cell.law;
+          }
+        }
+      }
+    }
+  };
+  auto m_of = [&](uint32_t h, uint64_t i) {
+    return draw_m_full(h, i, rep, cell.cell_id, cell.purpose, rk.k[0], rk.k[1]);
+  };
+  // a queued draw (i << 32 | h)
+  auto handle = [&](uint64_t e) {
+    const uint32_t h = (uint32_t)e;
+    const uint64_t i = e >> 32;
+    const uint32_t gw = sG[h >> (32 - kGuideBits)];
+    uint64_t m = 0;
+    uint32_t b;
+    if (!(gw & kGuideMulti)) {
+      b = gw & kGuideIndex;
+      if (b >= law.L2) m = m_of(h, i);
+    } else {
+      b = lookup_index_hi(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, h,
+                          [&] { return m_of(h, i); }, &m);
+    }
+    bin(b, m);
+  };
+  uint64_t *ql = queue + lane;  // this lane's entry k at ql[32 k]
+  uint32_t qk = 0;
+  auto drain = [&]() {
+    const uint32_t kmax = __reduce_max_sync(0xffffffffu, qk);
+    for (uint32_t k = 0; k < kmax; ++k)
+      if (k < qk) handle(ql[32 * k]);
+    qk = 0;
+  };
+  uint32_t acc = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+  auto flush = [&]() {
+    c0 += acc & 0x7fu;
+    c1 += (acc >> 8) & 0x7fu;
+    c2 += (acc >> 16) & 0x7fu;
+    c3 += (acc >> 24) & 0x7fu;
+    acc = 0;
+  };
+  const uint32_t *incl = sInc + lane;
+  auto step = [&](uint32_t h, uint64_t i) {
+    const uint32_t e = incl[(h >> (32 - kIncBits)) * 32];
+    acc += e;
+    if ((int32_t)e < 0) {
+      ql[32 * qk] = (i << 32) | h;
+      ++qk;
+    }
+  };
+  // full rounds (every lane has four valid draws: blocks below a multiple of
+  // 32 that is at most n/4), then one ragged round for the at most 32 blocks
+  // left; the trip counts are the same for every lane
+  const int64_t full = (n >> 2) & ~(int64_t)31;
+  int64_t p = lane;
+  while (p < full) {
+    const int64_t pend = min(full + lane, p + 32 * (int64_t)kFlushBlocks);
+    for (; p < pend; p += 32) {
+      const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
+      const uint64_t i0 = 4 * (uint64_t)p;
+      step(w.x, i0);
+      step(w.y, i0 + 1);
+      step(w.z, i0 + 2);
+      step(w.w, i0 + 3);
+      if (__any_sync(0xffffffffu, qk > (uint32_t)kQCap - 4u)) drain();
+    }
+    flush();
+  }
+  if (4 * full < n) {
+    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
+    const int64_t i0 = 4 * p;
+    if (i0 < n) step(w.x, (uint64_t)i0);
+    if (i0 + 1 < n) step(w.y, (uint64_t)i0 + 1);
+    if (i0 + 2 < n) step(w.z, (uint64_t)i0 + 2);
+    if (i0 + 3 < n) step(w.w, (uint64_t)i0 + 3);
+    flush();
+  }
+  drain();
+  __syncwarp();
+  const unsigned s0 = __reduce_add_sync(0xffffffffu, c0), s1 = __reduce_add_sync(0xffffffffu, c1);
+  const unsigned s2 = __reduce_add_sync(0xffffffffu, c2), s3 = __reduce_add_sync(0xffffffffu, c3);
+  if (lane == 0) {
+    hist[0] += s0 | (s1 << 16);
+    hist[1] += s2 | (s3 << 16);
+  }
+  __syncwarp();
+  // largest bin hit: highest nonzero word, then its upper half
+  int tw = -1;
+  for (int i = lane; i < words; i += 32)
+    if (hist[i]) tw = i;
+  tw = __reduce_max_sync(0xffffffffu, (unsigned)(tw + 1)) - 1;
+  if (tw < 0) return tw;
+  return 2 * (int64_t)tw + ((hist[tw] >> 16) ? 1 : 0);
+}
+
+__global__ void __launch_bounds__(kAWarps * 32, kABlocksPerSM) sample_hist_kernel(SampleLaunch a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
   uint32_t *sG = reinterpret_cast<uint32_t *>(smem + kL1 * 8);
-  uint32_t *sH = reinterpret_cast<uint32_t *>(smem + kL1 * 8 + kGuide * 4);
-  int *s_spill = reinterpret_cast<int *>(smem + kL1 * 8 + kGuide * 4 + kAWarps * (kHMax / 2) * 4);
+  uint32_t *sInc = reinterpret_cast<uint32_t *>(smem + kL1 * 8 + kGuide * 4);
+  uint32_t *sH = sInc + kIncBuckets * 32;
+  uint64_t *sQ = reinterpret_cast<uint64_t *>(sH + kAWarps * (kHMax / 2));
+  int *s_spill = reinterpret_cast<int *>(sQ + kAWarps * kQCap * 32);
   uint32_t *s_item = reinterpret_cast<uint32_t *>(s_spill + kAWarps);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(s_item + 2);
-  uint64_t *s_defer = mbar + 2;  // kAWarps * kDeferCap draws
-  StagedLaw staged{sT, sG, mbar};
+  StagedLaw staged{sT, sG, mbar, sInc};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t *hist = sH + warp * (kHMax / 2);
+  uint64_t *queue = sQ + warp * kQCap * 32;
   const TailQueue tq{a.tq_pos, a.tq_law, a.tq_count, a.tq_cap};
   if (threadIdx.x == 0) mbar_init(mbar, 1);
   __syncthreads();
@@ -968,12 +1141,8 @@ __global__ void __launch_bounds__(kAWarps * 32, 3) sample_hist_kernel(SampleLaun
       const uint32_t j = warp + jj * kAWarps;  // strided: small items still use every warp
       if (j >= wi.nrep) break;
       const uint64_t pos0 = wi.spill_off + (uint64_t)j * cell.scap;
-      const int64_t tmax =
-          cell.defer ? draw_replicate<true, true>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp],
-                                                  a.rec.spill + pos0, cell.scap, lane, &tq, pos0,
-                                                  s_defer + warp * kDeferCap)
-                     : draw_replicate<true, false>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp],
-                                                   a.rec.spill + pos0, cell.scap, lane, &tq, pos0, nullptr);
+      const int64_t tmax = draw_replicate_q(sT, sG, sInc, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp],
+                                            a.rec.spill + pos0, cell.scap, lane, &tq, pos0, queue);
       uint32_t *dense = reinterpret_cast<uint32_t *>(a.rec.dense + wi.dense_off + (uint64_t)j * cell.H);
       for (int64_t i = lane; i <= (tmax >> 1); i += 32) dense[i] = hist[i];
       if (lane == 0) a.rec.meta[wi.meta_off + j] = make_int2((int)tmax, s_spill[warp]);
@@ -1171,8 +1340,8 @@ cudaError_t launch_tail_queue_raw(const Law *laws, uint64_t *pos, uint32_t *law,
 }
 
 size_t sample_kernel_smem_bytes() {
-  return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kAWarps * (kHMax / 2) * 4 + kAWarps * 4 + 8 + 16 +
-         (size_t)kAWarps * kDeferCap * 8;
+  return (size_t)kL1 * 8 + kGuide * 4 + kIncBytes + (size_t)kAWarps * (kHMax / 2) * 4 +
+         (size_t)kAWarps * kQCap * 32 * 8 + kAWarps * 4 + 8 + 16;
 }
 
 int sample_kernel_blocks_per_sm() {
