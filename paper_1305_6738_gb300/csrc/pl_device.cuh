@@ -587,6 +587,15 @@ __device__ __forceinline__ uint32_t lookup_index_hi(const uint64_t *sT, const ui
   return lookup_index(sT, sG, gT, L2, xmin_f, tail_c, tail_e, *m);
 }
 
+// Value of a draw that a sampler left tagged (kTailTag | m): the exact table
+// search in global memory when the answer lies inside the table, else the
+// binary64 inversion beyond it.
+__device__ __forceinline__ uint64_t resolve_tagged(const Law &law, uint64_t m, bool *beyond) {
+  const uint32_t i = lookup_index(law.T, law.guide, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m);
+  *beyond = i >= law.L2;
+  return i < law.L2 ? law.xmin + i : tail_invert(law.alpha, law.Z, law.xmin + law.L2, m);
+}
+
 __device__ __forceinline__ uint64_t lookup_fast(const uint64_t *sT, const uint32_t *sG,
                                                 const uint64_t *gT, uint32_t L2, uint64_t xmin,
                                                 float xmin_f, float tail_c, float tail_e, uint64_t m) {

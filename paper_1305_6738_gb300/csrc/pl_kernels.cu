@@ -978,10 +978,13 @@ __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint
 // Every other draw (a larger value, a bucket holding a threshold, a value
 // beyond the table) is appended to the lane's queue in shared memory (column
 // `lane`, kQCap entries) with no warp vote; once a lane's queue may not take
-// another block's four draws the warp drains all queues, each lane its own
-// entries: guide word, table search where the bucket holds several values,
-// then a shared atomic below H or a spill.  Counts do not depend on the order
-// draws are binned in, and spills are sorted later, so the record equals
+// another block's four draws the warp drains all queues: the guide word, a
+// search of the shared level-1 table where the bucket holds several values
+// (compacted across the warp; level 2 of the table in global memory), then a
+// shared atomic below H or a spill.  A value beyond the table is spilled as
+// kTailTag | m and resolved by the tail kernel (binary64 inversion).  Counts
+// do not depend on the order draws are
+// binned in, and spills are sorted later, so the record equals
 // draw_replicate's.  Returns tmax and leaves the spill count in *s_count.
 constexpr int kQCap = PL_SAMPLER_QCAP;
 constexpr int kFlushBlocks = 31;
@@ -998,51 +1001,76 @@ __device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const ui
   for (int i = lane; i < words; i += 32) hist[i] = 0;
   if (lane == 0) *s_count = 0;
   __syncwarp();
-  // any table index b: two 16-bit bins per shared word below H, else a spill
-  auto bin = [&](uint32_t b, uint64_t m) {
+  // a table index b < L2: two 16-bit bins per shared word below H, else a spill
+  auto bin = [&](uint32_t b) {
     if (b < H) {
       atomicAdd(&hist[b >> 1], 1u << ((b & 1u) << 4));
     } else {
       const int slot = atomicAdd(s_count, 1);
-      if (slot < spill_capacity) {
-        if (b < law.L2) {
-          spill[slot] = xmin + b;
-        } else {
-          spill[slot] = kTailTag | m;
-          const unsigned q = atomicAdd(tq->count, 1u);
-          if (q < tq->cap) {
-            tq->pos[q] = spill_pos0 + (uint64_t)slot;
-            tq->law[q] = cell.law;
-          }
-        }
-      }
+      if (slot < spill_capacity) spill[slot] = xmin + b;
     }
   };
   auto m_of = [&](uint32_t h, uint64_t i) {
     return draw_m_full(h, i, rep, cell.cell_id, cell.purpose, rk.k[0], rk.k[1]);
   };
-  // a queued draw (i << 32 | h)
-  auto handle = [&](uint64_t e) {
-    const uint32_t h = (uint32_t)e;
-    const uint64_t i = e >> 32;
-    const uint32_t gw = sG[h >> (32 - kGuideBits)];
-    uint64_t m = 0;
-    uint32_t b;
-    if (!(gw & kGuideMulti)) {
-      b = gw & kGuideIndex;
-      if (b >= law.L2) m = m_of(h, i);
-    } else {
-      b = lookup_index_hi(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, h,
-                          [&] { return m_of(h, i); }, &m);
+  // a draw whose value lies beyond the table: spilled as kTailTag | m for the
+  // tail kernel
+  auto spill_tagged = [&](uint64_t m) {
+    const int slot = atomicAdd(s_count, 1);
+    if (slot < spill_capacity) {
+      spill[slot] = kTailTag | m;
+      const unsigned q = atomicAdd(tq->count, 1u);
+      if (q < tq->cap) {
+        tq->pos[q] = spill_pos0 + (uint64_t)slot;
+        tq->law[q] = cell.law;
+      }
     }
-    bin(b, m);
+  };
+  // a queued draw (i << 32 | h) whose bucket holds several values: search the
+  // table at m_first(h); its low word only when a threshold may lie in the
+  // draw's interval of m or the answer lies beyond the table
+  auto search = [&](uint64_t e) {
+    const uint32_t h = (uint32_t)e;
+    const uint32_t i0 = lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m_first(h));
+    if (i0 < law.L2 && (i0 == 0 || table_at(sT, law.T, i0 - 1) > m_last(h))) {
+      bin(i0);
+      return;
+    }
+    const uint64_t m = m_of(h, e >> 32);
+    const uint32_t b = lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m);
+    if (b < law.L2) bin(b);
+    else spill_tagged(m);
   };
   uint64_t *ql = queue + lane;  // this lane's entry k at ql[32 k]
   uint32_t qk = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  // Each lane bins its own entries of single-valued buckets; entries of
+  // multi-valued buckets are compacted to the front of the queue (row k is
+  // read before the ballot of step k, and at most 32 (k + 1) entries are
+  // compacted by then, so writes only reach rows already read) and searched
+  // 32 at a time with every lane busy.
   auto drain = [&]() {
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, qk);
-    for (uint32_t k = 0; k < kmax; ++k)
-      if (k < qk) handle(ql[32 * k]);
+    uint32_t ns = 0;
+    for (uint32_t k = 0; k < kmax; ++k) {
+      const bool act = k < qk;
+      const uint64_t e = act ? ql[32 * k] : 0ull;
+      const uint32_t h = (uint32_t)e;
+      const uint32_t gw = act ? sG[h >> (32 - kGuideBits)] : 0u;
+      const bool multi = act && (gw & kGuideMulti);
+      if (act && !multi) {
+        const uint32_t b = gw & kGuideIndex;
+        if (b < law.L2) bin(b);
+        else spill_tagged(m_of(h, e >> 32));
+      }
+      const unsigned bm = __ballot_sync(0xffffffffu, multi);
+      if (multi) queue[ns + __popc(bm & lt)] = e;
+      ns += __popc(bm);
+    }
+    __syncwarp();
+    for (uint32_t t0 = 0; t0 < ns; t0 += 32)
+      if (t0 + lane < ns) search(queue[t0 + lane]);
+    __syncwarp();
     qk = 0;
   };
   uint32_t acc = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0;
@@ -1321,13 +1349,13 @@ __global__ void __launch_bounds__(256) tail_queue_kernel(const Law *laws, TailQu
                                                          Counters *ctr) {
   const unsigned cnt = *tq.count;
   const unsigned nq = cnt < tq.cap ? cnt : tq.cap;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && nq) atomicAdd(&ctr->tail_draws, (unsigned long long)nq);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
     const uint64_t pos = tq.pos[i];
     const uint64_t x = spill[pos];
     if (x & kTailTag) {
-      const Law &law = laws[tq.law[i]];
-      spill[pos] = tail_invert(law.alpha, law.Z, law.xmin + law.L2, x & ~kTailTag);
+      bool beyond;
+      spill[pos] = resolve_tagged(laws[tq.law[i]], x & ~kTailTag, &beyond);
+      if (beyond) atomicAdd(&ctr->tail_draws, 1ull);
     }
   }
 }
@@ -1555,8 +1583,9 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
         for (int64_t k = lane; k < s; k += 32) {
           const uint64_t x = sp[k];
           if (x & kTailTag) {
-            atomicAdd(&a.ctr->tail_draws, 1ull);
-            sp[k] = tail_invert(law.alpha, law.Z, xmin + law.L2, x & ~kTailTag);
+            bool beyond;
+            sp[k] = resolve_tagged(law, x & ~kTailTag, &beyond);
+            if (beyond) atomicAdd(&a.ctr->tail_draws, 1ull);
           }
         }
         __syncwarp();
