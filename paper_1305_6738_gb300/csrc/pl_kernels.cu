@@ -158,16 +158,23 @@ struct StagedLaw {
   uint32_t *sG;
   uint64_t *mbar;
   uint32_t *sInc = nullptr;  // the increment table too, when given
+  float *sLn = nullptr;      // and the binary32 splits of ln(xmin + i), i < kHMax (hi, then lo)
 };
 
 constexpr uint32_t kIncBytes = (uint32_t)kIncBuckets * 32 * sizeof(uint32_t);
+constexpr uint32_t kLnBytes = (uint32_t)kHMax * sizeof(float);
 
 __device__ bool stage_law(const StagedLaw &s, const Law &law, uint32_t &phase, Counters *ctr) {
   if (threadIdx.x == 0) {
-    mbar_expect_tx(s.mbar, (uint32_t)(kL1 * sizeof(uint64_t) + kGuide * sizeof(uint32_t)) + (s.sInc ? kIncBytes : 0u));
+    mbar_expect_tx(s.mbar, (uint32_t)(kL1 * sizeof(uint64_t) + kGuide * sizeof(uint32_t)) + (s.sInc ? kIncBytes : 0u) +
+                               (s.sLn ? 2u * kLnBytes : 0u));
     bulk_g2s(s.sT, law.T, (uint32_t)(kL1 * sizeof(uint64_t)), s.mbar);
     bulk_g2s(s.sG, law.guide, (uint32_t)(kGuide * sizeof(uint32_t)), s.mbar);
     if (s.sInc) bulk_g2s(s.sInc, law.inc, kIncBytes, s.mbar);
+    if (s.sLn) {
+      bulk_g2s(s.sLn, law.lnT_hi, kLnBytes, s.mbar);
+      bulk_g2s(s.sLn + kHMax, law.lnT_lo, kLnBytes, s.mbar);
+    }
   }
   const bool ok = mbar_wait_bounded(s.mbar, phase);
   const int any_fail = __syncthreads_or(!ok);
@@ -595,7 +602,9 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
     // once the argument is large enough, else from the compensated sum of the
     // bins below it; then one compensated pass over the chunk.
     const int64_t nbins = tmax + 1;
-    const int64_t cs = (nbins + 31) >> 5;
+    // odd chunk length: the lanes' bins (and log splits) fall in 32 different
+    // shared-memory banks
+    const int64_t cs = ((nbins + 31) >> 5) | 1;
     const int64_t i0 = (int64_t)lane * cs;
     const int64_t i1 = i0 + cs < nbins ? i0 + cs : nbins;
     int64_t sc = 0;
@@ -1405,7 +1414,8 @@ __device__ __forceinline__ const uint16_t *stage_dense(const uint16_t *src, int6
 constexpr int64_t kLaneBins = 128;
 
 template <bool F32>
-__device__ __forceinline__ double lane_logsum(const uint16_t *dense, int64_t tmax, const Law &law) {
+__device__ __forceinline__ double lane_logsum(const uint16_t *dense, int64_t tmax, const Law &law, const float *lnHi,
+                                              const float *lnLo) {
   if (!F32) {
     double acc = 0.0;
     for (int64_t i = 0; i <= tmax; ++i) acc += (double)dense[i] * law.lnT[i];
@@ -1414,8 +1424,8 @@ __device__ __forceinline__ double lane_logsum(const uint16_t *dense, int64_t tma
   float Lh = 0.0f, Ll = 0.0f;
   for (int64_t i = 0; i <= tmax; ++i) {
     const float c = (float)dense[i];
-    const float ph = c * law.lnT_hi[i];
-    const float pe = fmaf(c, law.lnT_hi[i], -ph) + c * law.lnT_lo[i];
+    const float ph = c * lnHi[i];
+    const float pe = fmaf(c, lnHi[i], -ph) + c * lnLo[i];
     ff_add(Lh, Ll, ph, pe);
   }
   return (double)Lh + (double)Ll;
@@ -1423,7 +1433,7 @@ __device__ __forceinline__ double lane_logsum(const uint16_t *dense, int64_t tma
 
 template <bool F32>
 __device__ __forceinline__ double lane_ks(const uint16_t *dense, int64_t tmax, int64_t n, const FitOut &f,
-                                          const Law &law) {
+                                          const Law &law, const float *lnHi, const float *lnLo) {
   if (!F32) {
     const double invZ = 1.0 / f.Z, inv_n = 1.0 / (double)n;
     double F = 0.0, best = 0.0;
@@ -1439,7 +1449,7 @@ __device__ __forceinline__ double lane_ks(const uint16_t *dense, int64_t tmax, i
   float Fh = 0.0f, Fl = 0.0f, best = 0.0f;
   uint32_t C = 0;
   for (int64_t i = 0; i <= tmax; ++i) {
-    ff_add(Fh, Fl, exp_neg_prod(f.a_hi, f.a_lo, law.lnT_hi[i], law.lnT_lo[i]) * f.invZ, 0.0f);
+    ff_add(Fh, Fl, exp_neg_prod(f.a_hi, f.a_lo, lnHi[i], lnLo[i]) * f.invZ, 0.0f);
     C += dense[i];
     best = fmaxf(best, fabsf(Fh - (float)C * inv_n));
   }
@@ -1456,7 +1466,8 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
   int *s_spill = reinterpret_cast<int *>(smem + kL1 * 8 + kGuide * 4 + kWarps * kHMax * 4);
   uint32_t *s_item = reinterpret_cast<uint32_t *>(s_spill + kWarps);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kL1 * 8 + kGuide * 4 + kWarps * kHMax * 4 + 64);
-  StagedLaw staged{sT, sG, mbar};
+  float *sLn = reinterpret_cast<float *>(smem + kL1 * 8 + kGuide * 4 + kWarps * kHMax * 4 + 128);
+  StagedLaw staged{sT, sG, mbar, nullptr, F32 ? sLn : nullptr};
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t *hist = sH + warp * kHMax;
@@ -1482,6 +1493,8 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
       loaded = cell.law;
     }
     // the item's replicates spread evenly over the warps (at most 32 each)
+    // binary32 log splits: the staged copy for warp-form cells (bins < kHMax)
+    const float *lnHi = cell.wide ? law.lnT_hi : sLn, *lnLo = cell.wide ? law.lnT_lo : sLn + kHMax;
     const int per_warp = (int)((wi.nrep + kWarps - 1) / kWarps);
     const int j0 = warp * per_warp;
     const int nb = (int)min((int64_t)per_warp, (int64_t)wi.nrep - j0);
@@ -1506,7 +1519,7 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
         simple = m.y == 0 && m.x >= 0 && (int64_t)m.x < kLaneBins;
         if (simple) {
           my_tmax = m.x;
-          myL = lane_logsum<F32>(my_dense, my_tmax, law);
+          myL = lane_logsum<F32>(my_dense, my_tmax, law, lnHi, lnLo);
           if ((int64_t)my_dense[0] == n) myL += cc.ln_allmin;
         }
       }
@@ -1531,15 +1544,15 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
           double D;
           if (cell.wide) {
             D = ks_warp<F32, uint32_t>(reinterpret_cast<const uint32_t *>(dense), tm, pr, ns, n, xmin, fr, law.lnT,
-                                       law.lnT_hi, law.lnT_lo, lane);
+                                       lnHi, lnLo, lane);
           } else {
             const uint16_t *sd = stage_dense(dense, tm, hist, lane);
-            D = ks_warp<F32, uint16_t>(sd, tm, pr, ns, n, xmin, fr, law.lnT, law.lnT_hi, law.lnT_lo, lane);
+            D = ks_warp<F32, uint16_t>(sd, tm, pr, ns, n, xmin, fr, law.lnT, lnHi, lnLo, lane);
             __syncwarp();
           }
           if (lane == r) myD = D;
         }
-        if (mine && simple) myD = lane_ks<F32>(my_dense, my_tmax, n, fo, law);
+        if (mine && simple) myD = lane_ks<F32>(my_dense, my_tmax, n, fo, law, lnHi, lnLo);
         PL_PHASE(4);
         if (mine) {
           const int64_t o = cell.out_off + wi.r0 + j0 + lane;
@@ -1603,8 +1616,8 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
         } else {
           for (int64_t i = lane; i <= tmax; i += 32) {
             const float c = (float)(dense32 ? dense32[i] : (uint32_t)dsrc[i]);
-            const float ph = c * law.lnT_hi[i];
-            const float pe = fmaf(c, law.lnT_hi[i], -ph) + c * law.lnT_lo[i];
+            const float ph = c * lnHi[i];
+            const float pe = fmaf(c, lnHi[i], -ph) + c * lnLo[i];
             ff_add(Lh, Ll, ph, pe);
           }
           L = 0.0;
@@ -1658,7 +1671,7 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
 }
 
 size_t finish_kernel_smem_bytes() {
-  return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kWarps * kHMax * 4 + 64 + 16;
+  return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kWarps * kHMax * 4 + 128 + 2 * (size_t)kLnBytes;
 }
 
 int finish_kernel_blocks_per_sm(bool f32) {
