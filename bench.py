@@ -193,11 +193,10 @@ def serving_cpu_baseline(reqs, threads: int) -> dict:
                        f"and B={b2} and extrapolated linearly to B={SERVE_B}; requests served one at a time")}
 
 
-def serving_requests_and_data(args, pl, ctx, torch):
-    """Request schedule and host int32 data: power-law data from the library's
+def serving_data(reqs, pl, ctx, torch):
+    """Host int32 data of the requests: power-law data from the library's
     sampler (stream tag 2, cell id = request id, seed 4), lognormal data from
     the input module; generated before the clock starts."""
-    reqs = inputs.serving_requests(args.serve_warmup + args.duration, SERVE_RATE, seed=4)
     buf = torch.empty(max(r.n for r in reqs), dtype=torch.int64, device="cuda")
     data = []
     for r in reqs:
@@ -206,12 +205,87 @@ def serving_requests_and_data(args, pl, ctx, torch):
             continue
         ctx.pl_sample(r.alpha, r.xmin, 4, r.request_id, inputs.PURPOSE_TESTDATA, 0, 1, r.n, buf)
         data.append(buf[:r.n].clamp(max=inputs.INT32_MAX).to(torch.int32).cpu().numpy())
-    return reqs, data
+    return data
+
+
+def serve_measure(local: int, duration: float, warmup: float, workers: int, prec: int, pl, torch,
+                  serve_log: str = "") -> dict:
+    """Open-loop Poisson arrivals at SERVE_RATE for warmup + duration seconds
+    through the serving engine; latency = done - scheduled arrival of the
+    requests arriving after the warm-up."""
+    import threading
+    import numpy as np
+    ctx = pl.Context(local)
+    t0 = time.perf_counter()
+    reqs = inputs.serving_requests(warmup + duration, SERVE_RATE, seed=4)
+    data = serving_data(reqs, pl, ctx, torch)
+    generate_s = time.perf_counter() - t0
+    ctx.close()
+    srv = pl.Server(local, SERVE_BUDGET, workers=workers, prec=prec, seed=1, B=SERVE_B)
+    base = srv.pl_server_now() + 0.2
+    lag = []
+
+    def submit_all():
+        for r, x in zip(reqs, data):
+            dt = base + r.arrival_s - srv.pl_server_now()
+            if dt > 0:
+                time.sleep(dt)
+            lag.append(srv.pl_server_now() - (base + r.arrival_s))
+            srv.pl_server_submit(r.request_id, x, r.xmin)
+
+    sampler = None
+    results = {}
+    th = threading.Thread(target=submit_all)
+    th.start()
+    max_queue = max_running = 0
+    max_reserved = 0
+    launches0 = None
+    while len(results) < len(reqs):
+        now = srv.pl_server_now()
+        if sampler is None and now >= base + warmup:
+            sampler = ClockSampler(gpu_query_id(local))
+            launches0 = srv.pl_server_load()[3]
+        for res in srv.pl_server_poll(256, 0.01):
+            results[res["request_id"]] = res
+        q, run, rb, _ = srv.pl_server_load()
+        if sampler is not None:
+            max_queue, max_running, max_reserved = max(max_queue, q), max(max_running, run), max(max_reserved, rb)
+    th.join()
+    clocks = sampler.stop() if sampler else {}
+    launches = srv.pl_server_load()[3] - (launches0 or 0)
+    srv.close()
+    if serve_log:
+        with open(serve_log, "w") as f:
+            for r in reqs:
+                res = results[r.request_id]
+                f.write(json.dumps({"id": r.request_id, "n": r.n, "alpha": r.alpha, "lognormal": r.lognormal,
+                                    "arrival_s": base + r.arrival_s, "submit_s": res["submit_s"],
+                                    "start_s": res["start_s"], "done_s": res["done_s"],
+                                    "status": res["status"], "alpha_hat": res["alpha_hat"],
+                                    "p": res["p"]}) + "\n")
+    timed = [r for r in reqs if r.arrival_s >= warmup]
+    bad = [results[r.request_id]["status"] for r in timed if results[r.request_id]["status"] != 0]
+    lat = np.array([results[r.request_id]["done_s"] - (base + r.arrival_s) for r in timed]) * 1e3
+    wait = np.array([results[r.request_id]["start_s"] - results[r.request_id]["submit_s"] for r in timed]) * 1e3
+    t_first = base + timed[0].arrival_s
+    t_last = max(results[r.request_id]["done_s"] for r in timed)
+    span = t_last - t_first
+    big = np.array([r.n >= 100_000 for r in timed])
+    return {"value": len(timed) / span, "timed": timed, "warmup_requests": len(reqs) - len(timed),
+            "ms_per_request": 1e3 * span / len(timed), "generate_s": generate_s,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max()), "mean": float(lat.mean()),
+                           "p50_n_ge_1e5": float(np.percentile(lat[big], 50)) if big.any() else None,
+                           "p99_n_lt_1e5": float(np.percentile(lat[~big], 99)) if (~big).any() else None,
+                           "queue_wait_p99": float(np.percentile(wait, 99)),
+                           "submit_lag_p99": float(np.percentile(np.array(lag) * 1e3, 99))},
+            "draws_per_s": sum(SERVE_B * r.n for r in timed) / span, "failed_requests": len(bad),
+            "load": {"max_queued": max_queue, "max_running": max_running, "max_reserved_bytes": max_reserved},
+            "h2d_bytes_per_request": statistics.mean(4 * r.n for r in timed),
+            "launches": launches, "clocks": clocks}
 
 
 def run_serving(args):
-    import threading
-    import numpy as np
     threads = os.cpu_count() or 1
     config = serving_config(args)
     rank = int(os.environ.get("RANK", "0"))
@@ -235,84 +309,20 @@ def run_serving(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     from paper_1305_6738_gb300 import pl
-    ctx = pl.Context(local)
-    t0 = time.perf_counter()
-    reqs, data = serving_requests_and_data(args, pl, ctx, torch)
-    config["generate_s"] = time.perf_counter() - t0
-    ctx.close()
     prec = pl.PL_FP32_BULK if args.precision == "fp32-bulk" else pl.PL_FP64
-    srv = pl.Server(local, SERVE_BUDGET, workers=args.workers, prec=prec, seed=1, B=SERVE_B)
-    base = srv.pl_server_now() + 0.2
-    lag = []
-
-    def submit_all():
-        for r, x in zip(reqs, data):
-            dt = base + r.arrival_s - srv.pl_server_now()
-            if dt > 0:
-                time.sleep(dt)
-            lag.append(srv.pl_server_now() - (base + r.arrival_s))
-            srv.pl_server_submit(r.request_id, x, r.xmin)
-
-    sampler = None
-    results = {}
-    th = threading.Thread(target=submit_all)
-    th.start()
-    max_queue = max_running = 0
-    max_reserved = 0
-    launches0 = None
-    while len(results) < len(reqs):
-        now = srv.pl_server_now()
-        if sampler is None and now >= base + args.serve_warmup:
-            sampler = ClockSampler(gpu_query_id(local))
-            launches0 = srv.pl_server_load()[3]
-        for res in srv.pl_server_poll(256, 0.01):
-            results[res["request_id"]] = res
-        q, run, rb, _ = srv.pl_server_load()
-        if sampler is not None:
-            max_queue, max_running, max_reserved = max(max_queue, q), max(max_running, run), max(max_reserved, rb)
-    th.join()
-    clocks = sampler.stop() if sampler else {}
-    launches = srv.pl_server_load()[3] - (launches0 or 0)
-    srv.close()
-
-    if args.serve_log:
-        with open(args.serve_log, "w") as f:
-            for r in reqs:
-                res = results[r.request_id]
-                f.write(json.dumps({"id": r.request_id, "n": r.n, "alpha": r.alpha, "lognormal": r.lognormal,
-                                    "arrival_s": base + r.arrival_s, "submit_s": res["submit_s"],
-                                    "start_s": res["start_s"], "done_s": res["done_s"],
-                                    "status": res["status"], "alpha_hat": res["alpha_hat"],
-                                    "p": res["p"]}) + "\n")
-    timed = [r for r in reqs if r.arrival_s >= args.serve_warmup]
-    bad = [results[r.request_id]["status"] for r in timed if results[r.request_id]["status"] != 0]
-    lat = np.array([results[r.request_id]["done_s"] - (base + r.arrival_s) for r in timed]) * 1e3
-    wait = np.array([results[r.request_id]["start_s"] - results[r.request_id]["submit_s"] for r in timed]) * 1e3
-    t_first = base + timed[0].arrival_s
-    t_last = max(results[r.request_id]["done_s"] for r in timed)
-    span = t_last - t_first
-    value = len(timed) / span
-    draws = sum(SERVE_B * r.n for r in timed)
-    h2d = statistics.mean(4 * r.n for r in timed)
-    big = np.array([r.n >= 100_000 for r in timed])
-    line = {"metric": METRIC, "value": value, "unit": "requests/s", "n_gpus": 1, "steps": len(timed),
-            "warmup": sum(1 for r in reqs if r.arrival_s < args.serve_warmup),
-            "ms_per_step": 1e3 * span / len(timed), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if prec == pl.PL_FP32_BULK else "f64",
+    m = serve_measure(local, args.duration, args.serve_warmup, args.workers, prec, pl, torch, args.serve_log)
+    config["generate_s"] = m["generate_s"]
+    timed = m["timed"]
+    line = {"metric": METRIC, "value": m["value"], "unit": "requests/s", "n_gpus": 1, "steps": len(timed),
+            "warmup": m["warmup_requests"], "ms_per_step": m["ms_per_request"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == pl.PL_FP32_BULK else "f64",
             "data": "synthetic request stream (library sampler, stream tag 2; rounded lognormal)",
-            "config": config,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max()), "mean": float(lat.mean()),
-                           "p50_n_ge_1e5": float(np.percentile(lat[big], 50)) if big.any() else None,
-                           "p99_n_lt_1e5": float(np.percentile(lat[~big], 99)) if (~big).any() else None,
-                           "queue_wait_p99": float(np.percentile(wait, 99)),
-                           "submit_lag_p99": float(np.percentile(np.array(lag) * 1e3, 99))},
-            "draws_per_s": draws / span, "failed_requests": len(bad),
-            "load": {"max_queued": max_queue, "max_running": max_running, "max_reserved_bytes": max_reserved},
-            "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": h2d,
+            "config": config, "latency_ms": m["latency_ms"], "draws_per_s": m["draws_per_s"],
+            "failed_requests": m["failed_requests"], "load": m["load"],
+            "e2e": {"value": m["value"], "unit": "requests/s", "h2d_bytes_per_step": m["h2d_bytes_per_request"],
                     "d2h_bytes_per_step": 24,
                     "note": "the serving value is end to end: host data in, host results out"},
-            "gpu_launches": launches, "clocks": clocks}
+            "gpu_launches": m["launches"], "clocks": m["clocks"]}
     if not args.no_cpu_baseline:
         cb = serving_cpu_baseline(timed, threads)
         line["cpu_baseline"] = {"value": cb["value"], "unit": "requests/s", "cores": threads,
@@ -724,21 +734,25 @@ def run_bespoke(args):
 
 
 def cell_line(alpha: float, n: int, R: int, step_ms: float, sample_ms: float, finish_ms: float,
-              mul_peak_gmul: float) -> dict:
+              mul_peak_gmul: float, f64_peak_gflops: float | None = None) -> dict:
     """One (alpha, n) cell run alone: replicates/s and samples/s over the
-    call's device time, the sampler's fraction of the multiply-pipe peak and
-    the finisher's time per replicate."""
+    call's device time, the sampler's fraction of the multiply-pipe peak, the
+    finisher's time per replicate and the finisher's binary64 fraction (the
+    fit's binary64 operations per replicate over the binary64 peak)."""
     draws = R * n
+    fit_ops = FINISHER_NCU.get(kernel_source_hash(), {}).get("fit_f64_ops")
     return {"alpha": alpha, "n": n, "replicates": R, "ms": step_ms,
             "replicates_per_s": R / (step_ms / 1e3), "samples_per_s": draws / (step_ms / 1e3),
             "sampler_ms": sample_ms, "finisher_ms": finish_ms,
             "finisher_ns_per_replicate": finish_ms * 1e6 / R,
             "sampler_frac": (MUL_PER_DRAW * draws / (sample_ms / 1e3) / 1e9 / mul_peak_gmul
-                             if sample_ms > 0 else None)}
+                             if sample_ms > 0 else None),
+            "finisher_fp64_frac": (fit_ops * R / (finish_ms / 1e3) / 1e9 / f64_peak_gflops
+                                   if fit_ops and f64_peak_gflops and finish_ms > 0 else None)}
 
 
 def per_cell_rates(ctx, cells, seed: int, qs, prec: int, mul_peak_gmul: float, flush, torch,
-                   reps: int = 3) -> list:
+                   reps: int = 3, f64_peak_gflops: float | None = None) -> list:
     """Every cell of the sweep run alone (its own call, after one warm-up
     call): the median over `reps` timed calls, each after an L2 flush, with
     CUDA events on the call's stream and the library's per-kernel trace."""
@@ -761,8 +775,95 @@ def per_cell_rates(ctx, cells, seed: int, qs, prec: int, mul_peak_gmul: float, f
             sm.append(tr["sample_ms"])
             fm.append(tr["finish_ms"])
         rows.append(cell_line(c.alpha, c.n, c.replicates, statistics.median(ms), statistics.median(sm),
-                              statistics.median(fm), mul_peak_gmul))
+                              statistics.median(fm), mul_peak_gmul, f64_peak_gflops))
     return rows
+
+
+# Finisher figures from one ncu capture of the sweep at 4,000 replicates per
+# cell (FP32-bulk), keyed by the hash of the kernel sources they were taken on
+# (reported as null once the sources change): DRAM bytes read per replicate
+# (its replicate records) and binary64 operations per replicate (DFMA counted
+# as two, DADD and DMUL as one), mostly the fit.
+FINISHER_NCU = {}  # filled from the capture recorded under profiles/ for the current sources
+ALGO_BYTES_PER_REPLICATE = 16  # D (binary32 or binary64) and alpha-hat (binary64) out
+
+
+def finisher_roofline(fin_ms: float, total_R: int, waves: int, f64_peak_gflops: float, probe: dict) -> dict:
+    """The finisher's binary64 fraction and its record traffic per replicate."""
+    ncu = FINISHER_NCU.get(kernel_source_hash())
+    out = {"kernel": "finish_kernel", "bound": "fp64", "ms_per_step": fin_ms,
+           "ns_per_replicate": fin_ms * 1e6 / total_R, "launches_per_step": waves,
+           "peak": 2.0 * f64_peak_gflops, "unit": "Gflop/s (binary64)",
+           "peak_basis": (f"{probe['sms']} SMs x {probe['dfma_per_sm_clk']:.2f} binary64 FMA per SM per clock "
+                          "(pl_probe_rates) x max SM clock x 2"),
+           "algorithmic_bytes_per_replicate": ALGO_BYTES_PER_REPLICATE}
+    if ncu:
+        achieved = ncu["f64_ops_per_replicate"] * total_R / (fin_ms / 1e3) / 1e9
+        out.update({"binary64_ops_per_replicate": ncu["f64_ops_per_replicate"], "achieved": achieved,
+                    "frac": achieved / out["peak"],
+                    "record_bytes_per_replicate": ncu["dram_read_per_replicate"]})
+    else:
+        out.update({"binary64_ops_per_replicate": None, "achieved": None, "frac": None,
+                    "record_bytes_per_replicate": None})
+    return out
+
+
+def timed_calls(call, flush, torch, stream, steps: int, warmup: int) -> list:
+    """CUDA-event milliseconds of `steps` calls on `stream`, each after an L2 flush."""
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def fp64_form_record(ctx, cells, seed: int, qs, flush, torch, stream, pl, value_f32: float) -> dict:
+    """The same sweep in the binary64 form (fit, KS and sums all binary64)."""
+    cut = torch.empty(len(cells) * len(qs), dtype=torch.float64, device="cuda")
+    ms = timed_calls(lambda: ctx.pl_ks_cutoffs(cells, seed, qs, pl.PL_FP64, cutoffs=cut), flush, torch, stream,
+                     steps=3, warmup=1)
+    ctx.pl_set_tracing(True)
+    ctx.pl_ks_cutoffs(cells, seed, qs, pl.PL_FP64, cutoffs=cut)
+    tr = ctx.pl_trace()
+    R = sum(c.replicates for c in cells)
+    v = R / (statistics.mean(ms) / 1e3)
+    return {"value": v, "unit": "replicates/s", "ms_per_step": statistics.mean(ms), "steps": len(ms),
+            "sampler_ms": tr["sample_ms"], "finisher_ms": tr["finish_ms"],
+            "fp32_bulk_over_fp64": value_f32 / v}
+
+
+def c0_fp64_record(ctx, flush, torch, stream, pl) -> dict:
+    """The plain method in binary64: alpha = 2.5, xmin = 1, n = 100, 10,000
+    replicates, seed 1; device-resident cutoffs, and end to end with the host
+    cell table in and host cutoffs out."""
+    import numpy as np
+    c = inputs.cutoff_cell_small()[0]
+    cells = [pl.Cell(c.alpha, c.xmin, c.n, c.replicates, c.cell_id)]
+    cut = torch.empty(len(Q), dtype=torch.float64, device="cuda")
+    ms = timed_calls(lambda: ctx.pl_ks_cutoffs(cells, 1, Q, pl.PL_FP64, cutoffs=cut), flush, torch, stream,
+                     steps=20, warmup=3)
+    host = np.zeros(len(Q))
+    e2e = []
+    for _ in range(10):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.pl_ks_cutoffs(cells, 1, Q, pl.PL_FP64, cutoffs=host)
+        e2e.append(time.perf_counter() - t0)
+    return {"workload": "alpha=2.5, xmin=1, n=100, 10,000 replicates, seed 1, binary64 form",
+            "value": c.replicates / (statistics.median(ms) / 1e3), "unit": "replicates/s",
+            "ms_per_step": statistics.median(ms), "steps": len(ms),
+            "e2e": {"value": c.replicates / statistics.median(e2e), "unit": "replicates/s",
+                    "h2d_bytes_per_step": 40 + 8 * len(Q), "d2h_bytes_per_step": 8 * len(Q)},
+            "cutoffs": host.tolist()}
 
 
 def replica_seed(rank: int) -> int:
@@ -810,8 +911,13 @@ def main():
                          "bespoke: 64 data sets (both laws), each fitted with its own cutoffs from 10,000 "
                          "simulated replicates, plus 10^6 lookups in a tabulated grid and one lower-end "
                          "estimate on 10^6 values")
-    ap.add_argument("--per-cell", action="store_true",
-                    help="sweep: also time every (alpha, n) cell alone and add a per_cell list to the line")
+    ap.add_argument("--no-per-cell", action="store_true",
+                    help="sweep: skip timing every (alpha, n) cell alone (the per_cell list)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="sweep: skip the probe, the FP64-form sweep, the FP64 small cell and the short "
+                         "serving run")
+    ap.add_argument("--extras-serve-s", type=float, default=15.0,
+                    help="sweep: measured seconds of the short serving run")
     ap.add_argument("--large-n-replicates", type=int, default=10_000,
                     help="large-n: replicates (smaller values for profiler captures only)")
     ap.add_argument("--sampler", choices=["inverse-cdf", "multinomial"], default="inverse-cdf",
@@ -1032,11 +1138,33 @@ def main():
         if args.workload == "sweep":  # the same oracle on one core, a smaller sample
             c1 = cpu_oracle_rate(max(1, args.cpu_sample // 8), 1)
             line["cpu_baseline"]["one_core"] = {"value": c1["value"], "cores": 1, "sample": c1["sample"]}
-    if args.per_cell and args.workload == "sweep" and world == 1 and args.sampler == "inverse-cdf":
-        line["per_cell"] = per_cell_rates(ctx, cells, seed, QS, prec, mul_peak, flush, torch)
+    main_sweep = args.workload == "sweep" and world == 1 and args.sampler == "inverse-cdf"
+    f64_flops = None
+    if main_sweep and not args.no_extras:
+        probe = ctx.pl_probe_rates()
+        line["probe"] = probe
+        roofline["probe"] = {k: probe[k] for k in ("sm_clock_mhz", "mul_wide_per_sm_clk", "philox_words_per_s")}
+        f64_peak = props.multi_processor_count * probe["dfma_per_sm_clk"] * sm_max * 1e6 / 1e9  # Gflop/s of FMA
+        f64_flops = 2.0 * f64_peak
+        roofline["finisher"] = finisher_roofline(statistics.mean(fin_ms), total_R, waves, f64_peak, probe)
+        line["fp64_form"] = fp64_form_record(ctx, cells, seed, QS, flush, torch, stream, pl, value)
+        line["c0_fp64"] = c0_fp64_record(ctx, flush, torch, stream, pl)
+    if main_sweep and not args.no_per_cell:
+        line["per_cell"] = per_cell_rates(ctx, cells, seed, QS, prec, mul_peak, flush, torch,
+                                          f64_peak_gflops=f64_flops)
+    if main_sweep and not args.no_extras:
+        ctx.close()
+        ctx = None
+        m = serve_measure(local, args.extras_serve_s, 3.0, args.workers, pl.PL_FP32_BULK, pl, torch)
+        line["serving"] = {"workload": serving_config(args)["workload"], "offered_per_s": SERVE_RATE,
+                           "value": m["value"], "unit": "requests/s", "measured_s": args.extras_serve_s,
+                           "warmup_s": 3.0, "requests": len(m["timed"]), "latency_ms": m["latency_ms"],
+                           "failed_requests": m["failed_requests"], "draws_per_s": m["draws_per_s"],
+                           "load": m["load"], "clocks": m["clocks"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 

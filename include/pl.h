@@ -111,6 +111,26 @@ typedef struct {
 /* Synchronises `stream` and copies the counters to *out (host). */
 pl_status pl_counters(pl_ctx *ctx, void *stream, pl_counter_info *out);
 
+/* Issue rates of the units that bound the kernels, measured on the
+ * context's GPU (not a step of the method; the paper has no counterpart):
+ * each probe kernel keeps one 1024-thread block per SM busy with eight
+ * independent chains of one instruction, and the longest block's clock64
+ * count over the CUDA-event time gives the SM clock of the run.  The samplers' ceiling
+ * is the 32x32->64-bit multiply (Philox4x32-10 takes five per 32-bit draw);
+ * the fit and the binary64 KS run on the binary64 pipe.  Takes a few
+ * milliseconds; uses the context's workspace (about 600 KB per 100 SMs).
+ * Synchronises `stream`.  Errors: PL_EINVAL (null out), PL_ENOMEM, PL_ECUDA. */
+typedef struct {
+  double sm_clock_mhz;         /* SM clock during the multiply probe */
+  double mul_wide_per_sm_clk;  /* mul.wide.u32 per SM per clock */
+  double lop3_per_sm_clk;      /* three-input logic operations per SM per clock */
+  double dfma_per_sm_clk;      /* binary64 fused multiply-adds per SM per clock */
+  double philox_words_per_s;   /* 32-bit Philox4x32-10 words per second, whole GPU */
+  int32_t sms;                 /* SMs of the GPU */
+  int32_t pad;
+} pl_probe_info;
+pl_status pl_probe_rates(pl_ctx *ctx, void *stream, pl_probe_info *out);
+
 /* Tracing (no counterpart in the paper, which times whole runs with clock()).
  * With tracing on, pl_ks_cutoffs and pl_bootstrap_pvalue record CUDA events
  * on their stream around each phase; pl_trace synchronises `stream` and
@@ -446,8 +466,8 @@ pl_status pl_estimate_xmin(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
  * calls can synchronise the device).  Its scratch is a fixed device array
  * inside the library (about 6.3 MB on every GPU that loads it, held until
  * the process exits); no context is used.
- * alpha: NaN or <= 0 fits the exponent (Eq. 2) and evaluates D there; a value
- *   in (1, 64] evaluates D (Eq. 3) at that exponent.
+ * alpha: NaN or <= 0 fits the exponent by maximum likelihood and evaluates D
+ *   there; a value in (1, 64] evaluates D at that exponent.
  * x_dev: device int32[n], 1 <= n <= 262144 (larger n: PL_EINVAL), values >= xmin.
  * out_dev: device double[3], written in stream order: alpha (fitted or given),
  *   D, zeta(alpha, xmin); all NaN if a value is below xmin.

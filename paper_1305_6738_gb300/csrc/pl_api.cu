@@ -22,6 +22,7 @@
 #include "pl_lookup.cuh"
 #include "pl_xmin.cuh"
 #include "pl_multinomial.cuh"
+#include "pl_probe.cuh"
 
 using namespace pl;
 
@@ -40,6 +41,8 @@ struct pl_ctx {
   uint64_t launches = 0;
   // Capacity overrides for tests (environment, read at pl_create; 0 = off):
   // they only shrink buffers so that the overflow fallbacks run.
+  // PL_TEST_WAIT_CYCLES (cycles of the first shared-memory staging wait, in
+  // the device counters) makes the bounded waits run out.
   uint32_t dbg_spill_cap = 0;    // PL_TEST_SPILL_SLOT: record spill slot entries
   uint32_t dbg_tail_cap = 0;     // PL_TEST_TAIL_QUEUE: tail-queue entries
   size_t dbg_arena = 0;          // PL_TEST_ARENA_BYTES: finisher arena bytes per warp
@@ -702,6 +705,14 @@ pl_status pl_create(pl_ctx **out, int device, size_t mem_budget_bytes) {
   if (const char *e = getenv("PL_TEST_SPILL_SLOT")) ctx->dbg_spill_cap = (uint32_t)strtoul(e, nullptr, 10);
   if (const char *e = getenv("PL_TEST_TAIL_QUEUE")) ctx->dbg_tail_cap = (uint32_t)strtoul(e, nullptr, 10);
   if (const char *e = getenv("PL_TEST_ARENA_BYTES")) ctx->dbg_arena = (size_t)strtoull(e, nullptr, 10);
+  if (const char *e = getenv("PL_TEST_WAIT_CYCLES")) {
+    const unsigned long long w = strtoull(e, nullptr, 10);
+    if (cudaMemcpy(&ctx->ctr->wait_limit, &w, sizeof w, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(ctx->ctr);
+      delete ctx;
+      return PL_ECUDA;
+    }
+  }
   ctx->finish_blocks_per_sm[0] = finish_kernel_blocks_per_sm(false);
   ctx->finish_blocks_per_sm[1] = finish_kernel_blocks_per_sm(true);
   ctx->sample_blocks_per_sm = sample_kernel_blocks_per_sm();
@@ -768,6 +779,54 @@ pl_status pl_trace(pl_ctx *ctx, void *stream, pl_trace_info *out) {
 pl_status pl_sync(pl_ctx *ctx, void *stream) {
   if (pl_status s = check_ctx(ctx)) return s;
   return read_status(ctx, (cudaStream_t)stream);
+}
+
+pl_status pl_probe_rates(pl_ctx *ctx, void *stream, pl_probe_info *out) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(ctx, PL_EINVAL, "pl_probe_rates: null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  // one block of kProbeBlock threads per SM
+  const int grid = ctx->num_sms;
+  const size_t words = (size_t)grid * kProbeBlock;
+  if (pl_status s = ensure_ws(ctx, words * sizeof(uint32_t) + 256)) return s;
+  uint32_t *o = reinterpret_cast<uint32_t *>(ctx->ws);
+  long long *cyc = reinterpret_cast<long long *>(ctx->ws + ((words * sizeof(uint32_t) + 255) & ~(size_t)255));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PL_CUDA(cudaEventCreate(&e0));
+  PL_CUDA(cudaEventCreate(&e1));
+  // kind, loop iterations, operations per thread and iteration
+  const struct { int kind, iters; double ops; } runs[4] = {
+      {kProbeMulWide, 4096, (double)kProbeChains}, {kProbeLop3, 8192, (double)kProbeChains},
+      {kProbeDfma, 256, (double)kProbeChains}, {kProbePhilox, 1024, 20.0}};
+  double rate[4], mhz = 0.0, philox_ms = 0.0;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+    e = launch_probe(runs[k].kind, o, cyc, grid, runs[k].iters / 8, 1u, st);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = launch_probe(runs[k].kind, o, cyc, grid, runs[k].iters, 2u, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    long long c = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) e = cudaMemcpy(&c, cyc, sizeof c, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) break;
+    const double ops = (double)words * runs[k].iters * runs[k].ops;
+    rate[k] = c > 0 ? ops / ((double)ctx->num_sms * (double)c) : 0.0;
+    if (k == 0) mhz = ms > 0.0f ? (double)c / ((double)ms * 1e3) : 0.0;
+    if (k == 3) philox_ms = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(ctx, PL_ECUDA, "pl_probe_rates: %s", cudaGetErrorString(e));
+  out->sm_clock_mhz = mhz;
+  out->mul_wide_per_sm_clk = rate[0];
+  out->lop3_per_sm_clk = rate[1];
+  out->dfma_per_sm_clk = rate[2];
+  out->philox_words_per_s = philox_ms > 0.0 ? 4.0 * (double)words * runs[3].iters / (philox_ms * 1e-3) : 0.0;
+  out->sms = ctx->num_sms;
+  out->pad = 0;
+  return PL_OK;
 }
 
 pl_status pl_counters(pl_ctx *ctx, void *stream, pl_counter_info *out) {

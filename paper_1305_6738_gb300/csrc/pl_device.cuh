@@ -61,6 +61,7 @@ struct Counters {
   unsigned long long resampled;              // replicates whose spill slot overflowed
   unsigned int status;
   unsigned int work_next;                   // persistent-kernel work counter
+  unsigned long long wait_limit;            // test hook: the first staging wait runs out after this many cycles
 #ifdef PL_PHASE_TIMING
   unsigned long long phase_cycles[8];       // diagnostic build only
 #endif
@@ -696,7 +697,10 @@ __device__ __forceinline__ void warp_sum_ff(float &hi, float &lo) {
 // ---------------------------------------------------------------------------
 // Bounded mbarrier wait: gives up after ~2^31 clock cycles (about a second)
 // and reports false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity) {
+// Waits give up after kWaitCycles SM cycles (about a second at 2 GHz).
+constexpr long long kWaitCycles = 1ll << 31;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity, long long limit = kWaitCycles) {
   const uint32_t addr = (uint32_t)__cvta_generic_to_shared(mbar);
   const long long t0 = clock64();
   for (;;) {
@@ -709,7 +713,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parit
         : "r"(addr), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 

@@ -152,7 +152,9 @@ cudaError_t launch_law_setup(Law *laws_dev, int nlaws, cudaStream_t st) {
 // ===========================================================================
 // Shared-memory staging of a law's level-1 thresholds and guide table by the
 // bulk-copy (TMA) engine.  Every thread waits (bounded); the outcome is made
-// uniform across the block so that no thread leaves a barrier early.
+// uniform across the block so that no thread leaves a barrier early.  The
+// kernels keep two mbarriers: mbar[0] for the copies, mbar[1] never arrived at
+// (the flag a test makes the first wait run out on).
 struct StagedLaw {
   uint64_t *sT;
   uint32_t *sG;
@@ -176,11 +178,14 @@ __device__ bool stage_law(const StagedLaw &s, const Law &law, uint32_t &phase, C
       bulk_g2s(s.sLn + kHMax, law.lnT_lo, kLnBytes, s.mbar);
     }
   }
-  const bool ok = mbar_wait_bounded(s.mbar, phase);
+  // test hook (wait_limit set): wait instead on the block's second barrier,
+  // at which nothing ever arrives, for wait_limit cycles
+  const bool ok = ctr->wait_limit ? mbar_wait_bounded(s.mbar + 1, 0u, (long long)ctr->wait_limit)
+                                  : mbar_wait_bounded(s.mbar, phase);
   const int any_fail = __syncthreads_or(!ok);
   if (any_fail) {
     if (threadIdx.x == 0) atomicOr(&ctr->status, kErrTimeout);
-    mbar_wait_bounded(s.mbar, phase);  // let copies in flight land before exit
+    mbar_wait_bounded(s.mbar, phase);  // full bound: let copies in flight land before exit
     return false;
   }
   phase ^= 1u;
@@ -197,7 +202,10 @@ __global__ void __launch_bounds__(256) sample_kernel(const Law *law_p, uint64_t 
   extern __shared__ __align__(16) uint8_t smem[];
   StagedLaw s{(uint64_t *)smem, (uint32_t *)(smem + kL1 * 8), (uint64_t *)(smem + kL1 * 8 + kGuide * 4)};
   const Law law = *law_p;
-  if (threadIdx.x == 0) mbar_init(s.mbar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(s.mbar, 1);
+    mbar_init(s.mbar + 1, 1);
+  }
   __syncthreads();
   uint32_t phase = 0;
   if (!stage_law(s, law, phase, ctr)) return;
@@ -1159,11 +1167,15 @@ __global__ void __launch_bounds__(kAWarps * 32, kABlocksPerSM) sample_hist_kerne
   uint32_t *hist = sH + warp * (kHMax / 2);
   uint64_t *queue = sQ + warp * kQCap * 32;
   const TailQueue tq{a.tq_pos, a.tq_law, a.tq_count, a.tq_cap};
-  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);  // never arrived at: the wait-timeout test hook's flag
+  }
   __syncthreads();
   uint32_t phase = 0, loaded = 0xffffffffu;
   for (;;) {
-    if (threadIdx.x == 0) *s_item = atomicAdd(&a.ctr->work_next, 1u);
+    if (threadIdx.x == 0)  // no further items once a wait has run out: records may be incomplete
+      *s_item = (*(volatile unsigned int *)&a.ctr->status & kErrTimeout) ? a.nitems : atomicAdd(&a.ctr->work_next, 1u);
     __syncthreads();
     const uint32_t item = *s_item;
     if (item >= a.nitems) break;
@@ -1208,11 +1220,15 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
   uint64_t *defer_q = mbar + 2 + (threadIdx.x >> 5) * kDeferCap;
   const unsigned lt = (1u << lane) - 1u;
   const TailQueue tq{a.tq_pos, a.tq_law, a.tq_count, a.tq_cap};
-  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);  // never arrived at: the wait-timeout test hook's flag
+  }
   __syncthreads();
   uint32_t phase = 0, loaded = 0xffffffffu;
   for (;;) {
-    if (threadIdx.x == 0) *s_item = atomicAdd(&a.ctr->work_next, 1u);
+    if (threadIdx.x == 0)  // no further items once a wait has run out: records may be incomplete
+      *s_item = (*(volatile unsigned int *)&a.ctr->status & kErrTimeout) ? a.nitems : atomicAdd(&a.ctr->work_next, 1u);
     __syncthreads();
     const uint32_t item = *s_item;
     if (item >= a.nitems) break;
@@ -1475,12 +1491,16 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
   uint64_t *spill = reinterpret_cast<uint64_t *>(a.scratch + slot * (a.spill_cap * 8 + a.arena_bytes));
   uint8_t *arena = reinterpret_cast<uint8_t *>(spill + a.spill_cap);
 
-  if (threadIdx.x == 0) mbar_init(mbar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);  // never arrived at: the wait-timeout test hook's flag
+  }
   __syncthreads();
   uint32_t phase = 0, loaded = 0xffffffffu;
 
   for (;;) {
-    if (threadIdx.x == 0) *s_item = atomicAdd(&a.ctr->work_next, 1u);
+    if (threadIdx.x == 0)  // no further items once a wait has run out: records may be incomplete
+      *s_item = (*(volatile unsigned int *)&a.ctr->status & kErrTimeout) ? a.nitems : atomicAdd(&a.ctr->work_next, 1u);
     __syncthreads();
     const uint32_t item = *s_item;
     if (item >= a.nitems) break;

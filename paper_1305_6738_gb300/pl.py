@@ -26,7 +26,7 @@ PL_FP64, PL_FP32_BULK = 0, 1
 _NAMES = {1: "PL_EINVAL", 2: "PL_ENOMEM", 3: "PL_ENOCONV", 4: "PL_ETIMEOUT", 5: "PL_ECUDA",
           6: "PL_EBUSY"}
 
-EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters", "pl_set_tracing",
+EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters", "pl_probe_rates", "pl_set_tracing",
            "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue", "pl_fit_ks_noalloc", "pl_plan_cutoffs", "pl_plan_run",
            "pl_plan_destroy", "pl_autotune", "pl_set_split", "pl_server_create", "pl_server_submit",
@@ -57,6 +57,12 @@ class pl_counter_info(ctypes.Structure):
                 ("resampled", ctypes.c_uint64)]
 
 
+class pl_probe_info(ctypes.Structure):
+    _fields_ = [("sm_clock_mhz", ctypes.c_double), ("mul_wide_per_sm_clk", ctypes.c_double),
+                ("lop3_per_sm_clk", ctypes.c_double), ("dfma_per_sm_clk", ctypes.c_double),
+                ("philox_words_per_s", ctypes.c_double), ("sms", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 class pl_trace_info(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("law_ms", ctypes.c_float),
                 ("replicate_ms", ctypes.c_float), ("select_ms", ctypes.c_float),
@@ -83,6 +89,7 @@ _lib.pl_last_error.argtypes = [_vp]
 _lib.pl_last_error.restype = ctypes.c_char_p
 _lib.pl_sync.argtypes = [_vp, _vp]
 _lib.pl_counters.argtypes = [_vp, _vp, ctypes.POINTER(pl_counter_info)]
+_lib.pl_probe_rates.argtypes = [_vp, _vp, ctypes.POINTER(pl_probe_info)]
 _lib.pl_set_tracing.argtypes = [_vp, ctypes.c_int]
 _lib.pl_trace.argtypes = [_vp, _vp, ctypes.POINTER(pl_trace_info)]
 _lib.pl_sample.argtypes = [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
@@ -138,7 +145,7 @@ _lib.pl_bespoke_cutoffs_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctyp
                                           ctypes.c_int, ctypes.c_int, _f64p, _f64p, _f64p, _f64p, _vp]
 _lib.pl_server_destroy.restype = None
 for _f in ["pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_fit_ks_truncated", "pl_bespoke_cutoffs",
-           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin", "pl_ks_cutoffs_multinomial", "pl_bespoke_cutoffs_batch", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin", "pl_ks_cutoffs_multinomial", "pl_bespoke_cutoffs_batch", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_probe_rates", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -156,6 +163,22 @@ def _stream_ptr(stream) -> int | None:
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)
+
+
+def _data(x, what: str = "x"):
+    """A data-set argument: a contiguous int32 tensor on a CUDA device (the
+    entry points read it as int32[n] of device memory)."""
+    if not (getattr(x, "is_cuda", False) and str(x.dtype) == "torch.int32" and x.is_contiguous()):
+        raise ValueError(f"{what}: expected a contiguous torch.int32 CUDA tensor")
+    return x
+
+
+def _dev_f64(t, what: str, count: int):
+    """A device output of `count` binary64 values."""
+    if not (getattr(t, "is_cuda", False) and str(t.dtype) == "torch.float64" and t.is_contiguous()
+            and t.numel() >= count):
+        raise ValueError(f"{what}: expected a contiguous torch.float64 CUDA tensor of at least {count} elements")
+    return t
 
 
 def _ptr(t) -> int:
@@ -221,6 +244,11 @@ class Context:
         self._check(_lib.pl_counters(self._h, _stream_ptr(stream), ctypes.byref(c)))
         return {k: getattr(c, k) for k, _ in pl_counter_info._fields_}
 
+    def pl_probe_rates(self, stream=None) -> dict:
+        p = pl_probe_info()
+        self._check(_lib.pl_probe_rates(self._h, _stream_ptr(stream), ctypes.byref(p)))
+        return {k: getattr(p, k) for k, _ in pl_probe_info._fields_ if k != "pad"}
+
     def pl_set_tracing(self, on: bool = True):
         self._check(_lib.pl_set_tracing(self._h, 1 if on else 0))
 
@@ -239,13 +267,13 @@ class Context:
     def pl_fit_mle(self, x, xmin: int, stream=None) -> float:
         """x: torch.int32 device tensor."""
         a = ctypes.c_double()
-        self._check(_lib.pl_fit_mle(self._h, _ptr(x), x.numel(), xmin, ctypes.byref(a),
+        self._check(_lib.pl_fit_mle(self._h, _ptr(_data(x)), x.numel(), xmin, ctypes.byref(a),
                                     _stream_ptr(stream)))
         return a.value
 
     def pl_ks_stat(self, x, xmin: int, alpha: float, prec: int = PL_FP64, stream=None) -> float:
         d = ctypes.c_double()
-        self._check(_lib.pl_ks_stat(self._h, _ptr(x), x.numel(), xmin, alpha, prec, ctypes.byref(d),
+        self._check(_lib.pl_ks_stat(self._h, _ptr(_data(x)), x.numel(), xmin, alpha, prec, ctypes.byref(d),
                                     _stream_ptr(stream)))
         return d.value
 
@@ -305,7 +333,7 @@ class Context:
     def pl_fit_ks_truncated(self, x, K: int, gamma: float = float("nan"), prec: int = PL_FP64, stream=None):
         """x: torch.int32 device tensor (values 1..K).  Returns (gamma, D); gamma NaN fits it."""
         g, d = ctypes.c_double(), ctypes.c_double()
-        self._check(_lib.pl_fit_ks_truncated(self._h, _ptr(x), x.numel(), K, gamma, prec, ctypes.byref(g),
+        self._check(_lib.pl_fit_ks_truncated(self._h, _ptr(_data(x)), x.numel(), K, gamma, prec, ctypes.byref(g),
                                              ctypes.byref(d), _stream_ptr(stream)))
         return g.value, d.value
 
@@ -315,7 +343,7 @@ class Context:
         qa = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
         cut = np.zeros(qa.size)
         a, d, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-        self._check(_lib.pl_bespoke_cutoffs(self._h, _ptr(x), x.numel(), xmin, R, seed, request_id,
+        self._check(_lib.pl_bespoke_cutoffs(self._h, _ptr(_data(x)), x.numel(), xmin, R, seed, request_id,
                                             qa.ctypes.data_as(_f64p), qa.size, prec, ctypes.byref(a),
                                             ctypes.byref(d), ctypes.byref(p), cut.ctypes.data_as(_f64p),
                                             _stream_ptr(stream)))
@@ -325,7 +353,7 @@ class Context:
                                  stream=None):
         """xs: torch.int32 device tensors.  Returns (alpha_hat[], D[], p[], cutoffs[nsets, nq])."""
         k = len(xs)
-        ptrs = (ctypes.c_void_p * k)(*[_ptr(x) for x in xs])
+        ptrs = (ctypes.c_void_p * k)(*[_ptr(_data(x, "xs[]")) for x in xs])
         ns = (ctypes.c_int64 * k)(*[x.numel() for x in xs])
         xm = (ctypes.c_uint64 * k)(*[int(v) for v in xmins])
         rid = (ctypes.c_uint64 * k)(*[int(v) for v in request_ids])
@@ -343,7 +371,7 @@ class Context:
         qa = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
         cut = np.zeros(qa.size)
         g, d, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-        self._check(_lib.pl_bespoke_cutoffs_truncated(self._h, _ptr(x), x.numel(), K, R, seed, request_id,
+        self._check(_lib.pl_bespoke_cutoffs_truncated(self._h, _ptr(_data(x)), x.numel(), K, R, seed, request_id,
                                                       qa.ctypes.data_as(_f64p), qa.size, prec, ctypes.byref(g),
                                                       ctypes.byref(d), ctypes.byref(p), cut.ctypes.data_as(_f64p),
                                                       _stream_ptr(stream)))
@@ -364,7 +392,7 @@ class Context:
         """x: torch.int32 device tensor.  Returns the pl_xmin_result fields; cand_* are
         optional device tensors (uint64/int64, float64, float64, int64) of max_candidates."""
         r = pl_xmin_result()
-        self._check(_lib.pl_estimate_xmin(self._h, _ptr(x), x.numel(), max_candidates, min_tail, ctypes.byref(r),
+        self._check(_lib.pl_estimate_xmin(self._h, _ptr(_data(x)), x.numel(), max_candidates, min_tail, ctypes.byref(r),
                                           _ptr(cand_xmin), _ptr(cand_alpha), _ptr(cand_D), _ptr(cand_ntail),
                                           _stream_ptr(stream)))
         return {k: getattr(r, k) for k, _ in pl_xmin_result._fields_}
@@ -410,7 +438,7 @@ class Context:
     def pl_bootstrap_pvalue(self, x, xmin: int, B: int, seed: int, request_id: int,
                             prec: int = PL_FP64, stream=None):
         a, d, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-        self._check(_lib.pl_bootstrap_pvalue(self._h, _ptr(x), x.numel(), xmin, B, seed, request_id,
+        self._check(_lib.pl_bootstrap_pvalue(self._h, _ptr(_data(x)), x.numel(), xmin, B, seed, request_id,
                                              prec, ctypes.byref(a), ctypes.byref(d), ctypes.byref(p),
                                              _stream_ptr(stream)))
         return a.value, d.value, p.value
@@ -444,7 +472,8 @@ def pl_fit_ks_noalloc(x, xmin: int, alpha: float, out, prec: int = PL_FP64, stre
     fixed scratch instead of a context (no device allocation by the library).
     x: int32 device tensor (n <= 262144); out: float64 device tensor of 3 elements
     receiving (alpha, D, zeta(alpha, xmin)) in stream order."""
-    assert out.numel() >= 3 and out.element_size() == 8
+    _data(x)
+    _dev_f64(out, "out", 3)
     st = _lib.pl_fit_ks_noalloc(_ptr(x), x.numel(), xmin, alpha, prec, _ptr(out), _stream_ptr(stream))
     if st != PL_OK:
         raise PLError(st, "pl_fit_ks_noalloc failed")
