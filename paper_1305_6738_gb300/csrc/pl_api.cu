@@ -159,6 +159,7 @@ Law carve_law(Carver &cv, const LawPlan &lp) {
   l.L2 = lp.L2;
   l.T = cv.take<uint64_t>(lp.L2);
   l.guide = cv.take<uint32_t>(kGuide);
+  l.fine = cv.take<uint32_t>(kFine);
   l.inc = cv.take<uint32_t>((size_t)kIncBuckets * 32);
   l.lnT = cv.take<double>(kLnTable);
   l.lnT_hi = cv.take<float>(kLnTable);

@@ -29,6 +29,8 @@ constexpr uint64_t kXCap = 1ull << 62;      // simulated values saturate here
 constexpr int kL1 = PL_L1_ENTRIES;          // thresholds staged in shared memory
 constexpr int kGuideBits = 12;              // guide table: 2^12 buckets of m
 constexpr int kGuide = 1 << kGuideBits;
+constexpr int kFineBits = 13;               // the warp-form sampler's finer guide: 2^13 buckets
+constexpr int kFine = 1 << kFineBits;
 // A guide word holds the bucket's smallest answer index (low 31 bits) and, in
 // bit 31, whether the bucket holds more than one answer (a search is needed).
 constexpr uint32_t kGuideMulti = 0x80000000u, kGuideIndex = 0x7fffffffu;
@@ -80,6 +82,7 @@ struct Law {
   uint64_t *T;            // T[i] = floor(Q(xmin+i) 2^53) + 1, Q(k) = P(X > k)
   uint32_t *guide;        // guide[j] = min{i : T[i] <= (j+1) 2^(53-g)} (or L2) | kGuideMulti flag
   uint32_t *inc;          // increment table (kIncBuckets x 32 copies)
+  uint32_t *fine;         // guide of kFine buckets (same form as guide)
   double *lnT;            // ln(xmin + i), i < kLnTable
   float *lnT_hi;          // float split of lnT: hi + lo
   float *lnT_lo;
@@ -530,10 +533,12 @@ __device__ __forceinline__ uint64_t table_at(const uint64_t *sT, const uint64_t 
 }
 
 // Index form: returns i = X - xmin for answers inside the table, L2 beyond it.
+// GB: the guide's bucket bits (2^GB buckets of m).
+template <int GB = kGuideBits>
 __device__ __forceinline__ uint32_t lookup_index(const uint64_t *sT, const uint32_t *sG,
                                                  const uint64_t *gT, uint32_t L2, float xmin_f,
                                                  float tail_c, float tail_e, uint64_t m) {
-  const uint32_t j = (uint32_t)((m - 1ull) >> (53 - kGuideBits));
+  const uint32_t j = (uint32_t)((m - 1ull) >> (53 - GB));
   uint32_t lo = sG[j] & kGuideIndex;
   uint32_t hi = j ? sG[j - 1] & kGuideIndex : L2;
   if (hi - lo > 8) {

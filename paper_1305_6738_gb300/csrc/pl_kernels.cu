@@ -96,8 +96,9 @@ __global__ void __launch_bounds__(kFillEmWarps * 32) law_fill_em_kernel(Law *law
 // guide[j] = min{i < L2 : T[i] <= (j+1) 2^(53-g)}, or L2, with kGuideMulti
 // set unless the bucket's answers [guide[j], guide[j-1]] (L2 above bucket 0)
 // are a single index.
+template <int GB>
 __device__ __forceinline__ uint32_t guide_bound(const Law &law, uint32_t j) {
-  const uint64_t bound = (uint64_t)(j + 1) << (53 - kGuideBits);
+  const uint64_t bound = (uint64_t)(j + 1) << (53 - GB);
   uint32_t lo = 0, hi = law.L2;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
@@ -107,13 +108,14 @@ __device__ __forceinline__ uint32_t guide_bound(const Law &law, uint32_t j) {
   return lo;
 }
 
+template <int GB>
 __global__ void law_guide_kernel(Law *laws) {
   const Law law = laws[blockIdx.y];
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= (uint32_t)kGuide) return;
-  const uint32_t lo = guide_bound(law, j);
-  const uint32_t hi = j ? guide_bound(law, j - 1) : law.L2;
-  law.guide[j] = lo | (hi != lo ? kGuideMulti : 0u);
+  if (j >= (1u << GB)) return;
+  const uint32_t lo = guide_bound<GB>(law, j);
+  const uint32_t hi = j ? guide_bound<GB>(law, j - 1) : law.L2;
+  (GB == kGuideBits ? law.guide : law.fine)[j] = lo | (hi != lo ? kGuideMulti : 0u);
 }
 
 // Increment table: bucket j of the high word covers m in [j 2^45 + 1,
@@ -144,7 +146,8 @@ cudaError_t launch_law_setup(Law *laws_dev, int nlaws, cudaStream_t st) {
   law_fill_kernel<<<dim3(256, nlaws), 256, 0, st>>>(laws_dev);
   // entries with direct terms: xmin + i + 1 < 10 + 1.5 alpha, i < 105 for alpha <= 64
   law_fill_em_kernel<<<dim3(128 / kFillEmWarps, nlaws), kFillEmWarps * 32, 0, st>>>(laws_dev);
-  law_guide_kernel<<<dim3(kGuide / 256, nlaws), 256, 0, st>>>(laws_dev);
+  law_guide_kernel<kGuideBits><<<dim3(kGuide / 256, nlaws), 256, 0, st>>>(laws_dev);
+  law_guide_kernel<kFineBits><<<dim3(kFine / 256, nlaws), 256, 0, st>>>(laws_dev);
   law_inc_kernel<<<dim3(kIncBuckets / 8, nlaws), 256, 0, st>>>(laws_dev);
   return cudaGetLastError();
 }
@@ -159,7 +162,7 @@ struct StagedLaw {
   uint64_t *sT;
   uint32_t *sG;
   uint64_t *mbar;
-  uint32_t *sInc = nullptr;  // the increment table too, when given
+  uint32_t *sInc = nullptr;  // the increment table too, when given (with the fine guide in sG)
   float *sLn = nullptr;      // and the binary32 splits of ln(xmin + i), i < kHMax (hi, then lo)
 };
 
@@ -168,10 +171,11 @@ constexpr uint32_t kLnBytes = (uint32_t)kHMax * sizeof(float);
 
 __device__ bool stage_law(const StagedLaw &s, const Law &law, uint32_t &phase, Counters *ctr) {
   if (threadIdx.x == 0) {
-    mbar_expect_tx(s.mbar, (uint32_t)(kL1 * sizeof(uint64_t) + kGuide * sizeof(uint32_t)) + (s.sInc ? kIncBytes : 0u) +
+    const uint32_t gbytes = (uint32_t)((s.sInc ? kFine : kGuide) * sizeof(uint32_t));
+    mbar_expect_tx(s.mbar, (uint32_t)(kL1 * sizeof(uint64_t)) + gbytes + (s.sInc ? kIncBytes : 0u) +
                                (s.sLn ? 2u * kLnBytes : 0u));
     bulk_g2s(s.sT, law.T, (uint32_t)(kL1 * sizeof(uint64_t)), s.mbar);
-    bulk_g2s(s.sG, law.guide, (uint32_t)(kGuide * sizeof(uint32_t)), s.mbar);
+    bulk_g2s(s.sG, s.sInc ? law.fine : law.guide, gbytes, s.mbar);
     if (s.sInc) bulk_g2s(s.sInc, law.inc, kIncBytes, s.mbar);
     if (s.sLn) {
       bulk_g2s(s.sLn, law.lnT_hi, kLnBytes, s.mbar);
@@ -995,7 +999,8 @@ __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint
 // Every other draw (a larger value, a bucket holding a threshold, a value
 // beyond the table) is appended to the lane's queue in shared memory (column
 // `lane`, kQCap entries) with no warp vote; once a lane's queue may not take
-// another block's four draws the warp drains all queues: the guide word, a
+// another block's four draws the warp drains all queues: the word of the fine
+// guide (2^13 buckets), a
 // search of the shared level-1 table where the bucket holds several values
 // (compacted across the warp; level 2 of the table in global memory), then a
 // shared atomic below H or a spill.  A value beyond the table is spilled as
@@ -1048,13 +1053,14 @@ __device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const ui
   // draw's interval of m or the answer lies beyond the table
   auto search = [&](uint64_t e) {
     const uint32_t h = (uint32_t)e;
-    const uint32_t i0 = lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m_first(h));
+    const uint32_t i0 =
+        lookup_index<kFineBits>(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m_first(h));
     if (i0 < law.L2 && (i0 == 0 || table_at(sT, law.T, i0 - 1) > m_last(h))) {
       bin(i0);
       return;
     }
     const uint64_t m = m_of(h, e >> 32);
-    const uint32_t b = lookup_index(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m);
+    const uint32_t b = lookup_index<kFineBits>(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m);
     if (b < law.L2) bin(b);
     else spill_tagged(m);
   };
@@ -1073,7 +1079,7 @@ __device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const ui
       const bool act = k < qk;
       const uint64_t e = act ? ql[32 * k] : 0ull;
       const uint32_t h = (uint32_t)e;
-      const uint32_t gw = act ? sG[h >> (32 - kGuideBits)] : 0u;
+      const uint32_t gw = act ? sG[h >> (32 - kFineBits)] : 0u;
       const bool multi = act && (gw & kGuideMulti);
       if (act && !multi) {
         const uint32_t b = gw & kGuideIndex;
@@ -1156,7 +1162,7 @@ __global__ void __launch_bounds__(kAWarps * 32, kABlocksPerSM) sample_hist_kerne
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
   uint32_t *sG = reinterpret_cast<uint32_t *>(smem + kL1 * 8);
-  uint32_t *sInc = reinterpret_cast<uint32_t *>(smem + kL1 * 8 + kGuide * 4);
+  uint32_t *sInc = reinterpret_cast<uint32_t *>(smem + kL1 * 8 + kFine * 4);
   uint32_t *sH = sInc + kIncBuckets * 32;
   uint64_t *sQ = reinterpret_cast<uint64_t *>(sH + kAWarps * (kHMax / 2));
   int *s_spill = reinterpret_cast<int *>(sQ + kAWarps * kQCap * 32);
@@ -1393,7 +1399,7 @@ cudaError_t launch_tail_queue_raw(const Law *laws, uint64_t *pos, uint32_t *law,
 }
 
 size_t sample_kernel_smem_bytes() {
-  return (size_t)kL1 * 8 + kGuide * 4 + kIncBytes + (size_t)kAWarps * (kHMax / 2) * 4 +
+  return (size_t)kL1 * 8 + kFine * 4 + kIncBytes + (size_t)kAWarps * (kHMax / 2) * 4 +
          (size_t)kAWarps * kQCap * 32 * 8 + kAWarps * 4 + 8 + 16;
 }
 
