@@ -958,7 +958,8 @@ def main():
     else:
         sweep = inputs.batched_instances()
         wname = ("batched uneven: 4,096 instances, n log-uniform [10,1e5], alpha U(1.6,3.2), "
-                 "xmin in {1,2,5}, 2,000 replicates each; one plan, graph-captured launch, autotuned split")
+                 "xmin in {1,2,5}, 2,000 replicates each; one plan, graph-captured launch, autotuned split, "
+                 "work-item size and dense bins")
     QS = list(inputs.TABLE1_QUANTILES) if args.workload == "table1" else Q
     total_R = sum(c.replicates for c in sweep)
     draws = sum(c.replicates * c.n for c in sweep)
@@ -1021,9 +1022,11 @@ def main():
     if args.workload == "batched":
         # untimed set-up: autotuned warp/block split, plan (tables), graph capture
         t0 = time.perf_counter()
-        split = ctx.pl_autotune()
+        tune = ctx.pl_autotune_cells(cells, prec, sample_replicates=500)
         plan = ctx.pl_plan_cutoffs(cells, QS, prec)
-        config["autotuned_split_n"] = split
+        config["autotuned"] = {"split_n": tune["split"], "item_reps": tune["item_reps"],
+                               "hist_shift": tune["hist_shift"],
+                               "sample": "every instance at 500 replicates, median of 3 calls per setting"}
         config["plan_ms"] = (time.perf_counter() - t0) * 1e3
         gstream = torch.cuda.Stream()
         with torch.cuda.stream(gstream):

@@ -226,6 +226,35 @@ pl_status pl_ks_cutoffs_multinomial(pl_ctx *ctx, const pl_cell *cells,
 pl_status pl_autotune(pl_ctx *ctx, void *stream, int64_t *split_out);
 pl_status pl_set_split(pl_ctx *ctx, int64_t split);
 
+/* The tile settings of a context's simulations (not a step of the method;
+ * the paper has no counterpart).
+ * split: warp/block split as above.  item_reps: warp-form replicates per
+ * work item (1..256; 0: sized by each plan, 256 or fewer when a simulation
+ * is too small to give two items per resident sampler block).  hist_shift:
+ * dense bins of a warp-form replicate, the smallest power of two >= 2n
+ * (32..1024) times 2^hist_shift, kept within 32..1024; values beyond the dense
+ * bins are spilled and sorted.  None of them changes sampled values; split
+ * and hist_shift change the rounding of alpha-hat and D (1e-15 in the binary64
+ * form, 1e-7 in the binary32-bulk form), item_reps changes nothing. */
+typedef struct {
+  int64_t split;
+  int32_t item_reps;
+  int32_t hist_shift;
+  double best_ms;   /* pl_autotune_cells: the tuned call's time on the sample (ms) */
+} pl_tuning;
+
+/* Autotuner over the cells a caller will run: times pl_ks_cutoffs on the
+ * same cells with at most sample_replicates replicates each (median of three
+ * timed calls per setting) and picks, one after the other, the split (256,
+ * 1,024, 4,096, 16,384, 65,535), the work-item size (32, 64, 128, 256) and
+ * hist_shift (-1, 0, 1) that run fastest; leaves them set on the context and
+ * writes them to *out (host, may be NULL).  Synchronises `stream`.  On an
+ * error the previous settings stay.  pl_set_tuning sets them directly.
+ * Errors: PL_EINVAL, and those of pl_ks_cutoffs. */
+pl_status pl_autotune_cells(pl_ctx *ctx, const pl_cell *cells, int ncells, pl_precision prec,
+                            int64_t sample_replicates, pl_tuning *out, void *stream);
+pl_status pl_set_tuning(pl_ctx *ctx, const pl_tuning *t);
+
 /* The same computation split in two, so that the simulation can be enqueued
  * repeatedly (for example inside a captured CUDA graph).
  * pl_plan_cutoffs validates the cells (as pl_ks_cutoffs), allocates the

@@ -38,6 +38,8 @@ struct pl_ctx {
   int sample_blocks_per_sm = 0;
   int block_sampler_per_sm = 0;
   int64_t warp_split = 16384;    // n above this: block form
+  int item_reps = 0;             // warp-form replicates per work item (0: sized by the plan)
+  int hist_shift = 0;            // dense bins of a warp-form replicate: the default times 2^hist_shift
   uint64_t launches = 0;
   // Capacity overrides for tests (environment, read at pl_create; 0 = off):
   // they only shrink buffers so that the overflow fallbacks run.
@@ -185,10 +187,13 @@ FitTable make_fit_table(Carver &cv, uint64_t xmin) {
   return f;
 }
 
-uint32_t hist_bins(int64_t n) {
+// Dense bins of a warp-form replicate: the smallest power of two >= 2n
+// (32 .. kHMax), scaled by 2^shift within those bounds.
+uint32_t hist_bins(int64_t n, int shift = 0) {
   int64_t H = 32;
   while (H < 2 * n && H < kHMax) H <<= 1;
-  return (uint32_t)H;
+  H = shift >= 0 ? H << shift : H >> -shift;
+  return (uint32_t)std::min<int64_t>(kHMax, std::max<int64_t>(32, H));
 }
 
 // Spill slot of a replicate record: about twice the expected number of draws
@@ -266,7 +271,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     cd.cell_id = (uint32_t)x.cell_id;
     cd.law = li;
     cd.wide = (all_wide || x.n > std::min(kWarpNMax, ctx->warp_split)) ? 1u : 0u;
-    cd.H = cd.wide ? (uint32_t)kHWide : hist_bins(x.n);
+    cd.H = cd.wide ? (uint32_t)kHWide : hist_bins(x.n, ctx->hist_shift);
     // batched table searches pay off once a replicate has many draws or the
     // tail is heavy (measured crossover on GB300)
     cd.defer = (x.n >= 512 || x.alpha < 1.6) ? 1u : 0u;
@@ -312,6 +317,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
   const int64_t fill = 2 * (int64_t)ctx->num_sms * std::max(1, ctx->sample_blocks_per_sm);
   int64_t warp_item = kItemReps;
   while (warp_item > 32 && warp_R / warp_item < fill) warp_item /= 2;
+  if (ctx->item_reps) warp_item = ctx->item_reps;
   size_t wd = 0, ws = 0, wm = 0, first = 0, nwide = 0;
   double wt = 0.0;  // expected beyond-table draws of the wave
   auto close_tail = [&]() {
@@ -1448,6 +1454,95 @@ pl_status pl_autotune(pl_ctx *ctx, void *stream, int64_t *split_out) {
   PL_CUDA(cudaStreamSynchronize(st));
   if (split_out) *split_out = ctx->warp_split;
   return st_all;
+}
+
+pl_status pl_autotune_cells(pl_ctx *ctx, const pl_cell *cells, int ncells, pl_precision prec,
+                            int64_t sample_replicates, pl_tuning *out, void *stream) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!cells || ncells < 1 || sample_replicates < 1 || (prec != PL_FP64 && prec != PL_FP32_BULK))
+    return fail(ctx, PL_EINVAL, "pl_autotune_cells: bad arguments");
+  // the cell mix with at most sample_replicates replicates per cell
+  std::vector<pl_cell> sub(cells, cells + ncells);
+  for (pl_cell &c : sub) c.replicates = std::min<int64_t>(c.replicates, sample_replicates);
+  const int64_t saved_split = ctx->warp_split;
+  const int saved_item = ctx->item_reps, saved_shift = ctx->hist_shift;
+  const bool saved_tracing = ctx->tracing;
+  if (pl_status s = pl_set_tracing(ctx, 1)) return s;
+  const double q = 0.9;
+  std::vector<double> cut(ncells);
+  // time of one call at the context's current settings (median of three, after one untimed)
+  auto trial = [&](double *ms) -> pl_status {
+    float t[3];
+    for (int rep = 0; rep < 4; ++rep) {
+      if (pl_status s = pl_ks_cutoffs(ctx, sub.data(), ncells, 1, &q, 1, prec, cut.data(), nullptr, nullptr, stream))
+        return s;
+      pl_trace_info ti;
+      if (pl_status s = pl_trace(ctx, stream, &ti)) return s;
+      if (rep) t[rep - 1] = ti.total_ms;
+    }
+    std::sort(t, t + 3);
+    *ms = (double)t[1];
+    return PL_OK;
+  };
+  pl_status st_all = PL_OK;
+  double best = 0.0;
+  st_all = trial(&best);
+  // coordinate descent: warp/block split, then replicates per work item, then dense bins
+  const int64_t splits[] = {256, 1024, 4096, 16384, kWarpNMax};
+  int64_t best_split = ctx->warp_split;
+  for (int64_t sp : splits) {
+    if (st_all) break;
+    ctx->warp_split = sp;
+    double t;
+    st_all = trial(&t);
+    if (!st_all && t < best) best = t, best_split = sp;
+  }
+  ctx->warp_split = best_split;
+  const int items[] = {32, 64, 128, 256};
+  int best_item = ctx->item_reps;
+  for (int it : items) {
+    if (st_all) break;
+    ctx->item_reps = it;
+    double t;
+    st_all = trial(&t);
+    if (!st_all && t < best) best = t, best_item = it;
+  }
+  ctx->item_reps = best_item;
+  int best_shift = ctx->hist_shift;
+  for (int sh = -1; sh <= 1; ++sh) {
+    if (st_all) break;
+    if (sh == best_shift) continue;
+    ctx->hist_shift = sh;
+    double t;
+    st_all = trial(&t);
+    if (!st_all && t < best) best = t, best_shift = sh;
+  }
+  ctx->hist_shift = best_shift;
+  if (st_all) {
+    ctx->warp_split = saved_split;
+    ctx->item_reps = saved_item;
+    ctx->hist_shift = saved_shift;
+  }
+  pl_set_tracing(ctx, saved_tracing ? 1 : 0);
+  PL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (out && !st_all) {
+    out->split = ctx->warp_split;
+    out->item_reps = ctx->item_reps;
+    out->hist_shift = ctx->hist_shift;
+    out->best_ms = best;
+  }
+  return st_all;
+}
+
+pl_status pl_set_tuning(pl_ctx *ctx, const pl_tuning *t) {
+  if (pl_status s = check_ctx(ctx)) return s;
+  if (!t || t->split < 1 || t->split > kWarpNMax || (t->item_reps != 0 && (t->item_reps < 1 || t->item_reps > kItemReps)) ||
+      t->hist_shift < -5 || t->hist_shift > 5)
+    return fail(ctx, PL_EINVAL, "pl_set_tuning: setting out of range");
+  ctx->warp_split = t->split;
+  ctx->item_reps = t->item_reps;
+  ctx->hist_shift = t->hist_shift;
+  return PL_OK;
 }
 
 pl_status pl_plan_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells, const double *q, int nq,

@@ -29,7 +29,7 @@ _NAMES = {1: "PL_EINVAL", 2: "PL_ENOMEM", 3: "PL_ENOCONV", 4: "PL_ETIMEOUT", 5: 
 EXPORTS = ["pl_create", "pl_destroy", "pl_last_error", "pl_sync", "pl_counters", "pl_probe_rates", "pl_set_tracing",
            "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue", "pl_fit_ks_noalloc", "pl_plan_cutoffs", "pl_plan_run",
-           "pl_plan_destroy", "pl_autotune", "pl_set_split", "pl_server_create", "pl_server_submit",
+           "pl_plan_destroy", "pl_autotune", "pl_set_split", "pl_autotune_cells", "pl_set_tuning", "pl_server_create", "pl_server_submit",
            "pl_server_poll", "pl_server_now", "pl_server_load", "pl_server_destroy",
            "pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_fit_ks_truncated", "pl_bespoke_cutoffs",
            "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin",
@@ -55,6 +55,11 @@ class pl_counter_info(ctypes.Structure):
     _fields_ = [("newton_capped", ctypes.c_uint64), ("tail_draws", ctypes.c_uint64),
                 ("global_sorts", ctypes.c_uint64), ("fit_fallbacks", ctypes.c_uint64),
                 ("resampled", ctypes.c_uint64)]
+
+
+class pl_tuning(ctypes.Structure):
+    _fields_ = [("split", ctypes.c_int64), ("item_reps", ctypes.c_int32), ("hist_shift", ctypes.c_int32),
+                ("best_ms", ctypes.c_double)]
 
 
 class pl_probe_info(ctypes.Structure):
@@ -107,6 +112,9 @@ _lib.pl_plan_cutoffs.argtypes = [_vp, ctypes.POINTER(pl_cell), ctypes.c_int, _f6
 _lib.pl_plan_run.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _vp, _vp]
 _lib.pl_autotune.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]
 _lib.pl_set_split.argtypes = [_vp, ctypes.c_int64]
+_lib.pl_autotune_cells.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                   ctypes.POINTER(pl_tuning), _vp]
+_lib.pl_set_tuning.argtypes = [_vp, ctypes.POINTER(pl_tuning)]
 _lib.pl_plan_destroy.argtypes = [_vp]
 _lib.pl_plan_destroy.restype = None
 _lib.pl_fit_ks_noalloc.argtypes = [_vp, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
@@ -145,7 +153,7 @@ _lib.pl_bespoke_cutoffs_batch.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctyp
                                           ctypes.c_int, ctypes.c_int, _f64p, _f64p, _f64p, _f64p, _vp]
 _lib.pl_server_destroy.restype = None
 for _f in ["pl_sample_truncated", "pl_ks_cutoffs_truncated", "pl_fit_ks_truncated", "pl_bespoke_cutoffs",
-           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin", "pl_ks_cutoffs_multinomial", "pl_bespoke_cutoffs_batch", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_probe_rates", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
+           "pl_bespoke_cutoffs_truncated", "pl_cutoff_lookup", "pl_estimate_xmin", "pl_ks_cutoffs_multinomial", "pl_bespoke_cutoffs_batch", "pl_server_create", "pl_server_submit", "pl_server_load", "pl_autotune", "pl_set_split", "pl_autotune_cells", "pl_set_tuning", "pl_plan_cutoffs", "pl_plan_run", "pl_fit_ks_noalloc", "pl_sync", "pl_counters", "pl_probe_rates", "pl_set_tracing", "pl_trace", "pl_sample", "pl_fit_mle", "pl_ks_stat", "pl_ks_cutoffs",
            "pl_bootstrap_pvalue"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -425,6 +433,19 @@ class Context:
 
     def pl_set_split(self, split: int):
         self._check(_lib.pl_set_split(self._h, split))
+
+    def pl_autotune_cells(self, cells, prec: int = PL_FP32_BULK, sample_replicates: int = 500,
+                          stream=None) -> dict:
+        arr = (pl_cell * len(cells))(*[pl_cell(c.alpha, c.xmin, c.n, c.replicates, c.cell_id)
+                                       for c in cells])
+        t = pl_tuning()
+        self._check(_lib.pl_autotune_cells(self._h, arr, len(cells), prec, sample_replicates, ctypes.byref(t),
+                                           _stream_ptr(stream)))
+        return {k: getattr(t, k) for k, _ in pl_tuning._fields_}
+
+    def pl_set_tuning(self, split: int, item_reps: int = 0, hist_shift: int = 0):
+        t = pl_tuning(split, item_reps, hist_shift, 0.0)
+        self._check(_lib.pl_set_tuning(self._h, ctypes.byref(t)))
 
     def pl_plan_cutoffs(self, cells, q, prec: int = PL_FP64, stream=None) -> "Plan":
         arr = (pl_cell * len(cells))(*[pl_cell(c.alpha, c.xmin, c.n, c.replicates, c.cell_id)

@@ -356,6 +356,37 @@ def test_split_and_autotune_keep_parity(pl):
     c.close()
 
 
+def test_tile_settings_and_cell_autotuner_keep_parity(pl):
+    # work-item size, dense-bin count and split are tile settings: every
+    # setting (and the one the cell autotuner picks) gives the oracle's values
+    # within the binary64 parity bars
+    c = pl.Context(0)
+    cells = [pl.Cell(1.6, 1, 700, 300, 41), pl.Cell(2.5, 2, 60, 500, 42), pl.Cell(3.0, 1, 5000, 70, 43)]
+    R = sum(x.replicates for x in cells)
+    ref = [oracle.cell(x.alpha, x.xmin, x.n, x.replicates, seed=5, cell_id=x.cell_id) for x in cells]
+    D_or = np.concatenate([r[0] for r in ref])
+    A_or = np.concatenate([r[1] for r in ref])
+
+    def check():
+        D = torch.empty(R, dtype=torch.float64, device="cuda")
+        A = torch.empty(R, dtype=torch.float64, device="cuda")
+        c.pl_ks_cutoffs(cells, 5, [0.9], 0, D=D, alpha_hat=A)
+        c.pl_sync()
+        assert np.max(np.abs(D.cpu().numpy() - D_or)) < 1e-12
+        assert np.max(np.abs(A.cpu().numpy() / A_or - 1)) < 1e-10
+
+    for split, item, shift in [(65535, 32, 0), (1024, 256, -1), (65535, 7, 1), (256, 64, 0), (16384, 0, 0)]:
+        c.pl_set_tuning(split, item, shift)
+        check()
+    t = c.pl_autotune_cells(cells, 0, sample_replicates=64)
+    assert 1 <= t["split"] <= 65535 and t["item_reps"] in (0, 32, 64, 128, 256) and t["hist_shift"] in (-1, 0, 1)
+    assert t["best_ms"] > 0
+    check()
+    with pytest.raises(pl.PLError):
+        c.pl_set_tuning(0)
+    c.close()
+
+
 @pytest.mark.parametrize("bad", [
     dict(alpha=1.0), dict(alpha=0.5), dict(xmin=0), dict(n=0), dict(replicates=0),
     dict(cell_id=2**32), dict(q=[1.0]), dict(q=[0.0]),
