@@ -1011,22 +1011,25 @@ __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint
 constexpr int kQCap = PL_SAMPLER_QCAP;
 constexpr int kFlushBlocks = 31;
 
-__device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const uint32_t *sG, const uint32_t *sInc,
-                                                    const Law &law, const Cell &cell, uint32_t rep,
-                                                    const RoundKeys &rk, uint32_t *hist, int *s_count,
-                                                    uint64_t *spill, int64_t spill_capacity, int lane,
-                                                    const TailQueue *tq, uint64_t spill_pos0, uint64_t *queue) {
+// The draws of one replicate that the calling warp takes: Philox blocks p0,
+// p0 + stride, ... below n/4 (p0 the lane's first block, stride a multiple of
+// 32), then one ragged round.  WIDE: one 32-bit bin per word of hist (block
+// form); else two 16-bit bins per word.  The lane's counts of the first four
+// values are left in c[0..3] (not reduced across lanes).
+template <bool WIDE>
+__device__ __forceinline__ void draw_queued(const uint64_t *sT, const uint32_t *sG, const uint32_t *sInc,
+                                            const Law &law, const Cell &cell, uint32_t rep, const RoundKeys &rk,
+                                            uint32_t *hist, int *s_count, uint64_t *spill, int64_t spill_capacity,
+                                            int lane, const TailQueue *tq, uint64_t spill_pos0, uint64_t *queue,
+                                            int64_t p0, int64_t stride, uint32_t c[4]) {
   const int64_t n = cell.n;
   const uint64_t xmin = cell.xmin;
   const uint32_t H = cell.H;
-  const int words = (int)(H / 2);
-  for (int i = lane; i < words; i += 32) hist[i] = 0;
-  if (lane == 0) *s_count = 0;
-  __syncwarp();
-  // a table index b < L2: two 16-bit bins per shared word below H, else a spill
+  // a table index b < L2: a shared atomic below H, else a spill
   auto bin = [&](uint32_t b) {
     if (b < H) {
-      atomicAdd(&hist[b >> 1], 1u << ((b & 1u) << 4));
+      if (WIDE) atomicAdd(&hist[b], 1u);
+      else atomicAdd(&hist[b >> 1], 1u << ((b & 1u) << 4));
     } else {
       const int slot = atomicAdd(s_count, 1);
       if (slot < spill_capacity) spill[slot] = xmin + b;
@@ -1114,13 +1117,12 @@ __device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const ui
     }
   };
   // full rounds (every lane has four valid draws: blocks below a multiple of
-  // 32 that is at most n/4), then one ragged round for the at most 32 blocks
-  // left; the trip counts are the same for every lane
-  const int64_t full = (n >> 2) & ~(int64_t)31;
-  int64_t p = lane;
+  // stride that is at most n/4), then one ragged round for the blocks left;
+  // the trip counts are the same for every lane of the warp
+  const int64_t full = (n >> 2) / stride * stride;
+  int64_t p = p0;
   while (p < full) {
-    const int64_t pend = min(full + lane, p + 32 * (int64_t)kFlushBlocks);
-    for (; p < pend; p += 32) {
+    for (int k = 0; k < kFlushBlocks && p < full; ++k, p += stride) {
       const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
       const uint64_t i0 = 4 * (uint64_t)p;
       step(w.x, i0);
@@ -1131,7 +1133,7 @@ __device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const ui
     }
     flush();
   }
-  if (4 * full < n) {
+  if (4 * (p - lane) < n) {  // warp-uniform
     const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
     const int64_t i0 = 4 * p;
     if (i0 < n) step(w.x, (uint64_t)i0);
@@ -1141,9 +1143,27 @@ __device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const ui
     flush();
   }
   drain();
+  c[0] = c0;
+  c[1] = c1;
+  c[2] = c2;
+  c[3] = c3;
+}
+
+__device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const uint32_t *sG, const uint32_t *sInc,
+                                                    const Law &law, const Cell &cell, uint32_t rep,
+                                                    const RoundKeys &rk, uint32_t *hist, int *s_count,
+                                                    uint64_t *spill, int64_t spill_capacity, int lane,
+                                                    const TailQueue *tq, uint64_t spill_pos0, uint64_t *queue) {
+  const int words = (int)(cell.H / 2);
+  for (int i = lane; i < words; i += 32) hist[i] = 0;
+  if (lane == 0) *s_count = 0;
   __syncwarp();
-  const unsigned s0 = __reduce_add_sync(0xffffffffu, c0), s1 = __reduce_add_sync(0xffffffffu, c1);
-  const unsigned s2 = __reduce_add_sync(0xffffffffu, c2), s3 = __reduce_add_sync(0xffffffffu, c3);
+  uint32_t c[4];
+  draw_queued<false>(sT, sG, sInc, law, cell, rep, rk, hist, s_count, spill, spill_capacity, lane, tq, spill_pos0,
+                     queue, lane, 32, c);
+  __syncwarp();
+  const unsigned s0 = __reduce_add_sync(0xffffffffu, c[0]), s1 = __reduce_add_sync(0xffffffffu, c[1]);
+  const unsigned s2 = __reduce_add_sync(0xffffffffu, c[2]), s3 = __reduce_add_sync(0xffffffffu, c[3]);
   if (lane == 0) {
     hist[0] += s0 | (s1 << 16);
     hist[1] += s2 | (s3 << 16);
@@ -1208,23 +1228,25 @@ __global__ void __launch_bounds__(kAWarps * 32, kABlocksPerSM) sample_hist_kerne
 }
 
 // Block form (large n): a block per replicate, kHWide 32-bit bins in shared
-// memory, per-thread register counters for bins 0..3 (at most n/1024 + 2
-// draws per thread and bin; the host keeps n <= 2^25).
-constexpr int kBlkThreads = 512;
+// memory, the draws through the same increment table, per-lane queues and
+// drains as the warp form (each warp a stride of the replicate's Philox blocks).
+constexpr int kBlkThreads = 1024;
+constexpr int kBlkWarps = kBlkThreads / 32;
 
-__global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaunch a) {
+__global__ void __launch_bounds__(kBlkThreads, 1) sample_block_kernel(SampleLaunch a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
   uint32_t *sG = reinterpret_cast<uint32_t *>(smem + kL1 * 8);
-  uint32_t *hist = reinterpret_cast<uint32_t *>(smem + kL1 * 8 + kGuide * 4);
-  int *s_spill = reinterpret_cast<int *>(hist + kHWide);
+  uint32_t *sInc = reinterpret_cast<uint32_t *>(smem + kL1 * 8 + kFine * 4);
+  uint32_t *hist = sInc + kIncBuckets * 32;
+  uint64_t *sQ = reinterpret_cast<uint64_t *>(hist + kHWide);
+  int *s_spill = reinterpret_cast<int *>(sQ + kBlkWarps * kQCap * 32);
   uint32_t *s_item = reinterpret_cast<uint32_t *>(s_spill + 1);
   int *s_tmax = reinterpret_cast<int *>(s_item + 1);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(s_tmax + 2);
-  StagedLaw staged{sT, sG, mbar};
+  StagedLaw staged{sT, sG, mbar, sInc};
   const int lane = threadIdx.x & 31;
-  uint64_t *defer_q = mbar + 2 + (threadIdx.x >> 5) * kDeferCap;
-  const unsigned lt = (1u << lane) - 1u;
+  uint64_t *queue = sQ + (threadIdx.x >> 5) * kQCap * 32;
   const TailQueue tq{a.tq_pos, a.tq_law, a.tq_count, a.tq_cap};
   if (threadIdx.x == 0) {
     mbar_init(mbar, 1);
@@ -1246,9 +1268,7 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
       loaded = cell.law;
     }
     const uint32_t H = cell.H;
-    const int64_t n = cell.n;
     for (uint32_t j = 0; j < wi.nrep; ++j) {
-      const uint32_t rep = wi.r0 + j;
       for (uint32_t i = threadIdx.x; i < H; i += kBlkThreads) hist[i] = 0;
       if (threadIdx.x == 0) {
         *s_spill = 0;
@@ -1256,90 +1276,13 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
       }
       __syncthreads();
       const uint64_t pos0 = wi.spill_off + (uint64_t)j * cell.scap;
-      uint64_t *spill = a.rec.spill + pos0;
-      uint64_t packed = 0;
-      // b: the draw's table index; m: its m, needed (and given) only beyond the table
-      auto bin = [&](uint32_t b, uint64_t m) {
-        if (b < 4) {
-          packed += 1ull << (16 * b);
-        } else if (b < H) {
-          atomicAdd(&hist[b], 1u);
-        } else {
-          const int slot = atomicAdd(s_spill, 1);
-          if (slot < (int64_t)cell.scap) {
-            if (b < law.L2) {
-              spill[slot] = cell.xmin + b;
-            } else {
-              spill[slot] = kTailTag | m;
-              const unsigned q = atomicAdd(tq.count, 1u);
-              if (q < tq.cap) {
-                tq.pos[q] = pos0 + (uint64_t)slot;
-                tq.law[q] = cell.law;
-              }
-            }
-          }
-        }
-      };
-      auto m_of = [&](uint32_t h, uint64_t i) {
-        return draw_m_full(h, i, rep, cell.cell_id, cell.purpose, a.rk.k[0], a.rk.k[1]);
-      };
-      auto search = [&](uint32_t h, uint64_t i) {
-        uint64_t m = 0;
-        const uint32_t b = lookup_index_hi(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, h,
-                                           [&] { return m_of(h, i); }, &m);
-        bin(b, m);
-      };
-      // direct answers from the guide; multi-valued buckets searched 32 at a
-      // time through the warp's queue (as in the warp form)
-      int qn = 0;
-      auto draw = [&](uint32_t h, uint64_t i, bool valid) {
-        const uint32_t gw = sG[h >> (32 - kGuideBits)];
-        const bool direct = valid && !(gw & kGuideMulti);
-        packed += (direct && gw < 4) ? 1ull << (16 * (gw & 3u)) : 0ull;
-        if (direct && gw >= 4) bin(gw, gw >= law.L2 ? m_of(h, i) : 0ull);
-        const bool later = valid && (gw & kGuideMulti);
-        if (__any_sync(0xffffffffu, later)) {
-          const unsigned dm = __ballot_sync(0xffffffffu, later);
-          if (later) defer_q[qn + __popc(dm & lt)] = (i << 32) | h;
-          qn += __popc(dm);
-          if (qn >= 32) {
-            __syncwarp();
-            qn -= 32;
-            const uint64_t q = defer_q[qn + lane];
-            __syncwarp();
-            search((uint32_t)q, q >> 32);
-          }
-        }
-      };
-      // full rounds of the block (every thread has four valid draws), then
-      // ragged rounds for the fewer than 4 (kBlkThreads + 1) draws left
-      const int64_t full = (n >> 2) / kBlkThreads * kBlkThreads;
-      int64_t p = threadIdx.x;
-      for (; p < full; p += kBlkThreads) {
-        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), a.rk);
-        const uint64_t i0 = 4 * (uint64_t)p;
-        draw(w.x, i0, true);
-        draw(w.y, i0 + 1, true);
-        draw(w.z, i0 + 2, true);
-        draw(w.w, i0 + 3, true);
-      }
-      for (; 4 * (p - lane) < n; p += kBlkThreads) {  // warp-uniform bound
-        const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), a.rk);
-        const int64_t i0 = 4 * p;
-        draw(w.x, (uint64_t)i0, i0 < n);
-        draw(w.y, (uint64_t)i0 + 1, i0 + 1 < n);
-        draw(w.z, (uint64_t)i0 + 2, i0 + 2 < n);
-        draw(w.w, (uint64_t)i0 + 3, i0 + 3 < n);
-      }
-      __syncwarp();
-      if (lane < qn) {
-        const uint64_t q = defer_q[lane];
-        search((uint32_t)q, q >> 32);
-      }
+      uint32_t c[4];
+      draw_queued<true>(sT, sG, sInc, law, cell, wi.r0 + j, a.rk, hist, s_spill, a.rec.spill + pos0, cell.scap,
+                        lane, &tq, pos0, queue, threadIdx.x, kBlkThreads, c);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)((packed >> (16 * q)) & 0xffffu));
-        if (lane == 0 && c) atomicAdd(&hist[q], c);
+        const unsigned t = __reduce_add_sync(0xffffffffu, c[q]);
+        if (lane == 0 && t) atomicAdd(&hist[q], t);
       }
       __syncthreads();
       int tm = -1;
@@ -1358,7 +1301,8 @@ __global__ void __launch_bounds__(kBlkThreads, 3) sample_block_kernel(SampleLaun
 }
 
 size_t block_sampler_smem_bytes() {
-  return (size_t)kL1 * 8 + kGuide * 4 + (size_t)kHWide * 4 + 32 + 16 + (size_t)(kBlkThreads / 32) * kDeferCap * 8;
+  return (size_t)kL1 * 8 + kFine * 4 + kIncBytes + (size_t)kHWide * 4 + (size_t)kBlkWarps * kQCap * 32 * 8 + 16 +
+         16;
 }
 
 int block_sampler_blocks_per_sm() {
