@@ -839,12 +839,6 @@ constexpr int kAWarps = PL_SAMPLER_WARPS;
 constexpr int kARepsPerWarp = kItemReps / kAWarps;
 constexpr int kABlocksPerSM = kAWarps >= 32 ? 1 : 2;
 
-// Draws of one replicate into a histogram.  PACKED: two 16-bit bins per word
-// (hist holds H/2 words); otherwise one 32-bit bin per word.  Spills beyond the
-// capacity are counted but not stored.  Draws beyond the threshold table are
-// stored tagged (kTailTag | m) and, when a queue is given, their positions are
-// queued for the tail kernel.  Returns tmax (the largest bin index below H
-// that was hit, -1 if none) and leaves the spill count in *s_count.
 struct TailQueue {
   uint64_t *pos;          // element index in the record spill buffer
   uint32_t *law;          // law of the draw
@@ -852,19 +846,18 @@ struct TailQueue {
   uint32_t cap;
 };
 
-// Per-warp queue of draws whose guide bucket holds more than one value: they
-// are searched 32 at a time, so the warp's lanes search together instead of
-// one divergent lane holding up the others (histogram counts and the later
-// sorted spills do not depend on the order draws are binned in).
-constexpr int kDeferCap = 64;
-
-template <bool PACKED, bool DEFER>
+// Draws of one replicate into a histogram, one draw at a time (the
+// finisher's redraw of a replicate whose record spill slot overflowed).
+// PACKED: two 16-bit bins per word (hist holds H/2 words); otherwise one
+// 32-bit bin per word.  Spills beyond the capacity are counted but not stored;
+// draws beyond the threshold table are stored tagged (kTailTag | m).  Returns
+// tmax (the largest bin index below H that was hit, -1 if none) and leaves
+// the spill count in *s_count.  The same values as the samplers' draws.
+template <bool PACKED>
 __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint32_t *sG, const Law &law,
                                                   const Cell &cell, uint32_t rep, const RoundKeys &rk,
                                                   uint32_t *hist, int *s_count, uint64_t *spill,
-                                                  int64_t spill_capacity, int lane,
-                                                  const TailQueue *tq, uint64_t spill_pos0,
-                                                  uint64_t *defer_q) {
+                                                  int64_t spill_capacity, int lane) {
   const int64_t n = cell.n;
   const uint64_t xmin = cell.xmin;
   const uint32_t H = cell.H;
@@ -872,114 +865,37 @@ __device__ __forceinline__ int64_t draw_replicate(const uint64_t *sT, const uint
   for (int i = lane; i < words; i += 32) hist[i] = 0;
   if (lane == 0) *s_count = 0;
   __syncwarp();
-  uint64_t packed = 0;  // 16-bit counters of bins 0..3
   // b: the draw's table index; m: its m, needed (and given) only beyond the table
   auto bin = [&](uint32_t b, uint64_t m) {
-    if (b < 4) {
-      packed += 1ull << (16 * b);
-    } else if (b < H) {
+    if (b < H) {
       if (PACKED) atomicAdd(&hist[b >> 1], 1u << ((b & 1u) << 4));
       else atomicAdd(&hist[b], 1u);
     } else {
       const int slot = atomicAdd(s_count, 1);
-      if (slot < spill_capacity) {
-        if (b < law.L2) {
-          spill[slot] = xmin + b;
-        } else {
-          spill[slot] = kTailTag | m;
-          if (tq) {
-            const unsigned q = atomicAdd(tq->count, 1u);
-            if (q < tq->cap) {
-              tq->pos[q] = spill_pos0 + (uint64_t)slot;
-              tq->law[q] = cell.law;
-            }
-          }
-        }
-      }
+      if (slot < spill_capacity) spill[slot] = b < law.L2 ? xmin + b : (kTailTag | m);
     }
   };
-  // m of draw i from its high word h (a block of the low stream)
   auto m_of = [&](uint32_t h, uint64_t i) {
     return draw_m_full(h, i, rep, cell.cell_id, cell.purpose, rk.k[0], rk.k[1]);
   };
-  // a draw of a multi-valued guide bucket: table search on its high word
-  auto search = [&](uint32_t h, uint64_t i) {
-    uint64_t m = 0;
-    const uint32_t b = lookup_index_hi(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, h,
-                                       [&] { return m_of(h, i); }, &m);
-    bin(b, m);
-  };
-  int qn = 0;  // warp-uniform queue length (< 32 between draws)
-  const unsigned lt = (1u << lane) - 1u;
-  // One draw (high word h, index i): the guide word answers directly unless
-  // its bucket holds several values; bins 0..3 go to the lane's registers
-  // without a branch.  Queued draws keep (i, h).
-  auto draw = [&](uint32_t h, uint64_t i, bool valid) {
+  auto draw = [&](uint32_t h, uint64_t i) {
     const uint32_t gw = sG[h >> (32 - kGuideBits)];
-    if (DEFER) {
-      const bool direct = valid && !(gw & kGuideMulti);
-      packed += (direct && gw < 4) ? 1ull << (16 * (gw & 3u)) : 0ull;
-      if (direct && gw >= 4) bin(gw, gw >= law.L2 ? m_of(h, i) : 0ull);
-      const bool later = valid && (gw & kGuideMulti);
-      if (__any_sync(0xffffffffu, later)) {
-        const unsigned dm = __ballot_sync(0xffffffffu, later);
-        if (later) defer_q[qn + __popc(dm & lt)] = (i << 32) | h;
-        qn += __popc(dm);
-        if (qn >= 32) {
-          __syncwarp();
-          qn -= 32;
-          const uint64_t q = defer_q[qn + lane];
-          __syncwarp();
-          search((uint32_t)q, q >> 32);
-        }
-      }
-    } else if (valid) {
-      if (gw & kGuideMulti)
-        search(h, i);
-      else
-        bin(gw, gw >= law.L2 ? m_of(h, i) : 0ull);
+    if (gw & kGuideMulti) {
+      uint64_t m = 0;
+      const uint32_t b = lookup_index_hi(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, h,
+                                         [&] { return m_of(h, i); }, &m);
+      bin(b, m);
+    } else {
+      bin(gw, gw >= law.L2 ? m_of(h, i) : 0ull);
     }
   };
-  // full rounds (every lane has four valid draws: blocks below a multiple of
-  // 32 that is at most n/4), then one ragged round for the at most 32 blocks
-  // left
-  const int64_t full = (n >> 2) & ~(int64_t)31;
-  int64_t p = lane;
-  for (; p < full; p += 32) {
-    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
-    const uint64_t i0 = 4 * (uint64_t)p;
-    draw(w.x, i0, true);
-    draw(w.y, i0 + 1, true);
-    draw(w.z, i0 + 2, true);
-    draw(w.w, i0 + 3, true);
-  }
-  if (4 * full < n) {
+  for (int64_t p = lane; 4 * p < n; p += 32) {
     const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
     const int64_t i0 = 4 * p;
-    draw(w.x, (uint64_t)i0, i0 < n);
-    draw(w.y, (uint64_t)i0 + 1, i0 + 1 < n);
-    draw(w.z, (uint64_t)i0 + 2, i0 + 2 < n);
-    draw(w.w, (uint64_t)i0 + 3, i0 + 3 < n);
-  }
-  if (DEFER) {
-    __syncwarp();
-    if (lane < qn) {
-      const uint64_t q = defer_q[lane];
-      search((uint32_t)q, q >> 32);
-    }
-  }
-  __syncwarp();
-  unsigned c[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) c[q] = __reduce_add_sync(0xffffffffu, (unsigned)((packed >> (16 * q)) & 0xffffu));
-  if (lane == 0) {
-    if (PACKED) {
-      hist[0] += c[0] | (c[1] << 16);
-      hist[1] += c[2] | (c[3] << 16);
-    } else {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) hist[q] += c[q];
-    }
+    if (i0 < n) draw(w.x, (uint64_t)i0);
+    if (i0 + 1 < n) draw(w.y, (uint64_t)i0 + 1);
+    if (i0 + 2 < n) draw(w.z, (uint64_t)i0 + 2);
+    if (i0 + 3 < n) draw(w.w, (uint64_t)i0 + 3);
   }
   __syncwarp();
   // largest bin hit: highest nonzero word, then its upper half
@@ -1547,11 +1463,11 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
           // block form's histogram is rebuilt in place in the record
           if (lane == 0) atomicAdd(&a.ctr->resampled, 1ull);
           if (cell.wide) {
-            tmax = draw_replicate<false, false>(sT, sG, law, cell, wi.r0 + j, a.rk, dense32, &s_spill[warp], spill,
-                                                (int64_t)a.spill_cap, lane, nullptr, 0, nullptr);
+            tmax = draw_replicate<false>(sT, sG, law, cell, wi.r0 + j, a.rk, dense32, &s_spill[warp], spill,
+                                         (int64_t)a.spill_cap, lane);
           } else {
-            tmax = draw_replicate<false, false>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp], spill,
-                                                (int64_t)a.spill_cap, lane, nullptr, 0, nullptr);
+            tmax = draw_replicate<false>(sT, sG, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp], spill,
+                                         (int64_t)a.spill_cap, lane);
             for (int64_t i = lane; i <= tmax; i += 32) dense[i] = (uint16_t)hist[i];
           }
           __syncwarp();
