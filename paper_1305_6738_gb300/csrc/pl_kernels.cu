@@ -983,8 +983,11 @@ __device__ __forceinline__ void draw_queued(const uint64_t *sT, const uint32_t *
     if (b < law.L2) bin(b);
     else spill_tagged(m);
   };
-  uint64_t *ql = queue + lane;  // this lane's entry k at ql[32 k]
-  uint32_t qk = 0;
+  // queue entries: (h, i) as two 32-bit words, lane's entry k at queue[32 k + lane]
+  uint2 *queue2 = reinterpret_cast<uint2 *>(queue);
+  const uint32_t q0 = (uint32_t)__cvta_generic_to_shared(queue2 + lane);  // the lane's first entry
+  uint32_t qa = q0;  // shared address of the lane's next free entry (rows of 256 bytes)
+  const uint32_t q_full = q0 + 256u * (uint32_t)(kQCap - 4);  // beyond this a block's four draws may not fit
   const unsigned lt = (1u << lane) - 1u;
   // Each lane bins its own entries of single-valued buckets; entries of
   // multi-valued buckets are compacted to the front of the queue (row k is
@@ -992,28 +995,31 @@ __device__ __forceinline__ void draw_queued(const uint64_t *sT, const uint32_t *
   // compacted by then, so writes only reach rows already read) and searched
   // 32 at a time with every lane busy.
   auto drain = [&]() {
+    const uint32_t qk = (qa - q0) >> 8;
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, qk);
     uint32_t ns = 0;
     for (uint32_t k = 0; k < kmax; ++k) {
       const bool act = k < qk;
-      const uint64_t e = act ? ql[32 * k] : 0ull;
-      const uint32_t h = (uint32_t)e;
-      const uint32_t gw = act ? sG[h >> (32 - kFineBits)] : 0u;
+      const uint2 e = act ? queue2[32 * k + lane] : make_uint2(0u, 0u);
+      const uint32_t gw = act ? sG[e.x >> (32 - kFineBits)] : 0u;
       const bool multi = act && (gw & kGuideMulti);
       if (act && !multi) {
         const uint32_t b = gw & kGuideIndex;
         if (b < law.L2) bin(b);
-        else spill_tagged(m_of(h, e >> 32));
+        else spill_tagged(m_of(e.x, e.y));
       }
       const unsigned bm = __ballot_sync(0xffffffffu, multi);
-      if (multi) queue[ns + __popc(bm & lt)] = e;
+      if (multi) queue2[ns + __popc(bm & lt)] = e;
       ns += __popc(bm);
     }
     __syncwarp();
     for (uint32_t t0 = 0; t0 < ns; t0 += 32)
-      if (t0 + lane < ns) search(queue[t0 + lane]);
+      if (t0 + lane < ns) {
+        const uint2 e = queue2[t0 + lane];
+        search(((uint64_t)e.y << 32) | e.x);
+      }
     __syncwarp();
-    qk = 0;
+    qa = q0;
   };
   uint32_t acc = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0;
   auto flush = [&]() {
@@ -1023,39 +1029,43 @@ __device__ __forceinline__ void draw_queued(const uint64_t *sT, const uint32_t *
     c3 += (acc >> 24) & 0x7fu;
     acc = 0;
   };
-  const uint32_t *incl = sInc + lane;
-  auto step = [&](uint32_t h, uint64_t i) {
-    const uint32_t e = incl[(h >> (32 - kIncBits)) * 32];
+  // the lane's copy of the increment table: entry of bucket j at inc_lane + 128 j
+  const uint32_t inc_lane = (uint32_t)__cvta_generic_to_shared(sInc + lane);
+  auto step = [&](uint32_t h, uint32_t i) {
+    uint32_t e;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(e) : "r"(inc_lane + ((h >> (32 - kIncBits)) << 7)));
     acc += e;
     if ((int32_t)e < 0) {
-      ql[32 * qk] = (i << 32) | h;
-      ++qk;
+      asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(qa), "r"(h), "r"(i) : "memory");
+      qa += 256u;
     }
   };
   // full rounds (every lane has four valid draws: blocks below a multiple of
   // stride that is at most n/4), then one ragged round for the blocks left;
-  // the trip counts are the same for every lane of the warp
-  const int64_t full = (n >> 2) / stride * stride;
-  int64_t p = p0;
+  // the trip counts are the same for every lane of the warp (n < 2^30)
+  const uint32_t nn = (uint32_t)n, st = (uint32_t)stride;
+  const uint32_t full = (nn >> 2) / st * st;
+  uint32_t p = (uint32_t)p0;
   while (p < full) {
-    for (int k = 0; k < kFlushBlocks && p < full; ++k, p += stride) {
-      const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
-      const uint64_t i0 = 4 * (uint64_t)p;
+    const uint32_t pend = min(full, p - (uint32_t)lane + st * (uint32_t)kFlushBlocks);
+    for (; p < pend; p += st) {
+      const uint4 w = philox4x32_10_rk(make_uint4(p, rep, cell.cell_id, cell.purpose), rk);
+      const uint32_t i0 = 4u * p;
       step(w.x, i0);
-      step(w.y, i0 + 1);
-      step(w.z, i0 + 2);
-      step(w.w, i0 + 3);
-      if (__any_sync(0xffffffffu, qk > (uint32_t)kQCap - 4u)) drain();
+      step(w.y, i0 + 1u);
+      step(w.z, i0 + 2u);
+      step(w.w, i0 + 3u);
+      if (__any_sync(0xffffffffu, qa > q_full)) drain();
     }
     flush();
   }
-  if (4 * (p - lane) < n) {  // warp-uniform
-    const uint4 w = philox4x32_10_rk(make_uint4((uint32_t)p, rep, cell.cell_id, cell.purpose), rk);
-    const int64_t i0 = 4 * p;
-    if (i0 < n) step(w.x, (uint64_t)i0);
-    if (i0 + 1 < n) step(w.y, (uint64_t)i0 + 1);
-    if (i0 + 2 < n) step(w.z, (uint64_t)i0 + 2);
-    if (i0 + 3 < n) step(w.w, (uint64_t)i0 + 3);
+  if (4u * (p - (uint32_t)lane) < nn) {  // warp-uniform
+    const uint4 w = philox4x32_10_rk(make_uint4(p, rep, cell.cell_id, cell.purpose), rk);
+    const uint32_t i0 = 4u * p;
+    if (i0 < nn) step(w.x, i0);
+    if (i0 + 1u < nn) step(w.y, i0 + 1u);
+    if (i0 + 2u < nn) step(w.z, i0 + 2u);
+    if (i0 + 3u < nn) step(w.w, i0 + 3u);
     flush();
   }
   drain();
