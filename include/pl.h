@@ -198,18 +198,27 @@ pl_status pl_ks_cutoffs(pl_ctx *ctx, const pl_cell *cells, int ncells,
                         double *alpha_hat_dev_opt, void *stream);
 
 /* Cutoff table with the multinomial histogram sampler (a large-n variant;
- * not in the paper): each replicate's histogram is drawn bin by bin by
- * conditional binomials on the inverse-CDF sampler's law (its integer
- * thresholds T: bin xmin + i gets Bin(n_rem, (T[i-1] - T[i]) / (T[i-1] - 1))
- * of the n_rem values not yet placed, for i < 2048 while the expected count
- * is at least one) and the values left one by one conditional on lying
- * beyond, so the work grows with the occupied bins rather than with n
- * (~780 binomials and ~780 single draws at alpha = 2, n = 10^6).  Same law
- * as pl_ks_cutoffs, a different random stream (purpose 3: draw index j of
- * the replicate's stream is the j-th binomial or single value), so results
- * agree with pl_ks_cutoffs in distribution, not value by value.  Arguments,
- * outputs and errors as pl_ks_cutoffs (every cell runs in the block form,
- * n <= 2^21). */
+ * not in the paper): each replicate's histogram is drawn by conditional
+ * binomials on the inverse-CDF sampler's law, through its integer thresholds
+ * T (with T[-1] = 2^53 + 1, the index range [l, r) has mass
+ * (T[l-1] - T[r-1]) 2^-53).  With B = 2048: the count beyond the first B
+ * values is Bin(n, (T[B-1] - 1) 2^-53); the rest sits at node 1 of a binary
+ * tree over [0, B), and node k of range [l, r) passes
+ * Bin(c_k, (T[l-1] - T[mid-1]) / (T[l-1] - T[r-1])) of its count c_k to its
+ * left child 2k (range [l, mid)) and the others to 2k + 1; leaves B .. 2B - 1
+ * are the values xmin .. xmin + B - 1.  The values beyond are drawn one by
+ * one as the inverse CDF of m' uniform on [1, T[B-1] - 1] (the high 64 bits
+ * of a 64-bit random word times T[B-1] - 1, plus one).  The work grows with
+ * the occupied values rather than with n (~780 binomials and ~780 single
+ * values at alpha = 2, n = 10^6).  Random words (purpose 3): word j is 64
+ * bits, the low half word 2 (j mod 2) and the high half word 2 (j mod 2) + 1
+ * of the Philox block with counter (floor(j/2), replicate, cell_id, 3); a
+ * binomial takes the uniform (top 53 bits + 1) 2^-53 of its word.  Word 0
+ * is the count beyond, word k node k, word 2B + t the t-th value beyond.
+ * Same law as pl_ks_cutoffs, a
+ * different random stream, so results agree with pl_ks_cutoffs in
+ * distribution, not value by value.  Arguments, outputs and errors as
+ * pl_ks_cutoffs (every cell runs in the block form, n <= 2^21). */
 pl_status pl_ks_cutoffs_multinomial(pl_ctx *ctx, const pl_cell *cells,
                                     int ncells, uint64_t seed, const double *q,
                                     int nq, pl_precision prec, double *cutoffs,
