@@ -255,8 +255,10 @@ typedef struct {
 /* Autotuner over the cells a caller will run: times pl_ks_cutoffs on the
  * same cells with at most sample_replicates replicates each (median of three
  * timed calls per setting) and picks, one after the other, the split (256,
- * 1,024, 4,096, 16,384, 65,535), the work-item size (32, 64, 128, 256) and
- * hist_shift (-1, 0, 1) that run fastest; leaves them set on the context and
+ * 1,024, 4,096, 16,384, 65,535), the work-item size (32, 64, 128, 256; only
+ * when the sample is the whole workload, as on a sample the plan's own item
+ * sizing decides) and hist_shift (-1, 0, 1) that run fastest; leaves them set
+ * on the context and
  * writes them to *out (host, may be NULL).  Synchronises `stream`.  On an
  * error the previous settings stay.  pl_set_tuning sets them directly.
  * Errors: PL_EINVAL, and those of pl_ks_cutoffs. */

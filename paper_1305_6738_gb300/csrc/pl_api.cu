@@ -1498,10 +1498,15 @@ pl_status pl_autotune_cells(pl_ctx *ctx, const pl_cell *cells, int ncells, pl_pr
     if (!st_all && t < best) best = t, best_split = sp;
   }
   ctx->warp_split = best_split;
+  // the work-item size is tuned only on the whole workload: on a replicate
+  // sample the plan's own sizing (items small enough to fill the GPU) is what
+  // a sample of a larger workload would measure, not the full-size optimum
+  bool whole = true;
+  for (int c = 0; c < ncells; ++c) whole = whole && cells[c].replicates <= sample_replicates;
   const int items[] = {32, 64, 128, 256};
   int best_item = ctx->item_reps;
   for (int it : items) {
-    if (st_all) break;
+    if (st_all || !whole) break;
     ctx->item_reps = it;
     double t;
     st_all = trial(&t);

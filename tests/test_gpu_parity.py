@@ -378,9 +378,12 @@ def test_tile_settings_and_cell_autotuner_keep_parity(pl):
     for split, item, shift in [(65535, 32, 0), (1024, 256, -1), (65535, 7, 1), (256, 64, 0), (16384, 0, 0)]:
         c.pl_set_tuning(split, item, shift)
         check()
-    t = c.pl_autotune_cells(cells, 0, sample_replicates=64)
-    assert 1 <= t["split"] <= 65535 and t["item_reps"] in (0, 32, 64, 128, 256) and t["hist_shift"] in (-1, 0, 1)
+    t = c.pl_autotune_cells(cells, 0, sample_replicates=64)  # a sample: the item size stays the plan's
+    assert 1 <= t["split"] <= 65535 and t["item_reps"] == 0 and t["hist_shift"] in (-1, 0, 1)
     assert t["best_ms"] > 0
+    check()
+    t = c.pl_autotune_cells(cells, 0, sample_replicates=1000)  # the whole workload: the item size too
+    assert t["item_reps"] in (0, 32, 64, 128, 256)
     check()
     with pytest.raises(pl.PLError):
         c.pl_set_tuning(0)
