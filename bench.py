@@ -44,11 +44,11 @@ MUL_PER_DRAW = 5
 MUL_LANES_PER_SM = 32
 
 # DRAM bytes per replicate of the sampler from one ncu capture (sweep at 4,000
-# replicates per cell: 140.0 MB over 360,000 replicates, the replicate records
+# replicates per cell: 139.5 MB over 360,000 replicates, the replicate records
 # written), keyed by the hash of the kernel sources it was taken on (reported
 # as null once they change).  The bench scales it to a launch by the
 # replicates one launch processes.
-TRAFFIC_PER_REPLICATE = {"fa4487233448e1d5": (16.261632e6 + 123.773952e6) / 360000}
+TRAFFIC_PER_REPLICATE = {"8f068933e760f1f8": (16.186112e6 + 123.300096e6) / 360000}
 
 
 def kernel_source_hash() -> str:
@@ -785,11 +785,11 @@ def per_cell_rates(ctx, cells, seed: int, qs, prec: int, mul_peak_gmul: float, f
 # (reported as null once the sources change): DRAM bytes read per replicate
 # (its replicate records) and binary64 operations per replicate (DFMA counted
 # as two, DADD and DMUL as one), mostly the fit.
-FINISHER_NCU = {"fa4487233448e1d5": {
-    "dram_read_per_replicate": 345.616128e6 / 360000,
-    "f64_ops_per_replicate": (56.472754e6 + 41.413632e6 + 2 * 26.533120e6) / 360000,
+FINISHER_NCU = {"8f068933e760f1f8": {
+    "dram_read_per_replicate": 304.833024e6 / 360000,
+    "f64_ops_per_replicate": (62.514866e6 + 47.455744e6 + 2 * 26.533120e6) / 360000,
     # one alpha = 3.5, n = 10 cell of 200,000 replicates (no spills, trivial KS): the fit alone
-    "fit_f64_ops": (4.866842e6 + 2.852992e6 + 2 * 6.226912e6) / 200000}}
+    "fit_f64_ops": (4.875226e6 + 2.861376e6 + 2 * 6.226912e6) / 200000}}
 ALGO_BYTES_PER_REPLICATE = 16  # D (binary32 or binary64) and alpha-hat (binary64) out
 
 

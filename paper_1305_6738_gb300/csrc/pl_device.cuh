@@ -19,9 +19,10 @@ constexpr uint64_t kXCap = 1ull << 62;      // simulated values saturate here
 #define PL_L1_ENTRIES 2048
 #endif
 // finisher blocks per SM the compiler must fit (binary32 form / binary64
-// form): three trade some register spills for occupancy in the binary32 form
+// form): two (128 registers, few spills) ran faster than three (80
+// registers, more spills) on GB300, heavy-tailed cells most
 #ifndef PL_FIN_MIN_BLOCKS_F32
-#define PL_FIN_MIN_BLOCKS_F32 3
+#define PL_FIN_MIN_BLOCKS_F32 2
 #endif
 #ifndef PL_FIN_MIN_BLOCKS_F64
 #define PL_FIN_MIN_BLOCKS_F64 2
@@ -45,7 +46,10 @@ constexpr int kIncBuckets = 1 << kIncBits;
 constexpr uint32_t kIncOther = 0x80000000u;
 constexpr int kHMax = 1024;                 // dense histogram bins per warp
 constexpr int kHWide = 8192;                // dense histogram bins per block (block form)
-constexpr int kWarps = 8;                   // warps per block, warp form
+#ifndef PL_FIN_WARPS
+#define PL_FIN_WARPS 8
+#endif
+constexpr int kWarps = PL_FIN_WARPS;        // finisher warps per block
 constexpr int kSortSmem = kHMax / 2;        // replicates with more spills count as large sorts
 constexpr int kLnTable = 16384;             // ln(xmin + i) tables, i < kLnTable
 constexpr int kNewtonCap = 200;             // Newton iteration cap
@@ -107,6 +111,7 @@ struct Cell {
 // A block-sized batch of replicates of one cell, with the offsets of its
 // replicate records (dense counts, spill values, meta) in the record buffers.
 constexpr int kItemReps = 256;
+static_assert(kItemReps <= 32 * kWarps, "a finisher warp takes at most 32 replicates of an item (a lane each)");
 struct WorkItem {
   uint32_t cell;
   uint32_t r0;            // first replicate
