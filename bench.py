@@ -1065,7 +1065,7 @@ def main():
     sampler = ClockSampler(gpu_query_id(local))
     barrier()
     step_ms, kern_ms, fin_ms = [], [], []
-    waves = 0
+    waves = slaunch = 0
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -1078,7 +1078,7 @@ def main():
         if graph is None:
             kern_ms.append(tr["sample_ms"])
             fin_ms.append(tr["finish_ms"])
-            waves = tr["waves"]
+            waves, slaunch = tr["waves"], tr["sample_launches"]
     barrier()
     clocks = sampler.stop()
     launches = ctx.pl_trace()["launches"] - launches0
@@ -1102,7 +1102,8 @@ def main():
         ctx.pl_set_tracing(True)
         ctx.pl_ks_cutoffs(cells, seed, QS, prec, cutoffs=cut)
         tr = ctx.pl_trace()
-        kern_ms, fin_ms, waves = [tr["sample_ms"]], [tr["finish_ms"]], tr["waves"]
+        kern_ms, fin_ms = [tr["sample_ms"]], [tr["finish_ms"]]
+        waves, slaunch = tr["waves"], tr["sample_launches"]
     e2e_value = job_rate(total_R, world, max_over_ranks(statistics.mean(e2e_s), dist, "cuda"))
     h2d = len(cells) * 40 + len(QS) * 8
     d2h = host_cut.nbytes
@@ -1118,13 +1119,13 @@ def main():
     h = kernel_source_hash()
     roofline = {"bound": "alu", "achieved": achieved, "peak": mul_peak, "unit": "Gmul/s (32x32->64)",
                 "frac": achieved / mul_peak,
-                "traffic": (TRAFFIC_PER_REPLICATE[h] * total_R / max(1, waves)
+                "traffic": (TRAFFIC_PER_REPLICATE[h] * total_R / max(1, slaunch)
                             if h in TRAFFIC_PER_REPLICATE and args.workload == "sweep" else None),
                 "kernel": ("mn_sample_kernel" if args.sampler == "multinomial"
                            else "sample_block_kernel" if args.workload == "large-n"
                            else "sample_hist_kernel + sample_block_kernel" if args.workload == "batched"
                            else "sample_hist_kernel"),
-                "kernel_ms_per_step": kmean, "launches_per_step": waves,
+                "kernel_ms_per_step": kmean, "launches_per_step": slaunch,
                 "finisher_ms_per_step": statistics.mean(fin_ms),
                 "peak_basis": f"{props.multi_processor_count} SMs x {MUL_LANES_PER_SM} multiply lanes x "
                               f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json); "

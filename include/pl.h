@@ -144,8 +144,10 @@ typedef struct {
   float total_ms;      /* last traced call: first to last phase */
   float sample_ms;     /* last traced call: sampler launches, summed over waves */
   float finish_ms;     /* last traced call: finisher launches, summed over waves */
-  uint32_t waves;      /* last traced call: number of waves (sampler launches) */
+  uint32_t waves;      /* last traced call: number of waves */
   uint64_t draws;      /* last traced call: draws simulated */
+  uint32_t sample_launches; /* last traced call: sampler kernel launches (one
+                               per wave, form and binning mode) */
 } pl_trace_info;
 
 pl_status pl_set_tracing(pl_ctx *ctx, int on);

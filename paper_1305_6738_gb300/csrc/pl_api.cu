@@ -57,6 +57,7 @@ struct pl_ctx {
   std::map<uint64_t, FitTable> fit_cache;   // complete host copies (pointers into fit_mem)
   std::vector<void *> fit_mem;
   uint32_t traced_waves = 0;
+  uint32_t traced_sample_launches = 0;
   uint64_t traced_draws = 0;
   // pinned staging of the host-written tables and the event of its last copy
   void *staging = nullptr;
@@ -76,6 +77,10 @@ constexpr uint32_t kPurposeMultinomial = 3;  // stream tag of the multinomial sa
 constexpr int64_t kWarpNMax = 65535;     // warp form: n up to this (16-bit dense record counts)
 constexpr int64_t kWideNMax = 1 << 21;   // block form: n up to this (16-bit lane counters)
 constexpr uint32_t kWideItemReps = 8;    // block form: replicates per work item
+#ifndef PL_INLINE_ALPHA
+#define PL_INLINE_ALPHA 2.1
+#endif
+constexpr double kInlineAlpha = PL_INLINE_ALPHA;  // laws below this exponent bin in the draw loop
 static_assert(kWideItemReps == kWideReps, "block-form items as the multinomial sampler reads them");
 
 pl_status fail(pl_ctx *ctx, pl_status s, const char *fmt, ...) {
@@ -218,6 +223,7 @@ uint64_t next_pow2(uint64_t v) {
 struct Wave {
   size_t first, count;             // items [first, first + count)
   size_t wide;                     // the first `wide` items are block-form cells
+  size_t wide_inl, warp_inl;       // of the block-form and of the warp-form items, the first so many bin inline
 };
 
 struct SimPlan {
@@ -272,9 +278,10 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     cd.law = li;
     cd.wide = (all_wide || x.n > std::min(kWarpNMax, ctx->warp_split)) ? 1u : 0u;
     cd.H = cd.wide ? (uint32_t)kHWide : hist_bins(x.n, ctx->hist_shift);
-    // batched table searches pay off once a replicate has many draws or the
-    // tail is heavy (measured crossover on GB300)
-    cd.defer = (x.n >= 512 || x.alpha < 1.6) ? 1u : 0u;
+    // heavy tails (a third of the draws beyond the first four values at alpha
+    // 1.5): their single-valued draws are binned in the draw loop instead of
+    // queued; lighter tails queue them all (measured crossover on GB300)
+    cd.inline_bins = x.alpha < kInlineAlpha ? 1u : 0u;
     cd.purpose = purpose;
     cd.out_off = sp.total_R;
     auto fi = fit_of.find(x.xmin);
@@ -285,6 +292,9 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     cd.fit = fi->second;
     cd.scap = spill_capacity(x.alpha, x.xmin, x.n, cd.H);
     if (ctx->dbg_spill_cap) cd.scap = std::min(cd.scap, ctx->dbg_spill_cap);
+    // never below what a lane-finished replicate may hold, so that whether a
+    // replicate is finished by a lane does not depend on the slot size
+    cd.scap = std::max<uint32_t>(cd.scap, (uint32_t)std::min<int64_t>(x.n, kLaneSpills));
     sp.finisher_spill = std::max<int64_t>(sp.finisher_spill, cd.wide ? 2 * (int64_t)cd.scap : x.n);
     sp.total_R += x.replicates;
     sp.n_max = std::max(sp.n_max, x.n);
@@ -297,12 +307,14 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
   for (size_t l = 0; l < sp.laws.size(); ++l)
     sp.laws[l].L2 = std::max<uint32_t>(table_length(sp.laws[l].alpha, sp.laws[l].xmin, law_draws[l]),
                                        (uint32_t)next_pow2(2 * (uint64_t)law_hmax[l]));
-  // work items: cells grouped by law (the block keeps a law's table staged),
-  // larger n first within a law
+  // work items: block form first, then inline binning first (one launch per
+  // form and mode), cells grouped by law (the block keeps a law's table
+  // staged), larger n first within a law
   std::vector<int> order(ncells);
   for (int c = 0; c < ncells; ++c) order[c] = c;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     if (sp.cells[a].wide != sp.cells[b].wide) return sp.cells[a].wide > sp.cells[b].wide;
+    if (sp.cells[a].inline_bins != sp.cells[b].inline_bins) return sp.cells[a].inline_bins > sp.cells[b].inline_bins;
     if (sp.cells[a].law != sp.cells[b].law) return sp.cells[a].law < sp.cells[b].law;
     return sp.cells[a].n > sp.cells[b].n;
   });
@@ -318,7 +330,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
   int64_t warp_item = kItemReps;
   while (warp_item > 32 && warp_R / warp_item < fill) warp_item /= 2;
   if (ctx->item_reps) warp_item = ctx->item_reps;
-  size_t wd = 0, ws = 0, wm = 0, first = 0, nwide = 0;
+  size_t wd = 0, ws = 0, wm = 0, first = 0, nwide = 0, nwide_inl = 0, nwarp_inl = 0;
   double wt = 0.0;  // expected beyond-table draws of the wave
   auto close_tail = [&]() {
     const double cap = std::ceil(2.0 * wt + 10.0 * std::sqrt(wt) + 1024.0);
@@ -339,14 +351,15 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
       const size_t d = (size_t)it.nrep * cd.H * (cd.wide ? 2 : 1), sp_ = (size_t)it.nrep * cd.scap, m = it.nrep;
       const size_t bytes_after = (wd + d) * 2 + (ws + sp_) * 8 + (wm + m) * 8;
       if (sp.items.size() > first && bytes_after > wave_budget) {
-        sp.waves.push_back({first, sp.items.size() - first, nwide});
+        sp.waves.push_back({first, sp.items.size() - first, nwide, nwide_inl, nwarp_inl});
         close_tail();
         first = sp.items.size();
         wd = ws = wm = 0;
-        nwide = 0;
+        nwide = nwide_inl = nwarp_inl = 0;
         wt = 0.0;
       }
       if (cd.wide) ++nwide;
+      if (cd.inline_bins) ++(cd.wide ? nwide_inl : nwarp_inl);
       wt += (double)it.nrep * (double)cd.n * q_tail;
       it.dense_off = wd;
       it.spill_off = ws;
@@ -360,7 +373,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
       sp.items.push_back(it);
     }
   }
-  sp.waves.push_back({first, sp.items.size() - first, nwide});
+  sp.waves.push_back({first, sp.items.size() - first, nwide, nwide_inl, nwarp_inl});
   close_tail();
   if (ctx->dbg_tail_cap) sp.tail_cap = std::min(sp.tail_cap, ctx->dbg_tail_cap);
   return PL_OK;
@@ -507,6 +520,7 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
       ctx->wave_ev.push_back(e);
     }
     ctx->traced_waves = (uint32_t)sp.waves.size();
+    ctx->traced_sample_launches = 0;
     ctx->traced_draws = 0;
     for (const Cell &c : sp.cells) ctx->traced_draws += (uint64_t)c.n * (uint64_t)c.R;
   }
@@ -527,20 +541,27 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
     PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
     PL_CUDA(cudaMemsetAsync(b.tq_count, 0, sizeof(unsigned int), st));
     if (wev) PL_CUDA(cudaEventRecord(wev[0], st));
-    if (w.wide) {  // block form items come first in the wave
-      sl.items = b.items + w.first;
-      sl.nitems = (uint32_t)w.wide;
-      sl.blocks = (int)std::min<size_t>((size_t)b.block_sampler_blocks, w.wide);
-      PL_CUDA(launch_sample_block(sl, st));
+    // the wave's items in four runs: block form (inline binning, then not),
+    // warp form (likewise); a launch per nonempty run, each with its own count
+    const size_t run_first[4] = {w.first, w.first + w.wide_inl, w.first + w.wide, w.first + w.wide + w.warp_inl};
+    const size_t run_count[4] = {w.wide_inl, w.wide - w.wide_inl, w.warp_inl, w.count - w.wide - w.warp_inl};
+    bool counter_used = false;
+    for (int r = 0; r < 4; ++r) {
+      if (!run_count[r]) continue;
+      if (counter_used) PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
+      counter_used = true;
+      sl.items = b.items + run_first[r];
+      sl.nitems = (uint32_t)run_count[r];
+      const bool inl = (r & 1) == 0;
+      if (r < 2) {
+        sl.blocks = (int)std::min<size_t>((size_t)b.block_sampler_blocks, run_count[r]);
+        PL_CUDA(launch_sample_block(sl, inl, st));
+      } else {
+        sl.blocks = (int)std::min<size_t>((size_t)b.sample_blocks, run_count[r]);
+        PL_CUDA(launch_sample_hist(sl, inl, st));
+      }
       ctx->launches += 1;
-    }
-    if (w.count > w.wide) {
-      if (w.wide) PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
-      sl.items = b.items + w.first + w.wide;
-      sl.nitems = (uint32_t)(w.count - w.wide);
-      sl.blocks = (int)std::min<size_t>((size_t)b.sample_blocks, w.count - w.wide);
-      PL_CUDA(launch_sample_hist(sl, st));
-      ctx->launches += 1;
+      if (trace) ++ctx->traced_sample_launches;
     }
     if (wev) PL_CUDA(cudaEventRecord(wev[1], st));
     PL_CUDA(launch_tail_queue_raw(b.laws_dev, b.tq_pos, b.tq_law, b.tq_count, sp.tail_cap, b.rec.spill, ctx->ctr,
@@ -583,6 +604,7 @@ pl_status run_sim_mn(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t see
       ctx->wave_ev.push_back(e);
     }
     ctx->traced_waves = (uint32_t)sp.waves.size();
+    ctx->traced_sample_launches = (uint32_t)sp.waves.size();
     ctx->traced_draws = 0;
     for (const Cell &c : sp.cells) ctx->traced_draws += (uint64_t)c.n * (uint64_t)c.R;
   }
@@ -779,6 +801,7 @@ pl_status pl_trace(pl_ctx *ctx, void *stream, pl_trace_info *out) {
     }
     out->waves = ctx->traced_waves;
     out->draws = ctx->traced_draws;
+    out->sample_launches = ctx->traced_sample_launches;
   }
   return PL_OK;
 }
@@ -1106,6 +1129,7 @@ pl_status run_tz_cutoffs(pl_ctx *ctx, const pl_tcell *cells, int ncells, uint32_
   ctx->launches += 1;
   if (ctx->tracing) {
     ctx->traced_waves = 0;
+    ctx->traced_sample_launches = 0;
     ctx->traced_draws = 0;
     for (const TzCell &c : tp.cells) ctx->traced_draws += (uint64_t)c.n * (uint64_t)c.R;
   }

@@ -45,6 +45,9 @@ constexpr int kIncBits = 8;
 constexpr int kIncBuckets = 1 << kIncBits;
 constexpr uint32_t kIncOther = 0x80000000u;
 constexpr int kHMax = 1024;                 // dense histogram bins per warp
+// Warp-form replicates with at most this many spills are finished by one lane
+// (the record's spill slot always holds at least min(n, kLaneSpills)).
+constexpr int kLaneSpills = 8;
 constexpr int kHWide = 8192;                // dense histogram bins per block (block form)
 #ifndef PL_FIN_WARPS
 #define PL_FIN_WARPS 8
@@ -105,7 +108,7 @@ struct Cell {
   uint32_t fit;           // index into the fit-table array (one per xmin)
   uint32_t scap;          // spill slot capacity of a replicate record
   uint32_t wide;          // block form: 32-bit dense counts, H = kHWide
-  uint32_t defer;         // warp form: batch the table searches (see kDeferCap)
+  uint32_t inline_bins;   // draw loop: bin single-valued draws beyond the first four values at once (heavy tails)
 };
 
 // A block-sized batch of replicates of one cell, with the offsets of its

@@ -566,6 +566,40 @@ __device__ __forceinline__ float survival_em_f32(float af, float la_hi, float la
   return expf(-prod - f.lnc) * (1.0f - perr - f.lnc_lo) * br;
 }
 
+// The two candidates of a run of spilled values ending at v: |F(v) - Ca/n|
+// and |F(v - 1) - Cb/n| (Ca values at most v, Cb below v).
+__device__ __forceinline__ double spill_point_f64(uint64_t v, int64_t Ca, int64_t Cb, double a, double invZ,
+                                                  double inv_n) {
+  double q;
+  hurwitz_em<0, false>(a, (double)v + 1.0, &q);
+  const double Q = q * invZ;
+  const double pv = exp(-a * log((double)v)) * invZ;
+  const double Fv = 1.0 - Q;
+  const double Fb = 1.0 - (Q + pv);
+  return fmax(fabs(Fv - (double)Ca * inv_n), fabs(Fb - (double)Cb * inv_n));
+}
+
+__device__ __forceinline__ float spill_point_f32(uint64_t v, int64_t Ca, int64_t Cb, float inv_n, const FitOut &f) {
+  float Q, pv;
+  if (u64_to_f32(v + 1ull) < 10.0f + 1.5f * f.a_hi) {
+    // exponent too large for the short binary32 series at this argument
+    double q;
+    hurwitz_em<0, false>(f.ahat, (double)v + 1.0, &q);
+    Q = (float)(q * (double)f.invZ);
+    pv = (float)(exp(-f.ahat * log((double)v)) * (double)f.invZ);
+  } else {
+    float la_hi, la_lo, lv_hi, lv_lo;
+    ln_u64_ff(v + 1ull, la_hi, la_lo);
+    ln_u64_ff(v, lv_hi, lv_lo);
+    // Q(v) = zeta(s, v + 1)/Z
+    Q = survival_em_f32(u64_to_f32(v + 1ull), la_hi, la_lo, f);
+    pv = exp_neg_prod(f.a_hi, f.a_lo, lv_hi, lv_lo) * f.invZ;
+  }
+  const float Fv = 1.0f - Q;
+  const float Fb = 1.0f - (Q + pv);
+  return fmaxf(fabsf(Fv - (float)(uint32_t)Ca * inv_n), fabsf(Fb - (float)(uint32_t)Cb * inv_n));
+}
+
 template <bool F32, typename DT>
 __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, int64_t nsd,
                           int64_t n, uint64_t xmin, const FitOut &f, const double *lnT, const float *lnT_hi,
@@ -593,16 +627,7 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
       const uint64_t v = ok ? pairs[2 * k] : 0;
       const int64_t c = ok ? (int64_t)pairs[2 * k + 1] : 0;
       const int64_t Ca = carryC + warp_scan_i64(c, lane);
-      if (ok) {
-        const int64_t Cb = Ca - c;
-        double q;
-        hurwitz_em<0, false>(a, (double)v + 1.0, &q);
-        const double Q = q * invZ;
-        const double pv = exp(-a * log((double)v)) * invZ;
-        const double Fv = 1.0 - Q;
-        const double Fb = 1.0 - (Q + pv);
-        best = fmax(best, fmax(fabs(Fv - (double)Ca * inv_n), fabs(Fb - (double)Cb * inv_n)));
-      }
+      if (ok) best = fmax(best, spill_point_f64(v, Ca, Ca - c, a, invZ, inv_n));
       carryC = __shfl_sync(0xffffffffu, Ca, 31);
     }
     return warp_max(best);
@@ -645,28 +670,7 @@ __device__ double ks_warp(const DT *dense, int64_t tmax, const uint64_t *pairs, 
       const uint64_t v = ok ? pairs[2 * k] : 0;
       const int64_t c = ok ? (int64_t)pairs[2 * k + 1] : 0;
       const int64_t Ca = carryC + warp_scan_i64(c, lane);
-      if (ok && u64_to_f32(v + 1ull) < 10.0f + 1.5f * f.a_hi) {
-        // exponent too large for the short binary32 series at this argument
-        const int64_t Cb = Ca - c;
-        double q;
-        hurwitz_em<0, false>(f.ahat, (double)v + 1.0, &q);
-        const float Q = (float)(q * (double)f.invZ);
-        const float pv = (float)(exp(-f.ahat * log((double)v)) * (double)f.invZ);
-        const float Fv = 1.0f - Q;
-        const float Fb = 1.0f - (Q + pv);
-        best = fmaxf(best, fmaxf(fabsf(Fv - (float)(uint32_t)Ca * inv_n), fabsf(Fb - (float)(uint32_t)Cb * inv_n)));
-      } else if (ok) {
-        const int64_t Cb = Ca - c;
-        float la_hi, la_lo, lv_hi, lv_lo;
-        ln_u64_ff(v + 1ull, la_hi, la_lo);
-        ln_u64_ff(v, lv_hi, lv_lo);
-        // Q(v) = zeta(s, v + 1)/Z
-        const float Q = survival_em_f32(u64_to_f32(v + 1ull), la_hi, la_lo, f);
-        const float pv = exp_neg_prod(f.a_hi, f.a_lo, lv_hi, lv_lo) * f.invZ;
-        const float Fv = 1.0f - Q;
-        const float Fb = 1.0f - (Q + pv);
-        best = fmaxf(best, fmaxf(fabsf(Fv - (float)(uint32_t)Ca * inv_n), fabsf(Fb - (float)(uint32_t)Cb * inv_n)));
-      }
+      if (ok) best = fmaxf(best, spill_point_f32(v, Ca, Ca - c, inv_n, f));
       carryC = __shfl_sync(0xffffffffu, Ca, 31);
     }
     return (double)warp_maxf(best);
@@ -932,7 +936,7 @@ constexpr int kFlushBlocks = 31;
 // 32), then one ragged round.  WIDE: one 32-bit bin per word of hist (block
 // form); else two 16-bit bins per word.  The lane's counts of the first four
 // values are left in c[0..3] (not reduced across lanes).
-template <bool WIDE>
+template <bool WIDE, bool INL>
 __device__ __forceinline__ void draw_queued(const uint64_t *sT, const uint32_t *sG, const uint32_t *sInc,
                                             const Law &law, const Cell &cell, uint32_t rep, const RoundKeys &rk,
                                             uint32_t *hist, int *s_count, uint64_t *spill, int64_t spill_capacity,
@@ -1036,6 +1040,14 @@ __device__ __forceinline__ void draw_queued(const uint64_t *sT, const uint32_t *
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(e) : "r"(inc_lane + ((h >> (32 - kIncBits)) << 7)));
     acc += e;
     if ((int32_t)e < 0) {
+      if (INL) {
+        // heavy tails: a single-valued bucket of the fine guide is binned here
+        const uint32_t gw = sG[h >> (32 - kFineBits)], b = gw & kGuideIndex;
+        if (!(gw & kGuideMulti) && b < law.L2) {
+          bin(b);
+          return;
+        }
+      }
       asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(qa), "r"(h), "r"(i) : "memory");
       qa += 256u;
     }
@@ -1075,6 +1087,7 @@ __device__ __forceinline__ void draw_queued(const uint64_t *sT, const uint32_t *
   c[3] = c3;
 }
 
+template <bool INL>
 __device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const uint32_t *sG, const uint32_t *sInc,
                                                     const Law &law, const Cell &cell, uint32_t rep,
                                                     const RoundKeys &rk, uint32_t *hist, int *s_count,
@@ -1085,8 +1098,8 @@ __device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const ui
   if (lane == 0) *s_count = 0;
   __syncwarp();
   uint32_t c[4];
-  draw_queued<false>(sT, sG, sInc, law, cell, rep, rk, hist, s_count, spill, spill_capacity, lane, tq, spill_pos0,
-                     queue, lane, 32, c);
+  draw_queued<false, INL>(sT, sG, sInc, law, cell, rep, rk, hist, s_count, spill, spill_capacity, lane, tq,
+                          spill_pos0, queue, lane, 32, c);
   __syncwarp();
   const unsigned s0 = __reduce_add_sync(0xffffffffu, c[0]), s1 = __reduce_add_sync(0xffffffffu, c[1]);
   const unsigned s2 = __reduce_add_sync(0xffffffffu, c[2]), s3 = __reduce_add_sync(0xffffffffu, c[3]);
@@ -1104,6 +1117,9 @@ __device__ __forceinline__ int64_t draw_replicate_q(const uint64_t *sT, const ui
   return 2 * (int64_t)tw + ((hist[tw] >> 16) ? 1 : 0);
 }
 
+// INL: the launch's cells all bin in the draw loop (Cell::inline_bins), or none
+// do; one kernel per mode keeps each draw loop's code on its own.
+template <bool INL>
 __global__ void __launch_bounds__(kAWarps * 32, kABlocksPerSM) sample_hist_kernel(SampleLaunch a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
@@ -1142,7 +1158,7 @@ __global__ void __launch_bounds__(kAWarps * 32, kABlocksPerSM) sample_hist_kerne
       const uint32_t j = warp + jj * kAWarps;  // strided: small items still use every warp
       if (j >= wi.nrep) break;
       const uint64_t pos0 = wi.spill_off + (uint64_t)j * cell.scap;
-      const int64_t tmax = draw_replicate_q(sT, sG, sInc, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp],
+      const int64_t tmax = draw_replicate_q<INL>(sT, sG, sInc, law, cell, wi.r0 + j, a.rk, hist, &s_spill[warp],
                                             a.rec.spill + pos0, cell.scap, lane, &tq, pos0, queue);
       uint32_t *dense = reinterpret_cast<uint32_t *>(a.rec.dense + wi.dense_off + (uint64_t)j * cell.H);
       for (int64_t i = lane; i <= (tmax >> 1); i += 32) dense[i] = hist[i];
@@ -1159,6 +1175,7 @@ __global__ void __launch_bounds__(kAWarps * 32, kABlocksPerSM) sample_hist_kerne
 constexpr int kBlkThreads = 1024;
 constexpr int kBlkWarps = kBlkThreads / 32;
 
+template <bool INL>
 __global__ void __launch_bounds__(kBlkThreads, 1) sample_block_kernel(SampleLaunch a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
@@ -1203,8 +1220,8 @@ __global__ void __launch_bounds__(kBlkThreads, 1) sample_block_kernel(SampleLaun
       __syncthreads();
       const uint64_t pos0 = wi.spill_off + (uint64_t)j * cell.scap;
       uint32_t c[4];
-      draw_queued<true>(sT, sG, sInc, law, cell, wi.r0 + j, a.rk, hist, s_spill, a.rec.spill + pos0, cell.scap,
-                        lane, &tq, pos0, queue, threadIdx.x, kBlkThreads, c);
+      draw_queued<true, INL>(sT, sG, sInc, law, cell, wi.r0 + j, a.rk, hist, s_spill, a.rec.spill + pos0, cell.scap,
+                             lane, &tq, pos0, queue, threadIdx.x, kBlkThreads, c);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const unsigned t = __reduce_add_sync(0xffffffffu, c[q]);
@@ -1234,13 +1251,15 @@ size_t block_sampler_smem_bytes() {
 int block_sampler_blocks_per_sm() {
   int nb = 0;
   const size_t smem = block_sampler_smem_bytes();
-  cudaFuncSetAttribute(sample_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_block_kernel, kBlkThreads, smem);
+  cudaFuncSetAttribute(sample_block_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(sample_block_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_block_kernel<false>, kBlkThreads, smem);
   return nb;
 }
 
-cudaError_t launch_sample_block(const SampleLaunch &a, cudaStream_t st) {
-  sample_block_kernel<<<a.blocks, kBlkThreads, block_sampler_smem_bytes(), st>>>(a);
+cudaError_t launch_sample_block(const SampleLaunch &a, bool inl, cudaStream_t st) {
+  if (inl) sample_block_kernel<true><<<a.blocks, kBlkThreads, block_sampler_smem_bytes(), st>>>(a);
+  else sample_block_kernel<false><<<a.blocks, kBlkThreads, block_sampler_smem_bytes(), st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1276,13 +1295,15 @@ size_t sample_kernel_smem_bytes() {
 int sample_kernel_blocks_per_sm() {
   int nb = 0;
   const size_t smem = sample_kernel_smem_bytes();
-  cudaFuncSetAttribute(sample_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_hist_kernel, kAWarps * 32, smem);
+  cudaFuncSetAttribute(sample_hist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(sample_hist_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_hist_kernel<false>, kAWarps * 32, smem);
   return nb;
 }
 
-cudaError_t launch_sample_hist(const SampleLaunch &a, cudaStream_t st) {
-  sample_hist_kernel<<<a.blocks, kAWarps * 32, sample_kernel_smem_bytes(), st>>>(a);
+cudaError_t launch_sample_hist(const SampleLaunch &a, bool inl, cudaStream_t st) {
+  if (inl) sample_hist_kernel<true><<<a.blocks, kAWarps * 32, sample_kernel_smem_bytes(), st>>>(a);
+  else sample_hist_kernel<false><<<a.blocks, kAWarps * 32, sample_kernel_smem_bytes(), st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1299,11 +1320,77 @@ __device__ __forceinline__ const uint16_t *stage_dense(const uint16_t *src, int6
   return dst;
 }
 
-// Small replicates (warp form, no spills, largest bin below kLaneBins) are
-// finished by one lane each: the log-sum and the KS scan run serially over the
-// replicate's dense counts, with no warp reductions.  Same arithmetic as the
-// warp-cooperative path, summed in bin order.
+// Small replicates (warp form, largest bin below kLaneBins, at most
+// kLaneSpills spills that fit the record's slot) are finished by one lane
+// each: the log-sum and the KS scan run serially over the replicate's dense
+// counts and then its spills, sorted in place, with no warp reductions.  Same
+// arithmetic as the warp-cooperative path, summed in bin order and value
+// order.
 constexpr int64_t kLaneBins = 128;
+
+// A lane's spills: draws left tagged beyond the table resolved, then sorted
+// ascending in place (odd-even transposition network over kLaneSpills
+// registers, unused ones padded with the largest key).
+__device__ __forceinline__ void lane_sort_spills(uint64_t *sp, int s, const Law &law, Counters *ctr) {
+  for (int k = 0; k < s; ++k) {
+    const uint64_t x = sp[k];
+    if (x & kTailTag) {
+      bool beyond;
+      sp[k] = resolve_tagged(law, x & ~kTailTag, &beyond);
+      if (beyond) atomicAdd(&ctr->tail_draws, 1ull);
+    }
+  }
+  uint64_t v[kLaneSpills];
+#pragma unroll
+  for (int k = 0; k < kLaneSpills; ++k) v[k] = k < s ? sp[k] : ~0ull;
+#pragma unroll
+  for (int r = 0; r < kLaneSpills; ++r) {
+#pragma unroll
+    for (int k = r & 1; k + 1 < kLaneSpills; k += 2) {
+      const uint64_t lo = v[k] < v[k + 1] ? v[k] : v[k + 1], hi = v[k] < v[k + 1] ? v[k + 1] : v[k];
+      v[k] = lo;
+      v[k + 1] = hi;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kLaneSpills; ++k)
+    if (k < s) sp[k] = v[k];
+}
+
+template <bool F32>
+__device__ __forceinline__ double lane_logsum_spills(const uint64_t *sp, int s) {
+  if (!F32) {
+    double acc = 0.0;
+    for (int k = 0; k < s; ++k) acc += log((double)sp[k]);
+    return acc;
+  }
+  float Sh = 0.0f, Sl = 0.0f;
+  for (int k = 0; k < s; ++k) {
+    float vh, vl;
+    ln_u64_ff(sp[k], vh, vl);
+    ff_add(Sh, Sl, vh, vl);
+  }
+  return (double)Sh + (double)Sl;
+}
+
+// KS candidates of a lane's sorted spills (every value beyond the dense bins,
+// n - s values below them), one per run of equal values.
+template <bool F32>
+__device__ __forceinline__ double lane_ks_spills(const uint64_t *sp, int s, int64_t n, const FitOut &f,
+                                                 double best) {
+  int64_t Cb = n - s;
+  const double invZ = F32 ? 0.0 : 1.0 / f.Z, inv_n = F32 ? 0.0 : 1.0 / (double)n;
+  const float inv_nf = 1.0f / (float)(uint32_t)n;
+  for (int k = 0; k < s; ++k) {
+    const uint64_t v = sp[k];
+    if (k + 1 < s && sp[k + 1] == v) continue;
+    const int64_t Ca = n - s + k + 1;
+    if (F32) best = fmax(best, (double)spill_point_f32(v, Ca, Cb, inv_nf, f));
+    else best = fmax(best, spill_point_f64(v, Ca, Cb, f.ahat, invZ, inv_n));
+    Cb = Ca;
+  }
+  return best;
+}
 
 template <bool F32>
 __device__ __forceinline__ double lane_logsum(const uint16_t *dense, int64_t tmax, const Law &law, const float *lnHi,
@@ -1410,12 +1497,20 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
       const uint64_t dslot = (uint64_t)cell.H * (cell.wide ? 2 : 1);
       const uint16_t *my_dense = a.rec.dense + wi.dense_off + (uint64_t)(j0 + (lane < nb ? lane : 0)) * dslot;
       bool simple = false;
+      int my_s = 0;
+      const uint64_t *my_sp = a.rec.spill + wi.spill_off + (uint64_t)(j0 + (lane < nb ? lane : 0)) * cell.scap;
       if (!cell.wide && lane < nb) {
         const int2 m = a.rec.meta[wi.meta_off + j0 + lane];
-        simple = m.y == 0 && m.x >= 0 && (int64_t)m.x < kLaneBins;
+        // (a slot holds at least min(n, kLaneSpills) entries, so these never overflow)
+        simple = m.y >= 0 && m.y <= kLaneSpills && m.x >= 0 && (int64_t)m.x < kLaneBins;
         if (simple) {
           my_tmax = m.x;
+          my_s = m.y;
           myL = lane_logsum<F32>(my_dense, my_tmax, law, lnHi, lnLo);
+          if (my_s > 0) {
+            lane_sort_spills(const_cast<uint64_t *>(my_sp), my_s, law, a.ctr);
+            myL += lane_logsum_spills<F32>(my_sp, my_s);
+          }
           if ((int64_t)my_dense[0] == n) myL += cc.ln_allmin;
         }
       }
@@ -1448,7 +1543,10 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
           }
           if (lane == r) myD = D;
         }
-        if (mine && simple) myD = lane_ks<F32>(my_dense, my_tmax, n, fo, law, lnHi, lnLo);
+        if (mine && simple) {
+          myD = lane_ks<F32>(my_dense, my_tmax, n, fo, law, lnHi, lnLo);
+          if (my_s > 0) myD = lane_ks_spills<F32>(my_sp, my_s, n, fo, myD);
+        }
         PL_PHASE(4);
         if (mine) {
           const int64_t o = cell.out_off + wi.r0 + j0 + lane;

@@ -73,7 +73,7 @@ class pl_trace_info(ctypes.Structure):
                 ("replicate_ms", ctypes.c_float), ("select_ms", ctypes.c_float),
                 ("total_ms", ctypes.c_float), ("sample_ms", ctypes.c_float),
                 ("finish_ms", ctypes.c_float), ("waves", ctypes.c_uint32),
-                ("draws", ctypes.c_uint64)]
+                ("draws", ctypes.c_uint64), ("sample_launches", ctypes.c_uint32)]
 
 
 class pl_result(ctypes.Structure):
