@@ -1326,7 +1326,7 @@ __device__ __forceinline__ const uint16_t *stage_dense(const uint16_t *src, int6
 // counts and then its spills, sorted in place, with no warp reductions.  Same
 // arithmetic as the warp-cooperative path, summed in bin order and value
 // order.
-constexpr int64_t kLaneBins = 128;
+constexpr int64_t kLaneBins = 256;
 
 // A lane's spills: draws left tagged beyond the table resolved, then sorted
 // ascending in place (odd-even transposition network over kLaneSpills
@@ -1401,6 +1401,7 @@ __device__ __forceinline__ double lane_logsum(const uint16_t *dense, int64_t tma
     return acc;
   }
   float Lh = 0.0f, Ll = 0.0f;
+#pragma unroll 4
   for (int64_t i = 0; i <= tmax; ++i) {
     const float c = (float)dense[i];
     const float ph = c * lnHi[i];
@@ -1427,6 +1428,7 @@ __device__ __forceinline__ double lane_ks(const uint16_t *dense, int64_t tmax, i
   const float inv_n = 1.0f / (float)(uint32_t)n;
   float Fh = 0.0f, Fl = 0.0f, best = 0.0f;
   uint32_t C = 0;
+#pragma unroll 4
   for (int64_t i = 0; i <= tmax; ++i) {
     ff_add(Fh, Fl, exp_neg_prod(f.a_hi, f.a_lo, lnHi[i], lnLo[i]) * f.invZ, 0.0f);
     C += dense[i];
