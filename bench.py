@@ -44,11 +44,11 @@ MUL_PER_DRAW = 5
 MUL_LANES_PER_SM = 32
 
 # DRAM bytes per replicate of the sampler from one ncu capture (sweep at 4,000
-# replicates per cell: 139.5 MB over 360,000 replicates, the replicate records
-# written), keyed by the hash of the kernel sources it was taken on (reported
-# as null once they change).  The bench scales it to a launch by the
-# replicates one launch processes.
-TRAFFIC_PER_REPLICATE = {"8f068933e760f1f8": (16.186112e6 + 123.300096e6) / 360000}
+# replicates per cell: 91.9 MB over 360,000 replicates in its two launches,
+# mostly the replicate records written), keyed by the hash of the kernel
+# sources it was taken on (reported as null once they change).  The bench
+# scales it to a launch by the replicates per launch.
+TRAFFIC_PER_REPLICATE = {"bfe49f99bb2233cd": (9.987328e6 + 74.10944e6 + 3.624192e6 + 4.176896e6) / 360000}
 
 
 def kernel_source_hash() -> str:
@@ -350,11 +350,13 @@ def tz_source_hash() -> str:
 # one-pass ncu capture of a full Tables 2-6 launch (57.2 MB read + 148.3 MB
 # written for 45,000,000 replicates: the 4-byte D of each replicate plus the
 # tables), keyed by the hash of its sources (null once they change).
-# The second key is the same kernel after a change to pl_device.cuh that only
-# enlarged the untruncated sampler's guide table, which the truncated kernel
-# does not use (it has its own constants).
+# The later keys are the same kernel after changes to pl_device.cuh that only
+# touch the untruncated samplers (a larger guide table; the lane-finish spill
+# limit and the inline-binning flag of a cell), which the truncated kernel does
+# not use (it has its own constants and cells).
 TZ_TRAFFIC_PER_REPLICATE = {"bb5f053fedd20812": (57234944 + 148284928) / 45e6,
-                            "a2952dc4a133b7a3": (57234944 + 148284928) / 45e6}
+                            "a2952dc4a133b7a3": (57234944 + 148284928) / 45e6,
+                            "86ecba4b8d4d58e2": (57234944 + 148284928) / 45e6}
 
 
 def tz_cpu_oracle_rate(cells, sample_reps: int, threads: int) -> dict:
@@ -785,11 +787,11 @@ def per_cell_rates(ctx, cells, seed: int, qs, prec: int, mul_peak_gmul: float, f
 # (reported as null once the sources change): DRAM bytes read per replicate
 # (its replicate records) and binary64 operations per replicate (DFMA counted
 # as two, DADD and DMUL as one), mostly the fit.
-FINISHER_NCU = {"8f068933e760f1f8": {
-    "dram_read_per_replicate": 304.833024e6 / 360000,
-    "f64_ops_per_replicate": (62.514866e6 + 47.455744e6 + 2 * 26.533120e6) / 360000,
+FINISHER_NCU = {"bfe49f99bb2233cd": {
+    "dram_read_per_replicate": 325.596416e6 / 360000,
+    "f64_ops_per_replicate": (40.661756e6 + 29.640232e6 + 2 * 21.632840e6) / 360000,
     # one alpha = 3.5, n = 10 cell of 200,000 replicates (no spills, trivial KS): the fit alone
-    "fit_f64_ops": (4.875226e6 + 2.861376e6 + 2 * 6.226912e6) / 200000}}
+    "fit_f64_ops": (4.806451e6 + 2.804522e6 + 2 * 6.206738e6) / 200000}}
 ALGO_BYTES_PER_REPLICATE = 16  # D (binary32 or binary64) and alpha-hat (binary64) out
 
 
@@ -1093,7 +1095,7 @@ def main():
     # host cutoffs out (the call copies and synchronises), wall clock
     e2e_s = []
     host_cut = np.zeros(len(cells) * len(QS))
-    for _ in range(max(2, args.steps // 2)):
+    for _ in range(max(3, args.steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cutoffs_call(cells, seed, QS, prec, cutoffs=host_cut)
