@@ -282,6 +282,11 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     // 1.5): their single-valued draws are binned in the draw loop instead of
     // queued; lighter tails queue them all (measured crossover on GB300)
     cd.inline_bins = x.alpha < kInlineAlpha ? 1u : 0u;
+    // longer lane-serial finishing pays off in throughput (many replicates
+    // per finisher warp); a small cell keeps the shorter lanes, whose latency
+    // is lower.  Decided per cell, so a cell's results never depend on what
+    // it is simulated with.
+    cd.lane_bins = x.replicates >= kLaneLongMinReps ? kLaneBinsLong : kLaneBinsShort;
     cd.purpose = purpose;
     cd.out_off = sp.total_R;
     auto fi = fit_of.find(x.xmin);
@@ -582,6 +587,8 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
     fl.arena_bytes = b.arena_bytes;
     fl.ctr = ctx->ctr;
     fl.blocks = (int)std::min<size_t>((size_t)b.blocks, w.count);
+    fl.tq_count = b.tq_count;  // the sampler's beyond-table draws were queued and resolved
+    fl.tq_cap = sp.tail_cap;
     PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
     if (wev) PL_CUDA(cudaEventRecord(wev[2], st));
     PL_CUDA(launch_finish(fl, f32, st));

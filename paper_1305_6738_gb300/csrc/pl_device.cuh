@@ -48,6 +48,8 @@ constexpr int kHMax = 1024;                 // dense histogram bins per warp
 // Warp-form replicates with at most this many spills are finished by one lane
 // (the record's spill slot always holds at least min(n, kLaneSpills)).
 constexpr int kLaneSpills = 8;
+constexpr uint32_t kLaneBinsLong = 256, kLaneBinsShort = 128;
+constexpr int64_t kLaneLongMinReps = 32768;  // cells with at least this many replicates take the long lanes
 constexpr int kHWide = 8192;                // dense histogram bins per block (block form)
 #ifndef PL_FIN_WARPS
 #define PL_FIN_WARPS 8
@@ -109,6 +111,8 @@ struct Cell {
   uint32_t scap;          // spill slot capacity of a replicate record
   uint32_t wide;          // block form: 32-bit dense counts, H = kHWide
   uint32_t inline_bins;   // draw loop: bin single-valued draws beyond the first four values at once (heavy tails)
+  uint32_t lane_bins;     // finisher: warp-form replicates with a largest bin below this (and at most
+                          // kLaneSpills spills) are finished by one lane each
 };
 
 // A block-sized batch of replicates of one cell, with the offsets of its

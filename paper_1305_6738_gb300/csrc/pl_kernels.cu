@@ -1320,19 +1320,19 @@ __device__ __forceinline__ const uint16_t *stage_dense(const uint16_t *src, int6
   return dst;
 }
 
-// Small replicates (warp form, largest bin below kLaneBins, at most
-// kLaneSpills spills that fit the record's slot) are finished by one lane
+// Small replicates (warp form, largest bin below the cell's lane_bins, at
+// most kLaneSpills spills that fit the record's slot) are finished by one lane
 // each: the log-sum and the KS scan run serially over the replicate's dense
 // counts and then its spills, sorted in place, with no warp reductions.  Same
 // arithmetic as the warp-cooperative path, summed in bin order and value
 // order.
-constexpr int64_t kLaneBins = 256;
 
 // A lane's spills: draws left tagged beyond the table resolved, then sorted
 // ascending in place (odd-even transposition network over kLaneSpills
 // registers, unused ones padded with the largest key).
-__device__ __forceinline__ void lane_sort_spills(uint64_t *sp, int s, const Law &law, Counters *ctr) {
-  for (int k = 0; k < s; ++k) {
+__device__ __forceinline__ void lane_sort_spills(uint64_t *sp, int s, const Law &law, Counters *ctr,
+                                                 bool tags_left) {
+  for (int k = 0; tags_left && k < s; ++k) {
     const uint64_t x = sp[k];
     if (x & kTailTag) {
       bool beyond;
@@ -1462,6 +1462,7 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
   }
   __syncthreads();
   uint32_t phase = 0, loaded = 0xffffffffu;
+  const bool tags_left = !a.tq_count || *a.tq_count > a.tq_cap;
 
   for (;;) {
     if (threadIdx.x == 0)  // no further items once a wait has run out: records may be incomplete
@@ -1504,13 +1505,13 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
       if (!cell.wide && lane < nb) {
         const int2 m = a.rec.meta[wi.meta_off + j0 + lane];
         // (a slot holds at least min(n, kLaneSpills) entries, so these never overflow)
-        simple = m.y >= 0 && m.y <= kLaneSpills && m.x >= 0 && (int64_t)m.x < kLaneBins;
+        simple = m.y >= 0 && m.y <= kLaneSpills && m.x >= 0 && (uint32_t)m.x < cell.lane_bins;
         if (simple) {
           my_tmax = m.x;
           my_s = m.y;
           myL = lane_logsum<F32>(my_dense, my_tmax, law, lnHi, lnLo);
           if (my_s > 0) {
-            lane_sort_spills(const_cast<uint64_t *>(my_sp), my_s, law, a.ctr);
+            lane_sort_spills(const_cast<uint64_t *>(my_sp), my_s, law, a.ctr, tags_left);
             myL += lane_logsum_spills<F32>(my_sp, my_s);
           }
           if ((int64_t)my_dense[0] == n) myL += cc.ln_allmin;
@@ -1567,7 +1568,9 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
         uint16_t *dense = a.rec.dense + wi.dense_off + (uint64_t)j * dslot;
         uint32_t *dense32 = cell.wide ? reinterpret_cast<uint32_t *>(dense) : nullptr;
         uint64_t *sp = a.rec.spill + wi.spill_off + (uint64_t)j * cell.scap;
+        bool tags = tags_left;
         if (s > (int64_t)cell.scap) {
+          tags = true;
           // the record's spill slot overflowed: draw this replicate again with
           // the warp's global spill buffer (same stream, same values); the
           // block form's histogram is rebuilt in place in the record
@@ -1589,7 +1592,7 @@ __global__ void __launch_bounds__(kWarps * 32, F32 ? PL_FIN_MIN_BLOCKS_F32 : PL_
         }
         PL_PHASE(0);
         // resolve the draws that fell beyond the threshold table (binary64 inversion)
-        for (int64_t k = lane; k < s; k += 32) {
+        for (int64_t k = lane; tags && k < s; k += 32) {
           const uint64_t x = sp[k];
           if (x & kTailTag) {
             bool beyond;

@@ -73,6 +73,11 @@ struct FinishLaunch {
   size_t arena_bytes;     // per warp
   Counters *ctr;
   int blocks;             // persistent grid size
+  // the wave's tail queue: when it did not overflow, the tail kernel has
+  // resolved every draw a sampler left beyond the table, and only replicates
+  // drawn again here can hold such draws; null: the records may hold them
+  const unsigned int *tq_count;
+  uint32_t tq_cap;
 };
 int finish_kernel_blocks_per_sm(bool f32);
 size_t finish_kernel_smem_bytes();
