@@ -43,12 +43,12 @@ METRIC = "KS replicates/sec and samples/sec per (alpha,n) vs roofline; p50/p99 f
 MUL_PER_DRAW = 5
 MUL_LANES_PER_SM = 32
 
-# DRAM bytes per replicate of the sampler from one ncu capture (sweep at 4,000
-# replicates per cell: 91.9 MB over 360,000 replicates in its two launches,
-# mostly the replicate records written), keyed by the hash of the kernel
-# sources it was taken on (reported as null once they change).  The bench
-# scales it to a launch by the replicates per launch.
-TRAFFIC_PER_REPLICATE = {"bfe49f99bb2233cd": (9.987328e6 + 74.10944e6 + 3.624192e6 + 4.176896e6) / 360000}
+# DRAM bytes per replicate of the sampler from one ncu capture (sweep at 33,000
+# replicates per cell, 2.97e6 replicates in one wave: 1,509 MB in its two
+# launches, mostly the replicate records written), keyed by the hash of the
+# kernel sources it was taken on (reported as null once they change).  The
+# bench scales it to a launch by the replicates per launch.
+TRAFFIC_PER_REPLICATE = {"54f58ea48866146a": (72.602112e6 + 1050.500096e6 + 55.8144e6 + 330.102016e6) / 2.97e6}
 
 
 def kernel_source_hash() -> str:
@@ -782,14 +782,15 @@ def per_cell_rates(ctx, cells, seed: int, qs, prec: int, mul_peak_gmul: float, f
     return rows
 
 
-# Finisher figures from one ncu capture of the sweep at 4,000 replicates per
-# cell (FP32-bulk), keyed by the hash of the kernel sources they were taken on
+# Finisher figures from one ncu capture of the sweep at 33,000 replicates per
+# cell (FP32-bulk; from 32,768 replicates a cell takes the long lanes, as at
+# full size), keyed by the hash of the kernel sources they were taken on
 # (reported as null once the sources change): DRAM bytes read per replicate
 # (its replicate records) and binary64 operations per replicate (DFMA counted
 # as two, DADD and DMUL as one), mostly the fit.
-FINISHER_NCU = {"bfe49f99bb2233cd": {
-    "dram_read_per_replicate": 325.596416e6 / 360000,
-    "f64_ops_per_replicate": (40.661756e6 + 29.640232e6 + 2 * 21.632840e6) / 360000,
+FINISHER_NCU = {"54f58ea48866146a": {
+    "dram_read_per_replicate": 2804.329216e6 / 2.97e6,
+    "f64_ops_per_replicate": (333.951250e6 + 243.501708e6 + 2 * 176.302172e6) / 2.97e6,
     # one alpha = 3.5, n = 10 cell of 200,000 replicates (no spills, trivial KS): the fit alone
     "fit_f64_ops": (4.806451e6 + 2.804522e6 + 2 * 6.206738e6) / 200000}}
 ALGO_BYTES_PER_REPLICATE = 16  # D (binary32 or binary64) and alpha-hat (binary64) out
