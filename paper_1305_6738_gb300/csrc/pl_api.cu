@@ -37,6 +37,7 @@ struct pl_ctx {
   int finish_blocks_per_sm[2] = {0, 0};
   int sample_blocks_per_sm = 0;
   int block_sampler_per_sm = 0;
+  int lane_sampler_per_sm = 0;
   int64_t warp_split = 16384;    // n above this: block form
   int item_reps = 0;             // warp-form replicates per work item (0: sized by the plan)
   int hist_shift = 0;            // dense bins of a warp-form replicate: the default times 2^hist_shift
@@ -224,6 +225,7 @@ struct Wave {
   size_t first, count;             // items [first, first + count)
   size_t wide;                     // the first `wide` items are block-form cells
   size_t wide_inl, warp_inl;       // of the block-form and of the warp-form items, the first so many bin inline
+  size_t lane;                     // the next `lane` items (after the block form) are drawn in the lane form
 };
 
 struct SimPlan {
@@ -287,6 +289,8 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     // is lower.  Decided per cell, so a cell's results never depend on what
     // it is simulated with.
     cd.lane_bins = x.replicates >= kLaneLongMinReps ? kLaneBinsLong : kLaneBinsShort;
+    // small histograms: one thread per replicate draws the whole sample
+    cd.lane_sample = (!cd.wide && cd.H <= kLaneSampleBins) ? 1u : 0u;
     cd.purpose = purpose;
     cd.out_off = sp.total_R;
     auto fi = fit_of.find(x.xmin);
@@ -319,6 +323,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
   for (int c = 0; c < ncells; ++c) order[c] = c;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     if (sp.cells[a].wide != sp.cells[b].wide) return sp.cells[a].wide > sp.cells[b].wide;
+    if (sp.cells[a].lane_sample != sp.cells[b].lane_sample) return sp.cells[a].lane_sample > sp.cells[b].lane_sample;
     if (sp.cells[a].inline_bins != sp.cells[b].inline_bins) return sp.cells[a].inline_bins > sp.cells[b].inline_bins;
     if (sp.cells[a].law != sp.cells[b].law) return sp.cells[a].law < sp.cells[b].law;
     return sp.cells[a].n > sp.cells[b].n;
@@ -335,7 +340,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
   int64_t warp_item = kItemReps;
   while (warp_item > 32 && warp_R / warp_item < fill) warp_item /= 2;
   if (ctx->item_reps) warp_item = ctx->item_reps;
-  size_t wd = 0, ws = 0, wm = 0, first = 0, nwide = 0, nwide_inl = 0, nwarp_inl = 0;
+  size_t wd = 0, ws = 0, wm = 0, first = 0, nwide = 0, nwide_inl = 0, nwarp_inl = 0, nlane = 0;
   double wt = 0.0;  // expected beyond-table draws of the wave
   auto close_tail = [&]() {
     const double cap = std::ceil(2.0 * wt + 10.0 * std::sqrt(wt) + 1024.0);
@@ -356,15 +361,16 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
       const size_t d = (size_t)it.nrep * cd.H * (cd.wide ? 2 : 1), sp_ = (size_t)it.nrep * cd.scap, m = it.nrep;
       const size_t bytes_after = (wd + d) * 2 + (ws + sp_) * 8 + (wm + m) * 8;
       if (sp.items.size() > first && bytes_after > wave_budget) {
-        sp.waves.push_back({first, sp.items.size() - first, nwide, nwide_inl, nwarp_inl});
+        sp.waves.push_back({first, sp.items.size() - first, nwide, nwide_inl, nwarp_inl, nlane});
         close_tail();
         first = sp.items.size();
         wd = ws = wm = 0;
-        nwide = nwide_inl = nwarp_inl = 0;
+        nwide = nwide_inl = nwarp_inl = nlane = 0;
         wt = 0.0;
       }
       if (cd.wide) ++nwide;
-      if (cd.inline_bins) ++(cd.wide ? nwide_inl : nwarp_inl);
+      if (cd.lane_sample) ++nlane;
+      else if (cd.inline_bins) ++(cd.wide ? nwide_inl : nwarp_inl);
       wt += (double)it.nrep * (double)cd.n * q_tail;
       it.dense_off = wd;
       it.spill_off = ws;
@@ -378,7 +384,7 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
       sp.items.push_back(it);
     }
   }
-  sp.waves.push_back({first, sp.items.size() - first, nwide, nwide_inl, nwarp_inl});
+  sp.waves.push_back({first, sp.items.size() - first, nwide, nwide_inl, nwarp_inl, nlane});
   close_tail();
   if (ctx->dbg_tail_cap) sp.tail_cap = std::min(sp.tail_cap, ctx->dbg_tail_cap);
   return PL_OK;
@@ -546,24 +552,29 @@ pl_status run_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, uint64_t seed, 
     PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
     PL_CUDA(cudaMemsetAsync(b.tq_count, 0, sizeof(unsigned int), st));
     if (wev) PL_CUDA(cudaEventRecord(wev[0], st));
-    // the wave's items in four runs: block form (inline binning, then not),
-    // warp form (likewise); a launch per nonempty run, each with its own count
-    const size_t run_first[4] = {w.first, w.first + w.wide_inl, w.first + w.wide, w.first + w.wide + w.warp_inl};
-    const size_t run_count[4] = {w.wide_inl, w.wide - w.wide_inl, w.warp_inl, w.count - w.wide - w.warp_inl};
+    // the wave's items in five runs: block form (inline binning, then not),
+    // lane form, warp form (inline binning, then not); a launch per nonempty
+    // run, each with its own count
+    const size_t wl = w.first + w.wide + w.lane;  // the first warp-form item
+    const size_t run_first[5] = {w.first, w.first + w.wide_inl, w.first + w.wide, wl, wl + w.warp_inl};
+    const size_t run_count[5] = {w.wide_inl, w.wide - w.wide_inl, w.lane, w.warp_inl,
+                                 w.count - w.wide - w.lane - w.warp_inl};
     bool counter_used = false;
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < 5; ++r) {
       if (!run_count[r]) continue;
       if (counter_used) PL_CUDA(cudaMemsetAsync(&ctx->ctr->work_next, 0, sizeof(unsigned int), st));
       counter_used = true;
       sl.items = b.items + run_first[r];
       sl.nitems = (uint32_t)run_count[r];
-      const bool inl = (r & 1) == 0;
       if (r < 2) {
         sl.blocks = (int)std::min<size_t>((size_t)b.block_sampler_blocks, run_count[r]);
-        PL_CUDA(launch_sample_block(sl, inl, st));
+        PL_CUDA(launch_sample_block(sl, r == 0, st));
+      } else if (r == 2) {
+        sl.blocks = (int)std::min<size_t>((size_t)ctx->num_sms * std::max(1, ctx->lane_sampler_per_sm), run_count[r]);
+        PL_CUDA(launch_sample_lane(sl, st));
       } else {
         sl.blocks = (int)std::min<size_t>((size_t)b.sample_blocks, run_count[r]);
-        PL_CUDA(launch_sample_hist(sl, inl, st));
+        PL_CUDA(launch_sample_hist(sl, r == 3, st));
       }
       ctx->launches += 1;
       if (trace) ++ctx->traced_sample_launches;
@@ -753,6 +764,7 @@ pl_status pl_create(pl_ctx **out, int device, size_t mem_budget_bytes) {
   ctx->finish_blocks_per_sm[1] = finish_kernel_blocks_per_sm(true);
   ctx->sample_blocks_per_sm = sample_kernel_blocks_per_sm();
   ctx->block_sampler_per_sm = block_sampler_blocks_per_sm();
+  ctx->lane_sampler_per_sm = sample_lane_blocks_per_sm();
   cudaGetLastError();
   *out = ctx;
   return PL_OK;

@@ -50,6 +50,12 @@ constexpr int kHMax = 1024;                 // dense histogram bins per warp
 constexpr int kLaneSpills = 8;
 constexpr uint32_t kLaneBinsLong = 256, kLaneBinsShort = 128;
 constexpr int64_t kLaneLongMinReps = 32768;  // cells with at least this many replicates take the long lanes
+// Warp-form cells whose dense histogram has at most this many bins (small n)
+// are drawn by the lane-form sampler, one thread per replicate.
+#ifndef PL_LANE_SAMPLE_BINS
+#define PL_LANE_SAMPLE_BINS 64
+#endif
+constexpr uint32_t kLaneSampleBins = PL_LANE_SAMPLE_BINS;
 constexpr int kHWide = 8192;                // dense histogram bins per block (block form)
 #ifndef PL_FIN_WARPS
 #define PL_FIN_WARPS 8
@@ -113,6 +119,7 @@ struct Cell {
   uint32_t inline_bins;   // draw loop: bin single-valued draws beyond the first four values at once (heavy tails)
   uint32_t lane_bins;     // finisher: warp-form replicates with a largest bin below this (and at most
                           // kLaneSpills spills) are finished by one lane each
+  uint32_t lane_sample;   // drawn by the lane-form sampler (warp form, H <= kLaneSampleBins)
 };
 
 // A block-sized batch of replicates of one cell, with the offsets of its

@@ -1307,6 +1307,142 @@ cudaError_t launch_sample_hist(const SampleLaunch &a, bool inl, cudaStream_t st)
   return cudaGetLastError();
 }
 
+// Lane form (warp-form cells of histograms of at most kLaneSampleBins bins,
+// small n): one thread per replicate of a work item draws all its values, with
+// no warp-wide steps.  A value's high word takes the lane's copy of the
+// increment table (the first four values count in four 7-bit register fields,
+// n < 128); any other draw reads the fine guide and, where the bucket holds
+// several values, searches the staged table (its low word only when a
+// threshold lies in the draw's interval or the answer lies beyond the table).
+// Bins below H go to the thread's own histogram in shared memory (word w of
+// thread t at w * kLaneSampleThreads + t, so a warp's accesses never share a
+// bank), values beyond H to the record's spill slot, draws beyond the table to
+// the tail queue.  The record (dense counts up to tmax, spills, meta) is the
+// one the warp form writes: the finisher cannot tell the two apart.
+constexpr int kLaneSampleThreads = kItemReps;
+constexpr int kLaneSampleWords = kLaneSampleBins / 2;
+
+size_t sample_lane_smem_bytes() {
+  return (size_t)kL1 * 8 + kFine * 4 + kIncBytes + (size_t)kLaneSampleWords * kLaneSampleThreads * 4 + 16 + 16;
+}
+
+__global__ void __launch_bounds__(kLaneSampleThreads) sample_lane_kernel(SampleLaunch a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint64_t *sT = reinterpret_cast<uint64_t *>(smem);
+  uint32_t *sG = reinterpret_cast<uint32_t *>(smem + kL1 * 8);
+  uint32_t *sInc = reinterpret_cast<uint32_t *>(smem + kL1 * 8 + kFine * 4);
+  uint32_t *sH = sInc + kIncBuckets * 32;
+  uint32_t *s_item = sH + kLaneSampleWords * kLaneSampleThreads;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(s_item + 4);
+  StagedLaw staged{sT, sG, mbar, sInc};
+  const int t = threadIdx.x, lane = t & 31;
+  uint32_t *hist = sH + t;  // word w at hist[w * kLaneSampleThreads]
+  for (int w = 0; w < kLaneSampleWords; ++w) hist[w * kLaneSampleThreads] = 0;
+  const TailQueue tq{a.tq_pos, a.tq_law, a.tq_count, a.tq_cap};
+  if (t == 0) {
+    mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);  // never arrived at: the wait-timeout test hook's flag
+  }
+  __syncthreads();
+  uint32_t phase = 0, loaded = 0xffffffffu;
+  const uint32_t *inc = sInc + lane;  // the lane's copy: bucket j at inc[32 j]
+  for (;;) {
+    if (t == 0)  // no further items once a wait has run out: records may be incomplete
+      *s_item = (*(volatile unsigned int *)&a.ctr->status & kErrTimeout) ? a.nitems : atomicAdd(&a.ctr->work_next, 1u);
+    __syncthreads();
+    const uint32_t item = *s_item;
+    if (item >= a.nitems) break;
+    const WorkItem wi = a.items[item];
+    const Cell cell = a.cells[wi.cell];
+    const Law law = a.laws[cell.law];
+    if (cell.law != loaded) {
+      if (!stage_law(staged, law, phase, a.ctr)) return;
+      loaded = cell.law;
+    }
+    if ((uint32_t)t < wi.nrep) {
+      const uint32_t j = (uint32_t)t, rep = wi.r0 + j;
+      const uint32_t n = (uint32_t)cell.n, H = cell.H;
+      const uint64_t pos0 = wi.spill_off + (uint64_t)j * cell.scap;
+      uint64_t *spill = a.rec.spill + pos0;
+      int s = 0;  // spills (all of them: a count beyond the slot makes the finisher draw again)
+      uint32_t acc = 0;
+      auto spill_value = [&](uint64_t v) {
+        if (s < (int)cell.scap) spill[s] = v;
+        ++s;
+      };
+      auto bin = [&](uint32_t b) {
+        if (b < H) hist[(b >> 1) * kLaneSampleThreads] += 1u << ((b & 1u) << 4);
+        else spill_value(cell.xmin + b);
+      };
+      auto tagged = [&](uint64_t m) {
+        if (s < (int)cell.scap) {
+          const unsigned q = atomicAdd(tq.count, 1u);
+          if (q < tq.cap) {
+            tq.pos[q] = pos0 + (uint64_t)s;
+            tq.law[q] = cell.law;
+          }
+        }
+        spill_value(kTailTag | m);
+      };
+      auto step = [&](uint32_t h, uint32_t i) {
+        const uint32_t e = inc[(h >> (32 - kIncBits)) << 5];
+        acc += e;
+        if ((int32_t)e >= 0) return;
+        const uint32_t gw = sG[h >> (32 - kFineBits)];
+        uint32_t b = gw & kGuideIndex;
+        if (gw & kGuideMulti) {
+          b = lookup_index<kFineBits>(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m_first(h));
+          if (b < law.L2 && (b == 0 || table_at(sT, law.T, b - 1) > m_last(h))) {
+            bin(b);
+            return;
+          }
+        } else if (b < law.L2) {
+          bin(b);
+          return;
+        }
+        const uint64_t m = draw_m_full(h, i, rep, cell.cell_id, cell.purpose, a.rk.k[0], a.rk.k[1]);
+        b = lookup_index<kFineBits>(sT, sG, law.T, law.L2, law.xmin_f, law.tail_c, law.tail_e, m);
+        if (b < law.L2) bin(b);
+        else tagged(m);
+      };
+      for (uint32_t p = 0; 4u * p < n; ++p) {
+        const uint4 w = philox4x32_10_rk(make_uint4(p, rep, cell.cell_id, cell.purpose), a.rk);
+        const uint32_t i0 = 4u * p;
+        step(w.x, i0);
+        if (i0 + 1u < n) step(w.y, i0 + 1u);
+        if (i0 + 2u < n) step(w.z, i0 + 2u);
+        if (i0 + 3u < n) step(w.w, i0 + 3u);
+      }
+      // the first four values' counts (7-bit fields, n < 128) into bins 0..3
+      hist[0] += (acc & 0x7fu) | (((acc >> 8) & 0x7fu) << 16);
+      hist[kLaneSampleThreads] += ((acc >> 16) & 0x7fu) | (((acc >> 24) & 0x7fu) << 16);
+      int tw = (int)(H >> 1) - 1;
+      while (tw >= 0 && hist[tw * kLaneSampleThreads] == 0u) --tw;
+      const int tmax = tw < 0 ? -1 : 2 * tw + ((hist[tw * kLaneSampleThreads] >> 16) ? 1 : 0);
+      uint32_t *dense = reinterpret_cast<uint32_t *>(a.rec.dense + wi.dense_off + (uint64_t)j * H);
+      for (int w = 0; w <= tw; ++w) {
+        dense[w] = hist[w * kLaneSampleThreads];
+        hist[w * kLaneSampleThreads] = 0;
+      }
+      a.rec.meta[wi.meta_off + j] = make_int2(tmax, s);
+    }
+    __syncthreads();
+  }
+}
+
+int sample_lane_blocks_per_sm() {
+  int nb = 0;
+  const size_t smem = sample_lane_smem_bytes();
+  cudaFuncSetAttribute(sample_lane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_lane_kernel, kLaneSampleThreads, smem);
+  return nb;
+}
+
+cudaError_t launch_sample_lane(const SampleLaunch &a, cudaStream_t st) {
+  sample_lane_kernel<<<a.blocks, kLaneSampleThreads, sample_lane_smem_bytes(), st>>>(a);
+  return cudaGetLastError();
+}
+
 // Copy the dense counts 0..tmax of a warp-form record (16-byte aligned, H >= 32
 // bins) to the warp's shared memory with 16-byte loads, so that the scans
 // below read them on chip instead of one dependent global load per bin.

@@ -52,6 +52,8 @@ struct SampleLaunch {
 int sample_kernel_blocks_per_sm();
 size_t sample_kernel_smem_bytes();
 cudaError_t launch_sample_hist(const SampleLaunch &a, bool inl, cudaStream_t st);
+int sample_lane_blocks_per_sm();
+cudaError_t launch_sample_lane(const SampleLaunch &a, cudaStream_t st);
 int block_sampler_blocks_per_sm();
 cudaError_t launch_sample_block(const SampleLaunch &a, bool inl, cudaStream_t st);
 cudaError_t launch_tail_queue_raw(const Law *laws, uint64_t *pos, uint32_t *law, unsigned int *count,
