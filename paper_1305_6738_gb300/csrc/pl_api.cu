@@ -202,14 +202,18 @@ uint32_t hist_bins(int64_t n, int shift = 0) {
   return (uint32_t)std::min<int64_t>(kHMax, std::max<int64_t>(32, H));
 }
 
+// P(X >= xmin + H) by the continuous tail approximation.
+double tail_beyond(double alpha, uint64_t xmin, uint32_t H) {
+  const double x = (double)xmin;
+  const double Zapprox = std::pow(x, -alpha) + std::pow(x + 0.5, 1.0 - alpha) / (alpha - 1.0);
+  return std::min(1.0, std::pow(x + H - 0.5, 1.0 - alpha) / ((alpha - 1.0) * Zapprox));
+}
+
 // Spill slot of a replicate record: about twice the expected number of draws
 // at or beyond xmin + H plus ten standard deviations (continuous tail
 // approximation); a replicate that overflows it is drawn again by the finisher.
 uint32_t spill_capacity(double alpha, uint64_t xmin, int64_t n, uint32_t H) {
-  const double x = (double)xmin;
-  const double Zapprox = std::pow(x, -alpha) + std::pow(x + 0.5, 1.0 - alpha) / (alpha - 1.0);
-  const double Q = std::pow(x + H - 0.5, 1.0 - alpha) / ((alpha - 1.0) * Zapprox);
-  const double mu = (double)n * std::min(1.0, Q);
+  const double mu = (double)n * tail_beyond(alpha, xmin, H);
   const double cap = std::ceil(2.0 * mu + 10.0 * std::sqrt(mu) + 32.0);
   return (uint32_t)std::max<double>(1.0, std::min<double>((double)n, cap));
 }
@@ -289,8 +293,14 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     // is lower.  Decided per cell, so a cell's results never depend on what
     // it is simulated with.
     cd.lane_bins = x.replicates >= kLaneLongMinReps ? kLaneBinsLong : kLaneBinsShort;
-    // small histograms: one thread per replicate draws the whole sample
-    cd.lane_sample = (!cd.wide && cd.H <= kLaneSampleBins) ? 1u : 0u;
+    // light tails: kLaneSampleBins dense bins when at most one value per
+    // replicate is expected beyond them (those become spills), so that the
+    // records are short and almost every replicate is finished by a lane
+    if (!cd.wide && cd.H > kLaneSampleBins && (double)x.n * tail_beyond(x.alpha, x.xmin, kLaneSampleBins) <= 1.0)
+      cd.H = kLaneSampleBins;
+    // small histograms of small samples: one thread per replicate draws the
+    // whole sample
+    cd.lane_sample = (!cd.wide && cd.H <= kLaneSampleBins && x.n <= kLaneSampleNMax) ? 1u : 0u;
     cd.purpose = purpose;
     cd.out_off = sp.total_R;
     auto fi = fit_of.find(x.xmin);

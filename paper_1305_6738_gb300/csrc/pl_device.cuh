@@ -56,6 +56,12 @@ constexpr int64_t kLaneLongMinReps = 32768;  // cells with at least this many re
 #define PL_LANE_SAMPLE_BINS 64
 #endif
 constexpr uint32_t kLaneSampleBins = PL_LANE_SAMPLE_BINS;
+// ... and at most this many values per replicate (a light-tailed cell of more
+// values may have kLaneSampleBins bins too; it stays in the warp form).
+#ifndef PL_LANE_SAMPLE_NMAX
+#define PL_LANE_SAMPLE_NMAX 100
+#endif
+constexpr int64_t kLaneSampleNMax = PL_LANE_SAMPLE_NMAX;
 constexpr int kHWide = 8192;                // dense histogram bins per block (block form)
 #ifndef PL_FIN_WARPS
 #define PL_FIN_WARPS 8

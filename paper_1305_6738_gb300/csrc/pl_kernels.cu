@@ -1307,11 +1307,12 @@ cudaError_t launch_sample_hist(const SampleLaunch &a, bool inl, cudaStream_t st)
   return cudaGetLastError();
 }
 
-// Lane form (warp-form cells of histograms of at most kLaneSampleBins bins,
-// small n): one thread per replicate of a work item draws all its values, with
-// no warp-wide steps.  A value's high word takes the lane's copy of the
-// increment table (the first four values count in four 7-bit register fields,
-// n < 128); any other draw reads the fine guide and, where the bucket holds
+// Lane form (warp-form cells of histograms of at most kLaneSampleBins bins:
+// small n, or light tails with up to kLaneSampleNMax values): one thread per
+// replicate of a work item draws all its values, with no warp-wide steps.  A
+// value's high word takes the lane's copy of the increment table (the first
+// four values count in four 7-bit register fields, flushed every kFlushBlocks
+// Philox blocks); any other draw reads the fine guide and, where the bucket holds
 // several values, searches the staged table (its low word only when a
 // threshold lies in the draw's interval or the answer lies beyond the table).
 // Bins below H go to the thread's own histogram in shared memory (word w of
@@ -1405,6 +1406,13 @@ __global__ void __launch_bounds__(kLaneSampleThreads) sample_lane_kernel(SampleL
         if (b < law.L2) bin(b);
         else tagged(m);
       };
+      // the first four values' counts (7-bit fields) into bins 0..3, every
+      // kFlushBlocks Philox blocks (at most 124 increments)
+      auto flush = [&]() {
+        hist[0] += (acc & 0x7fu) | (((acc >> 8) & 0x7fu) << 16);
+        hist[kLaneSampleThreads] += ((acc >> 16) & 0x7fu) | (((acc >> 24) & 0x7fu) << 16);
+        acc = 0;
+      };
       for (uint32_t p = 0; 4u * p < n; ++p) {
         const uint4 w = philox4x32_10_rk(make_uint4(p, rep, cell.cell_id, cell.purpose), a.rk);
         const uint32_t i0 = 4u * p;
@@ -1412,10 +1420,9 @@ __global__ void __launch_bounds__(kLaneSampleThreads) sample_lane_kernel(SampleL
         if (i0 + 1u < n) step(w.y, i0 + 1u);
         if (i0 + 2u < n) step(w.z, i0 + 2u);
         if (i0 + 3u < n) step(w.w, i0 + 3u);
+        if (p % kFlushBlocks == kFlushBlocks - 1) flush();
       }
-      // the first four values' counts (7-bit fields, n < 128) into bins 0..3
-      hist[0] += (acc & 0x7fu) | (((acc >> 8) & 0x7fu) << 16);
-      hist[kLaneSampleThreads] += ((acc >> 16) & 0x7fu) | (((acc >> 24) & 0x7fu) << 16);
+      flush();
       int tw = (int)(H >> 1) - 1;
       while (tw >= 0 && hist[tw * kLaneSampleThreads] == 0u) --tw;
       const int tmax = tw < 0 ? -1 : 2 * tw + ((hist[tw * kLaneSampleThreads] >> 16) ? 1 : 0);
