@@ -293,11 +293,15 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
     // is lower.  Decided per cell, so a cell's results never depend on what
     // it is simulated with.
     cd.lane_bins = x.replicates >= kLaneLongMinReps ? kLaneBinsLong : kLaneBinsShort;
-    // light tails: kLaneSampleBins dense bins when at most one value per
-    // replicate is expected beyond them (those become spills), so that the
-    // records are short and almost every replicate is finished by a lane
-    if (!cd.wide && cd.H > kLaneSampleBins && (double)x.n * tail_beyond(x.alpha, x.xmin, kLaneSampleBins) <= 1.0)
-      cd.H = kLaneSampleBins;
+    // the fewest dense bins (64, 128 or 256) beyond which at most
+    // kLightSpills values per replicate are expected (those become spills), so
+    // that records are short and almost every replicate is finished by a lane
+    if (!cd.wide)
+      for (uint32_t h = kLaneSampleBins; h < cd.H && h <= kLaneBinsLong; h <<= 1)
+        if ((double)x.n * tail_beyond(x.alpha, x.xmin, h) <= kLightSpills) {
+          cd.H = h;
+          break;
+        }
     // small histograms of small samples: one thread per replicate draws the
     // whole sample
     cd.lane_sample = (!cd.wide && cd.H <= kLaneSampleBins && x.n <= kLaneSampleNMax) ? 1u : 0u;

@@ -62,6 +62,12 @@ constexpr uint32_t kLaneSampleBins = PL_LANE_SAMPLE_BINS;
 #define PL_LANE_SAMPLE_NMAX 100
 #endif
 constexpr int64_t kLaneSampleNMax = PL_LANE_SAMPLE_NMAX;
+// Expected values per replicate beyond the dense bins that a warp-form cell's
+// shortened histogram may leave to the spills.
+#ifndef PL_LIGHT_SPILLS
+#define PL_LIGHT_SPILLS 6.0
+#endif
+constexpr double kLightSpills = PL_LIGHT_SPILLS;
 constexpr int kHWide = 8192;                // dense histogram bins per block (block form)
 #ifndef PL_FIN_WARPS
 #define PL_FIN_WARPS 8
