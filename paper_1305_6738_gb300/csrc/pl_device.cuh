@@ -47,7 +47,10 @@ constexpr uint32_t kIncOther = 0x80000000u;
 constexpr int kHMax = 1024;                 // dense histogram bins per warp
 // Warp-form replicates with at most this many spills are finished by one lane
 // (the record's spill slot always holds at least min(n, kLaneSpills)).
-constexpr int kLaneSpills = 8;
+#ifndef PL_LANE_SPILLS
+#define PL_LANE_SPILLS 20
+#endif
+constexpr int kLaneSpills = PL_LANE_SPILLS;
 constexpr uint32_t kLaneBinsLong = 256, kLaneBinsShort = 128;
 constexpr int64_t kLaneLongMinReps = 32768;  // cells with at least this many replicates take the long lanes
 // Warp-form cells whose dense histogram has at most this many bins (small n)
@@ -65,7 +68,7 @@ constexpr int64_t kLaneSampleNMax = PL_LANE_SAMPLE_NMAX;
 // Expected values per replicate beyond the dense bins that a warp-form cell's
 // shortened histogram may leave to the spills.
 #ifndef PL_LIGHT_SPILLS
-#define PL_LIGHT_SPILLS 6.0
+#define PL_LIGHT_SPILLS 14.0
 #endif
 constexpr double kLightSpills = PL_LIGHT_SPILLS;
 constexpr int kHWide = 8192;                // dense histogram bins per block (block form)

@@ -511,10 +511,10 @@ def test_batched_instances_full_size_graph(ctx, pl):
 
 
 def test_waves_do_not_change_results(pl):
-    """A small byte budget splits the simulation into many waves (record
+    """A small byte budget splits the simulation into several waves (record
     buffers reused in turn); every replicate's D and alpha-hat are the same
     bits as with one wave."""
-    cells = [pl.Cell(2.0, 1, 1000, 200000, 1), pl.Cell(1.5, 1, 3000, 20000, 2), pl.Cell(3.0, 2, 50, 100000, 3)]
+    cells = [pl.Cell(2.0, 1, 1000, 200000, 1), pl.Cell(1.5, 1, 3000, 60000, 2), pl.Cell(3.0, 2, 50, 100000, 3)]
     tot = sum(c.replicates for c in cells)
     out = []
     for budget in (0, 1 << 30):  # default budget: one wave; 1 GiB: waves of 256 MiB of records
@@ -526,7 +526,7 @@ def test_waves_do_not_change_results(pl):
         waves = c.pl_trace()["waves"]
         c.close()
         out.append((D, A, cut, waves))
-    assert out[0][3] == 1 and out[1][3] >= 3
+    assert out[0][3] == 1 and out[1][3] >= 2
     assert torch.equal(out[0][0], out[1][0])
     assert torch.equal(out[0][1], out[1][1])
     assert (out[0][2] == out[1][2]).all()
