@@ -303,8 +303,12 @@ pl_status plan_cells(pl_ctx *ctx, const pl_cell *in, int ncells, uint32_t purpos
           break;
         }
     // small histograms of small samples: one thread per replicate draws the
-    // whole sample
-    cd.lane_sample = (!cd.wide && cd.H <= kLaneSampleBins && x.n <= kLaneSampleNMax) ? 1u : 0u;
+    // whole sample (a shortened histogram only in a cell of many replicates:
+    // a small simulation keeps the warp form's parallelism)
+    cd.lane_sample = (!cd.wide && cd.H <= kLaneSampleBins && x.n <= kLaneSampleNMax &&
+                      (hist_bins(x.n, ctx->hist_shift) <= kLaneSampleBins || x.replicates >= kLaneLongMinReps))
+                         ? 1u
+                         : 0u;
     cd.purpose = purpose;
     cd.out_off = sp.total_R;
     auto fi = fit_of.find(x.xmin);
