@@ -750,11 +750,45 @@ __device__ void warp_radix_sort(uint64_t *a, uint64_t *b, int64_t s, uint32_t *c
   }
 }
 
+// Bitonic sort of 32 < s <= 64 values in place: lane l holds elements 2l and
+// 2l + 1 in registers (padding with the largest key); stride 1 is an exchange
+// within a lane, larger strides exchanges with lane l ^ (stride / 2).
+__device__ __forceinline__ void warp_bitonic_sort64(uint64_t *a, int64_t s, int lane) {
+  uint64_t v[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) v[k] = 2 * lane + k < s ? a[2 * lane + k] : ~0ull;
+#pragma unroll
+  for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride == 1) {
+        const bool up = ((2 * lane) & size) == 0;
+        const uint64_t mn = v[0] < v[1] ? v[0] : v[1], mx = v[0] < v[1] ? v[1] : v[0];
+        v[0] = up ? mn : mx;
+        v[1] = up ? mx : mn;
+      } else {
+        const int ls = stride >> 1;
+        const bool lower = (lane & ls) == 0, up = ((2 * lane) & size) == 0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const uint64_t y = __shfl_xor_sync(0xffffffffu, v[k], ls);
+          const uint64_t mn = v[k] < y ? v[k] : y, mx = v[k] < y ? y : v[k];
+          v[k] = (lower == up) ? mn : mx;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    if (2 * lane + k < s) a[2 * lane + k] = v[k];
+  __syncwarp();
+}
+
 // Sort the s spill values of one replicate, in place (up to 32: a bitonic
-// network across the lanes' registers; more: the warp radix sort with `pairs`
-// as the second buffer) and run-length encode them into interleaved
-// (value, count) pairs at `pairs` (room for 2 s entries).  Returns the number
-// of distinct values.
+// network across the lanes' registers; up to 64: the same with two values per
+// lane; more: the warp radix sort with `pairs` as the second buffer) and
+// run-length encode them into interleaved (value, count) pairs at `pairs`
+// (room for 2 s entries).  Returns the number of distinct values.
 __device__ int64_t spill_compact(uint64_t *spill, uint32_t *onchip, int64_t s, uint64_t *pairs,
                                  int lane, Counters *ctr) {
   if (s <= 0) return 0;
@@ -782,8 +816,12 @@ __device__ int64_t spill_compact(uint64_t *spill, uint32_t *onchip, int64_t s, u
     __syncwarp();
     return __popc(bal);
   }
-  if (s > kSortSmem && lane == 0) atomicAdd(&ctr->global_sorts, 1ull);
-  warp_radix_sort(spill, pairs, s, onchip, lane);
+  if (s <= 64) {
+    warp_bitonic_sort64(spill, s, lane);
+  } else {
+    if (s > kSortSmem && lane == 0) atomicAdd(&ctr->global_sorts, 1ull);
+    warp_radix_sort(spill, pairs, s, onchip, lane);
+  }
   const uint64_t *buf = spill;
   int64_t base = 0;
   for (int64_t i0 = 0; i0 < s; i0 += 32) {
