@@ -353,11 +353,13 @@ def tz_source_hash() -> str:
 # tables), keyed by the hash of its sources (null once they change).
 # The later keys are the same kernel after changes to pl_device.cuh that only
 # touch the untruncated samplers (a larger guide table; the lane-finish spill
-# limit and the inline-binning flag of a cell), which the truncated kernel does
-# not use (it has its own constants and cells).
+# limit and lane sizes, the lane-form sampler's limits, the shortened-histogram
+# bound and the per-cell flags), which the truncated kernel does not use (it
+# has its own constants and cells).
 TZ_TRAFFIC_PER_REPLICATE = {"bb5f053fedd20812": (57234944 + 148284928) / 45e6,
                             "a2952dc4a133b7a3": (57234944 + 148284928) / 45e6,
-                            "86ecba4b8d4d58e2": (57234944 + 148284928) / 45e6}
+                            "86ecba4b8d4d58e2": (57234944 + 148284928) / 45e6,
+                            "1141582e0e9bcfe7": (57234944 + 148284928) / 45e6}
 
 
 def tz_cpu_oracle_rate(cells, sample_reps: int, threads: int) -> dict:
