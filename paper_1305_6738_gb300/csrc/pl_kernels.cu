@@ -1073,19 +1073,34 @@ __device__ __forceinline__ void draw_queued(const uint64_t *sT, const uint32_t *
   };
   // the lane's copy of the increment table: entry of bucket j at inc_lane + 128 j
   const uint32_t inc_lane = (uint32_t)__cvta_generic_to_shared(sInc + lane);
+  const uint32_t hist_s = (uint32_t)__cvta_generic_to_shared(hist);
   auto step = [&](uint32_t h, uint32_t i) {
     uint32_t e;
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(e) : "r"(inc_lane + ((h >> (32 - kIncBits)) << 7)));
     acc += e;
-    if ((int32_t)e < 0) {
-      if (INL) {
-        // heavy tails: a single-valued bucket of the fine guide is binned here
-        const uint32_t gw = sG[h >> (32 - kFineBits)], b = gw & kGuideIndex;
-        if (!(gw & kGuideMulti) && b < law.L2) {
-          bin(b);
-          return;
-        }
-      }
+    if (INL) {
+      // heavy tails: nearly every warp has a lane beyond the first four
+      // values at each step, so the step takes no branch.  The fine-guide
+      // word is read for every draw; a single-valued bucket below H is binned
+      // by a predicated shared reduction, and every other draw beyond the
+      // first four values (multi-valued bucket, spill, beyond the table) is
+      // queued for the drain, which bins or searches it.
+      const uint32_t gw = sG[h >> (32 - kFineBits)], b = gw & kGuideIndex;
+      const bool beyond = (int32_t)e < 0;
+      const uint32_t direct = beyond && !(gw & kGuideMulti) && b < H;
+      const uint32_t queued = beyond && !direct;
+      const uint32_t addr = WIDE ? hist_s + 4u * b : hist_s + 2u * (b & ~1u);
+      const uint32_t v = WIDE ? 1u : 1u << ((b & 1u) << 4);
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %0, 0;\n\t@p red.shared.add.u32 [%1], %2;\n\t}" ::"r"(direct),
+          "r"(addr), "r"(v)
+          : "memory");
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %0, 0;\n\t@p st.shared.v2.u32 [%1], {%2, %3};\n\t}" ::"r"(queued),
+          "r"(qa), "r"(h), "r"(i)
+          : "memory");
+      qa += queued << 8;
+    } else if ((int32_t)e < 0) {
       asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(qa), "r"(h), "r"(i) : "memory");
       qa += 256u;
     }
