@@ -878,8 +878,11 @@ __device__ int64_t spill_compact(uint64_t *spill, uint32_t *onchip, int64_t s, u
 #define PL_SAMPLER_QCAP 8
 #endif
 constexpr int kAWarps = PL_SAMPLER_WARPS;
-constexpr int kARepsPerWarp = kItemReps / kAWarps;
-constexpr int kABlocksPerSM = kAWarps >= 32 ? 1 : 2;
+constexpr int kARepsPerWarp = (kItemReps + kAWarps - 1) / kAWarps;
+#ifndef PL_SAMPLER_BLOCKS
+#define PL_SAMPLER_BLOCKS (PL_SAMPLER_WARPS >= 24 ? 1 : 2)
+#endif
+constexpr int kABlocksPerSM = PL_SAMPLER_BLOCKS;
 
 struct TailQueue {
   uint64_t *pos;          // element index in the record spill buffer
