@@ -48,8 +48,8 @@ MUL_LANES_PER_SM = 32
 # launches, mostly the replicate records written), keyed by the hash of the
 # kernel sources it was taken on (reported as null once they change).  The
 # bench scales it to a launch by the replicates per launch.
-TRAFFIC_PER_REPLICATE = {"539daae9864228e9": (43.670528e6 + 62.925056e6 + 54.693888e6 + 768.537088e6 + 44.369664e6
-                                              + 115.008e6) / 2.97e6}
+TRAFFIC_PER_REPLICATE = {"ea8ed0c73be72e29": (43.672064e6 + 63.077632e6 + 54.589696e6 + 768.846336e6 + 44.230912e6
+                                              + 114.299904e6) / 2.97e6}
 
 
 def kernel_source_hash() -> str:
@@ -791,8 +791,8 @@ def per_cell_rates(ctx, cells, seed: int, qs, prec: int, mul_peak_gmul: float, f
 # (reported as null once the sources change): DRAM bytes read per replicate
 # (its replicate records) and binary64 operations per replicate (DFMA counted
 # as two, DADD and DMUL as one), mostly the fit.
-FINISHER_NCU = {"539daae9864228e9": {
-    "dram_read_per_replicate": 2154.081792e6 / 2.97e6,
+FINISHER_NCU = {"ea8ed0c73be72e29": {
+    "dram_read_per_replicate": 2155.349760e6 / 2.97e6,
     "f64_ops_per_replicate": (231.771286e6 + 170.849080e6 + 2 * 146.157496e6) / 2.97e6,
     # one alpha = 3.5, n = 10 cell of 200,000 replicates (no spills, trivial KS): the fit alone
     "fit_f64_ops": (4.806451e6 + 2.804522e6 + 2 * 6.206738e6) / 200000}}
