@@ -81,7 +81,11 @@ typedef struct {
 } pl_cell;
 
 /* Create a context on CUDA device `device`; the library's workspace never
- * exceeds mem_budget_bytes (0 = 40 GiB).  *out receives the context.
+ * exceeds mem_budget_bytes (0 = 40 GiB).  Besides the workspace, the context
+ * keeps the fit tables (Eq. 2's exponent as a function of the mean log, a
+ * function of xmin alone) of the first 16 values of xmin its calls use, about
+ * 0.2 MB each, and later calls copy them on the device instead of building
+ * them again.  *out receives the context.
  * Errors: PL_EINVAL (out NULL, bad device), PL_ECUDA. */
 pl_status pl_create(pl_ctx **out, int device, size_t mem_budget_bytes);
 
@@ -305,8 +309,8 @@ pl_status pl_bootstrap_pvalue(pl_ctx *ctx, const int32_t *x_dev, int64_t n,
  * paper has no serving layer; each request computes what pl_bootstrap_pvalue
  * computes (Eq. 2, Eq. 3 and the bootstrap p-value at alpha-hat), and the
  * engine only schedules them.
- * `workers` host threads each own a context (with the fit tables of every
- * xmin seen kept on the device) and a non-blocking stream, so up to `workers`
+ * `workers` host threads each own a context (with the fit tables of the
+ * xmin values seen kept on the device) and a non-blocking stream, so up to `workers`
  * requests run on the GPU at the same time.  A request is admitted, oldest
  * first, when a worker is free and its planned device workspace (sized at a
  * fitted exponent of 1.4; each worker's context also keeps to the budget)

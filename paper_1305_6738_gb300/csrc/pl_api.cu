@@ -53,9 +53,11 @@ struct pl_ctx {
   bool traced = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> wave_ev;   // 4 per wave: sampler start/end, finisher start/end
-  // Fit tables depend only on xmin; a serving context keeps them.
-  bool cache_fits = false;
-  std::map<uint64_t, FitTable> fit_cache;   // complete host copies (pointers into fit_mem)
+  // Fit tables depend only on xmin: the context keeps those of the first
+  // kFitCacheMax values of xmin it meets (nodes, guide and the finished
+  // FitTable in one device allocation each, outside the byte budget).
+  static constexpr size_t kFitCacheMax = 16;
+  std::map<uint64_t, FitTable *> fit_cache;  // xmin -> the cached FitTable (device)
   std::vector<void *> fit_mem;
   uint32_t traced_waves = 0;
   uint32_t traced_sample_launches = 0;
@@ -477,20 +479,23 @@ pl_status staging(pl_ctx *ctx, size_t bytes, uint8_t **out) {
 }
 
 pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t st) {
-  std::vector<size_t> fresh;  // fit tables to build
+  std::vector<size_t> fresh;                             // fit tables to build
+  std::vector<std::pair<size_t, FitTable *>> from, to;  // copies from / into the cache
   for (size_t i = 0; i < b.fits_host.size(); ++i) {
     const uint64_t xm = b.fits_host[i].xmin;
-    if (ctx->cache_fits) {
-      auto it = ctx->fit_cache.find(xm);
-      if (it != ctx->fit_cache.end()) {
-        b.fits_host[i] = it->second;
-        continue;
-      }
+    auto it = ctx->fit_cache.find(xm);
+    if (it != ctx->fit_cache.end()) {
+      from.push_back({i, it->second});
+      continue;
+    }
+    if (ctx->fit_cache.size() < pl_ctx::kFitCacheMax) {
       void *mem = nullptr;
-      PL_CUDA(cudaMalloc(&mem, sizeof(FitNode) * kFitNodes + sizeof(int) * kFitGuides));
+      const size_t tab = sizeof(FitNode) * kFitNodes + sizeof(int) * kFitGuides;
+      PL_CUDA(cudaMalloc(&mem, tab + sizeof(FitTable)));
       ctx->fit_mem.push_back(mem);
       b.fits_host[i].node = reinterpret_cast<FitNode *>(mem);
       b.fits_host[i].guide = reinterpret_cast<int *>(reinterpret_cast<FitNode *>(mem) + kFitNodes);
+      to.push_back({i, reinterpret_cast<FitTable *>(static_cast<uint8_t *>(mem) + tab)});
     }
     fresh.push_back(i);
   }
@@ -529,12 +534,15 @@ pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t
     for (size_t i : fresh) PL_CUDA(launch_fit_tables(b.fits_dev + i, 1, st));
     ctx->launches += 3 * fresh.size();
   }
-  if (ctx->cache_fits && !fresh.empty()) {  // keep the completed tables (guide origin set on device)
-    PL_CUDA(cudaMemcpyAsync(b.fits_host.data(), b.fits_dev, sizeof(FitTable) * b.fits_host.size(),
-                            cudaMemcpyDeviceToHost, st));
-    PL_CUDA(cudaStreamSynchronize(st));
-    for (size_t i : fresh) ctx->fit_cache[b.fits_host[i].xmin] = b.fits_host[i];
+  // stream-ordered device copies of the finished FitTable (its guide origin
+  // is set on the device): into the cache after a build, out of it for the
+  // tables built by an earlier call (after this call's upload overwrote them)
+  for (const auto &c : to) {
+    PL_CUDA(cudaMemcpyAsync(c.second, b.fits_dev + c.first, sizeof(FitTable), cudaMemcpyDeviceToDevice, st));
+    ctx->fit_cache[b.fits_host[c.first].xmin] = c.second;
   }
+  for (const auto &c : from)
+    PL_CUDA(cudaMemcpyAsync(b.fits_dev + c.first, c.second, sizeof(FitTable), cudaMemcpyDeviceToDevice, st));
   return PL_OK;
 }
 
@@ -721,7 +729,6 @@ pl_status read_status(pl_ctx *ctx, cudaStream_t st) {
 
 // Hooks for the serving engine (pl_server.cu).
 namespace pl {
-void ctx_enable_fit_cache(pl_ctx *ctx) { ctx->cache_fits = true; }
 uint64_t ctx_launches(const pl_ctx *ctx) { return ctx->launches; }
 
 // Device bytes a bootstrap request of n values and B replicates plans (the

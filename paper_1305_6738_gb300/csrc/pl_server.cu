@@ -21,7 +21,6 @@
 #include "pl_kernels.cuh"
 
 namespace pl {
-void ctx_enable_fit_cache(pl_ctx *ctx);
 size_t ctx_bootstrap_bytes(pl_ctx *ctx, int64_t n, uint64_t xmin, int64_t B);
 uint64_t ctx_launches(const pl_ctx *ctx);
 }  // namespace pl
@@ -164,7 +163,6 @@ pl_status pl_server_create(pl_server **out, int device, size_t mem_budget_bytes,
       delete srv;
       return st;
     }
-    pl::ctx_enable_fit_cache(w.ctx);
   }
   for (Worker &w : srv->workers) w.thread = std::thread(worker_loop, srv, &w);
   *out = srv;
