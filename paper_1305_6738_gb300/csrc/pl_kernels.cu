@@ -48,16 +48,15 @@ __global__ void law_z_kernel(Law *laws, int nlaws) {
 
 // T[i] = floor(Q(xmin+i) 2^53) + 1 and the log tables of xmin + i.
 // Entries whose survival needs Euler-Maclaurin direct terms (argument below
-// 10 + 1.5 alpha, at most ~100 entries) are left to law_fill_em_kernel.
+// 10 + 1.5 alpha, at most ~100 entries) are left to law_fill_em_block.
 __device__ __forceinline__ bool survival_needs_terms(const Law &law, uint32_t i) {
   return (double)(law.xmin + i) + 1.0 < 10.0 + 1.5 * law.alpha;
 }
 
-__global__ void law_fill_kernel(Law *laws) {
-  const Law law = laws[blockIdx.y];
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < law.L2 || i < (uint32_t)kLnTable;
-       i += stride) {
+// blocks b of nb (256 threads each) of one law
+__device__ __forceinline__ void law_fill_blocks(const Law &law, uint32_t b, uint32_t nb) {
+  const uint32_t stride = nb * blockDim.x;
+  for (uint32_t i = b * blockDim.x + threadIdx.x; i < law.L2 || i < (uint32_t)kLnTable; i += stride) {
     if (i < law.L2 && !survival_needs_terms(law, i)) {
       const double Q = survival(law.alpha, law.Z, law.xmin + i);
       law.T[i] = (uint64_t)(Q * 0x1p53) + 1ull;
@@ -76,9 +75,8 @@ __global__ void law_fill_kernel(Law *laws) {
 // lanes share the terms, a fixed-shape warp reduction adds them.
 constexpr int kFillEmWarps = 8;
 
-__global__ void __launch_bounds__(kFillEmWarps * 32) law_fill_em_kernel(Law *laws) {
-  const Law law = laws[blockIdx.y];
-  const uint32_t i = blockIdx.x * kFillEmWarps + (threadIdx.x >> 5);
+__device__ __forceinline__ void law_fill_em_block(const Law &law, uint32_t b) {
+  const uint32_t i = b * kFillEmWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= law.L2 || !survival_needs_terms(law, i)) return;  // warp-uniform
   const double a = (double)(law.xmin + i) + 1.0;
@@ -91,6 +89,17 @@ __global__ void __launch_bounds__(kFillEmWarps * 32) law_fill_em_kernel(Law *law
     hurwitz_em_tail<0, true>(law.alpha, a + (double)M, &t);
     law.T[i] = (uint64_t)((z + t) / law.Z * 0x1p53) + 1ull;
   }
+}
+
+// Both fills in one launch (they depend only on Z): the first kFillEmBlocks
+// blocks of a law take the entries with direct terms, the others the rest.
+constexpr uint32_t kFillEmBlocks = 128 / kFillEmWarps;  // entries with direct terms: i < 105 for alpha <= 64
+constexpr uint32_t kFillBlocks = 256;
+
+__global__ void __launch_bounds__(kFillEmWarps * 32) law_fill_kernel(Law *laws) {
+  const Law law = laws[blockIdx.y];
+  if (blockIdx.x < kFillEmBlocks) law_fill_em_block(law, blockIdx.x);
+  else law_fill_blocks(law, blockIdx.x - kFillEmBlocks, kFillBlocks);
 }
 
 // guide[j] = min{i < L2 : T[i] <= (j+1) 2^(53-g)}, or L2, with kGuideMulti
@@ -109,9 +118,8 @@ __device__ __forceinline__ uint32_t guide_bound(const Law &law, uint32_t j) {
 }
 
 template <int GB>
-__global__ void law_guide_kernel(Law *laws) {
-  const Law law = laws[blockIdx.y];
-  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void law_guide_block(const Law &law, uint32_t b) {
+  const uint32_t j = b * blockDim.x + threadIdx.x;
   if (j >= (1u << GB)) return;
   const uint32_t lo = guide_bound<GB>(law, j);
   const uint32_t hi = j ? guide_bound<GB>(law, j - 1) : law.L2;
@@ -131,24 +139,32 @@ __device__ __forceinline__ uint32_t answer_at(const Law &law, uint64_t m) {
   return lo;
 }
 
-__global__ void law_inc_kernel(Law *laws) {
-  const Law law = laws[blockIdx.y];
-  const uint32_t j = blockIdx.x * 8 + (threadIdx.x >> 5), l = threadIdx.x & 31;
+__device__ __forceinline__ void law_inc_block(const Law &law, uint32_t blk) {
+  const uint32_t j = blk * 8 + (threadIdx.x >> 5), l = threadIdx.x & 31;
   if (j >= (uint32_t)kIncBuckets) return;
   const uint64_t m_lo = ((uint64_t)j << (53 - kIncBits)) + 1ull, m_hi = (uint64_t)(j + 1) << (53 - kIncBits);
   const uint32_t a = answer_at(law, m_lo), b = answer_at(law, m_hi);
   law.inc[j * 32 + l] = (a == b && a < 4) ? 1u << (8 * a) : kIncOther;
 }
 
+// The guides and the increment table in one launch (they depend only on T):
+// blocks [0, 16) the 2^12-bucket guide, [16, 48) the 2^13-bucket guide,
+// [48, 80) the increment table, 256 threads each.
+constexpr uint32_t kGuideBlocks = kGuide / 256, kFineBlocks = kFine / 256, kIncBlocks = kIncBuckets / 8;
+
+__global__ void __launch_bounds__(256) law_index_kernel(Law *laws) {
+  const Law law = laws[blockIdx.y];
+  const uint32_t b = blockIdx.x;
+  if (b < kGuideBlocks) law_guide_block<kGuideBits>(law, b);
+  else if (b < kGuideBlocks + kFineBlocks) law_guide_block<kFineBits>(law, b - kGuideBlocks);
+  else law_inc_block(law, b - kGuideBlocks - kFineBlocks);
+}
+
 cudaError_t launch_law_setup(Law *laws_dev, int nlaws, cudaStream_t st) {
   if (nlaws <= 0) return cudaSuccess;
   law_z_kernel<<<(nlaws + 1) / 2, 64, 0, st>>>(laws_dev, nlaws);
-  law_fill_kernel<<<dim3(256, nlaws), 256, 0, st>>>(laws_dev);
-  // entries with direct terms: xmin + i + 1 < 10 + 1.5 alpha, i < 105 for alpha <= 64
-  law_fill_em_kernel<<<dim3(128 / kFillEmWarps, nlaws), kFillEmWarps * 32, 0, st>>>(laws_dev);
-  law_guide_kernel<kGuideBits><<<dim3(kGuide / 256, nlaws), 256, 0, st>>>(laws_dev);
-  law_guide_kernel<kFineBits><<<dim3(kFine / 256, nlaws), 256, 0, st>>>(laws_dev);
-  law_inc_kernel<<<dim3(kIncBuckets / 8, nlaws), 256, 0, st>>>(laws_dev);
+  law_fill_kernel<<<dim3(kFillEmBlocks + kFillBlocks, nlaws), kFillEmWarps * 32, 0, st>>>(laws_dev);
+  law_index_kernel<<<dim3(kGuideBlocks + kFineBlocks + kIncBlocks, nlaws), 256, 0, st>>>(laws_dev);
   return cudaGetLastError();
 }
 
