@@ -44,15 +44,12 @@ MUL_PER_DRAW = 5
 MUL_LANES_PER_SM = 32
 
 # DRAM bytes per replicate of the sampler from one ncu capture (sweep at 33,000
-# replicates per cell, 2.97e6 replicates in one wave: 1,089 MB in its three
+# replicates per cell, 2.97e6 replicates in one wave: 1,090 MB in its three
 # launches, mostly the replicate records written), keyed by the hash of the
 # kernel sources it was taken on (reported as null once they change).  The
-# bench scales it to a launch by the replicates per launch.  The second key
-# is the same sampler and finisher code after a change to the law set-up
-# kernels alone (the fills, guides and increment table merged into fewer
-# launches), which neither kernel counted here runs.
-_SAMPLER_BYTES_33K = (43.672064e6 + 63.077632e6 + 54.589696e6 + 768.846336e6 + 44.230912e6 + 114.299904e6) / 2.97e6
-TRAFFIC_PER_REPLICATE = {"ea8ed0c73be72e29": _SAMPLER_BYTES_33K, "02839dd94f8d082d": _SAMPLER_BYTES_33K}
+# bench scales it to a launch by the replicates per launch.
+TRAFFIC_PER_REPLICATE = {"77de4ab9190f9e35": (43.686400e6 + 63.156224e6 + 55.547648e6 + 768.805632e6 + 44.524288e6
+                                              + 114.458880e6) / 2.97e6}
 
 
 def kernel_source_hash() -> str:
@@ -794,13 +791,11 @@ def per_cell_rates(ctx, cells, seed: int, qs, prec: int, mul_peak_gmul: float, f
 # (reported as null once the sources change): DRAM bytes read per replicate
 # (its replicate records) and binary64 operations per replicate (DFMA counted
 # as two, DADD and DMUL as one), mostly the fit.
-FINISHER_NCU = {"ea8ed0c73be72e29": {
-    "dram_read_per_replicate": 2155.349760e6 / 2.97e6,
+FINISHER_NCU = {"77de4ab9190f9e35": {
+    "dram_read_per_replicate": 2154.048000e6 / 2.97e6,
     "f64_ops_per_replicate": (231.771286e6 + 170.849080e6 + 2 * 146.157496e6) / 2.97e6,
     # one alpha = 3.5, n = 10 cell of 200,000 replicates (no spills, trivial KS): the fit alone
     "fit_f64_ops": (4.806451e6 + 2.804522e6 + 2 * 6.206738e6) / 200000}}
-# the same finisher after the law set-up change (see TRAFFIC_PER_REPLICATE)
-FINISHER_NCU["02839dd94f8d082d"] = FINISHER_NCU["ea8ed0c73be72e29"]
 ALGO_BYTES_PER_REPLICATE = 16  # D (binary32 or binary64) and alpha-hat (binary64) out
 
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpl.so")
-SOURCES = ["pl_kernels.cu", "pl_api.cu", "pl_noalloc.cu", "pl_server.cu", "pl_truncated.cu", "pl_lookup.cu", "pl_xmin.cu", "pl_multinomial.cu", "pl_probe.cu"]
+SOURCES = ["pl_kernels.cu", "pl_tables.cu", "pl_api.cu", "pl_noalloc.cu", "pl_server.cu", "pl_truncated.cu", "pl_lookup.cu", "pl_xmin.cu", "pl_multinomial.cu", "pl_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + ARCH
 
