@@ -526,7 +526,7 @@ pl_status upload_sim(pl_ctx *ctx, const SimPlan &sp, SimBuffers &b, cudaStream_t
   PL_CUDA(cudaEventRecord(ctx->staging_ev, st));
   ctx->staged = true;
   PL_CUDA(launch_law_setup(b.laws_dev, (int)b.laws_host.size(), st));
-  ctx->launches += b.laws_host.empty() ? 0 : 4;
+  ctx->launches += b.laws_host.empty() ? 0 : kLawSetupLaunches;
   if (fresh.size() == b.fits_host.size()) {
     PL_CUDA(launch_fit_tables(b.fits_dev, (int)b.fits_host.size(), st));
     ctx->launches += b.fits_host.empty() ? 0 : 3;
@@ -937,7 +937,7 @@ pl_status pl_sample(pl_ctx *ctx, double alpha, uint64_t xmin, uint64_t seed, uin
   ld = cv.take<Law>(1);
   PL_CUDA(cudaMemcpyAsync(ld, &lh, sizeof lh, cudaMemcpyHostToDevice, st));
   PL_CUDA(launch_law_setup(ld, 1, st));
-  ctx->launches += 5;  // four law set-up kernels and the sampler
+  ctx->launches += kLawSetupLaunches + 1;  // the law set-up and the sampler
   PL_CUDA(launch_sample(ld, seed, (uint32_t)cell_id, purpose, (uint32_t)rep0, nrep, n, out_dev, ctx->ctr,
                         ctx->num_sms, st));
   return PL_OK;
@@ -1310,7 +1310,7 @@ pl_status run_dataset(pl_ctx *ctx, const int32_t *x, int64_t n, uint64_t xmin, b
   lay(cv, lh, ld, spill, pairs, out);
   PL_CUDA(cudaMemcpyAsync(ld, &lh, sizeof lh, cudaMemcpyHostToDevice, st));
   PL_CUDA(launch_law_setup(ld, 1, st));
-  ctx->launches += 5;  // four law set-up kernels and the data-set kernel
+  ctx->launches += kLawSetupLaunches + 1;  // the law set-up and the data-set kernel
   PL_CUDA(launch_dataset(x, n, xmin, fit, alpha, ld, cell_const(xmin), prec == PL_FP32_BULK, spill, pairs, out,
                          ctx->ctr, st));
   PL_CUDA(cudaMemcpyAsync(out_host, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1842,7 +1842,7 @@ pl_status pl_bespoke_cutoffs_batch(pl_ctx *ctx, int nsets, const int32_t *const 
   for (size_t k = 0; k < lps.size(); ++k) {
     PL_CUDA(cudaMemcpyAsync(ld[k], &lh[k], sizeof(Law), cudaMemcpyHostToDevice, st));
     PL_CUDA(launch_law_setup(ld[k], 1, st));
-    ctx->launches += 4;
+    ctx->launches += kLawSetupLaunches;
   }
   // the fits are independent one-block kernels: spread over the side streams
   const int naux = std::min(nsets, pl_ctx::kAux);

@@ -19,6 +19,7 @@ struct CellConst {
 cudaError_t launch_fit_tables(FitTable *fts_dev, int nfit, cudaStream_t st);
 
 cudaError_t launch_law_setup(Law *laws_dev, int nlaws, cudaStream_t st);
+constexpr int kLawSetupLaunches = 3;  // kernels launch_law_setup enqueues
 
 cudaError_t launch_sample(const Law *law_dev, uint64_t seed, uint32_t cell_id, uint32_t purpose,
                           uint32_t rep0, int64_t nrep, int64_t n, uint64_t *out, Counters *ctr,
