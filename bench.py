@@ -48,8 +48,8 @@ MUL_LANES_PER_SM = 32
 # launches, mostly the replicate records written), keyed by the hash of the
 # kernel sources it was taken on (reported as null once they change).  The
 # bench scales it to a launch by the replicates per launch.
-TRAFFIC_PER_REPLICATE = {"77de4ab9190f9e35": (43.686400e6 + 63.156224e6 + 55.547648e6 + 768.805632e6 + 44.524288e6
-                                              + 114.458880e6) / 2.97e6}
+TRAFFIC_PER_REPLICATE = {"4104ca9b1f7015f2": (43.655168e6 + 62.887168e6 + 54.574848e6 + 768.936192e6 + 44.339456e6
+                                              + 114.823424e6) / 2.97e6}
 
 
 def kernel_source_hash() -> str:
@@ -791,8 +791,8 @@ def per_cell_rates(ctx, cells, seed: int, qs, prec: int, mul_peak_gmul: float, f
 # (reported as null once the sources change): DRAM bytes read per replicate
 # (its replicate records) and binary64 operations per replicate (DFMA counted
 # as two, DADD and DMUL as one), mostly the fit.
-FINISHER_NCU = {"77de4ab9190f9e35": {
-    "dram_read_per_replicate": 2154.048000e6 / 2.97e6,
+FINISHER_NCU = {"4104ca9b1f7015f2": {
+    "dram_read_per_replicate": 2154.135296e6 / 2.97e6,
     "f64_ops_per_replicate": (231.771286e6 + 170.849080e6 + 2 * 146.157496e6) / 2.97e6,
     # one alpha = 3.5, n = 10 cell of 200,000 replicates (no spills, trivial KS): the fit alone
     "fit_f64_ops": (4.806451e6 + 2.804522e6 + 2 * 6.206738e6) / 200000}}
